@@ -1,0 +1,102 @@
+"""The oracle's pins must catch plausible mistakes.
+
+Each mutant below is a one-line textual change to a temporary copy of
+oracle/ec_oracle.c (a flipped comparison, a dropped term, a wrong sign or
+index), compiled on the CPU and loaded as a separate module.  Every mutant must
+fail at least one of the pin tests; the real oracle passes them all.
+"""
+import importlib.util
+import os
+import shutil
+import subprocess
+import sys
+
+import numpy as np
+import pytest
+
+import test_oracle_alpha as TA
+import test_oracle_depth as TD
+import test_oracle_depth_grad as TG
+import test_oracle_rle as TR
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+ORACLE = os.path.join(ROOT, "oracle")
+
+MUTANTS = {
+    "depth_tie_le": ("if (d < best_d[p])", "if (d <= best_d[p])"),
+    "depth_background": ("best_d[p] = 1.0f; best_i[p] = -1;", "best_d[p] = 2.0f; best_i[p] = -1;"),
+    "roi_inclusive_edge": ("(int64_t)px < (int64_t)r.x + r.w", "(int64_t)px <= (int64_t)r.x + r.w"),
+    "merge_roi_drops_y": ("if (c.y < y0) y0 = c.y;", ""),
+    "over_drops_T": ("C[ch] += T * c[ch];", "C[ch] += c[ch];"),
+    "over_wrong_channel": ("T *= 1.0 - c[3];", "T *= 1.0 - c[2];"),
+    "half_exponent": ("ldexp((double)(m + 1024), e - 25)", "ldexp((double)(m + 1024), e - 24)"),
+    "grad_alpha_sign": ("d[3] = T[k] * (gp[3] - R);", "d[3] = T[k] * (gp[3] + R);"),
+    "grad_R_no_transmit": ("R = gc + (1.0 - ck[3]) * R;", "R = gc + R;"),
+    "grad_colour_T_next": ("d[0] = gp[0] * T[k];", "d[0] = gp[0] * T[k + 1];"),
+    "depth_grad_to_all": ("d[ch] = winner[p] == i ? g[4 * p + ch] : 0.0f;", "d[ch] = g[4 * p + ch];"),
+    "rle_repeat_threshold": ("if (L >= 3) {", "if (L >= 2) {"),
+    "rle_repeat_control": ("out[o++] = (uint8_t)(128 + piece - 1);", "out[o++] = (uint8_t)(128 + piece);"),
+    "rle_piece_127": ("size_t piece = left >= 128 ? 128 : left;", "size_t piece = left >= 127 ? 127 : left;"),
+    "rle_literal_control": ("out[o++] = (uint8_t)(piece - 1);", "out[o++] = (uint8_t)(piece);"),
+    "swizzle_component_order": ("s |= ((b >> (6 - 2 * k)) & 3u) << (6 - 2 * j);",
+                                "s |= ((b >> (6 - 2 * k)) & 3u) << (2 * j);"),
+    "decoder_no_length_check": ("if (o != len) return ORC_ECORRUPT;", ""),
+}
+
+
+def _load_mutant(tmp_path, name, old, new):
+    src = open(os.path.join(ORACLE, "ec_oracle.c")).read()
+    assert src.count(old) == 1, f"mutant {name}: pattern must occur exactly once"
+    d = tmp_path / name
+    d.mkdir()
+    shutil.copy(os.path.join(ORACLE, "ec_oracle.h"), d / "ec_oracle.h")
+    (d / "ec_oracle.c").write_text(src.replace(old, new))
+    so = d / "liboracle.so"
+    subprocess.check_call(["gcc", "-O2", "-std=c11", "-shared", "-fPIC", "-o", str(so),
+                           str(d / "ec_oracle.c"), "-lm"])
+    spec = importlib.util.spec_from_file_location(f"oracle_mutant_{name}",
+                                                  os.path.join(ORACLE, "__init__.py"))
+    mod = importlib.util.module_from_spec(spec)
+    sys.modules[spec.name] = mod
+    spec.loader.exec_module(mod)
+    mod._LIB = str(so)
+    mod.build = lambda force=False: str(so)
+    return mod
+
+
+def _pins(orc):
+    """The pin checks, as callables of the oracle module."""
+    yield lambda: [TD.test_matches_independent_argmin(orc, s) for s in range(24)]
+    yield lambda: TD.test_out_roi_is_bbox_union(orc)
+    yield lambda: TD.test_single_source_is_masked_copy(orc)
+    yield lambda: [TA.test_equal_alpha_closed_form(orc, n, a) for n, a in [(3, 0.1), (8, 0.3)]]
+    yield lambda: TA.test_fp16_layers_decoded_exactly(orc)
+    yield lambda: TA.test_roi_outside_is_transparent(orc)
+    yield lambda: [TA.test_gradient_matches_exact_central_differences(orc, s) for s in range(3)]
+    yield lambda: TA.test_gradient_closed_forms(orc)
+    yield lambda: TG.test_depth_grad_routes_to_winner(orc)
+    yield lambda: [TR.test_golden_worked_examples(orc, c) for c in range(len(TR._golden()))]
+    yield lambda: TR.test_swizzle_is_a_bit_permutation(orc)
+    yield lambda: [TR.test_streams_decode_and_have_canonical_size(orc, n, 1)
+                   for n in ("run_lengths", "lit_run_mix", "boxes")]
+    yield lambda: TR.test_decoder_rejects_corrupt_streams(orc)
+
+
+def _caught(orc):
+    for pin in _pins(orc):
+        try:
+            pin()
+        except (AssertionError, RuntimeError, ValueError, IndexError):
+            return True
+    return False
+
+
+@pytest.mark.parametrize("name", sorted(MUTANTS))
+def test_pins_catch_mutant(tmp_path, name):
+    old, new = MUTANTS[name]
+    mut = _load_mutant(tmp_path, name, old, new)
+    assert _caught(mut), f"mutant {name} survived every pin"
+
+
+def test_real_oracle_passes_all_pins(orc):
+    assert not _caught(orc)
