@@ -1,0 +1,502 @@
+#!/usr/bin/env python
+"""Benchmark of the sort-last compositing hot path on GB300.
+
+Default workload (one "step"): 16 partial images of a 1920x1080 frame,
+RGBA8 + float32 depth, ~30% coverage each, stored cropped to their ROI; every
+source's colour (swizzled, mode 2) and depth (mode 1) is RLE-compressed, the
+streams are decompressed, and the 16 decompressed sources are depth-composited
+into the frame (thesis 5.2.1, 5.3, 5.5.1).  Inputs are resident in HBM when a
+step starts; L2 is flushed (2x its size written) between timed steps, outside
+the timed events.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ec|reference]
+                    [--workload cfg2|cfg1|cfg3|cfg3h|cfg5d|cfg5a]
+
+Prints ONE JSON line (rank 0).  Metric: composited Gpixel-layers/s (sum over
+sources of |roi_i ∩ frame| per step, divided by the step time).  With N > 1
+(launched by torch.distributed.run) each rank runs an independent replica of
+the workload on its own GPU ("replicas only": nothing is exchanged), value is
+all ranks' pixel-layers over the slowest rank's time.
+
+--impl reference times the CPU oracle (test infrastructure, plain C) on the
+same workload on the host cores, as the reference arm.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+from concurrent.futures import ThreadPoolExecutor
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+import torch  # noqa: E402
+
+METRIC = "composited Gpixel-layers/s"
+UNIT = "Gpixel-layers/s"
+FALLBACK_HBM_GBS = 6800.0
+
+
+def log(*a):
+    print(*a, file=sys.stderr, flush=True)
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=2000)
+    p.add_argument("--warmup", type=int, default=20)
+    p.add_argument("--impl", default="ec", choices=["ec", "reference"])
+    p.add_argument("--workload", default="cfg2")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    return p.parse_args()
+
+
+# ----------------------------------------------------------------- plumbing
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def dist_init(world, local):
+    if world > 1:
+        import torch.distributed as dist
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if backend == "nccl":
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend)
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x: float, world: int) -> float:
+    if world == 1:
+        return x
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda" if torch.cuda.is_available() else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def hbm_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.proc = None
+        self.path = None
+        self.gpu = gpu_index
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", str(self.gpu)], stdout=open(self.path, "w"),
+                stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [s.strip() for s in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    mx.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, parts[5:9]):
+                    if v.lower() == "active":
+                        reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def kernel_hash() -> str:
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1902_08755_gb300", "csrc")
+    for fn in sorted(os.listdir(csrc)):
+        with open(os.path.join(csrc, fn), "rb") as f:
+            h.update(fn.encode() + f.read())
+    return h.hexdigest()[:16]
+
+
+def measured_traffic(kernel: str, workload: str):
+    """dram bytes per launch from the committed ncu summary, if it was taken on
+    the current kernel sources."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        e = d[workload][kernel]
+        if e.get("source_hash") == kernel_hash():
+            return float(e["dram_bytes_per_launch"])
+    except (OSError, KeyError, ValueError):
+        pass
+    return None
+
+
+# ---------------------------------------------------------------- workloads
+
+
+class DepthPipeline:
+    """cfg1 / cfg2 / cfg5d: RLE compress -> decompress -> depth composite."""
+
+    def __init__(self, cfg, n, W, H, coverage, clustered, cropped, device):
+        import paper_1902_08755_gb300 as ec
+        import synthetic as S
+        self.ec = ec
+        self.W, self.H, self.n, self.cfg = W, H, n, cfg
+        self.desc = (f"{n} sources {W}x{H} RGBA8+Z32, ~{int(coverage * 100)}% coverage, "
+                     f"{'ROI-cropped' if cropped else 'uncropped'}; RLE compress (colour mode 2, "
+                     f"depth mode 1) -> decompress -> depth composite")
+        self.srcs = S.depth_sources(cfg, n, W, H, coverage, clustered=clustered, cropped=cropped,
+                                    device=device)
+        self.planes = []
+        for s in self.srcs:
+            self.planes.append((s.color, 2))
+            self.planes.append((s.depth.view(torch.uint32), 1))
+        self.units = sum(max(0, min(s.roi[2], W)) * max(0, min(s.roi[3], H)) for s in self.srcs)
+        self.stored_px = sum(s.pvp[2] * s.pvp[3] for s in self.srcs)
+        self.kernels = ["rle_compress", "rle_decompress", "composite_depth"]
+        if torch.device(device).type != "cuda":
+            return
+        self.ctx = ec.default_context(torch.device(device).index or 0)
+        self.bufs = [torch.empty(ec.rle_max_size(t.shape[1], t.shape[0]), dtype=torch.uint8, device=device)
+                     for t, _ in self.planes]
+        self.sizes = [torch.zeros(1, dtype=torch.uint64, device=device) for _ in self.planes]
+        self.dec = [torch.empty_like(t) for t, _ in self.planes]
+        self.imgs = [ec.Image(color=self.dec[2 * i], depth=self.dec[2 * i + 1].view(torch.float32),
+                              pvp=s.pvp, roi=s.roi) for i, s in enumerate(self.srcs)]
+        self.out_c = torch.empty((H, W), dtype=torch.int32, device=device).view(torch.uint32)
+        self.out_d = torch.empty((H, W), dtype=torch.float32, device=device)
+        self.cjobs = [(t, m, None, b, sz) for (t, m), b, sz in zip(self.planes, self.bufs, self.sizes)]
+
+    def step(self, ev=None):
+        ec = self.ec
+        if ev:
+            ev[0].record()
+        ec.rle_compress_batch(self.cjobs, ctx=self.ctx)
+        if ev:
+            ev[1].record()
+        ec.rle_decompress_batch([(b, t.shape[1], t.shape[0], d, None)
+                                 for b, (t, _), d in zip(self.bufs, self.planes, self.dec)], ctx=self.ctx)
+        if ev:
+            ev[2].record()
+        ec.composite_depth(self.imgs, self.out_c, self.out_d, ctx=self.ctx)
+        if ev:
+            ev[3].record()
+
+    def launches_per_step(self):
+        return 3
+
+    def compressed_bytes(self):
+        return sum(int(s.item()) for s in self.sizes)
+
+    def algorithmic_bytes(self):
+        comp = self.compressed_bytes()
+        raw = 8 * self.stored_px
+        return {"rle_compress": raw + comp, "rle_decompress": comp + raw,
+                "composite_depth": 8 * self.units + 8 * self.W * self.H}
+
+    # end to end: sources from pinned host memory, frame back to pinned host memory
+    def setup_e2e(self):
+        self.h_planes = [t.view(torch.int32).cpu().pin_memory() for t, _ in self.planes]
+        self.h_out = torch.empty((self.H, self.W), dtype=torch.int32).pin_memory()
+        self.h_outd = torch.empty((self.H, self.W), dtype=torch.float32).pin_memory()
+        self.h2d = sum(t.numel() * 4 for t in self.h_planes)
+        self.d2h = self.H * self.W * 8
+
+    def e2e_step(self):
+        for (t, _), h in zip(self.planes, self.h_planes):
+            t.view(torch.int32).copy_(h, non_blocking=True)
+        self.step()
+        self.h_out.copy_(self.out_c.view(torch.int32), non_blocking=True)
+        self.h_outd.copy_(self.out_d, non_blocking=True)
+
+    # oracle (reference arm / cpu baseline): same pipeline on the host cores
+    def oracle_step(self, pool, cores):
+        import oracle
+        host = [(t.view(torch.int32).cpu().numpy().view(np.uint32), m) for t, m in self.planes] \
+            if not hasattr(self, "_host") else self._host
+        self._host = host
+        t0 = time.perf_counter()
+        streams = list(pool.map(lambda a: oracle.rle_compress(a[0], a[1]), host))
+        dec = list(pool.map(lambda a: oracle.rle_decompress(a[0], a[1][0].shape[1], a[1][0].shape[0]),
+                            zip(streams, host)))
+        imgs = [oracle.Image(s.pvp, s.roi, dec[2 * i], dec[2 * i + 1].view(np.float32))
+                for i, s in enumerate(self.srcs)]
+        bands = np.linspace(0, self.H, cores + 1).astype(int)
+
+        def part(k):
+            y0, y1 = int(bands[k]), int(bands[k + 1])
+            return oracle.composite_depth(imgs, (0, y0, self.W, y1 - y0))
+        list(pool.map(part, range(cores)))
+        return time.perf_counter() - t0
+
+
+class AlphaForward:
+    """cfg3 / cfg3h / cfg5a: ordered front-to-back 'over' of L layers."""
+
+    def __init__(self, cfg, L, W, H, amax, dtype, device):
+        import paper_1902_08755_gb300 as ec
+        import synthetic as S
+        self.ec = ec
+        self.W, self.H, self.L = W, H, L
+        self.desc = f"{L} layers {W}x{H} premultiplied RGBA {'FP16' if dtype == torch.float16 else 'FP32'} storage, alpha in [0,{amax}]; ordered 'over' forward"
+        self.lay = S.alpha_layers(cfg, L, W, H, amax, dtype=dtype, device=device)
+        self.units = L * W * H
+        self.bpp = 16 if dtype == torch.float32 else 8
+        self.kernels = ["composite_alpha"]
+        if torch.device(device).type != "cuda":
+            return
+        self.imgs = [ec.Image(color=self.lay[k]) for k in range(L)]
+        self.out = torch.empty((H, W, 4), dtype=dtype, device=device)
+        self.ctx = ec.default_context(torch.device(device).index or 0)
+
+    def step(self, ev=None):
+        if ev:
+            ev[0].record()
+        self.ec.composite_alpha(self.imgs, self.out, ctx=self.ctx)
+        if ev:
+            ev[1].record()
+
+    def launches_per_step(self):
+        return 1
+
+    def algorithmic_bytes(self):
+        return {"composite_alpha": self.units * self.bpp + self.W * self.H * self.bpp}
+
+    def setup_e2e(self):
+        self.h_lay = self.lay.cpu().pin_memory()
+        self.h_out = torch.empty_like(self.out, device="cpu").pin_memory()
+        self.h2d = self.h_lay.numel() * self.h_lay.element_size()
+        self.d2h = self.h_out.numel() * self.h_out.element_size()
+
+    def e2e_step(self):
+        self.lay.copy_(self.h_lay, non_blocking=True)
+        self.step()
+        self.h_out.copy_(self.out, non_blocking=True)
+
+    def oracle_step(self, pool, cores):
+        import oracle
+        rows = max(1, min(self.H, 16))       # bounded sample: the first rows
+        host = self.lay[:, :rows].cpu().numpy()
+        t0 = time.perf_counter()
+        bands = np.linspace(0, rows, min(cores, rows) + 1).astype(int)
+
+        def part(k):
+            y0, y1 = int(bands[k]), int(bands[k + 1])
+            ims = [oracle.Image((0, y0, self.W, y1 - y0), (0, y0, self.W, y1 - y0),
+                                np.ascontiguousarray(host[j, y0:y1])) for j in range(self.L)]
+            return oracle.composite_alpha(ims, (0, y0, self.W, y1 - y0))
+        list(pool.map(part, range(len(bands) - 1)))
+        self.sample_fraction = rows / self.H
+        return (time.perf_counter() - t0) / self.sample_fraction
+
+
+def make_workload(name, device):
+    if name == "cfg1":
+        return DepthPipeline(1, 4, 640, 480, 0.4, False, False, device)
+    if name == "cfg2":
+        return DepthPipeline(2, 16, 1920, 1080, 0.3, True, True, device)
+    if name == "cfg5d":
+        return DepthPipeline(5, 64, 7680, 4320, 0.25, True, True, device)
+    if name == "cfg3":
+        return AlphaForward(3, 32, 2048, 2048, 0.3, torch.float32, device)
+    if name == "cfg3h":
+        return AlphaForward(3, 32, 2048, 2048, 0.3, torch.float16, device)
+    if name == "cfg5a":
+        return AlphaForward(5, 128, 3840, 2160, 0.1, torch.float16, device)
+    raise SystemExit(f"unknown workload {name}")
+
+
+# -------------------------------------------------------------------- arms
+
+
+def cpu_baseline(wl, budget_s=12.0, max_reps=20):
+    cores = os.cpu_count() or 1
+    with ThreadPoolExecutor(max_workers=cores) as pool:
+        times = []
+        t_start = time.perf_counter()
+        while len(times) < max_reps and (time.perf_counter() - t_start) < budget_s:
+            times.append(wl.oracle_step(pool, cores))
+    t = statistics.median(times)
+    frac = getattr(wl, "sample_fraction", 1.0)
+    sample = (f"{len(times)} full steps of the workload" if frac == 1.0 else
+              f"{len(times)} x the first {frac:.4f} of each frame's rows, scaled to a full step")
+    return {"value": wl.units / t / 1e9, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": sample, "ms_per_step": t * 1e3}
+
+
+def run_reference(args):
+    rank, world, local = dist_env()
+    if rank != 0:
+        return
+    wl = make_workload(args.workload, "cpu")
+    cores = os.cpu_count() or 1
+    with ThreadPoolExecutor(max_workers=cores) as pool:
+        for _ in range(min(args.warmup, 1)):
+            wl.oracle_step(pool, cores)
+        times = [wl.oracle_step(pool, cores) for _ in range(max(1, min(args.steps, 10)))]
+    t = statistics.mean(times)
+    val = wl.units / t / 1e9
+    frac = getattr(wl, "sample_fraction", 1.0)
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": len(times), "warmup": min(args.warmup, 1), "ms_per_step": t * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "rgba8+f32",
+            "data": "synthetic", "config": {"workload": f"{args.workload}: {wl.desc}"},
+            "cpu_baseline": {"value": val, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": "full steps" if frac == 1.0 else f"first {frac:.4f} of rows, scaled"},
+            "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ec(args):
+    rank, world, local = dist_env()
+    dist_init(world, local)
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA GPU")
+    torch.cuda.set_device(local)
+    device = f"cuda:{local}"
+    import paper_1902_08755_gb300 as ec
+    ec.load()
+    wl = make_workload(args.workload, device)
+    l2 = torch.cuda.get_device_properties(local).L2_cache_size
+    flush = torch.empty(max(2 * l2, 256 << 20), dtype=torch.uint8, device=device)
+
+    for _ in range(max(3, args.warmup)):
+        wl.step()
+    wl.ctx.check_status(what="warm-up")
+    torch.cuda.synchronize()
+
+    nk = len(wl.kernels)
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(nk + 1)] for _ in range(args.steps)]
+    clocks = Clocks(local)
+    barrier(world)
+    torch.cuda.synchronize()
+    clocks.start()
+    t_wall = time.perf_counter()
+    for k in range(args.steps):
+        flush.fill_(k & 0xFF)                  # evict the previous step's data from L2
+        wl.step(evs[k])
+    torch.cuda.synchronize()
+    t_wall = time.perf_counter() - t_wall
+    clk = clocks.stop()
+    barrier(world)
+    st = wl.ctx.status_sync()
+    if st != 0:
+        raise SystemExit(f"device status {st} after the timed region")
+    per_kernel = [[evs[k][i].elapsed_time(evs[k][i + 1]) for k in range(args.steps)] for i in range(nk)]
+    step_ms = [sum(per_kernel[i][k] for i in range(nk)) for k in range(args.steps)]
+    ms = statistics.mean(step_ms)
+    ms = max_over_ranks(ms, world)
+    value = world * wl.units / (ms * 1e-3) / 1e9
+
+    # end to end through the public API, host buffers in pinned memory
+    wl.setup_e2e()
+    for _ in range(3):
+        wl.e2e_step()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e2e_steps = max(5, min(args.steps // 10, 200))
+    barrier(world)
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(e2e_steps):
+        wl.e2e_step()
+    e1.record()
+    torch.cuda.synchronize()
+    e2e_ms = max_over_ranks(e0.elapsed_time(e1) / e2e_steps, world)
+
+    if rank != 0:
+        return
+    peak, peak_src = hbm_peak()
+    algo = wl.algorithmic_bytes()
+    kern = {}
+    for i, name in enumerate(wl.kernels):
+        kms = statistics.mean(per_kernel[i])
+        gbs = algo[name] / (kms * 1e-3) / 1e9
+        kern[name] = {"ms": kms, "share": kms / statistics.mean(step_ms), "algorithmic_bytes": algo[name],
+                      "achieved_gbs": gbs, "frac_of_peak": gbs / peak}
+    dom = max(kern, key=lambda k: kern[k]["ms"])
+    traffic = measured_traffic(dom, args.workload)
+    roof = {"bound": "hbm", "kernel": dom, "achieved": kern[dom]["achieved_gbs"], "peak": peak,
+            "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)" if peak_src == "measured" else "fallback",
+            "unit": "GB/s", "frac": kern[dom]["achieved_gbs"] / peak, "traffic": traffic}
+    cfg = {"workload": f"{args.workload}: {wl.desc}",
+           "l2": "flushed between timed steps (2x L2 written, outside the events)",
+           "pixel_layers_per_step": wl.units, "parallelism": f"replicas x{world}"}
+    if hasattr(wl, "compressed_bytes"):
+        cfg["rle_compressed_bytes_per_step"] = wl.compressed_bytes()
+        cfg["rle_raw_bytes_per_step"] = 8 * wl.stored_px
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": max(3, args.warmup), "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "rgba8+f32" if isinstance(wl, DepthPipeline) else "f32",
+            "data": "synthetic (seeded boxes / layers shaped like the thesis's workloads)",
+            "config": cfg, "roofline": roof, "kernels": kern,
+            "e2e": {"value": world * wl.units / (e2e_ms * 1e-3) / 1e9, "unit": UNIT,
+                    "ms_per_step": e2e_ms, "h2d_bytes_per_step": wl.h2d, "d2h_bytes_per_step": wl.d2h},
+            "gpu_launches": wl.launches_per_step() * args.steps,
+            "clocks": clk, "wall_s_timed_loop": t_wall}
+    if world == 1 and not args.no_cpu_baseline:
+        wl_cpu = wl
+        line["cpu_baseline"] = cpu_baseline(wl_cpu)
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ec(args)
+
+
+if __name__ == "__main__":
+    main()

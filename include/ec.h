@@ -1,0 +1,243 @@
+/*
+ * ec.h -- C ABI of libec, GB300 (sm_103a) sort-last image compositing and
+ * run-length pixel coding, after Eilemann, "Parallel Rendering and Large Data
+ * Visualization" (arXiv 1902.08755), chapter 5 "Compositing".
+ *
+ * The thesis states the compositing problem as: N input frames, each with
+ * colour (and optionally depth) buffers, a pixel viewport and a region of
+ * interest, combined in a given order into one destination frame (3.6, 5.2,
+ * 5.3).  Every entry point below is one step of that problem, run by
+ * hand-written CUDA kernels on the caller's stream.
+ *
+ * Conventions
+ *  - Coordinates are destination-frame pixels.  A rect {x, y, w, h} covers
+ *    x <= px < x+w, y <= py < y+h; w, h >= 0 (0 = empty).
+ *  - An image stores the pixels of its pvp ("pixel viewport"): pixel (px, py)
+ *    is element (py - pvp.y) * pitch + (px - pvp.x) of its buffers; pitch is in
+ *    pixels and >= pvp.w.  Its roi (region of interest, thesis 5.3) is a
+ *    sub-rectangle of pvp; outside the roi the image is background (depth mode)
+ *    or fully transparent (alpha mode) and is never read.
+ *  - Ownership: the caller owns every image, target, stream and gradient
+ *    buffer.  libec allocates only what an ec_ctx or ec_batch holds and frees
+ *    it in ec_destroy / ec_batch_free.
+ *  - Asynchrony: every call enqueues work on stream s and returns at once.  The
+ *    return value reports argument validation only (and CUDA launch errors).
+ *    Errors found on the device (corrupt stream, wait timeout) are recorded in
+ *    the context's device status word, and ec_status_sync reports them.  A
+ *    kernel that finds an error stops early and never writes outside the
+ *    caller's buffers.
+ *  - Pointers are device pointers unless marked "host".  Host arrays are read
+ *    before the call returns and may be freed afterwards.
+ *  - Vector path: when an image's colour/depth pointers are 16-byte aligned,
+ *    pitch * bytes-per-pixel is a multiple of 16 and its pvp.x is offset from
+ *    the target's pvp.x by a multiple of 16 bytes of pixels, kernels move 16
+ *    bytes per access; otherwise they fall back to per-pixel accesses.  Both
+ *    give identical results.
+ *  - A context is used from one host thread at a time; calls on one context
+ *    that overlap on the device must be on the same stream (they share its
+ *    scratch memory and status word).
+ */
+#ifndef EC_H
+#define EC_H
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    EC_OK = 0,
+    EC_ERR_INVALID_ARG = 1,  /* bad rect, size, pointer, format or order      */
+    EC_ERR_CAPACITY = 2,     /* destination smaller than ec_rle_max_size      */
+    EC_ERR_CUDA = 3,         /* a CUDA runtime call failed                    */
+    EC_ERR_CORRUPT = 4,      /* malformed run-length stream (device-side)     */
+    EC_ERR_UNSUPPORTED = 5,  /* valid but outside this build's limits         */
+    EC_ERR_TIMEOUT = 6       /* a bounded device-side wait gave up            */
+} ec_status;
+
+typedef struct { int32_t x, y, w, h; } ec_rect;
+
+typedef enum {
+    EC_RGBA8 = 0,    /* uint32 per pixel, R in the low byte                    */
+    EC_RGBA32F = 1,  /* float[4] per pixel, premultiplied in alpha mode        */
+    EC_RGBA16F = 2   /* IEEE half[4] per pixel, premultiplied in alpha mode    */
+} ec_format;
+
+typedef void* ec_stream_t; /* a cudaStream_t; NULL = the legacy default stream */
+
+/* One input frame (thesis 3.6: an input frame with colour/depth buffers, a
+ * pixel viewport and a region of interest). */
+typedef struct {
+    ec_rect pvp;        /* rectangle the stored pixels cover                   */
+    ec_rect roi;        /* sub-rectangle of pvp holding data                   */
+    int32_t pitch;      /* pixels per stored row, >= pvp.w                     */
+    int32_t format;     /* ec_format of color                                  */
+    const void* color;  /* [pvp.h][pitch] pixels                               */
+    const float* depth; /* [pvp.h][pitch] depth, depth mode only (else NULL)   */
+} ec_image;
+
+/* The destination frame. */
+typedef struct {
+    ec_rect pvp;        /* rectangle the output covers                         */
+    int32_t pitch;      /* pixels per row, >= pvp.w                            */
+    int32_t format;     /* ec_format of color                                  */
+    void* color;        /* [pvp.h][pitch] pixels, written in full              */
+    float* depth;       /* [pvp.h][pitch] depth out, or NULL                   */
+} ec_target;
+
+typedef struct ec_ctx ec_ctx;
+
+/* Limits of this build. */
+#define EC_MAX_SOURCES 512          /* images per compositing call            */
+#define EC_RLE_CHUNK 4096           /* elements per independently coded chunk */
+#define EC_RLE_MAX_ELEMS (1u << 27) /* elements per run-length coded image    */
+#define EC_RLE_MAX_JOBS 512         /* images per batched codec call          */
+
+/* Create a context on CUDA device `device`: a device status word and scratch
+ * memory for the codec.  *ctx is NULL on failure. */
+ec_status ec_create(ec_ctx** ctx, int device);
+void ec_destroy(ec_ctx* ctx);
+
+/* Wait for stream s, then return the first device-side error recorded since
+ * the last call (EC_OK if none) and clear it. */
+ec_status ec_status_sync(ec_ctx* ctx, ec_stream_t s);
+
+/* Human-readable name of a status code (static string). */
+const char* ec_status_string(ec_status st);
+
+/* ---------------------------------------------------------------- compositing
+ * Depth-sorted sort-last compositing, thesis 5.2.1: every output pixel takes
+ * the colour and depth of the input with the smallest depth there.  Inputs may
+ * arrive in any order (thesis 3.6, 5.6), so ties go to the lower input index;
+ * the cleared background (colour bytes 0, depth 1.0) wins ties at 1.0 and NaN
+ * depths never win.  Inputs are read only inside roi_i ∩ out->pvp (thesis 5.3).
+ *   in      host array of n images; all share one colour format
+ *           (EC_RGBA8 or EC_RGBA32F), depth must be non-NULL.
+ *   out     colour (same format) over the whole out->pvp; depth if non-NULL.
+ *   winner  device int16 [out->pvp.h][out->pvp.w] (dense), index of the
+ *           winning input or -1, or NULL.  Needed by the backward pass.
+ *   out_roi host, may be NULL: bounding box of the union of roi_i ∩ out->pvp,
+ *           {0,0,0,0} if empty (thesis 5.3, the merged ROI).
+ * n == 0 writes the background.  n <= EC_MAX_SOURCES. */
+ec_status ec_composite_depth(ec_ctx* ctx, const ec_image* in, int32_t n,
+                             const ec_target* out, int16_t* winner,
+                             ec_rect* out_roi, ec_stream_t s);
+
+/* Ordered sort-last compositing, thesis 5.2.1 (spatial decomposition, images
+ * blended in sorted order): front-to-back Porter-Duff "over" of premultiplied
+ * RGBA, C += T * c_k, T *= (1 - a_k), in FP32 arithmetic.
+ *   in      host array of n layers, all EC_RGBA32F or all EC_RGBA16F.
+ *   order   host array of n distinct layer indices, order[0] in front; NULL
+ *           means 0..n-1.
+ *   out     same format as the layers, written over the whole out->pvp.
+ *   t_final device float [out->pvp.h][out->pvp.w] (dense) remaining
+ *           transmittance, or NULL.
+ * Outside roi_k a layer is transparent.  n <= EC_MAX_SOURCES. */
+ec_status ec_composite_alpha(ec_ctx* ctx, const ec_image* in, const int32_t* order,
+                             int32_t n, const ec_target* out, float* t_final,
+                             ec_rect* out_roi, ec_stream_t s);
+
+/* Backward pass of ec_composite_alpha for L = sum(grad_out * out): writes
+ *   dL/dc_k^{RGB} = g^{RGB} T_k,  dL/da_k = T_k (g^A - R_k),
+ *   R_k = sum_{j>k} g.c_j prod_{k<m<j} (1 - a_m)   (reverse "behind" scan),
+ * recomputing T_k on chip (no per-layer state is stored by the forward).
+ *   out_pvp    the forward's output viewport.
+ *   grad_out   device float4 [out_pvp.h][out_pvp.w] (dense), upstream gradient.
+ *   grad       host array of n device pointers; grad[i] has layer i's shape
+ *              ([pvp_i.h][pitch_i] pixels of grad_format, EC_RGBA32F or
+ *              EC_RGBA16F) and is written over pvp_i ∩ out_pvp (0 outside
+ *              roi_i); other elements are not written. */
+ec_status ec_composite_alpha_backward(ec_ctx* ctx, const ec_image* in,
+                                      const int32_t* order, int32_t n, ec_rect out_pvp,
+                                      const float* grad_out, void* const* grad,
+                                      int32_t grad_format, ec_stream_t s);
+
+/* Forward and backward in one pass, for a loss L = sum(w * out) whose weights
+ * w are known before the forward (w = grad_out above).  Reads every layer
+ * once; writes out (and t_final if non-NULL) like ec_composite_alpha and the
+ * gradients like ec_composite_alpha_backward. */
+ec_status ec_composite_alpha_fwd_bwd(ec_ctx* ctx, const ec_image* in,
+                                     const int32_t* order, int32_t n,
+                                     const ec_target* out, float* t_final,
+                                     const float* w, void* const* grad,
+                                     int32_t grad_format, ec_rect* out_roi,
+                                     ec_stream_t s);
+
+/* Backward pass of ec_composite_depth with EC_RGBA32F colour: an output pixel
+ * is a copy of its winner's colour, so grad_i[p] = grad_out[p] where
+ * winner[p] == i and 0 elsewhere (no gradient reaches depth).
+ *   winner   device int16 [out_pvp.h][out_pvp.w] from the forward.
+ *   grad_out device float4 [out_pvp.h][out_pvp.w] (dense).
+ *   pvps, pitches  host arrays of n: each input's pvp and pitch.
+ *   grad     host array of n device float4 buffers of the inputs' shapes,
+ *            written over pvp_i ∩ out_pvp. */
+ec_status ec_composite_depth_backward(ec_ctx* ctx, const int16_t* winner,
+                                      ec_rect out_pvp, const float* grad_out,
+                                      int32_t n, const ec_rect* pvps,
+                                      const int32_t* pitches, float* const* grad,
+                                      ec_stream_t s);
+
+/* ------------------------------------------------------------ run-length codec
+ * Thesis 5.5.1 (enhanced RLE): the image is coded as four independent byte
+ * streams, one per component (mode 1), optionally after regrouping the 32 bits
+ * of each element by significance (mode 2, the swizzle preconditioner); the
+ * image is cut into independently coded sub-images for parallelism.
+ *
+ * Container "ECR1" (little-endian):
+ *   u32 magic 0x31524345, u16 version 1, u16 mode, u32 w, u32 h,
+ *   u32 elem_bytes 4, u32 chunk 4096, u32 n_chunks, u32 n_planes 4  (32 bytes)
+ *   u32 end[4 * n_chunks]: exclusive end of stream 4c+p, relative to payload
+ *   payload: streams in order chunk-major, plane-minor.
+ * Elements are read row-major, q = y*w + x (pitch is storage only); chunk c
+ * holds q in [4096c, min(4096(c+1), w*h)); plane p of an element is its byte
+ * p (mode 1) or byte p of its swizzled value (mode 2: byte k gathers bits
+ * 7-2k..6-2k of components R,G,B,A, R highest).  Each stream is a sequence of
+ * tokens: control c < 128 -> the next c+1 bytes are literals; c >= 128 -> the
+ * next byte repeats c-127 times.  Runs of >= 3 equal bytes are coded as
+ * repeats, maximal spans of shorter runs as literals, at most 128 bytes per
+ * token with full tokens first.  Every (image, mode) has exactly one encoding.
+ * A decoder accepts any token sequence that yields exactly the chunk's bytes,
+ * but rejects a stream longer than len + ceil(len/128) bytes (the all-literal
+ * coding of its chunk, the longest the encoder emits).
+ */
+
+/* Upper bound on a stream's size: 32 + 16 n_chunks + sum over streams of
+ * (len + ceil(len/128)).  0 for negative sizes. */
+size_t ec_rle_max_size(int32_t w, int32_t h);
+
+/* Compress w x h uint32 elements at src (row pitch `pitch` elements) into dst
+ * (capacity dst_capacity >= ec_rle_max_size(w, h), else EC_ERR_CAPACITY).
+ * The stream's size in bytes is written to *d_size (device uint64) when the
+ * kernel finishes.  w * h <= EC_RLE_MAX_ELEMS.  Uses the context's scratch
+ * memory. */
+ec_status ec_rle_compress(ec_ctx* ctx, const void* src, int32_t w, int32_t h,
+                          int32_t pitch, uint32_t mode, void* dst, size_t dst_capacity,
+                          uint64_t* d_size, ec_stream_t s);
+
+/* Decompress a stream of src_size bytes into dst (w x h elements, row pitch
+ * `pitch`).  The header must name the same w and h.  Malformed input records
+ * EC_ERR_CORRUPT in the status word; the kernel never reads past src_size nor
+ * writes outside the w x h elements of dst. */
+ec_status ec_rle_decompress(ec_ctx* ctx, const void* src, size_t src_size, void* dst,
+                            int32_t w, int32_t h, int32_t pitch, ec_stream_t s);
+
+/* Several images in one launch (the codec's data decomposition spans them). */
+typedef struct {
+    const void* src;     /* compress: elements; decompress: stream             */
+    void* dst;           /* compress: stream; decompress: elements             */
+    size_t capacity;     /* compress: dst capacity; decompress: src size       */
+    uint64_t* d_size;    /* compress: device uint64 receiving the size         */
+    int32_t w, h, pitch; /* image size and row pitch in elements               */
+    uint32_t mode;       /* compress: 1 or 2; ignored by decompress            */
+} ec_rle_job;
+
+ec_status ec_rle_compress_batch(ec_ctx* ctx, const ec_rle_job* jobs, int32_t njobs,
+                                ec_stream_t s);
+ec_status ec_rle_decompress_batch(ec_ctx* ctx, const ec_rle_job* jobs, int32_t njobs,
+                                  ec_stream_t s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

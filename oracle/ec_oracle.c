@@ -494,6 +494,8 @@ int orc_rle_decompress(const uint8_t* src, size_t size, uint32_t* dst,
         for (uint32_t p = 0; p < 4; ++p) {
             size_t end = get_u32(table + 4u * (4u * c + p));
             if (end < begin || end > payload_size) return ORC_ECORRUPT;
+            /* no valid stream is longer than the all-literal coding of its chunk */
+            if (end - begin > len + (len + 127) / 128) return ORC_ECORRUPT;
             /* decode: control < 128 copies control+1 bytes, otherwise the next
              * byte repeats control-127 times */
             size_t i = begin, o = 0;

@@ -1,0 +1,353 @@
+"""Python binding of libec: the C ABI of include/ec.h over torch tensors.
+
+Argument marshalling only -- every step runs in the CUDA kernels behind the C
+ABI.  Tensors must live on the context's CUDA device; the functions enqueue
+work on the current torch stream (or the one given) and return at once.
+Names follow the C ABI without its ``ec_`` prefix.
+
+Tensor layouts (pitch = row stride in pixels, taken from the tensor's stride):
+  RGBA8    uint32 [h][pitch]          (R in the low byte)
+  RGBA32F  float32 [h][pitch][4]
+  RGBA16F  float16 [h][pitch][4]
+  depth    float32 [h][pitch], same pitch as the colour
+"""
+from __future__ import annotations
+
+import ctypes as C
+from dataclasses import dataclass
+from typing import List, Optional, Sequence, Tuple
+
+import torch
+
+from . import _abi as A
+from ._abi import EcError, check, ec_image, ec_rect, ec_rle_job, ec_target
+
+Rect = Tuple[int, int, int, int]
+
+
+def _lib():
+    return A.load()
+
+
+def _stream_handle(stream) -> Optional[int]:
+    if stream is None:
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+class Context:
+    """An ec_ctx: device status word and codec scratch memory on one device."""
+
+    def __init__(self, device: Optional[int] = None):
+        if not torch.cuda.is_available():
+            raise RuntimeError("libec needs a CUDA device")
+        self.device = torch.cuda.current_device() if device is None else int(device)
+        h = C.c_void_p()
+        check(_lib().ec_create(C.byref(h), self.device), "ec_create")
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None) is not None and self.h.value:
+            _lib().ec_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def status_sync(self, stream=None) -> int:
+        """Wait for the stream; return and clear the first device-side error."""
+        return int(_lib().ec_status_sync(self.h, _stream_handle(stream)))
+
+    def check_status(self, stream=None, what: str = "device"):
+        check(self.status_sync(stream), what)
+
+
+_default_ctx = {}
+
+
+def default_context(device: Optional[int] = None) -> Context:
+    dev = torch.cuda.current_device() if device is None else int(device)
+    if dev not in _default_ctx:
+        _default_ctx[dev] = Context(dev)
+    return _default_ctx[dev]
+
+
+@dataclass
+class Image:
+    """One input frame: colour (and depth) buffers, pixel viewport and ROI."""
+    color: torch.Tensor
+    depth: Optional[torch.Tensor] = None
+    pvp: Optional[Rect] = None
+    roi: Optional[Rect] = None
+
+
+def pixel_layout(t: torch.Tensor) -> Tuple[int, int, int, int]:
+    """(format, pitch, width, height) of a colour tensor."""
+    if t.dim() == 2 and t.dtype in (torch.uint32, torch.int32):
+        if t.stride(1) != 1:
+            raise ValueError("RGBA8 tensor needs unit column stride")
+        return A.EC_RGBA8, t.stride(0), t.shape[1], t.shape[0]
+    if t.dim() == 3 and t.shape[2] == 4 and t.dtype in (torch.float32, torch.float16):
+        if t.stride(2) != 1 or t.stride(1) != 4 or t.stride(0) % 4:
+            raise ValueError("RGBA float tensor needs strides (4*pitch, 4, 1)")
+        fmt = A.EC_RGBA32F if t.dtype == torch.float32 else A.EC_RGBA16F
+        return fmt, t.stride(0) // 4, t.shape[1], t.shape[0]
+    raise ValueError(f"unsupported colour tensor {t.dtype} {tuple(t.shape)}")
+
+
+def _rect(r) -> ec_rect:
+    return ec_rect(*[int(v) for v in r])
+
+
+def _on_device(t: Optional[torch.Tensor], dev: int, what: str):
+    if t is None:
+        return
+    if not t.is_cuda or t.device.index != dev:
+        raise ValueError(f"{what} must be a CUDA tensor on device {dev}")
+
+
+def _image_struct(im: Image, dev: int, need_depth: bool) -> ec_image:
+    fmt, pitch, w, h = pixel_layout(im.color)
+    _on_device(im.color, dev, "colour")
+    pvp = tuple(im.pvp) if im.pvp is not None else (0, 0, w, h)
+    roi = tuple(im.roi) if im.roi is not None else pvp
+    if pvp[2] > w or pvp[3] > h:
+        raise ValueError("pvp larger than the colour tensor")
+    dptr = None
+    if need_depth:
+        if im.depth is None:
+            raise ValueError("depth compositing needs depth buffers")
+        _on_device(im.depth, dev, "depth")
+        d = im.depth
+        if d.dtype != torch.float32 or d.dim() != 2 or d.stride(1) != 1 or d.stride(0) != pitch \
+                or d.shape[0] < pvp[3] or d.shape[1] < pvp[2]:
+            raise ValueError("depth must be float32 [h][pitch] with the colour's pitch")
+        dptr = d.data_ptr()
+    return ec_image(_rect(pvp), _rect(roi), pitch, fmt, im.color.data_ptr(), dptr)
+
+
+def _target(color: torch.Tensor, depth: Optional[torch.Tensor], pvp, dev: int) -> ec_target:
+    fmt, pitch, w, h = pixel_layout(color)
+    _on_device(color, dev, "output colour")
+    pvp = tuple(pvp) if pvp is not None else (0, 0, w, h)
+    if pvp[2] > w or pvp[3] > h:
+        raise ValueError("output pvp larger than the output tensor")
+    dptr = None
+    if depth is not None:
+        _on_device(depth, dev, "output depth")
+        if depth.dtype != torch.float32 or depth.stride(0) != pitch or depth.stride(1) != 1:
+            raise ValueError("output depth must be float32 with the colour's pitch")
+        dptr = depth.data_ptr()
+    return ec_target(_rect(pvp), pitch, fmt, color.data_ptr(), dptr)
+
+
+def _dense(t: Optional[torch.Tensor], shape, dtype, dev: int, what: str) -> Optional[int]:
+    if t is None:
+        return None
+    _on_device(t, dev, what)
+    if t.dtype != dtype or not t.is_contiguous() or t.numel() < int(torch.tensor(shape).prod()):
+        raise ValueError(f"{what} must be a contiguous {dtype} tensor of shape {shape}")
+    return t.data_ptr()
+
+
+def composite_depth(images: Sequence[Image], out_color: torch.Tensor,
+                    out_depth: Optional[torch.Tensor] = None, out_pvp: Optional[Rect] = None,
+                    winner: Optional[torch.Tensor] = None, ctx: Optional[Context] = None,
+                    stream=None) -> Rect:
+    """ec_composite_depth: per-pixel depth-test merge.  Returns the merged ROI."""
+    ctx = ctx or default_context(out_color.device.index)
+    dev = ctx.device
+    arr = (ec_image * max(1, len(images)))(*[_image_struct(im, dev, True) for im in images])
+    tgt = _target(out_color, out_depth, out_pvp, dev)
+    wp = _dense(winner, (tgt.pvp.h, tgt.pvp.w), torch.int16, dev, "winner")
+    roi = ec_rect()
+    check(_lib().ec_composite_depth(ctx.h, arr, len(images), C.byref(tgt), wp, C.byref(roi),
+                                    _stream_handle(stream)), "ec_composite_depth")
+    return roi.tup()
+
+
+def _order(order, n):
+    if order is None:
+        return None
+    o = (C.c_int32 * max(1, n))(*[int(v) for v in order])
+    if len(order) != n:
+        raise ValueError("order needs one entry per layer")
+    return o
+
+
+def composite_alpha(layers: Sequence[Image], out: torch.Tensor, order=None,
+                    out_pvp: Optional[Rect] = None, t_final: Optional[torch.Tensor] = None,
+                    ctx: Optional[Context] = None, stream=None) -> Rect:
+    """ec_composite_alpha: front-to-back premultiplied 'over'.  Returns the merged ROI."""
+    ctx = ctx or default_context(out.device.index)
+    dev = ctx.device
+    arr = (ec_image * max(1, len(layers)))(*[_image_struct(im, dev, False) for im in layers])
+    tgt = _target(out, None, out_pvp, dev)
+    tp = _dense(t_final, (tgt.pvp.h, tgt.pvp.w), torch.float32, dev, "t_final")
+    roi = ec_rect()
+    check(_lib().ec_composite_alpha(ctx.h, arr, _order(order, len(layers)), len(layers),
+                                    C.byref(tgt), tp, C.byref(roi), _stream_handle(stream)),
+          "ec_composite_alpha")
+    return roi.tup()
+
+
+def composite_alpha_backward(layers: Sequence[Image], out_pvp: Rect, grad_out: torch.Tensor,
+                             grads: Sequence[torch.Tensor], order=None,
+                             ctx: Optional[Context] = None, stream=None):
+    """ec_composite_alpha_backward: dL/dlayer for L = sum(grad_out * out)."""
+    ctx = ctx or default_context(grad_out.device.index)
+    dev = ctx.device
+    n = len(layers)
+    arr = (ec_image * max(1, n))(*[_image_struct(im, dev, False) for im in layers])
+    gp = _dense(grad_out, (out_pvp[3], out_pvp[2], 4), torch.float32, dev, "grad_out")
+    gfmt = _grad_format(grads, layers, dev)
+    ptrs = (C.c_void_p * max(1, n))(*[g.data_ptr() for g in grads])
+    check(_lib().ec_composite_alpha_backward(ctx.h, arr, _order(order, n), n, _rect(out_pvp), gp,
+                                             ptrs, gfmt, _stream_handle(stream)),
+          "ec_composite_alpha_backward")
+
+
+def _grad_format(grads, layers, dev) -> int:
+    if len(grads) != len(layers):
+        raise ValueError("one gradient buffer per layer")
+    fmt = None
+    for g, im in zip(grads, layers):
+        _on_device(g, dev, "gradient")
+        f, pitch, w, h = pixel_layout(g)
+        if f == A.EC_RGBA8 or pitch != pixel_layout(im.color)[1] or g.shape[:2] != im.color.shape[:2]:
+            raise ValueError("gradients must have their layer's shape and pitch (float32/float16)")
+        if fmt is not None and f != fmt:
+            raise ValueError("all gradients share one format")
+        fmt = f
+    return A.EC_RGBA32F if fmt is None else fmt
+
+
+def composite_alpha_fwd_bwd(layers: Sequence[Image], out: torch.Tensor, w: torch.Tensor,
+                            grads: Sequence[torch.Tensor], order=None,
+                            out_pvp: Optional[Rect] = None, t_final: Optional[torch.Tensor] = None,
+                            ctx: Optional[Context] = None, stream=None) -> Rect:
+    """ec_composite_alpha_fwd_bwd: forward and gradients of sum(w * out) in one pass."""
+    ctx = ctx or default_context(out.device.index)
+    dev = ctx.device
+    n = len(layers)
+    arr = (ec_image * max(1, n))(*[_image_struct(im, dev, False) for im in layers])
+    tgt = _target(out, None, out_pvp, dev)
+    tp = _dense(t_final, (tgt.pvp.h, tgt.pvp.w), torch.float32, dev, "t_final")
+    wp = _dense(w, (tgt.pvp.h, tgt.pvp.w, 4), torch.float32, dev, "w")
+    gfmt = _grad_format(grads, layers, dev)
+    ptrs = (C.c_void_p * max(1, n))(*[g.data_ptr() for g in grads])
+    roi = ec_rect()
+    check(_lib().ec_composite_alpha_fwd_bwd(ctx.h, arr, _order(order, n), n, C.byref(tgt), tp, wp,
+                                            ptrs, gfmt, C.byref(roi), _stream_handle(stream)),
+          "ec_composite_alpha_fwd_bwd")
+    return roi.tup()
+
+
+def composite_depth_backward(winner: torch.Tensor, out_pvp: Rect, grad_out: torch.Tensor,
+                             images: Sequence[Image], grads: Sequence[torch.Tensor],
+                             ctx: Optional[Context] = None, stream=None):
+    """ec_composite_depth_backward: route grad_out to each pixel's winning input."""
+    ctx = ctx or default_context(grad_out.device.index)
+    dev = ctx.device
+    n = len(images)
+    wp = _dense(winner, (out_pvp[3], out_pvp[2]), torch.int16, dev, "winner")
+    gp = _dense(grad_out, (out_pvp[3], out_pvp[2], 4), torch.float32, dev, "grad_out")
+    pvps, pitches = [], []
+    for im, g in zip(images, grads):
+        f, pitch, w, h = pixel_layout(im.color)
+        gf, gpitch, _, _ = pixel_layout(g)
+        if gf != A.EC_RGBA32F or gpitch != pitch:
+            raise ValueError("depth gradients are float32 [h][pitch][4] with the input's pitch")
+        _on_device(g, dev, "gradient")
+        pvps.append(_rect(im.pvp if im.pvp is not None else (0, 0, w, h)))
+        pitches.append(pitch)
+    rp = (ec_rect * max(1, n))(*pvps)
+    pp = (C.c_int32 * max(1, n))(*pitches)
+    ptrs = (C.c_void_p * max(1, n))(*[g.data_ptr() for g in grads])
+    check(_lib().ec_composite_depth_backward(ctx.h, wp, _rect(out_pvp), gp, n, rp, pp, ptrs,
+                                             _stream_handle(stream)),
+          "ec_composite_depth_backward")
+
+
+def rle_max_size(w: int, h: int) -> int:
+    return int(_lib().ec_rle_max_size(int(w), int(h)))
+
+
+def _elem_layout(t: torch.Tensor) -> Tuple[int, int, int]:
+    """(pitch, w, h) of a 2-D tensor of 4-byte elements."""
+    if t.dim() != 2 or t.element_size() != 4:
+        raise ValueError("codec images are 2-D tensors of 4-byte elements")
+    if t.numel() == 0:
+        return t.shape[1], t.shape[1], t.shape[0]
+    if t.stride(1) != 1:
+        raise ValueError("codec images need unit column stride")
+    return t.stride(0), t.shape[1], t.shape[0]
+
+
+def rle_compress(src: torch.Tensor, mode: int, w: Optional[int] = None,
+                 dst: Optional[torch.Tensor] = None, d_size: Optional[torch.Tensor] = None,
+                 ctx: Optional[Context] = None, stream=None):
+    """ec_rle_compress.  Returns (dst uint8 buffer, d_size uint64[1] device tensor)."""
+    ctx = ctx or default_context(src.device.index)
+    jobs = [(src, mode, w, dst, d_size)]
+    out = rle_compress_batch(jobs, ctx=ctx, stream=stream)
+    return out[0]
+
+
+def rle_compress_batch(jobs, ctx: Optional[Context] = None, stream=None):
+    """ec_rle_compress_batch over [(src, mode, w|None, dst|None, d_size|None)].
+    Returns [(dst, d_size)]."""
+    ctx = ctx or default_context(jobs[0][0].device.index)
+    dev = ctx.device
+    arr = (ec_rle_job * max(1, len(jobs)))()
+    outs = []
+    for i, (src, mode, w, dst, d_size) in enumerate(jobs):
+        _on_device(src, dev, "codec source")
+        pitch, tw, h = _elem_layout(src)
+        w = tw if w is None else int(w)
+        cap = rle_max_size(w, h)
+        if dst is None:
+            dst = torch.empty(max(cap, 16), dtype=torch.uint8, device=src.device)
+        if d_size is None:
+            d_size = torch.zeros(1, dtype=torch.uint64, device=src.device)
+        _on_device(dst, dev, "codec destination")
+        arr[i] = ec_rle_job(src.data_ptr(), dst.data_ptr(), dst.numel() * dst.element_size(),
+                            d_size.data_ptr(), w, h, pitch, int(mode))
+        outs.append((dst, d_size))
+    check(_lib().ec_rle_compress_batch(ctx.h, arr, len(jobs), _stream_handle(stream)),
+          "ec_rle_compress_batch")
+    return outs
+
+
+def rle_decompress(src: torch.Tensor, w: int, h: int, dst: Optional[torch.Tensor] = None,
+                   src_size: Optional[int] = None, ctx: Optional[Context] = None, stream=None):
+    """ec_rle_decompress into a uint32 [h][w] tensor (or the given dst)."""
+    ctx = ctx or default_context(src.device.index)
+    return rle_decompress_batch([(src, w, h, dst, src_size)], ctx=ctx, stream=stream)[0]
+
+
+def rle_decompress_batch(jobs, ctx: Optional[Context] = None, stream=None):
+    """ec_rle_decompress_batch over [(src, w, h, dst|None, src_size|None)]."""
+    ctx = ctx or default_context(jobs[0][0].device.index)
+    dev = ctx.device
+    arr = (ec_rle_job * max(1, len(jobs)))()
+    outs = []
+    for i, (src, w, h, dst, src_size) in enumerate(jobs):
+        _on_device(src, dev, "codec stream")
+        if dst is None:
+            dst = torch.empty((h, w), dtype=torch.uint32, device=src.device)
+        _on_device(dst, dev, "codec destination")
+        pitch, dw, dh = _elem_layout(dst)
+        if dw < w or dh < h:
+            raise ValueError("destination smaller than the image")
+        size = src.numel() * src.element_size() if src_size is None else int(src_size)
+        arr[i] = ec_rle_job(src.data_ptr(), dst.data_ptr(), size, None, int(w), int(h), pitch, 0)
+        outs.append(dst)
+    check(_lib().ec_rle_decompress_batch(ctx.h, arr, len(jobs), _stream_handle(stream)),
+          "ec_rle_decompress_batch")
+    return outs

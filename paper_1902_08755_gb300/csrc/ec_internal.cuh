@@ -1,0 +1,111 @@
+// ec_internal.cuh -- internal definitions shared by libec's translation units.
+//
+// Host-side argument validation turns every input into flat descriptors whose
+// coordinates are relative to the destination's pvp origin; the kernels never
+// see ec_image directly.
+#pragma once
+
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/ec.h"
+
+struct ec_ctx {
+    int device = 0;
+    uint32_t* d_status = nullptr;   // first device-side error (0 = none)
+    void* scratch = nullptr;        // codec look-back flags + ticket counter
+    size_t scratch_bytes = 0;
+    int sm_count = 0;
+};
+
+namespace ec {
+
+// Per-source descriptor (48 bytes).  Coordinates are relative to the output
+// viewport origin; [x0,x1) x [y0,y1) is roi ∩ out.pvp, (ox, oy) the stored
+// pvp origin, so pixel (x, y) is element (y - oy) * pitch + (x - ox).
+struct SrcDesc {
+    int32_t x0, y0, x1, y1;
+    int32_t ox, oy;
+    int32_t pitch;
+    int32_t vec;           // 1 if this source may be read with 16-byte accesses
+    const void* color;
+    const float* depth;
+};
+static_assert(sizeof(SrcDesc) == 48, "descriptor layout");
+
+// Source lists travel as kernel parameters (no staging copy, capturable in a
+// CUDA graph).  Three capacities keep small calls' parameter blocks small.
+template <int N>
+struct SrcList {
+    int32_t n;
+    int32_t pad[3];
+    SrcDesc s[N];
+};
+static_assert(sizeof(SrcList<512>) < 32764 - 256, "kernel parameter limit");
+
+// Destination descriptor.
+struct DstDesc {
+    int32_t W, H;          // out.pvp size
+    int32_t pitch;         // pixels
+    int32_t vec;           // 16-byte stores allowed
+    void* color;
+    float* depth;          // may be null
+    int16_t* winner;       // may be null, dense [H][W]
+    float* tfinal;         // may be null, dense [H][W]
+};
+
+// Device status word: the first error wins.
+__device__ __forceinline__ void set_status(uint32_t* st, uint32_t code)
+{
+    atomicCAS(st, 0u, code);
+}
+
+// Streaming (evict-first) 16-byte global loads and stores: every input pixel
+// is read once per launch.
+__device__ __forceinline__ uint4 ld_stream(const uint4* p) { return __ldcs(p); }
+__device__ __forceinline__ float4 ld_stream(const float4* p) { return __ldcs(p); }
+__device__ __forceinline__ void st_stream(uint4* p, uint4 v) { __stcs(p, v); }
+__device__ __forceinline__ void st_stream(float4* p, float4 v) { __stcs(p, v); }
+
+inline int ceil_div(int a, int b) { return (a + b - 1) / b; }
+
+// ---- launchers (defined in the kernel translation units) -------------------
+cudaError_t launch_depth(const SrcDesc* src, int n, int color_bytes, const DstDesc& dst,
+                         cudaStream_t s);
+cudaError_t launch_alpha_fwd(const SrcDesc* src, int n, bool f16, const DstDesc& dst,
+                             cudaStream_t s);
+
+struct RleJobDesc {
+    const uint32_t* src;   // compress: elements; decompress: stream bytes (as u8)
+    void* dst;
+    uint64_t* d_size;
+    uint64_t capacity;     // decompress: source size in bytes
+    int32_t w, h, pitch;
+    uint32_t mode;
+    uint32_t n_chunks;     // ceil(w*h / 4096)
+    uint32_t first_unit;   // first global work unit of this job
+    uint32_t vec;          // 16-byte element loads/stores allowed
+    uint32_t pad;
+};
+static_assert(sizeof(RleJobDesc) == 64, "rle job layout");
+
+// At most kRleJobsPerLaunch jobs travel in one launch's parameters; larger
+// batches are split into several launches.
+constexpr int kRleJobsPerLaunch = 256;
+
+template <int N>
+struct RleJobList {
+    int32_t n;
+    uint32_t total_units;
+    int32_t pad[2];
+    RleJobDesc j[N];
+};
+static_assert(sizeof(RleJobList<kRleJobsPerLaunch>) < 32764 - 256, "kernel parameter limit");
+
+cudaError_t launch_rle_compress(const RleJobDesc* jobs, int n, uint32_t total_units,
+                                void* scratch, uint32_t* status, cudaStream_t s);
+cudaError_t launch_rle_decompress(const RleJobDesc* jobs, int n, uint32_t total_units,
+                                  uint32_t* status, cudaStream_t s);
+
+}  // namespace ec

@@ -1,0 +1,370 @@
+// k_composite.cu -- sort-last compositing kernels for sm_103a.
+//
+// Depth merge (thesis 5.2.1, depth-sorted compositing; 3.6 unordered
+// compositing) and ordered front-to-back "over" (thesis 5.2.1, spatial
+// compositing), both restricted to each input's ROI (thesis 5.3).
+//
+// Design: the work is a streaming read of every input pixel inside its ROI
+// plus one write of the output, so the kernels are HBM-bound.  A CTA owns a
+// tile of output pixels and first intersects every input's ROI with its tile
+// (one warp, ballot + popc compaction into shared memory, ascending input
+// order).  Each thread then owns 16 bytes of every layer at its pixels (4
+// RGBA8 pixels + their 4 depths, 1 RGBA32F pixel, 2 RGBA16F pixels), issues
+// the loads of several inputs back to back (independent 16-byte loads in
+// flight) and folds them in order in registers.  The per-pixel order of
+// operations is fixed by the input order alone, so results do not depend on
+// the tile shape.
+#include "ec_internal.cuh"
+
+namespace ec {
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kRows = kThreads / 32;   // one warp per tile row
+
+// Inputs whose clipped ROI meets the tile [tx0,tx1) x [ty0,ty1), ascending.
+template <int N>
+__device__ __forceinline__ int active_sources(const SrcList<N>& L, int tx0, int ty0, int tx1,
+                                              int ty1, int16_t* act, int* nact)
+{
+    const int lane = threadIdx.x & 31;
+    if (threadIdx.x < 32) {
+        int base = 0;
+        for (int i0 = 0; i0 < L.n; i0 += 32) {
+            const int i = i0 + lane;
+            bool hit = false;
+            if (i < L.n) {
+                const SrcDesc& s = L.s[i];
+                hit = s.x0 < tx1 && s.x1 > tx0 && s.y0 < ty1 && s.y1 > ty0;
+            }
+            const unsigned m = __ballot_sync(0xffffffffu, hit);
+            if (hit) act[base + __popc(m & ((1u << lane) - 1u))] = (int16_t)i;
+            base += __popc(m);
+        }
+        if (lane == 0) *nact = base;
+    }
+    __syncthreads();
+    return *nact;
+}
+
+// ----------------------------------------------------------------- depth ---
+
+template <int CB> struct ColorT;
+template <> struct ColorT<4> { using T = uint32_t; };
+template <> struct ColorT<16> { using T = float4; };
+
+__device__ __forceinline__ void zero(uint32_t& c) { c = 0u; }
+__device__ __forceinline__ void zero(float4& c) { c = make_float4(0.f, 0.f, 0.f, 0.f); }
+
+// 4 consecutive pixels of one source: 16-byte loads (vec) or per-pixel loads.
+template <int CB>
+__device__ __forceinline__ void load4(const SrcDesc& s, int x, int y, float (&d)[4],
+                                      typename ColorT<CB>::T (&c)[4])
+{
+    using C = typename ColorT<CB>::T;
+    const size_t e = (size_t)(y - s.oy) * (size_t)s.pitch + (size_t)(x - s.ox);
+    const float* dp = s.depth + e;
+    const C* cp = reinterpret_cast<const C*>(s.color) + e;
+    if (s.vec) {
+        const float4 d4 = ld_stream(reinterpret_cast<const float4*>(dp));
+        d[0] = d4.x; d[1] = d4.y; d[2] = d4.z; d[3] = d4.w;
+        if constexpr (CB == 4) {
+            const uint4 c4 = ld_stream(reinterpret_cast<const uint4*>(cp));
+            c[0] = c4.x; c[1] = c4.y; c[2] = c4.z; c[3] = c4.w;
+        } else {
+#pragma unroll
+            for (int j = 0; j < 4; ++j) c[j] = ld_stream(cp + j);
+        }
+    } else {
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int xj = x + j;
+            if (xj >= s.x0 && xj < s.x1) {
+                d[j] = __ldcs(dp + j);
+                if constexpr (CB == 4) c[j] = __ldcs(reinterpret_cast<const unsigned int*>(cp + j));
+                else c[j] = __ldcs(cp + j);
+            } else {
+                d[j] = 1.0f;
+                zero(c[j]);
+            }
+        }
+    }
+}
+
+template <int N, int CB>
+__global__ void __launch_bounds__(kThreads)
+k_depth(const __grid_constant__ SrcList<N> L, const __grid_constant__ DstDesc D)
+{
+    using C = typename ColorT<CB>::T;
+    constexpr int kTW = 128;     // 32 lanes x 4 pixels
+    constexpr int U = 4;         // inputs in flight per thread
+    __shared__ int16_t act[N > 0 ? N : 1];
+    __shared__ int nact_s;
+
+    const int lane = threadIdx.x & 31, row = threadIdx.x >> 5;
+    const int tx0 = blockIdx.x * kTW, ty0 = blockIdx.y * kRows;
+    const int nact = active_sources(L, tx0, ty0, min(tx0 + kTW, D.W), min(ty0 + kRows, D.H),
+                                    act, &nact_s);
+    const int x = tx0 + lane * 4, y = ty0 + row;
+    if (x >= D.W || y >= D.H) return;
+
+    float bd[4] = {1.0f, 1.0f, 1.0f, 1.0f};   // cleared depth
+    C bc[4];
+    int bi[4] = {-1, -1, -1, -1};
+#pragma unroll
+    for (int j = 0; j < 4; ++j) zero(bc[j]);
+
+    for (int a = 0; a < nact; a += U) {
+        float d[U][4];
+        C c[U][4];
+        int idx[U];
+        bool live[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            idx[u] = (a + u < nact) ? act[a + u] : -1;
+            live[u] = false;
+            if (idx[u] >= 0) {
+                const SrcDesc& s = L.s[idx[u]];
+                live[u] = y >= s.y0 && y < s.y1 && x + 4 > s.x0 && x < s.x1;
+                if (live[u]) load4<CB>(s, x, y, d[u], c[u]);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            if (!live[u]) continue;
+            const SrcDesc& s = L.s[idx[u]];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int xj = x + j;
+                // strict '<': ties keep the earlier (lower-index) winner or the
+                // background; NaN never compares less
+                if (xj >= s.x0 && xj < s.x1 && d[u][j] < bd[j]) {
+                    bd[j] = d[u][j];
+                    bc[j] = c[u][j];
+                    bi[j] = idx[u];
+                }
+            }
+        }
+    }
+
+    const size_t o = (size_t)y * (size_t)D.pitch + (size_t)x;
+    C* oc = reinterpret_cast<C*>(D.color) + o;
+    if (D.vec && x + 4 <= D.W) {
+        if constexpr (CB == 4) st_stream(reinterpret_cast<uint4*>(oc), make_uint4(bc[0], bc[1], bc[2], bc[3]));
+        else {
+#pragma unroll
+            for (int j = 0; j < 4; ++j) st_stream(oc + j, bc[j]);
+        }
+        if (D.depth) st_stream(reinterpret_cast<float4*>(D.depth + o), make_float4(bd[0], bd[1], bd[2], bd[3]));
+    } else {
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            if (x + j < D.W) {
+                oc[j] = bc[j];
+                if (D.depth) D.depth[o + j] = bd[j];
+            }
+        }
+    }
+    if (D.winner) {
+        int16_t* w = D.winner + (size_t)y * D.W + x;
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+            if (x + j < D.W) w[j] = (int16_t)bi[j];
+    }
+}
+
+// ----------------------------------------------------------------- alpha ---
+
+__device__ __forceinline__ float4 h4_to_f4(uint2 v)
+{
+    const __half2 lo = *reinterpret_cast<const __half2*>(&v.x);
+    const __half2 hi = *reinterpret_cast<const __half2*>(&v.y);
+    const float2 a = __half22float2(lo), b = __half22float2(hi);
+    return make_float4(a.x, a.y, b.x, b.y);
+}
+
+__device__ __forceinline__ uint2 f4_to_h4(float4 f)
+{
+    const __half2 lo = __floats2half2_rn(f.x, f.y);
+    const __half2 hi = __floats2half2_rn(f.z, f.w);
+    uint2 v;
+    v.x = *reinterpret_cast<const uint32_t*>(&lo);
+    v.y = *reinterpret_cast<const uint32_t*>(&hi);
+    return v;
+}
+
+// PX pixels (16 bytes) of one premultiplied layer.
+template <bool F16>
+__device__ __forceinline__ void load_px(const SrcDesc& s, int x, int y, float4 (&c)[F16 ? 2 : 1])
+{
+    constexpr int PX = F16 ? 2 : 1;
+    const size_t e = (size_t)(y - s.oy) * (size_t)s.pitch + (size_t)(x - s.ox);
+    if constexpr (!F16) {
+        const float4* p = reinterpret_cast<const float4*>(s.color) + e;
+        if (s.vec) {
+            c[0] = ld_stream(p);
+        } else {
+            const float* f = reinterpret_cast<const float*>(p);
+            c[0] = make_float4(__ldcs(f), __ldcs(f + 1), __ldcs(f + 2), __ldcs(f + 3));
+        }
+    } else {
+        const uint2* p = reinterpret_cast<const uint2*>(s.color) + e;
+        if (s.vec) {
+            const uint4 v = ld_stream(reinterpret_cast<const uint4*>(p));
+            c[0] = h4_to_f4(make_uint2(v.x, v.y));
+            c[1] = h4_to_f4(make_uint2(v.z, v.w));
+        } else {
+#pragma unroll
+            for (int j = 0; j < PX; ++j) {
+                const int xj = x + j;
+                if (xj >= s.x0 && xj < s.x1) {
+                    const unsigned short* h = reinterpret_cast<const unsigned short*>(p + j);
+                    c[j] = make_float4(__half2float(__ushort_as_half(__ldcs(h))),
+                                       __half2float(__ushort_as_half(__ldcs(h + 1))),
+                                       __half2float(__ushort_as_half(__ldcs(h + 2))),
+                                       __half2float(__ushort_as_half(__ldcs(h + 3))));
+                } else {
+                    c[j] = make_float4(0.f, 0.f, 0.f, 0.f);
+                }
+            }
+        }
+    }
+}
+
+template <int N, bool F16>
+__global__ void __launch_bounds__(kThreads)
+k_alpha_fwd(const __grid_constant__ SrcList<N> L, const __grid_constant__ DstDesc D)
+{
+    constexpr int PX = F16 ? 2 : 1;      // pixels per 16 bytes
+    constexpr int kTW = 32 * PX;
+    constexpr int U = 8;                 // layers in flight per thread
+    __shared__ int16_t act[N > 0 ? N : 1];
+    __shared__ int nact_s;
+
+    const int lane = threadIdx.x & 31, row = threadIdx.x >> 5;
+    const int tx0 = blockIdx.x * kTW, ty0 = blockIdx.y * kRows;
+    const int nact = active_sources(L, tx0, ty0, min(tx0 + kTW, D.W), min(ty0 + kRows, D.H),
+                                    act, &nact_s);
+    const int x = tx0 + lane * PX, y = ty0 + row;
+    if (x >= D.W || y >= D.H) return;
+
+    float4 acc[PX];
+    float T[PX];
+#pragma unroll
+    for (int j = 0; j < PX; ++j) { acc[j] = make_float4(0.f, 0.f, 0.f, 0.f); T[j] = 1.0f; }
+
+    for (int a = 0; a < nact; a += U) {
+        float4 c[U][PX];
+        bool live[U];
+        int idx[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            idx[u] = (a + u < nact) ? act[a + u] : -1;
+            live[u] = false;
+            if (idx[u] >= 0) {
+                const SrcDesc& s = L.s[idx[u]];
+                live[u] = y >= s.y0 && y < s.y1 && x + PX > s.x0 && x < s.x1;
+                if (live[u]) load_px<F16>(s, x, y, c[u]);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            if (!live[u]) continue;
+            const SrcDesc& s = L.s[idx[u]];
+#pragma unroll
+            for (int j = 0; j < PX; ++j) {
+                const int xj = x + j;
+                if (xj < s.x0 || xj >= s.x1) continue;   // transparent outside the ROI
+                // C += T c (premultiplied, all four channels); T *= (1 - a)
+                acc[j].x = fmaf(T[j], c[u][j].x, acc[j].x);
+                acc[j].y = fmaf(T[j], c[u][j].y, acc[j].y);
+                acc[j].z = fmaf(T[j], c[u][j].z, acc[j].z);
+                acc[j].w = fmaf(T[j], c[u][j].w, acc[j].w);
+                T[j] = fmaf(-T[j], c[u][j].w, T[j]);
+            }
+        }
+    }
+
+    const size_t o = (size_t)y * (size_t)D.pitch + (size_t)x;
+    if constexpr (!F16) {
+        float4* op = reinterpret_cast<float4*>(D.color) + o;
+        if (D.vec) st_stream(op, acc[0]);
+        else { float* f = reinterpret_cast<float*>(op); f[0] = acc[0].x; f[1] = acc[0].y; f[2] = acc[0].z; f[3] = acc[0].w; }
+    } else {
+        uint2* op = reinterpret_cast<uint2*>(D.color) + o;
+        const uint2 h0 = f4_to_h4(acc[0]), h1 = f4_to_h4(acc[1]);
+        if (D.vec && x + 2 <= D.W) {
+            st_stream(reinterpret_cast<uint4*>(op), make_uint4(h0.x, h0.y, h1.x, h1.y));
+        } else {
+            unsigned short* hp = reinterpret_cast<unsigned short*>(op);
+            hp[0] = (unsigned short)h0.x; hp[1] = (unsigned short)(h0.x >> 16);
+            hp[2] = (unsigned short)h0.y; hp[3] = (unsigned short)(h0.y >> 16);
+            if (x + 1 < D.W) {
+                hp[4] = (unsigned short)h1.x; hp[5] = (unsigned short)(h1.x >> 16);
+                hp[6] = (unsigned short)h1.y; hp[7] = (unsigned short)(h1.y >> 16);
+            }
+        }
+    }
+    if (D.tfinal) {
+        float* t = D.tfinal + (size_t)y * D.W + x;
+#pragma unroll
+        for (int j = 0; j < PX; ++j)
+            if (x + j < D.W) t[j] = T[j];
+    }
+}
+
+template <int N>
+SrcList<N> make_list(const SrcDesc* src, int n)
+{
+    SrcList<N> L;
+    L.n = n;
+    L.pad[0] = L.pad[1] = L.pad[2] = 0;
+    for (int i = 0; i < n; ++i) L.s[i] = src[i];
+    return L;
+}
+
+template <int N>
+cudaError_t depth_n(const SrcDesc* src, int n, int cb, const DstDesc& D, cudaStream_t s)
+{
+    const dim3 grid(ceil_div(D.W, 128), ceil_div(D.H, kRows));
+    const SrcList<N> L = make_list<N>(src, n);
+    if (cb == 4) k_depth<N, 4><<<grid, kThreads, 0, s>>>(L, D);
+    else k_depth<N, 16><<<grid, kThreads, 0, s>>>(L, D);
+    return cudaGetLastError();
+}
+
+template <int N>
+cudaError_t alpha_n(const SrcDesc* src, int n, bool f16, const DstDesc& D, cudaStream_t s)
+{
+    const SrcList<N> L = make_list<N>(src, n);
+    if (f16) {
+        const dim3 grid(ceil_div(D.W, 64), ceil_div(D.H, kRows));
+        k_alpha_fwd<N, true><<<grid, kThreads, 0, s>>>(L, D);
+    } else {
+        const dim3 grid(ceil_div(D.W, 32), ceil_div(D.H, kRows));
+        k_alpha_fwd<N, false><<<grid, kThreads, 0, s>>>(L, D);
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_depth(const SrcDesc* src, int n, int color_bytes, const DstDesc& D,
+                         cudaStream_t s)
+{
+    if (D.W <= 0 || D.H <= 0) return cudaSuccess;
+    if (n <= 16) return depth_n<16>(src, n, color_bytes, D, s);
+    if (n <= 64) return depth_n<64>(src, n, color_bytes, D, s);
+    return depth_n<EC_MAX_SOURCES>(src, n, color_bytes, D, s);
+}
+
+cudaError_t launch_alpha_fwd(const SrcDesc* src, int n, bool f16, const DstDesc& D,
+                             cudaStream_t s)
+{
+    if (D.W <= 0 || D.H <= 0) return cudaSuccess;
+    if (n <= 16) return alpha_n<16>(src, n, f16, D, s);
+    if (n <= 64) return alpha_n<64>(src, n, f16, D, s);
+    return alpha_n<EC_MAX_SOURCES>(src, n, f16, D, s);
+}
+
+}  // namespace ec

@@ -257,6 +257,24 @@ def test_decoder_rejects_corrupt_streams(orc):
     # ... and a stream that runs one byte long ("83 01" -> "84 01")
     short[HDR + 16] = 0x84
     assert orc.rle_decompress_status(bytes(short), 4, 1) == orc.ECORRUPT
+    # a non-canonical but parseable stream is accepted within the length bound
+    # (4 one-byte literals "00 01" x4 = 8 bytes > 4 + 1), and rejected above it
+    lits = bytes([0x00, 0x01] * 4)
+    streams = [lits, bytes([0x83, 0x01]), bytes([0x83, 0x01]), bytes([0x83, 0x01])]
+    ends, off = [], 0
+    for st in streams:
+        off += len(st)
+        ends.append(off)
+    hdr = bytes(four[:HDR])
+    table = b"".join(e.to_bytes(4, "little") for e in ends)
+    assert orc.rle_decompress_status(hdr + table + b"".join(streams), 4, 1) == orc.ECORRUPT
+    streams[0] = bytes([0x00, 0x01, 0x82, 0x01])       # 4 bytes <= bound: accepted
+    ends, off = [], 0
+    for st in streams:
+        off += len(st)
+        ends.append(off)
+    table = b"".join(e.to_bytes(4, "little") for e in ends)
+    assert orc.rle_decompress_status(hdr + table + b"".join(streams), 4, 1) == 0
 
 
 @pytest.mark.parametrize("seed", range(20))
