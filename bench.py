@@ -57,6 +57,8 @@ def parse():
     p.add_argument("--impl", default="ec", choices=["ec", "reference"])
     p.add_argument("--workload", default="cfg2")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-extras", action="store_true",
+                   help="skip the alpha forward/backward ratio measurements")
     return p.parse_args()
 
 
@@ -340,6 +342,56 @@ class AlphaForward:
         return (time.perf_counter() - t0) / self.sample_fraction
 
 
+def _timed(fn, flush, reps):
+    """Mean CUDA-event time (ms) of fn over reps calls, L2 flushed before each."""
+    ts = []
+    for k in range(reps):
+        flush.fill_(k & 0xFF)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        fn()
+        b.record()
+        ts.append((a, b))
+    torch.cuda.synchronize()
+    return statistics.mean(a.elapsed_time(b) for a, b in ts)
+
+
+def alpha_fwd_bwd_ratio(device, flush, peak, reps=20):
+    """Ordered compositing of 32 layers at 2048^2 (FP32 and FP16 storage): plain
+    forward, separate backward (autograd path: forward, then backward) and the
+    fused forward+backward, with the ratios to the plain forward."""
+    import paper_1902_08755_gb300 as ec
+    import synthetic as S
+    res = {}
+    L, W, H = 32, 2048, 2048
+    w = S.grad_weights(3, W, H, device=device)
+    for dtype, tag in ((torch.float32, "fp32"), (torch.float16, "fp16")):
+        lay = S.alpha_layers(3, L, W, H, 0.3, dtype=dtype, device=device)
+        imgs = [ec.Image(color=lay[k]) for k in range(L)]
+        out = torch.empty((H, W, 4), dtype=dtype, device=device)
+        grads = [torch.empty_like(lay[k]) for k in range(L)]
+        s = 16 if dtype == torch.float32 else 8
+        px = W * H
+        fwd = lambda: ec.composite_alpha(imgs, out)
+        bwd = lambda: ec.composite_alpha_backward(imgs, (0, 0, W, H), w, grads)
+        fused = lambda: ec.composite_alpha_fwd_bwd(imgs, out, w, grads)
+        for f in (fwd, bwd, fused):
+            f()
+        torch.cuda.synchronize()
+        t_f, t_b, t_x = _timed(fwd, flush, reps), _timed(bwd, flush, reps), _timed(fused, flush, reps)
+        b_f = L * px * s + px * s
+        b_b = L * px * s + px * 16 + L * px * s
+        b_x = L * px * s + px * 16 + px * s + L * px * s
+        gb = lambda b, t: b / (t * 1e-3) / 1e9
+        res[tag] = {"fwd_ms": t_f, "bwd_ms": t_b, "fused_fwd_bwd_ms": t_x,
+                    "fwd_plus_bwd_over_fwd": (t_f + t_b) / t_f, "fused_over_fwd": t_x / t_f,
+                    "fwd_frac_of_peak": gb(b_f, t_f) / peak, "bwd_frac_of_peak": gb(b_b, t_b) / peak,
+                    "fused_frac_of_peak": gb(b_x, t_x) / peak,
+                    "fwd_gpixel_layers_s": L * px / (t_f * 1e-3) / 1e9}
+        del lay, imgs, out, grads
+    return res
+
+
 def make_workload(name, device):
     if name == "cfg1":
         return DepthPipeline(1, 4, 640, 480, 0.4, False, False, device)
@@ -484,6 +536,8 @@ def run_ec(args):
                     "ms_per_step": e2e_ms, "h2d_bytes_per_step": wl.h2d, "d2h_bytes_per_step": wl.d2h},
             "gpu_launches": wl.launches_per_step() * args.steps,
             "clocks": clk, "wall_s_timed_loop": t_wall}
+    if args.workload == "cfg2" and not args.no_extras:
+        line["alpha_fwd_bwd"] = alpha_fwd_bwd_ratio(device, flush, peak)
     if world == 1 and not args.no_cpu_baseline:
         wl_cpu = wl
         line["cpu_baseline"] = cpu_baseline(wl_cpu)

@@ -36,3 +36,4 @@ from .api import (  # noqa: F401
     rle_decompress_batch,
     rle_max_size,
 )
+from .autograd import alpha_composite, alpha_composite_fwd_bwd, depth_composite  # noqa: F401,E402

@@ -284,7 +284,7 @@ static ec_status rle_job_desc(const ec_rle_job& j, bool compress, RleJobDesc* d)
     if (j.w < 0 || j.h < 0 || j.pitch < j.w) return EC_ERR_INVALID_ARG;
     const uint64_t n = (uint64_t)j.w * (uint64_t)j.h;
     if (n > EC_RLE_MAX_ELEMS) return EC_ERR_UNSUPPORTED;
-    if (!j.dst || (n > 0 && !j.src)) return EC_ERR_INVALID_ARG;
+    if ((compress && !j.dst) || (n > 0 && (!j.src || !j.dst))) return EC_ERR_INVALID_ARG;
     memset(d, 0, sizeof(*d));
     d->src = reinterpret_cast<const uint32_t*>(j.src);
     d->dst = j.dst;
@@ -386,3 +386,139 @@ ec_status ec_rle_decompress(ec_ctx* ctx, const void* src, size_t src_size, void*
 
 static_assert(sizeof(ec_image) == 56 && sizeof(ec_target) == 40 && sizeof(ec_rle_job) == 48,
               "ABI struct layouts are mirrored by the Python binding");
+
+// ------------------------------------------------------------- backward ----
+
+namespace {
+
+bool aligned(const void* p, int a) { return (reinterpret_cast<uintptr_t>(p) % (uintptr_t)a) == 0; }
+
+int align_class(const void* p, int px_bytes)
+{
+    for (int a = px_bytes; a >= 2; a >>= 1)
+        if (aligned(p, a)) return a;
+    return 1;
+}
+
+// Descriptor of one layer for a backward pass (roi/pvp clipped to out_pvp).
+ec_status make_bwd_desc(const ec_rect& pvp, const ec_rect& roi, int32_t pitch, const void* color,
+                        void* grad, int px_bytes, int grad_px_bytes, const ec_rect& out_pvp,
+                        BwdDesc* d)
+{
+    if (!rect_ok(pvp) || !rect_ok(roi) || pitch < pvp.w || !rect_inside(roi, pvp)) return EC_ERR_INVALID_ARG;
+    memset(d, 0, sizeof(*d));
+    const ec_rect c = intersect(roi, out_pvp), g = intersect(pvp, out_pvp);
+    if (!rect_empty(c)) {
+        if (!color) return EC_ERR_INVALID_ARG;
+        d->x0 = c.x - out_pvp.x; d->y0 = c.y - out_pvp.y; d->x1 = d->x0 + c.w; d->y1 = d->y0 + c.h;
+    }
+    if (!rect_empty(g)) {
+        if (!grad || !aligned(grad, 2)) return EC_ERR_INVALID_ARG;
+        d->gx0 = g.x - out_pvp.x; d->gy0 = g.y - out_pvp.y; d->gx1 = d->gx0 + g.w; d->gy1 = d->gy0 + g.h;
+    }
+    const int64_t ox = (int64_t)pvp.x - out_pvp.x, oy = (int64_t)pvp.y - out_pvp.y;
+    if (ox < INT32_MIN || ox > INT32_MAX || oy < INT32_MIN || oy > INT32_MAX) return EC_ERR_INVALID_ARG;
+    d->ox = (int32_t)ox;
+    d->oy = (int32_t)oy;
+    d->pitch = pitch;
+    d->cls = (int16_t)(color ? align_class(color, px_bytes) : px_bytes);
+    if (color && d->cls < 2) return EC_ERR_INVALID_ARG;
+    d->gvec = (int16_t)(grad ? aligned(grad, grad_px_bytes) : 0);
+    d->color = color;
+    d->grad = grad;
+    return EC_OK;
+}
+
+ec_status alpha_bwd_common(ec_ctx* ctx, const ec_image* in, const int32_t* order, int32_t n,
+                           const ec_rect& out_pvp, const float* g, void* const* grad,
+                           int32_t grad_format, std::vector<BwdDesc>& d, bool* f16, bool* g16)
+{
+    if (!ctx || n < 0 || (n > 0 && (!in || !grad))) return EC_ERR_INVALID_ARG;
+    if (n > kMaxBwdLayers) return EC_ERR_UNSUPPORTED;
+    if (!rect_ok(out_pvp)) return EC_ERR_INVALID_ARG;
+    if (!rect_empty(out_pvp) && (!g || !aligned(g, 16))) return EC_ERR_INVALID_ARG;
+    if (grad_format != EC_RGBA32F && grad_format != EC_RGBA16F) return EC_ERR_INVALID_ARG;
+    const int fmt = n > 0 ? in[0].format : EC_RGBA32F;
+    if (fmt != EC_RGBA32F && fmt != EC_RGBA16F) return EC_ERR_INVALID_ARG;
+    *f16 = fmt == EC_RGBA16F;
+    *g16 = grad_format == EC_RGBA16F;
+    d.assign((size_t)std::max(n, 1), BwdDesc{});
+    std::vector<char> seen((size_t)std::max(n, 1), 0);
+    for (int k = 0; k < n; ++k) {
+        const int i = order ? order[k] : k;
+        if (i < 0 || i >= n || seen[i]) return EC_ERR_INVALID_ARG;
+        seen[i] = 1;
+        if (in[i].format != fmt) return EC_ERR_INVALID_ARG;
+        const ec_status st = make_bwd_desc(in[i].pvp, in[i].roi, in[i].pitch, in[i].color, grad[i],
+                                           bytes_per_px(fmt), bytes_per_px(grad_format), out_pvp, &d[k]);
+        if (st != EC_OK) return st;
+    }
+    return EC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+ec_status ec_composite_alpha_backward(ec_ctx* ctx, const ec_image* in, const int32_t* order,
+                                      int32_t n, ec_rect out_pvp, const float* grad_out,
+                                      void* const* grad, int32_t grad_format, ec_stream_t s)
+{
+    std::vector<BwdDesc> d;
+    bool f16 = false, g16 = false;
+    ec_status st = alpha_bwd_common(ctx, in, order, n, out_pvp, grad_out, grad, grad_format, d, &f16, &g16);
+    if (st != EC_OK) return st;
+    DstDesc D{};
+    D.W = out_pvp.w;
+    D.H = out_pvp.h;
+    DeviceGuard g(ctx->device);
+    if (!g.ok) return EC_ERR_CUDA;
+    return cuda_status(launch_alpha_bwd(d.data(), n, f16, g16, false, D, grad_out, (cudaStream_t)s));
+}
+
+ec_status ec_composite_alpha_fwd_bwd(ec_ctx* ctx, const ec_image* in, const int32_t* order,
+                                     int32_t n, const ec_target* out, float* t_final, const float* w,
+                                     void* const* grad, int32_t grad_format, ec_rect* out_roi,
+                                     ec_stream_t s)
+{
+    ec_status st = check_target(out, EC_RGBA32F, EC_RGBA16F);
+    if (st != EC_OK) return st;
+    if (n > 0 && in && in[0].format != out->format) return EC_ERR_INVALID_ARG;
+    std::vector<BwdDesc> d;
+    bool f16 = false, g16 = false;
+    st = alpha_bwd_common(ctx, in, order, n, out->pvp, w, grad, grad_format, d, &f16, &g16);
+    if (st != EC_OK) return st;
+    if (n == 0) f16 = out->format == EC_RGBA16F;
+    DstDesc D{};
+    D.W = out->pvp.w;
+    D.H = out->pvp.h;
+    D.pitch = out->pitch;
+    D.color = out->color;
+    D.tfinal = t_final;
+    D.vec = aligned(out->color, f16 ? 8 : 16);
+    if (out_roi) *out_roi = merged_roi(in, n, out->pvp);
+    DeviceGuard g(ctx->device);
+    if (!g.ok) return EC_ERR_CUDA;
+    return cuda_status(launch_alpha_bwd(d.data(), n, f16, g16, true, D, w, (cudaStream_t)s));
+}
+
+ec_status ec_composite_depth_backward(ec_ctx* ctx, const int16_t* winner, ec_rect out_pvp,
+                                      const float* grad_out, int32_t n, const ec_rect* pvps,
+                                      const int32_t* pitches, float* const* grad, ec_stream_t s)
+{
+    if (!ctx || n < 0 || (n > 0 && (!pvps || !pitches || !grad)) || !rect_ok(out_pvp)) return EC_ERR_INVALID_ARG;
+    if (n > kMaxBwdLayers) return EC_ERR_UNSUPPORTED;
+    if (!rect_empty(out_pvp) && (!winner || !grad_out || !aligned(grad_out, 16))) return EC_ERR_INVALID_ARG;
+    std::vector<BwdDesc> d((size_t)std::max(n, 1));
+    for (int i = 0; i < n; ++i) {
+        const ec_status st = make_bwd_desc(pvps[i], ec_rect{pvps[i].x, pvps[i].y, 0, 0}, pitches[i], nullptr,
+                                           grad[i], 16, 16, out_pvp, &d[i]);
+        if (st != EC_OK) return st;
+        if (grad[i] && !aligned(grad[i], 4)) return EC_ERR_INVALID_ARG;
+    }
+    DeviceGuard g(ctx->device);
+    if (!g.ok) return EC_ERR_CUDA;
+    return cuda_status(launch_depth_bwd(d.data(), n, out_pvp.w, out_pvp.h, winner, grad_out, (cudaStream_t)s));
+}
+
+}  // extern "C"

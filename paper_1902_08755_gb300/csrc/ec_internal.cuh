@@ -70,7 +70,36 @@ __device__ __forceinline__ void st_stream(float4* p, float4 v) { __stcs(p, v); }
 
 inline int ceil_div(int a, int b) { return (a + b - 1) / b; }
 
+// Per-layer descriptor of the backward passes (64 bytes), in compositing
+// order.  [x0,x1) x [y0,y1) is roi ∩ out.pvp, [gx0,gx1) x [gy0,gy1) is
+// pvp ∩ out.pvp (where gradients are written), both relative to out.pvp.
+constexpr int kMaxBwdLayers = 256;
+struct BwdDesc {
+    int32_t x0, y0, x1, y1;
+    int32_t gx0, gy0, gx1, gy1;
+    int32_t ox, oy;
+    int32_t pitch;
+    int16_t cls;           // alignment of the colour data in bytes (16, 8, 4 or 2)
+    int16_t gvec;          // gradient stores may be one vector per pixel
+    const void* color;
+    void* grad;
+};
+static_assert(sizeof(BwdDesc) == 64, "backward descriptor layout");
+
+template <int N>
+struct BwdList {
+    int32_t n;
+    int32_t pad[3];
+    BwdDesc d[N];
+};
+static_assert(sizeof(BwdList<kMaxBwdLayers>) < 32764 - 256, "kernel parameter limit");
+
 // ---- launchers (defined in the kernel translation units) -------------------
+int alpha_bwd_chunk(int n, bool f16);
+cudaError_t launch_alpha_bwd(const BwdDesc* d, int n, bool f16, bool g16, bool fused,
+                             const DstDesc& dst, const float* g, cudaStream_t s);
+cudaError_t launch_depth_bwd(const BwdDesc* d, int n, int W, int H, const int16_t* winner,
+                             const float* g, cudaStream_t s);
 cudaError_t launch_depth(const SrcDesc* src, int n, int color_bytes, const DstDesc& dst,
                          cudaStream_t s);
 cudaError_t launch_alpha_fwd(const SrcDesc* src, int n, bool f16, const DstDesc& dst,

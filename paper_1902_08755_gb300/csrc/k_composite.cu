@@ -193,41 +193,43 @@ __device__ __forceinline__ uint2 f4_to_h4(float4 f)
     return v;
 }
 
-// PX pixels (16 bytes) of one premultiplied layer.
+// Raw 16 bytes of one premultiplied layer at the thread's pixels (1 RGBA32F or
+// 2 RGBA16F pixels), zero outside the layer's ROI on the per-pixel path.
 template <bool F16>
-__device__ __forceinline__ void load_px(const SrcDesc& s, int x, int y, float4 (&c)[F16 ? 2 : 1])
+__device__ __forceinline__ uint4 load_raw(const SrcDesc& s, int x, int y)
 {
-    constexpr int PX = F16 ? 2 : 1;
     const size_t e = (size_t)(y - s.oy) * (size_t)s.pitch + (size_t)(x - s.ox);
     if constexpr (!F16) {
-        const float4* p = reinterpret_cast<const float4*>(s.color) + e;
-        if (s.vec) {
-            c[0] = ld_stream(p);
-        } else {
-            const float* f = reinterpret_cast<const float*>(p);
-            c[0] = make_float4(__ldcs(f), __ldcs(f + 1), __ldcs(f + 2), __ldcs(f + 3));
-        }
+        const uint4* p = reinterpret_cast<const uint4*>(s.color) + e;
+        if (s.vec) return ld_stream(p);
+        const unsigned int* f = reinterpret_cast<const unsigned int*>(p);
+        return make_uint4(__ldcs(f), __ldcs(f + 1), __ldcs(f + 2), __ldcs(f + 3));
     } else {
         const uint2* p = reinterpret_cast<const uint2*>(s.color) + e;
-        if (s.vec) {
-            const uint4 v = ld_stream(reinterpret_cast<const uint4*>(p));
-            c[0] = h4_to_f4(make_uint2(v.x, v.y));
-            c[1] = h4_to_f4(make_uint2(v.z, v.w));
-        } else {
+        if (s.vec) return ld_stream(reinterpret_cast<const uint4*>(p));
+        uint32_t w[4] = {0u, 0u, 0u, 0u};
 #pragma unroll
-            for (int j = 0; j < PX; ++j) {
-                const int xj = x + j;
-                if (xj >= s.x0 && xj < s.x1) {
-                    const unsigned short* h = reinterpret_cast<const unsigned short*>(p + j);
-                    c[j] = make_float4(__half2float(__ushort_as_half(__ldcs(h))),
-                                       __half2float(__ushort_as_half(__ldcs(h + 1))),
-                                       __half2float(__ushort_as_half(__ldcs(h + 2))),
-                                       __half2float(__ushort_as_half(__ldcs(h + 3))));
-                } else {
-                    c[j] = make_float4(0.f, 0.f, 0.f, 0.f);
-                }
+        for (int j = 0; j < 2; ++j) {
+            const int xj = x + j;
+            if (xj >= s.x0 && xj < s.x1) {
+                const unsigned short* h = reinterpret_cast<const unsigned short*>(p + j);
+                w[2 * j] = (uint32_t)__ldcs(h) | ((uint32_t)__ldcs(h + 1) << 16);
+                w[2 * j + 1] = (uint32_t)__ldcs(h + 2) | ((uint32_t)__ldcs(h + 3) << 16);
             }
         }
+        return make_uint4(w[0], w[1], w[2], w[3]);
+    }
+}
+
+// Pixel j of a raw 16-byte word as float RGBA.
+template <bool F16>
+__device__ __forceinline__ float4 pixel_of(const uint4& v, int j)
+{
+    if constexpr (!F16) {
+        return make_float4(__uint_as_float(v.x), __uint_as_float(v.y), __uint_as_float(v.z),
+                           __uint_as_float(v.w));
+    } else {
+        return j == 0 ? h4_to_f4(make_uint2(v.x, v.y)) : h4_to_f4(make_uint2(v.z, v.w));
     }
 }
 
@@ -254,7 +256,7 @@ k_alpha_fwd(const __grid_constant__ SrcList<N> L, const __grid_constant__ DstDes
     for (int j = 0; j < PX; ++j) { acc[j] = make_float4(0.f, 0.f, 0.f, 0.f); T[j] = 1.0f; }
 
     for (int a = 0; a < nact; a += U) {
-        float4 c[U][PX];
+        uint4 raw[U];
         bool live[U];
         int idx[U];
 #pragma unroll
@@ -264,7 +266,7 @@ k_alpha_fwd(const __grid_constant__ SrcList<N> L, const __grid_constant__ DstDes
             if (idx[u] >= 0) {
                 const SrcDesc& s = L.s[idx[u]];
                 live[u] = y >= s.y0 && y < s.y1 && x + PX > s.x0 && x < s.x1;
-                if (live[u]) load_px<F16>(s, x, y, c[u]);
+                if (live[u]) raw[u] = load_raw<F16>(s, x, y);
             }
         }
 #pragma unroll
@@ -275,12 +277,13 @@ k_alpha_fwd(const __grid_constant__ SrcList<N> L, const __grid_constant__ DstDes
             for (int j = 0; j < PX; ++j) {
                 const int xj = x + j;
                 if (xj < s.x0 || xj >= s.x1) continue;   // transparent outside the ROI
+                const float4 c = pixel_of<F16>(raw[u], j);
                 // C += T c (premultiplied, all four channels); T *= (1 - a)
-                acc[j].x = fmaf(T[j], c[u][j].x, acc[j].x);
-                acc[j].y = fmaf(T[j], c[u][j].y, acc[j].y);
-                acc[j].z = fmaf(T[j], c[u][j].z, acc[j].z);
-                acc[j].w = fmaf(T[j], c[u][j].w, acc[j].w);
-                T[j] = fmaf(-T[j], c[u][j].w, T[j]);
+                acc[j].x = fmaf(T[j], c.x, acc[j].x);
+                acc[j].y = fmaf(T[j], c.y, acc[j].y);
+                acc[j].z = fmaf(T[j], c.z, acc[j].z);
+                acc[j].w = fmaf(T[j], c.w, acc[j].w);
+                T[j] = fmaf(-T[j], c.w, T[j]);
             }
         }
     }

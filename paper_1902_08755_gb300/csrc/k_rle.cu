@@ -37,13 +37,10 @@ constexpr int kT = 256;                              // threads per CTA
 constexpr int kPer = kChunk / kT;                    // 16 positions per thread
 constexpr int kPlaneCap = kChunk + kChunk / 128;     // worst-case stream bytes
 constexpr int kStage = 4 * kPlaneCap;                // 16512
-constexpr int kSmemWords = kChunk + (kChunk / 32) * 4;
 constexpr uint32_t kMagic = 0x31524345u;             // "ECR1"
 constexpr uint64_t kAgg = 1ull << 62, kInc = 2ull << 62, kVal = (1ull << 62) - 1;
 constexpr int kSpinLimit = 1 << 22;
 constexpr int kTok = 256;                            // tokens per plane per round
-
-__device__ __forceinline__ int pidx(int q) { return q + ((q >> 5) << 2); }
 
 // Bit-swizzle: byte k of the result gathers bit pair (7-2k, 6-2k) of the four
 // components, component 0 (R) in the top pair.  This is a transpose of the 4x4
@@ -152,18 +149,59 @@ __device__ __forceinline__ uint32_t lane16(P4 v, int p)
 
 // ------------------------------------------------------------- compress ----
 
+// The most significant bit of each byte of w, gathered into bits 0..3.
+__device__ __forceinline__ uint32_t byte_msbs(uint32_t w)
+{
+    return ((w & 0x80808080u) * 0x00204081u) >> 28;
+}
+
+// 4-bit mask of the bytes of a and b that are equal (bit i = byte i).
+__device__ __forceinline__ uint32_t eq_bytes(uint32_t a, uint32_t b)
+{
+    const uint32_t x = a ^ b;                                   // zero byte <=> equal
+    const uint32_t t = ~(((x & 0x7F7F7F7Fu) + 0x7F7F7F7Fu) | x | 0x7F7F7F7Fu);
+    return byte_msbs(t);
+}
+
+// 4x4 byte transpose: word b of the result holds byte b of e0..e3 (e0 lowest).
+__device__ __forceinline__ uint4 transpose4(uint32_t e0, uint32_t e1, uint32_t e2, uint32_t e3)
+{
+    const uint32_t lo01 = __byte_perm(e0, e1, 0x5140), lo23 = __byte_perm(e2, e3, 0x5140);
+    const uint32_t hi01 = __byte_perm(e0, e1, 0x7362), hi23 = __byte_perm(e2, e3, 0x7362);
+    return make_uint4(__byte_perm(lo01, lo23, 0x5410), __byte_perm(lo01, lo23, 0x7632),
+                      __byte_perm(hi01, hi23, 0x5410), __byte_perm(hi01, hi23, 0x7632));
+}
+
+// Bits [lo, hi) set (0 <= lo, hi <= 31).
+__device__ __forceinline__ uint32_t bit_range(int lo, int hi)
+{
+    lo = max(lo, 0);
+    hi = min(hi, 31);
+    return hi > lo ? ((1u << hi) - 1u) & ~((1u << lo) - 1u) : 0u;
+}
+
+__device__ __forceinline__ uint64_t warp_sum(uint64_t v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+constexpr int kPlaneStride = kChunk + 32;   // 16 bytes of slack before and after
+
 template <int N>
-__global__ void __launch_bounds__(kT)
+__global__ void __launch_bounds__(kT, 4)
 k_rle_compress(const __grid_constant__ RleJobList<N> J, uint64_t* flags, uint32_t* ticket,
                uint32_t* status)
 {
-    __shared__ __align__(16) uint32_t se[kSmemWords];
+    // plane-major copy of the chunk: pl[b][16 + q] = plane b of element q
+    __shared__ __align__(16) uint8_t pl[4][kPlaneStride];
     __shared__ __align__(16) uint8_t stage[kStage + 16];
     __shared__ P4 wt_max[kT / 32], wt_sum[kT / 32];
     __shared__ uint32_t s_unit;
     __shared__ uint64_t s_off;
 
-    const int tid = threadIdx.x;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     if (tid == 0) s_unit = atomicAdd(ticket, 1u);
     __syncthreads();
     const uint32_t unit = s_unit;
@@ -184,95 +222,77 @@ k_rle_compress(const __grid_constant__ RleJobList<N> J, uint64_t* flags, uint32_
     const int len = (int)min((uint32_t)kChunk, n - q0);
     const uint32_t w = (uint32_t)jb.w;
 
-    // 1. load
+    // 1. load, swizzle (mode 2) and split into byte planes
     if (jb.vec) {
+        const bool dense = jb.pitch == jb.w;       // element q at src + q
         for (int g = tid; 4 * g < len; g += kT) {
-            const uint32_t q = q0 + 4u * g, y = q / w, x = q - y * w;
-            uint4 v = ld_stream(reinterpret_cast<const uint4*>(jb.src + (size_t)y * jb.pitch + x));
+            const uint32_t q = q0 + 4u * g;
+            size_t e = q;
+            if (!dense) {
+                const uint32_t y = q / w;
+                e = (size_t)y * jb.pitch + (q - y * w);
+            }
+            uint4 v = ld_stream(reinterpret_cast<const uint4*>(jb.src + e));
             if (jb.mode == 2) { v.x = swizzle(v.x); v.y = swizzle(v.y); v.z = swizzle(v.z); v.w = swizzle(v.w); }
-            *reinterpret_cast<uint4*>(se + pidx(4 * g)) = v;
+            const uint4 t = transpose4(v.x, v.y, v.z, v.w);
+            *reinterpret_cast<uint32_t*>(&pl[0][16 + 4 * g]) = t.x;
+            *reinterpret_cast<uint32_t*>(&pl[1][16 + 4 * g]) = t.y;
+            *reinterpret_cast<uint32_t*>(&pl[2][16 + 4 * g]) = t.z;
+            *reinterpret_cast<uint32_t*>(&pl[3][16 + 4 * g]) = t.w;
         }
     } else {
         for (int t = tid; t < len; t += kT) {
             const uint32_t q = q0 + t, y = q / w, x = q - y * w;
             uint32_t v = __ldcs(jb.src + (size_t)y * jb.pitch + x);
             if (jb.mode == 2) v = swizzle(v);
-            se[pidx(t)] = v;
+            pl[0][16 + t] = (uint8_t)v;
+            pl[1][16 + t] = (uint8_t)(v >> 8);
+            pl[2][16 + t] = (uint8_t)(v >> 16);
+            pl[3][16 + t] = (uint8_t)(v >> 24);
         }
     }
     __syncthreads();
 
-    // 2. classify positions P0-3 .. P0+19 (i = p - P0 + 3)
+    // 2. classify this thread's 16 positions of every plane with bit masks.
+    // Bit i of the 24-bit masks stands for position P0 - 4 + i.
     const int P0 = tid * kPer;
-    constexpr int NV = kPer + 7;
-    uint32_t val[NV];
+    const uint32_t VQ = bit_range(4 - P0, len - P0 + 4);          // 0 <= q < len
+    const uint32_t VEQ = bit_range(5 - P0, len - P0 + 4);         // 1 <= q < len
+    const uint32_t HIGH = bit_range(len - P0 + 4, 24);            // q >= len
+    const uint32_t Q0 = P0 == 0 ? (1u << 4) : 0u;                 // q == 0
+    uint32_t REP[4], SEG[4];
+    uint4 bytes[4];
 #pragma unroll
-    for (int i = 0; i < NV; ++i) {
-        const int p = P0 - 3 + i;
-        val[i] = (p >= 0 && p < len) ? se[pidx(p)] : 0u;
+    for (int b = 0; b < 4; ++b) {
+        const uint8_t* base = &pl[b][16 + P0];
+        const uint4 v = *reinterpret_cast<const uint4*>(base);
+        const uint32_t wm = *reinterpret_cast<const uint32_t*>(base - 4);
+        const uint32_t wp = *reinterpret_cast<const uint32_t*>(base + 16);
+        bytes[b] = v;
+        // eq bit i: byte at position P0-4+i equals its predecessor
+        uint32_t EQ = eq_bytes(wm, wm << 8);
+        EQ |= eq_bytes(v.x, __funnelshift_l(wm, v.x, 8)) << 4;
+        EQ |= eq_bytes(v.y, __funnelshift_l(v.x, v.y, 8)) << 8;
+        EQ |= eq_bytes(v.z, __funnelshift_l(v.y, v.z, 8)) << 12;
+        EQ |= eq_bytes(v.w, __funnelshift_l(v.z, v.w, 8)) << 16;
+        EQ |= eq_bytes(wp, __funnelshift_l(v.w, wp, 8)) << 20;
+        EQ &= VEQ & ~1u;                                          // bit 0 has no predecessor here
+        const uint32_t T3 = EQ & (EQ << 1);                       // positions i-2, i-1, i equal
+        const uint32_t R = (T3 | (T3 >> 1) | (T3 >> 2)) & VQ;     // byte lies in a run >= 3
+        const uint32_t S = (((R & ~EQ) | (~R & (R << 1))) & VQ) | HIGH | Q0;
+        REP[b] = (R >> 4) & 0xFFFFu;
+        SEG[b] = (S >> 4) & 0x1FFFFu;                             // bit 16: position P0+16
     }
-    uint32_t eq[NV];
-    eq[0] = 0u;
-#pragma unroll
-    for (int i = 1; i < NV; ++i) {
-        const int p = P0 - 3 + i;
-        eq[i] = (p >= 1 && p < len) ? __vcmpeq4(val[i], val[i - 1]) : 0u;
-    }
-    uint32_t t3[NV];
-    t3[0] = t3[1] = 0u;
-#pragma unroll
-    for (int i = 2; i < NV; ++i) t3[i] = eq[i] & eq[i - 1];
-    // rep[i] for i in [2, NV-2): the byte lies in a run of >= 3
-    uint32_t rep[NV];
-#pragma unroll
-    for (int i = 2; i < NV - 2; ++i) rep[i] = t3[i] | t3[i + 1] | t3[i + 2];
-    // segment starts at p in [P0, P0+16); positions >= len count as starts.
-    // Mlo holds planes 0 (bits 0-15) and 1 (bits 16-31), Mhi planes 2 and 3.
-    uint32_t Mlo = 0u, Mhi = 0u;
-#pragma unroll
-    for (int k = 0; k < kPer; ++k) {
-        const int i = k + 3, p = P0 + k;
-        uint32_t seg;
-        if (p >= len) {
-            seg = 0xFFFFFFFFu;
-        } else {
-            const uint32_t rs = rep[i] & ~eq[i];
-            const uint32_t ls = ~rep[i] & (p == 0 ? 0xFFFFFFFFu : rep[i - 1]);
-            seg = rs | ls;
-        }
-        Mlo |= ((seg >> 7) & 1u) << k | ((seg >> 15) & 1u) << (k + 16);
-        Mhi |= ((seg >> 23) & 1u) << k | ((seg >> 31) & 1u) << (k + 16);
-    }
-    // 16-bit mask of segment starts at positions P0..P0+15 of one plane
-    auto mask_of = [&](int pl) -> uint32_t {
-        const uint32_t m = pl < 2 ? Mlo : Mhi;
-        return (pl & 1) ? (m >> 16) : (m & 0xFFFFu);
-    };
-    // whether position P0+16 starts a segment, per plane
-    uint32_t next_seg[4];
-    {
-        const int p = P0 + kPer;
-        uint32_t seg;
-        if (p >= len) {
-            seg = 0xFFFFFFFFu;
-        } else {
-            const int i = kPer + 3;
-            const uint32_t rs = rep[i] & ~eq[i];
-            const uint32_t ls = ~rep[i] & rep[i - 1];
-            seg = rs | ls;
-        }
-#pragma unroll
-        for (int pl = 0; pl < 4; ++pl) next_seg[pl] = (seg >> (8 * pl + 7)) & 1u;
-    }
+    const uint32_t VALID = (VQ >> 4) & 0xFFFFu;
 
-    // 3. last segment start before this thread (max-scan of position + 1)
+    // 3. last segment start before each thread (max-scan of position + 1)
     P4 mine;
     {
         uint32_t l[4];
 #pragma unroll
-        for (int pl = 0; pl < 4; ++pl) {
-            const uint32_t m = mask_of(pl);
-            l[pl] = m ? (uint32_t)(P0 + 31 - __clz(m) + 1) : 0u;
+        for (int b = 0; b < 4; ++b) {
+            const uint32_t m = SEG[b] & 0xFFFFu;
+            l[b] = m ? (uint32_t)(P0 + 31 - __clz(m) + 1) : 0u;
         }
         mine.a = l[0] | (l[1] << 16);
         mine.b = l[2] | (l[3] << 16);
@@ -280,93 +300,103 @@ k_rle_compress(const __grid_constant__ RleJobList<N> J, uint64_t* flags, uint32_
     P4 tot_max;
     const P4 before = block_scan<true>(mine, wt_max, &tot_max);
 
-    // 4. output sizes: repeat piece start 2, literal piece start 2, literal 1
-    uint32_t cost[4];
+    // 4. piece starts (tokens hold <= 128 bytes) and output sizes
+    uint32_t PSV[4], PE[4], LIT[4], cost[4];
+    int sbin[4];
 #pragma unroll
-    for (int pl = 0; pl < 4; ++pl) {
-        const uint32_t m = mask_of(pl);
-        int sb = (int)lane16(before, pl) - 1;
-        uint32_t sum = 0;
-#pragma unroll
-        for (int k = 0; k < kPer; ++k) {
-            const int p = P0 + k;
-            if (p < len) {
-                if ((m >> k) & 1u) sb = p;
-                const bool ps = ((p - sb) & 127) == 0;
-                const bool isrep = (rep[k + 3] >> (8 * pl)) & 0xFFu;
-                sum += isrep ? (ps ? 2u : 0u) : (ps ? 2u : 1u);
-            }
+    for (int b = 0; b < 4; ++b) {
+        const uint32_t seg16 = SEG[b] & 0xFFFFu;
+        const int sb_in = (int)lane16(before, b) - 1;            // -1 only for position 0
+        sbin[b] = sb_in;
+        uint32_t PS = seg16;
+        const int first = seg16 ? __ffs(seg16) - 1 : 16;
+        if (sb_in >= 0) {                                        // continuing segment
+            const int r = (P0 - sb_in) & 127;
+            const int d = r ? 128 - r : 0;
+            if (d < first) PS |= 1u << d;
         }
-        cost[pl] = sum;
+        const int sb15 = seg16 ? P0 + 31 - __clz(seg16) : sb_in;
+        const uint32_t next = ((SEG[b] >> 16) & 1u) | (((P0 + 16 - sb15) & 127) == 0 ? 1u : 0u);
+        PSV[b] = PS & VALID;
+        PE[b] = ((PS | (next << 16)) >> 1) & VALID;
+        LIT[b] = ~REP[b] & VALID;
+        cost[b] = __popc(LIT[b]) + __popc(PSV[b]) + __popc(PSV[b] & REP[b]);
     }
     P4 tot;
     const P4 off0 = block_scan<false>(P4{cost[0] | (cost[1] << 16), cost[2] | (cost[3] << 16)},
                                       wt_sum, &tot);
     uint32_t ptot[4], pbase[4], total = 0;
 #pragma unroll
-    for (int pl = 0; pl < 4; ++pl) {
-        ptot[pl] = lane16(tot, pl);
-        pbase[pl] = total;
-        total += ptot[pl];
+    for (int b = 0; b < 4; ++b) {
+        ptot[b] = lane16(tot, b);
+        pbase[b] = total;
+        total += ptot[b];
     }
 
-    // 5. chunk offset: decoupled look-back (thread 0), bounded waits
-    if (tid == 0) {
+    // 5. chunk offset: warp-wide decoupled look-back, bounded waits
+    if (warp == 0) {
         uint64_t* f = flags + unit;
+        uint64_t acc = 0;
         if (c == 0) {
-            st_release(f, kInc | (uint64_t)total);
-            s_off = 0;
+            if (lane == 0) st_release(f, kInc | (uint64_t)total);
         } else {
-            st_release(f, kAgg | (uint64_t)total);
-            uint64_t acc = 0;
-            uint32_t k = unit - 1;
+            if (lane == 0) st_release(f, kAgg | (uint64_t)total);
+            int64_t hi = (int64_t)unit - 1;
             int spins = 0;
             for (;;) {
-                const uint64_t v = ld_acquire(flags + k);
-                if ((v & ~kVal) == 0) {
+                const int64_t k = hi - lane;
+                const uint64_t v = k >= (int64_t)jb.first_unit ? ld_acquire(flags + k) : kInc;
+                const uint32_t st = (uint32_t)(v >> 62);
+                const uint32_t incm = __ballot_sync(0xffffffffu, st == 2u);
+                const uint32_t zerom = __ballot_sync(0xffffffffu, st == 0u);
+                const uint32_t upto = incm ? ((incm & (0u - incm)) << 1) - 1u : 0xffffffffu;
+                if (zerom & upto) {
                     if (++spins > kSpinLimit) {
-                        set_status(status, EC_ERR_TIMEOUT);
+                        if (lane == 0) set_status(status, EC_ERR_TIMEOUT);
                         break;
                     }
                     __nanosleep(64);
                     continue;
                 }
-                acc += v & kVal;
-                if ((v & ~kVal) == kInc || k == jb.first_unit) break;
-                --k;
+                acc += warp_sum(((upto >> lane) & 1u) ? (v & kVal) : 0ull);
+                if (incm) break;
+                hi -= 32;
             }
-            st_release(f, kInc | (acc + total));
-            s_off = acc;
+            if (lane == 0) st_release(f, kInc | (acc + total));
         }
+        if (lane == 0) s_off = acc;
     }
 
-    // emit into the stage
+    // emit bytes and control codes into the stage
 #pragma unroll
-    for (int pl = 0; pl < 4; ++pl) {
-        const uint32_t m = mask_of(pl) | (next_seg[pl] << kPer);
-        int sb = (int)lane16(before, pl) - 1;
-        uint32_t off = lane16(off0, pl);
-        uint8_t* out = stage + pbase[pl];
-#pragma unroll
-        for (int k = 0; k < kPer; ++k) {
-            const int p = P0 + k;
-            if (p < len) {
-                if ((m >> k) & 1u) sb = p;
-                const int j = p - sb;
-                const bool ps = (j & 127) == 0;
-                const bool isrep = (rep[k + 3] >> (8 * pl)) & 0xFFu;
-                off += isrep ? (ps ? 2u : 0u) : (ps ? 2u : 1u);
-                const bool last = ((m >> (k + 1)) & 1u) || ((j + 1) & 127) == 0;
-                const uint8_t byte = (uint8_t)(val[k + 3] >> (8 * pl));
-                if (isrep) {
-                    if (last) {
-                        out[off - 2] = (uint8_t)(0x80 + (j & 127));
-                        out[off - 1] = byte;
-                    }
-                } else {
-                    out[off - 1] = byte;
-                    if (last) out[off - 2 - (j & 127)] = (uint8_t)(j & 127);
-                }
+    for (int b = 0; b < 4; ++b) {
+        uint8_t* out = stage + pbase[b];
+        const uint32_t off = lane16(off0, b);
+        const uint32_t lit = LIT[b], psv = PSV[b], psr = PSV[b] & REP[b], seg16 = SEG[b] & 0xFFFFu;
+        const uint4 v = bytes[b];
+        auto byte_at = [&](int k) -> uint8_t {
+            const uint32_t wd = k < 8 ? (k < 4 ? v.x : v.y) : (k < 12 ? v.z : v.w);
+            return (uint8_t)(wd >> (8 * (k & 3)));
+        };
+        auto inc_at = [&](int k) -> uint32_t {
+            const uint32_t le = (2u << k) - 1u;
+            return off + __popc(lit & le) + __popc(psv & le) + __popc(psr & le);
+        };
+        for (uint32_t m = lit; m; m &= m - 1u) {
+            const int k = __ffs(m) - 1;
+            out[inc_at(k) - 1] = byte_at(k);
+        }
+        for (uint32_t m = PE[b]; m; m &= m - 1u) {
+            const int k = __ffs(m) - 1;
+            const uint32_t inc = inc_at(k);
+            const uint32_t h = seg16 & ((2u << k) - 1u);
+            const int sbk = h ? P0 + 31 - __clz(h) : sbin[b];
+            const uint32_t jj = (uint32_t)(P0 + k - sbk) & 127u;
+            if ((REP[b] >> k) & 1u) {
+                out[inc - 2] = (uint8_t)(0x80u + jj);
+                out[inc - 1] = byte_at(k);
+            } else {
+                out[inc - 2 - jj] = (uint8_t)jj;
             }
         }
     }
@@ -383,16 +413,15 @@ k_rle_compress(const __grid_constant__ RleJobList<N> J, uint64_t* flags, uint32_
             for (uint32_t i = tid; i < total; i += kT) o[i] = stage[i];
         } else {
             const uint32_t head = (uint32_t)(w0 - a0), tail0 = (uint32_t)(w1 - a0);
-            if (tid < head) o[tid] = stage[tid];
+            if ((uint32_t)tid < head) o[tid] = stage[tid];
             for (uint32_t i = tail0 + tid; i < total; i += kT) o[i] = stage[i];
             const uint32_t nw = (uint32_t)((w1 - w0) >> 2);
             const uint32_t* s32 = reinterpret_cast<const uint32_t*>(stage);
-            const uint32_t sh = 8u * (head & 3u);
+            const uint32_t sh = 8u * head;
             uint32_t* o32 = reinterpret_cast<uint32_t*>(w0);
             for (uint32_t k = tid; k < nw; k += kT) {
-                // stage bytes [head + 4k, head + 4k + 4): head < 4
-                const uint32_t lo = s32[k + (head >> 2)], hi = s32[k + (head >> 2) + 1];
-                o32[k] = __funnelshift_r(lo, hi, sh);
+                // stage bytes [head + 4k, head + 4k + 4), head < 4
+                o32[k] = __funnelshift_r(s32[k], s32[k + 1], sh);
             }
         }
     }
@@ -415,6 +444,7 @@ k_rle_decompress(const __grid_constant__ RleJobList<N> J, uint32_t* status)
     __shared__ int ntok[4], pref[5];
     __shared__ uint32_t s_beg[5];
     __shared__ int s_fail, s_mode, s_live;
+    __shared__ uint8_t s_hdr[52];
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const uint32_t unit = blockIdx.x;
@@ -424,28 +454,38 @@ k_rle_decompress(const __grid_constant__ RleJobList<N> J, uint32_t* status)
     const uint32_t nc = jb.n_chunks;
     const uint32_t c = unit - jb.first_unit;
 
+    // header (32 bytes) and this chunk's end-table entries 4c-1 .. 4c+3 (20 bytes),
+    // fetched in one round trip by 52 threads
+    const bool has_hdr = size >= 32, has_tab = nc > 0 && size >= 32ull + 16ull * nc;
+    if (tid < 32) {
+        s_hdr[tid] = has_hdr ? src[tid] : 0;
+    } else if (tid < 52) {
+        const int i = tid - 32;
+        s_hdr[tid] = (has_tab && !(c == 0 && i < 4)) ? src[32 + 16ull * c - 4 + i] : 0;
+    }
+    __syncthreads();
     if (tid == 0) {
         int bad = 0;
-        if (size < 32) bad = 1;
+        if (!has_hdr) bad = 1;
         else {
-            const uint32_t mode = (uint32_t)src[6] | ((uint32_t)src[7] << 8);
-            bad |= get_u32(src) != kMagic;
-            bad |= (src[4] | (src[5] << 8)) != 1;
+            const uint8_t* h = s_hdr;
+            const uint32_t mode = (uint32_t)h[6] | ((uint32_t)h[7] << 8);
+            bad |= get_u32(h) != kMagic;
+            bad |= (h[4] | (h[5] << 8)) != 1;
             bad |= mode != 1u && mode != 2u;
-            bad |= get_u32(src + 8) != (uint32_t)jb.w || get_u32(src + 12) != (uint32_t)jb.h;
-            bad |= get_u32(src + 16) != 4u || get_u32(src + 20) != (uint32_t)kChunk;
-            bad |= get_u32(src + 24) != nc || get_u32(src + 28) != 4u;
+            bad |= get_u32(h + 8) != (uint32_t)jb.w || get_u32(h + 12) != (uint32_t)jb.h;
+            bad |= get_u32(h + 16) != 4u || get_u32(h + 20) != (uint32_t)kChunk;
+            bad |= get_u32(h + 24) != nc || get_u32(h + 28) != 4u;
             s_mode = (int)mode;
-            if (!bad && size < 32ull + 16ull * nc) bad = 1;
+            if (!bad && nc > 0 && !has_tab) bad = 1;
             if (!bad && nc > 0) {
-                const uint8_t* tab = src + 32;
                 const uint64_t psize = size - 32ull - 16ull * nc;
                 const uint32_t n = (uint32_t)jb.w * (uint32_t)jb.h;
                 const uint32_t clen = min((uint32_t)kChunk, n - c * (uint32_t)kChunk);
                 const uint32_t cap = clen + (clen + 127u) / 128u;   // all-literal coding
-                s_beg[0] = c == 0 ? 0u : get_u32(tab + 4u * (4u * c - 1u));
+                s_beg[0] = get_u32(h + 32);                         // 0 for chunk 0
                 for (int p = 0; p < 4; ++p) {
-                    s_beg[p + 1] = get_u32(tab + 4u * (4u * c + p));
+                    s_beg[p + 1] = get_u32(h + 36 + 4 * p);
                     bad |= s_beg[p + 1] < s_beg[p];
                     bad |= s_beg[p + 1] - s_beg[p] > cap;   // longer than any valid stream
                 }
@@ -479,17 +519,32 @@ k_rle_decompress(const __grid_constant__ RleJobList<N> J, uint32_t* status)
         if (lane == 0 && warp < 4) {
             int cnt = 0;
             if (!done) {
+                int last_rep = -1;           // list index of a repeat this token may extend
+                int last_val = -1;
                 while (cnt < kTok && in < in_end) {
                     const int ctl = sbuf[in];
-                    int m, next;
-                    uint32_t rep;
-                    if (ctl < 128) { m = ctl + 1; next = in + 1 + m; rep = 0; }
-                    else { m = ctl - 127; next = in + 2; rep = 1; }
-                    if (next > in_end || outp + m > len) { s_fail = 1; break; }
-                    toks[warp][cnt++] = make_uint2((uint32_t)outp | ((uint32_t)(m - 1) << 16) | (rep << 31),
-                                                   (uint32_t)(in + 1));
-                    outp += m;
-                    in = next;
+                    if (ctl < 128) {
+                        const int m = ctl + 1, next = in + 1 + m;
+                        if (next > in_end || outp + m > len) { s_fail = 1; break; }
+                        toks[warp][cnt++] = make_uint2((uint32_t)outp | ((uint32_t)m << 16), (uint32_t)(in + 1));
+                        last_rep = -1;
+                        outp += m;
+                        in = next;
+                    } else {
+                        const int m = ctl - 127, next = in + 2;
+                        if (next > in_end || outp + m > len) { s_fail = 1; break; }
+                        const int v = sbuf[in + 1];
+                        if (last_rep >= 0 && v == last_val) {
+                            toks[warp][last_rep].x += (uint32_t)m << 16;     // one longer run
+                        } else {
+                            toks[warp][cnt] = make_uint2((uint32_t)outp | ((uint32_t)m << 16),
+                                                         (uint32_t)(in + 1) | (1u << 31));
+                            last_rep = cnt++;
+                            last_val = v;
+                        }
+                        outp += m;
+                        in = next;
+                    }
                 }
                 if (in >= in_end && !s_fail) {
                     done = true;
@@ -512,13 +567,20 @@ k_rle_decompress(const __grid_constant__ RleJobList<N> J, uint32_t* status)
         for (int t = warp; t < pref[4]; t += kT / 32) {
             const int p = t < pref[1] ? 0 : t < pref[2] ? 1 : t < pref[3] ? 2 : 3;
             const uint2 tk = toks[p][t - pref[p]];
-            const int o = (int)(tk.x & 0xFFFFu), m = (int)((tk.x >> 16) & 0x7Fu) + 1;
-            const int s0 = (int)tk.y;
-            if (tk.x >> 31) {
+            const int o = (int)(tk.x & 0xFFFFu), m = (int)(tk.x >> 16);
+            const int s0 = (int)(tk.y & 0xFFFFu);
+            uint8_t* d = &planes[p][o];
+            if (tk.y >> 31) {                    // run: head bytes, 32-bit words, tail bytes
                 const uint8_t v = sbuf[s0];
-                for (int i = lane; i < m; i += 32) planes[p][o + i] = v;
+                const int head = min(m, (4 - (o & 3)) & 3);
+                const int body = (m - head) >> 2, tail = (m - head) & 3;
+                if (lane < head) d[lane] = v;
+                uint32_t* wd = reinterpret_cast<uint32_t*>(d + head);
+                const uint32_t word = 0x01010101u * v;
+                for (int i = lane; i < body; i += 32) wd[i] = word;
+                if (lane < tail) d[head + 4 * body + lane] = v;
             } else {
-                for (int i = lane; i < m; i += 32) planes[p][o + i] = sbuf[s0 + i];
+                for (int i = lane; i < m; i += 32) d[i] = sbuf[s0 + i];
             }
         }
         __syncthreads();
@@ -530,18 +592,21 @@ k_rle_decompress(const __grid_constant__ RleJobList<N> J, uint32_t* status)
     const uint32_t w = (uint32_t)jb.w;
     const bool sw = s_mode == 2;
     if (jb.vec) {
+        const bool dense = jb.pitch == jb.w;
         for (int g = tid; 4 * g < len; g += kT) {
             const uint32_t A = *reinterpret_cast<const uint32_t*>(&planes[0][4 * g]);
             const uint32_t B = *reinterpret_cast<const uint32_t*>(&planes[1][4 * g]);
             const uint32_t C = *reinterpret_cast<const uint32_t*>(&planes[2][4 * g]);
             const uint32_t D = *reinterpret_cast<const uint32_t*>(&planes[3][4 * g]);
-            const uint32_t ab_lo = __byte_perm(A, B, 0x5140), cd_lo = __byte_perm(C, D, 0x5140);
-            const uint32_t ab_hi = __byte_perm(A, B, 0x7362), cd_hi = __byte_perm(C, D, 0x7362);
-            uint4 v = make_uint4(__byte_perm(ab_lo, cd_lo, 0x5410), __byte_perm(ab_lo, cd_lo, 0x7632),
-                                 __byte_perm(ab_hi, cd_hi, 0x5410), __byte_perm(ab_hi, cd_hi, 0x7632));
+            uint4 v = transpose4(A, B, C, D);                 // planes -> elements
             if (sw) { v.x = swizzle(v.x); v.y = swizzle(v.y); v.z = swizzle(v.z); v.w = swizzle(v.w); }
-            const uint32_t q = q0 + 4u * g, y = q / w, x = q - y * w;
-            st_stream(reinterpret_cast<uint4*>(dstp + (size_t)y * jb.pitch + x), v);
+            const uint32_t q = q0 + 4u * g;
+            size_t e = q;
+            if (!dense) {
+                const uint32_t y = q / w;
+                e = (size_t)y * jb.pitch + (q - y * w);
+            }
+            st_stream(reinterpret_cast<uint4*>(dstp + e), v);
         }
     } else {
         for (int t = tid; t < len; t += kT) {
