@@ -237,6 +237,38 @@ ec_status ec_rle_compress_batch(ec_ctx* ctx, const ec_rle_job* jobs, int32_t njo
 ec_status ec_rle_decompress_batch(ec_ctx* ctx, const ec_rle_job* jobs, int32_t njobs,
                                   ec_stream_t s);
 
+/* ------------------------------------------------ allocation-free compressor
+ * The thesis has no counterpart to this entry point; it exists for callers
+ * that cannot allocate device memory.  ec_rle_compress takes its scratch
+ * memory (look-back words and a ticket) from an ec_ctx, which allocates it
+ * with cudaMalloc.  Code that must not allocate once it runs -- a frame loop
+ * that reserved all of its memory at start-up, code whose device memory is
+ * owned by another framework's pool, or code that cannot absorb the implicit
+ * device synchronisation cudaMalloc/cudaFree may cause -- can call this
+ * variant instead: it allocates nothing and needs no context.
+ *
+ * Its scratch is a fixed array of EC_RLE_NOALLOC_SCRATCH_BYTES compiled into
+ * libec; every GPU that loads the library holds one copy until the process
+ * exits.  Images of more than EC_RLE_NOALLOC_MAX_CHUNKS chunks (4096 elements
+ * each, 33,554,432 elements in all, enough for one 7680x4320 frame) are
+ * refused with EC_ERR_UNSUPPORTED.  The first call on a device looks up the
+ * array's device address with that device current; make that first call
+ * before any stream capture.  All calls share the one array and it keeps the
+ * last call's contents (each call clears what it needs with a memset on s), so
+ * calls that overlap on the GPU -- on different streams or from several host
+ * threads -- race; serialise them.
+ *
+ * Arguments are those of ec_rle_compress without the context, on the current
+ * device, plus d_status: a device uint32 that the caller zeroes and that
+ * receives the first device-side error (EC_ERR_TIMEOUT if a bounded wait gave
+ * up), since there is no context status word.  The stream written is byte for
+ * byte the one ec_rle_compress writes. */
+#define EC_RLE_NOALLOC_MAX_CHUNKS 8192
+#define EC_RLE_NOALLOC_SCRATCH_BYTES (16 + 8 * EC_RLE_NOALLOC_MAX_CHUNKS)
+ec_status ec_rle_compress_noalloc(const void* src, int32_t w, int32_t h, int32_t pitch,
+                                  uint32_t mode, void* dst, size_t dst_capacity,
+                                  uint64_t* d_size, uint32_t* d_status, ec_stream_t s);
+
 #ifdef __cplusplus
 }
 #endif

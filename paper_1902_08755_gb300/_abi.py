@@ -18,6 +18,7 @@ EC_MAX_SOURCES = 512
 EC_RLE_CHUNK = 4096
 EC_RLE_MAX_ELEMS = 1 << 27
 EC_RLE_MAX_JOBS = 512
+EC_RLE_NOALLOC_MAX_CHUNKS = 8192
 
 STATUS_NAMES = {0: "EC_OK", 1: "EC_ERR_INVALID_ARG", 2: "EC_ERR_CAPACITY", 3: "EC_ERR_CUDA",
                 4: "EC_ERR_CORRUPT", 5: "EC_ERR_UNSUPPORTED", 6: "EC_ERR_TIMEOUT"}
@@ -75,6 +76,7 @@ SIGNATURES = {
     "ec_rle_decompress": (_S, [_P, _P, C.c_size_t, _P, _I, _I, _I, _P]),
     "ec_rle_compress_batch": (_S, [_P, _P, _I, _P]),
     "ec_rle_decompress_batch": (_S, [_P, _P, _I, _P]),
+    "ec_rle_compress_noalloc": (_S, [_P, _I, _I, _I, C.c_uint32, _P, C.c_size_t, _P, _P, _P]),
 }
 
 _lib = None
