@@ -178,6 +178,58 @@ ec_status ec_composite_depth_backward(ec_ctx* ctx, const int16_t* winner,
                                       const int32_t* pitches, float* const* grad,
                                       ec_stream_t s);
 
+/* --------------------------------------------------------- batched compositing
+ * Many independent composites in one persistent launch.  Thesis 4.2.4 (tile
+ * compounds): fixed-size work packages wait in a queue and are pulled until it
+ * is empty, which balances uneven work.  A plan cuts every job's destination
+ * into tiles (work items), sorts them by estimated cost (largest first),
+ * uploads all descriptors once and captures one launch -- a queue-head reset
+ * and a grid of resident CTAs that pull items with an atomic counter -- in a
+ * CUDA graph; ec_batch_run replays that graph.  Results are bit-identical to
+ * calling ec_composite_depth / ec_composite_alpha per job, whatever the tile
+ * shapes. */
+enum { EC_JOB_DEPTH = 0, EC_JOB_ALPHA = 1 };
+#define EC_MAX_BATCH_INPUTS 128     /* inputs per job of a batch              */
+
+typedef struct {
+    int32_t mode;           /* EC_JOB_DEPTH or EC_JOB_ALPHA                        */
+    int32_t n;              /* inputs, <= EC_MAX_BATCH_INPUTS                      */
+    const ec_image* in;     /* host array of n (read while planning)               */
+    const int32_t* order;   /* alpha: host array of n or NULL; depth: ignored      */
+    ec_target out;          /* destination, as in the single calls                 */
+    int16_t* winner;        /* depth: optional winner plane                        */
+    float* t_final;         /* alpha: optional transmittance                       */
+} ec_job;
+
+/* Tile shapes per job kind, in pixels.  Widths are multiples of the pixels a
+ * warp covers in a row: 128 for depth jobs, 32 for RGBA32F and 64 for RGBA16F
+ * alpha jobs.  ctas_per_sm = 0 means as many as fit. */
+typedef struct {
+    int32_t depth_tile_w, depth_tile_h;
+    int32_t alpha32_tile_w, alpha32_tile_h;
+    int32_t alpha16_tile_w, alpha16_tile_h;
+    int32_t ctas_per_sm;
+} ec_batch_config;
+
+typedef struct ec_batch ec_batch;
+
+/* Validate the jobs and build a plan.  cfg == NULL autotunes: every candidate
+ * tile shape is timed on the jobs themselves (so planning runs the batch, and
+ * writes the destinations, several times) and the fastest is kept; the choice
+ * is cached per device and job signature for the process (and in the file
+ * named by the environment variable EC_AUTOTUNE_CACHE, if set).  The plan
+ * refers to the callers' buffers by address: they must stay allocated and in
+ * place until ec_batch_free.  Planning allocates device memory and
+ * synchronises the device. */
+ec_status ec_batch_plan(ec_ctx* ctx, const ec_job* jobs, int32_t njobs,
+                        const ec_batch_config* cfg, ec_batch** plan);
+/* Enqueue the captured launch on stream s. */
+ec_status ec_batch_run(ec_batch* plan, ec_stream_t s);
+/* The plan's tile shapes, work-item count and grid size (host pointers, any may be NULL). */
+ec_status ec_batch_get_config(const ec_batch* plan, ec_batch_config* cfg, int32_t* n_items,
+                              int32_t* grid);
+void ec_batch_free(ec_batch* plan);
+
 /* ------------------------------------------------------------ run-length codec
  * Thesis 5.5.1 (enhanced RLE): the image is coded as four independent byte
  * streams, one per component (mode 1), optionally after regrouping the 32 bits

@@ -53,6 +53,20 @@ class ec_rle_job(C.Structure):
                 ("pitch", C.c_int32), ("mode", C.c_uint32)]
 
 
+class ec_job(C.Structure):
+    _fields_ = [("mode", C.c_int32), ("n", C.c_int32), ("in_", C.c_void_p), ("order", C.c_void_p),
+                ("out", ec_target), ("winner", C.c_void_p), ("t_final", C.c_void_p)]
+
+
+class ec_batch_config(C.Structure):
+    _fields_ = [("depth_tile_w", C.c_int32), ("depth_tile_h", C.c_int32),
+                ("alpha32_tile_w", C.c_int32), ("alpha32_tile_h", C.c_int32),
+                ("alpha16_tile_w", C.c_int32), ("alpha16_tile_h", C.c_int32),
+                ("ctas_per_sm", C.c_int32)]
+
+
+EC_JOB_DEPTH, EC_JOB_ALPHA = 0, 1
+assert C.sizeof(ec_job) == 80 and C.sizeof(ec_batch_config) == 28
 assert C.sizeof(ec_image) == 56 and C.sizeof(ec_target) == 40 and C.sizeof(ec_rle_job) == 48
 
 _P = C.c_void_p
@@ -76,6 +90,10 @@ SIGNATURES = {
     "ec_rle_decompress": (_S, [_P, _P, C.c_size_t, _P, _I, _I, _I, _P]),
     "ec_rle_compress_batch": (_S, [_P, _P, _I, _P]),
     "ec_rle_decompress_batch": (_S, [_P, _P, _I, _P]),
+    "ec_batch_plan": (_S, [_P, _P, _I, _P, C.POINTER(C.c_void_p)]),
+    "ec_batch_run": (_S, [_P, _P]),
+    "ec_batch_get_config": (_S, [_P, _P, _P, _P]),
+    "ec_batch_free": (None, [_P]),
     "ec_rle_compress_noalloc": (_S, [_P, _I, _I, _I, C.c_uint32, _P, C.c_size_t, _P, _P, _P]),
 }
 

@@ -351,3 +351,80 @@ def rle_decompress_batch(jobs, ctx: Optional[Context] = None, stream=None):
     check(_lib().ec_rle_decompress_batch(ctx.h, arr, len(jobs), _stream_handle(stream)),
           "ec_rle_decompress_batch")
     return outs
+
+
+# ------------------------------------------------------------------ batches
+
+
+@dataclass
+class Job:
+    """One composite of a batch: mode 'depth' or 'alpha', inputs, destination."""
+    mode: str
+    images: Sequence[Image]
+    out_color: torch.Tensor
+    out_depth: Optional[torch.Tensor] = None
+    out_pvp: Optional[Rect] = None
+    order: Optional[Sequence[int]] = None
+    winner: Optional[torch.Tensor] = None
+    t_final: Optional[torch.Tensor] = None
+
+
+class Batch:
+    """ec_batch: many composites in one persistent, graph-captured launch.
+
+    ``config=None`` autotunes the tile shapes on the jobs themselves (running
+    them, so the destinations are written during construction).  The tensors
+    must stay alive and in place while the batch exists."""
+
+    def __init__(self, jobs: Sequence[Job], config: Optional[dict] = None,
+                 ctx: Optional[Context] = None):
+        self.ctx = ctx or default_context(jobs[0].out_color.device.index if jobs else None)
+        dev = self.ctx.device
+        self._keep = []
+        arr = (A.ec_job * max(1, len(jobs)))()
+        for k, jb in enumerate(jobs):
+            depth = jb.mode == "depth"
+            imgs = (ec_image * max(1, len(jb.images)))(*[_image_struct(im, dev, depth) for im in jb.images])
+            order = None if depth else _order(jb.order, len(jb.images))
+            tgt = _target(jb.out_color, jb.out_depth if depth else None, jb.out_pvp, dev)
+            wp = _dense(jb.winner, (tgt.pvp.h, tgt.pvp.w), torch.int16, dev, "winner") if depth else None
+            tp = None if depth else _dense(jb.t_final, (tgt.pvp.h, tgt.pvp.w), torch.float32, dev, "t_final")
+            self._keep += [imgs, order, jb]
+            arr[k] = A.ec_job(A.EC_JOB_DEPTH if depth else A.EC_JOB_ALPHA, len(jb.images),
+                              C.cast(imgs, C.c_void_p), None if order is None else C.cast(order, C.c_void_p),
+                              tgt, wp, tp)
+        cfg = None
+        if config is not None:
+            cfg = A.ec_batch_config(config.get("depth_tile_w", 128), config.get("depth_tile_h", 8),
+                                    config.get("alpha32_tile_w", 32), config.get("alpha32_tile_h", 8),
+                                    config.get("alpha16_tile_w", 64), config.get("alpha16_tile_h", 8),
+                                    config.get("ctas_per_sm", 0))
+        h = C.c_void_p()
+        check(_lib().ec_batch_plan(self.ctx.h, arr, len(jobs), C.byref(cfg) if cfg else None,
+                                   C.byref(h)), "ec_batch_plan")
+        self.h = h
+
+    def run(self, stream=None):
+        check(_lib().ec_batch_run(self.h, _stream_handle(stream)), "ec_batch_run")
+
+    @property
+    def config(self) -> dict:
+        cfg = A.ec_batch_config()
+        n = C.c_int32()
+        g = C.c_int32()
+        check(_lib().ec_batch_get_config(self.h, C.byref(cfg), C.byref(n), C.byref(g)), "ec_batch_get_config")
+        d = {f: getattr(cfg, f) for f, _ in cfg._fields_}
+        d["n_items"] = n.value
+        d["grid"] = g.value
+        return d
+
+    def close(self):
+        if getattr(self, "h", None) is not None and self.h.value:
+            _lib().ec_batch_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -384,7 +384,8 @@ ec_status ec_rle_decompress(ec_ctx* ctx, const void* src, size_t src_size, void*
 
 }  // extern "C"
 
-static_assert(sizeof(ec_image) == 56 && sizeof(ec_target) == 40 && sizeof(ec_rle_job) == 48,
+static_assert(sizeof(ec_image) == 56 && sizeof(ec_target) == 40 && sizeof(ec_rle_job) == 48 &&
+                  sizeof(ec_job) == 80 && sizeof(ec_batch_config) == 28,
               "ABI struct layouts are mirrored by the Python binding");
 
 // ------------------------------------------------------------- backward ----
@@ -519,6 +520,342 @@ ec_status ec_composite_depth_backward(ec_ctx* ctx, const int16_t* winner, ec_rec
     DeviceGuard g(ctx->device);
     if (!g.ok) return EC_ERR_CUDA;
     return cuda_status(launch_depth_bwd(d.data(), n, out_pvp.w, out_pvp.h, winner, grad_out, (cudaStream_t)s));
+}
+
+}  // extern "C"
+
+// -------------------------------------------------------------- batching ----
+
+#include <cstdio>
+#include <cstdlib>
+#include <map>
+#include <mutex>
+#include <string>
+
+struct ec_batch {
+    ec_ctx* ctx = nullptr;
+    std::vector<BatchJob> jobs;
+    std::vector<SrcDesc> srcs;
+    BatchJob* d_jobs = nullptr;
+    SrcDesc* d_srcs = nullptr;
+    BatchItem* d_items = nullptr;
+    uint32_t* d_head = nullptr;
+    size_t items_cap = 0;
+    int n_items = 0;
+    BatchShape shape{};
+    int grid = 0;
+    int ctas_per_sm = 0;
+    cudaStream_t stream = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+};
+
+namespace {
+
+std::mutex g_tune_lock;
+std::map<std::string, BatchShape> g_tune_cache;
+
+int job_kind(const BatchJob& j) { return j.mode; }
+
+// Work items for one tile shape, sorted by estimated bytes moved, largest first.
+std::vector<BatchItem> make_items(const ec_batch& b, const BatchShape& sh)
+{
+    struct Costed { double cost; int idx; BatchItem it; };
+    std::vector<Costed> v;
+    for (size_t j = 0; j < b.jobs.size(); ++j) {
+        const BatchJob& J = b.jobs[j];
+        const int m = job_kind(J);
+        const int TW = sh.tw[m], TH = sh.th[m];
+        const int bpp = m == 0 ? 8 : (m == 1 ? 20 : (m == 2 ? 16 : 8));
+        const int tx = ceil_div(J.D.W, TW), ty = ceil_div(J.D.H, TH);
+        for (int y = 0; y < ty; ++y)
+            for (int x = 0; x < tx; ++x) {
+                const int x0 = x * TW, y0 = y * TH;
+                const int x1 = std::min(x0 + TW, J.D.W), y1 = std::min(y0 + TH, J.D.H);
+                double cost = (double)(x1 - x0) * (y1 - y0) * bpp;           // output
+                for (int i = 0; i < J.n; ++i) {
+                    const SrcDesc& s = b.srcs[J.first + i];
+                    const int64_t w = std::min(x1, s.x1) - std::max(x0, s.x0);
+                    const int64_t h = std::min(y1, s.y1) - std::max(y0, s.y0);
+                    if (w > 0 && h > 0) cost += (double)w * h * bpp;
+                }
+                BatchItem it;
+                it.job = (int32_t)j;
+                it.tx = (int16_t)x;
+                it.ty = (int16_t)y;
+                v.push_back({cost, (int)v.size(), it});
+            }
+    }
+    std::stable_sort(v.begin(), v.end(), [](const Costed& a, const Costed& c) { return a.cost > c.cost; });
+    std::vector<BatchItem> out(v.size());
+    for (size_t i = 0; i < v.size(); ++i) out[i] = v[i].it;
+    return out;
+}
+
+ec_status upload_items(ec_batch& b, const BatchShape& sh)
+{
+    const std::vector<BatchItem> items = make_items(b, sh);
+    if (items.size() > b.items_cap) {
+        if (b.d_items) cudaFree(b.d_items);
+        b.d_items = nullptr;
+        if (cudaMalloc(&b.d_items, std::max<size_t>(items.size(), 1) * sizeof(BatchItem)) != cudaSuccess)
+            return EC_ERR_CUDA;
+        b.items_cap = items.size();
+    }
+    if (!items.empty() &&
+        cudaMemcpy(b.d_items, items.data(), items.size() * sizeof(BatchItem), cudaMemcpyHostToDevice) != cudaSuccess)
+        return EC_ERR_CUDA;
+    b.n_items = (int)items.size();
+    b.shape = sh;
+    return EC_OK;
+}
+
+ec_status capture(ec_batch& b)
+{
+    if (b.exec) { cudaGraphExecDestroy(b.exec); b.exec = nullptr; }
+    if (b.graph) { cudaGraphDestroy(b.graph); b.graph = nullptr; }
+    if (cudaStreamBeginCapture(b.stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return EC_ERR_CUDA;
+    const cudaError_t e = launch_batch(b.d_jobs, b.d_srcs, b.d_items, b.n_items, b.d_head, b.shape, b.grid, b.stream);
+    const cudaError_t e2 = cudaStreamEndCapture(b.stream, &b.graph);
+    if (e != cudaSuccess || e2 != cudaSuccess) return EC_ERR_CUDA;
+    if (cudaGraphInstantiate(&b.exec, b.graph, 0) != cudaSuccess) return EC_ERR_CUDA;
+    return EC_OK;
+}
+
+// Mean device time of a few direct launches (after one warm-up).
+float time_shape(ec_batch& b, const BatchShape& sh)
+{
+    if (upload_items(b, sh) != EC_OK) return 1e30f;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    float best = 1e30f;
+    for (int r = 0; r < 4; ++r) {
+        cudaEventRecord(e0, b.stream);
+        launch_batch(b.d_jobs, b.d_srcs, b.d_items, b.n_items, b.d_head, b.shape, b.grid, b.stream);
+        cudaEventRecord(e1, b.stream);
+        cudaEventSynchronize(e1);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (r > 0) best = std::min(best, ms);
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return best;
+}
+
+std::string signature(const ec_batch& b, int device)
+{
+    cudaDeviceProp prop{};
+    cudaGetDeviceProperties(&prop, device);
+    uint64_t h = 1469598103934665603ull;
+    auto mix = [&](int64_t v) { h ^= (uint64_t)v; h *= 1099511628211ull; };
+    mix(b.ctas_per_sm);
+    for (const BatchJob& J : b.jobs) {
+        mix(J.mode); mix(J.n); mix(J.D.W); mix(J.D.H);
+        for (int i = 0; i < J.n; ++i) {
+            const SrcDesc& s = b.srcs[J.first + i];
+            mix(s.x1 - s.x0); mix(s.y1 - s.y0);
+        }
+    }
+    char buf[64];
+    snprintf(buf, sizeof(buf), "%016llx", (unsigned long long)h);
+    return std::string(prop.name) + "/" + std::to_string(prop.multiProcessorCount) + "/" + buf;
+}
+
+bool cache_lookup(const std::string& sig, BatchShape* sh)
+{
+    std::lock_guard<std::mutex> lk(g_tune_lock);
+    auto it = g_tune_cache.find(sig);
+    if (it != g_tune_cache.end()) { *sh = it->second; return true; }
+    const char* path = getenv("EC_AUTOTUNE_CACHE");
+    if (!path) return false;
+    FILE* f = fopen(path, "r");
+    if (!f) return false;
+    char key[256];
+    BatchShape s{};
+    bool found = false;
+    while (fscanf(f, "%255s %d %d %d %d %d %d %d %d", key, &s.tw[0], &s.th[0], &s.tw[1], &s.th[1],
+                  &s.tw[2], &s.th[2], &s.tw[3], &s.th[3]) == 9) {
+        if (sig == key) { *sh = s; found = true; }
+    }
+    fclose(f);
+    if (found) g_tune_cache[sig] = *sh;
+    return found;
+}
+
+void cache_store(const std::string& sig, const BatchShape& sh)
+{
+    std::lock_guard<std::mutex> lk(g_tune_lock);
+    g_tune_cache[sig] = sh;
+    const char* path = getenv("EC_AUTOTUNE_CACHE");
+    if (!path) return;
+    FILE* f = fopen(path, "a");
+    if (!f) return;
+    fprintf(f, "%s %d %d %d %d %d %d %d %d\n", sig.c_str(), sh.tw[0], sh.th[0], sh.tw[1], sh.th[1],
+            sh.tw[2], sh.th[2], sh.tw[3], sh.th[3]);
+    fclose(f);
+}
+
+bool shape_ok(const BatchShape& sh)
+{
+    for (int m = 0; m < 4; ++m) {
+        const int wpx = batch_warp_px(m);
+        if (sh.tw[m] <= 0 || sh.th[m] <= 0 || sh.tw[m] % wpx || sh.tw[m] > 32768 || sh.th[m] > 32768)
+            return false;
+    }
+    return true;
+}
+
+// Coordinate-descent search: depth shapes with the alpha shapes fixed, then
+// each alpha format in turn.
+BatchShape autotune(ec_batch& b)
+{
+    BatchShape best{{128, 128, 32, 64}, {8, 8, 8, 8}};
+    bool has[4] = {false, false, false, false};
+    for (const BatchJob& J : b.jobs) has[J.mode] = true;
+    float t_best = time_shape(b, best);
+    auto try_mode = [&](std::initializer_list<int> modes, std::initializer_list<int> widths) {
+        for (int w : widths)
+            for (int h : {4, 8, 16, 32}) {
+                BatchShape c = best;
+                for (int m : modes) { c.tw[m] = w; c.th[m] = h; }
+                if (!shape_ok(c)) continue;
+                const float t = time_shape(b, c);
+                if (t < t_best) { t_best = t; best = c; }
+            }
+    };
+    if (has[0] || has[1]) try_mode({0, 1}, {128, 256});
+    if (has[2]) try_mode({2}, {32, 64, 128});
+    if (has[3]) try_mode({3}, {64, 128});
+    return best;
+}
+
+}  // namespace
+
+extern "C" {
+
+ec_status ec_batch_plan(ec_ctx* ctx, const ec_job* jobs, int32_t njobs, const ec_batch_config* cfg,
+                        ec_batch** plan)
+{
+    if (!ctx || !plan || njobs < 0 || (njobs > 0 && !jobs)) return EC_ERR_INVALID_ARG;
+    *plan = nullptr;
+    ec_batch* b = new ec_batch;
+    b->ctx = ctx;
+    ec_status st = EC_OK;
+    for (int j = 0; j < njobs && st == EC_OK; ++j) {
+        const ec_job& job = jobs[j];
+        if (job.n < 0 || (job.n > 0 && !job.in)) { st = EC_ERR_INVALID_ARG; break; }
+        if (job.n > EC_MAX_BATCH_INPUTS) { st = EC_ERR_UNSUPPORTED; break; }
+        BatchJob J{};
+        J.n = job.n;
+        J.first = (int32_t)b->srcs.size();
+        const ec_target* out = &job.out;
+        std::vector<SrcDesc> d;
+        if (job.mode == EC_JOB_DEPTH) {
+            if ((st = check_target(out, EC_RGBA8, EC_RGBA32F)) != EC_OK) break;
+            d.resize((size_t)std::max(job.n, 1));
+            for (int i = 0; i < job.n && st == EC_OK; ++i) {
+                if (job.in[i].format != out->format) st = EC_ERR_INVALID_ARG;
+                else st = make_desc(job.in[i], out->pvp, 4, true, &d[i]);
+            }
+            J.mode = out->format == EC_RGBA8 ? 0 : 1;
+            J.D.vec = aligned16(out->color) && (!out->depth || aligned16(out->depth)) && out->pitch % 4 == 0;
+            J.D.winner = job.winner;
+            J.D.depth = out->depth;
+        } else if (job.mode == EC_JOB_ALPHA) {
+            if ((st = check_target(out, EC_RGBA32F, EC_RGBA16F)) != EC_OK) break;
+            st = alpha_descs(job.in, job.order, job.n, out->format, out->pvp, d);
+            const bool f16 = out->format == EC_RGBA16F;
+            J.mode = f16 ? 3 : 2;
+            J.D.vec = aligned16(out->color) && (!f16 || out->pitch % 2 == 0);
+            J.D.tfinal = job.t_final;
+        } else {
+            st = EC_ERR_INVALID_ARG;
+        }
+        if (st != EC_OK) break;
+        J.D.W = out->pvp.w;
+        J.D.H = out->pvp.h;
+        J.D.pitch = out->pitch;
+        J.D.color = out->color;
+        for (int i = 0; i < job.n; ++i) b->srcs.push_back(d[i]);
+        b->jobs.push_back(J);
+    }
+    if (st != EC_OK) { delete b; return st; }
+
+    DeviceGuard g(ctx->device);
+    if (!g.ok) { delete b; return EC_ERR_CUDA; }
+    auto fail = [&](ec_status e) { ec_batch_free(b); return e; };
+    // the autotuner runs the batch on the plan's own stream: inputs written
+    // by earlier work on any stream must be complete
+    if (cudaDeviceSynchronize() != cudaSuccess) return fail(EC_ERR_CUDA);
+    if (cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) != cudaSuccess) return fail(EC_ERR_CUDA);
+    if (cudaMalloc(&b->d_jobs, std::max<size_t>(b->jobs.size(), 1) * sizeof(BatchJob)) != cudaSuccess ||
+        cudaMalloc(&b->d_srcs, std::max<size_t>(b->srcs.size(), 1) * sizeof(SrcDesc)) != cudaSuccess ||
+        cudaMalloc(&b->d_head, sizeof(uint32_t)) != cudaSuccess)
+        return fail(EC_ERR_CUDA);
+    if ((!b->jobs.empty() && cudaMemcpy(b->d_jobs, b->jobs.data(), b->jobs.size() * sizeof(BatchJob), cudaMemcpyHostToDevice) != cudaSuccess) ||
+        (!b->srcs.empty() && cudaMemcpy(b->d_srcs, b->srcs.data(), b->srcs.size() * sizeof(SrcDesc), cudaMemcpyHostToDevice) != cudaSuccess))
+        return fail(EC_ERR_CUDA);
+    b->ctas_per_sm = (cfg && cfg->ctas_per_sm > 0) ? cfg->ctas_per_sm : batch_ctas_per_sm();
+    b->grid = std::max(1, ctx->sm_count * b->ctas_per_sm);
+
+    BatchShape sh;
+    if (cfg) {
+        sh = BatchShape{{cfg->depth_tile_w, cfg->depth_tile_w, cfg->alpha32_tile_w, cfg->alpha16_tile_w},
+                        {cfg->depth_tile_h, cfg->depth_tile_h, cfg->alpha32_tile_h, cfg->alpha16_tile_h}};
+        if (!shape_ok(sh)) return fail(EC_ERR_INVALID_ARG);
+    } else {
+        const std::string sig = signature(*b, ctx->device);
+        if (!cache_lookup(sig, &sh)) {
+            sh = autotune(*b);
+            cache_store(sig, sh);
+        }
+    }
+    if ((st = upload_items(*b, sh)) != EC_OK) return fail(st);
+    if ((st = capture(*b)) != EC_OK) return fail(st);
+    if (cudaStreamSynchronize(b->stream) != cudaSuccess) return fail(EC_ERR_CUDA);
+    *plan = b;
+    return EC_OK;
+}
+
+ec_status ec_batch_run(ec_batch* b, ec_stream_t s)
+{
+    if (!b || !b->exec) return EC_ERR_INVALID_ARG;
+    DeviceGuard g(b->ctx->device);
+    if (!g.ok) return EC_ERR_CUDA;
+    return cudaGraphLaunch(b->exec, (cudaStream_t)s) == cudaSuccess ? EC_OK : EC_ERR_CUDA;
+}
+
+ec_status ec_batch_get_config(const ec_batch* b, ec_batch_config* cfg, int32_t* n_items, int32_t* grid)
+{
+    if (!b) return EC_ERR_INVALID_ARG;
+    if (cfg) {
+        cfg->depth_tile_w = b->shape.tw[0];
+        cfg->depth_tile_h = b->shape.th[0];
+        cfg->alpha32_tile_w = b->shape.tw[2];
+        cfg->alpha32_tile_h = b->shape.th[2];
+        cfg->alpha16_tile_w = b->shape.tw[3];
+        cfg->alpha16_tile_h = b->shape.th[3];
+        cfg->ctas_per_sm = b->ctas_per_sm;
+    }
+    if (n_items) *n_items = b->n_items;
+    if (grid) *grid = b->grid;
+    return EC_OK;
+}
+
+void ec_batch_free(ec_batch* b)
+{
+    if (!b) return;
+    DeviceGuard g(b->ctx->device);
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    if (b->stream) cudaStreamDestroy(b->stream);
+    if (b->d_jobs) cudaFree(b->d_jobs);
+    if (b->d_srcs) cudaFree(b->d_srcs);
+    if (b->d_items) cudaFree(b->d_items);
+    if (b->d_head) cudaFree(b->d_head);
+    delete b;
 }
 
 }  // extern "C"

@@ -94,6 +94,34 @@ struct BwdList {
 };
 static_assert(sizeof(BwdList<kMaxBwdLayers>) < 32764 - 256, "kernel parameter limit");
 
+// ---- batched compositing ----------------------------------------------------
+// One job = one full composite; mode 0 depth RGBA8, 1 depth RGBA32F, 2 alpha
+// RGBA32F, 3 alpha RGBA16F.  Its n inputs are srcs[first, first + n), in
+// compositing order.  A work item is one output tile (tx, ty) of one job.
+struct BatchJob {
+    int32_t mode;
+    int32_t n;
+    int32_t first;
+    int32_t pad;
+    DstDesc D;
+};
+static_assert(sizeof(BatchJob) == 64, "batch job layout");
+
+struct BatchItem {
+    int32_t job;
+    int16_t tx, ty;
+};
+
+struct BatchShape {
+    int32_t tw[4], th[4];   // tile width / height in pixels, per mode
+};
+
+int batch_warp_px(int mode);
+int batch_ctas_per_sm();
+cudaError_t launch_batch(const BatchJob* jobs, const SrcDesc* srcs, const BatchItem* items,
+                         int n_items, uint32_t* head, const BatchShape& shape, int grid,
+                         cudaStream_t s);
+
 // ---- launchers (defined in the kernel translation units) -------------------
 int alpha_bwd_chunk(int n, bool f16);
 cudaError_t launch_alpha_bwd(const BwdDesc* d, int n, bool f16, bool g16, bool fused,
