@@ -10,7 +10,7 @@ step starts; L2 is flushed (2x its size written) between timed steps, outside
 the timed events.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ec|reference]
-                    [--workload cfg2|cfg1|cfg3|cfg3h|cfg5d|cfg5a]
+                    [--workload cfg2|cfg1|cfg3|cfg3h|cfg3fused|cfg3hfused|cfg4|cfg5d|cfg5a|cfg5afused]
 
 Prints ONE JSON line (rank 0).  Metric: composited Gpixel-layers/s (sum over
 sources of |roi_i ∩ frame| per step, divided by the step time).  With N > 1
@@ -342,6 +342,43 @@ class AlphaForward:
         return (time.perf_counter() - t0) / self.sample_fraction
 
 
+class AlphaFused(AlphaForward):
+    """cfg3fused / cfg3hfused / cfg5afused: forward and the gradient of
+    L = sum(w * out) with respect to every layer, in one kernel pass."""
+
+    def __init__(self, cfg, L, W, H, amax, dtype, device):
+        super().__init__(cfg, L, W, H, amax, dtype, device)
+        import synthetic as S
+        self.desc = self.desc.replace("ordered 'over' forward", "fused forward + backward of sum(w * out)")
+        self.w = S.grad_weights(cfg, W, H, device=device)
+        self.kernels = ["composite_alpha_fwd_bwd"]
+        if torch.device(device).type != "cuda":
+            return
+        self.grads = [torch.empty_like(self.lay[k]) for k in range(L)]
+
+    def step(self, ev=None):
+        if ev:
+            ev[0].record()
+        self.ec.composite_alpha_fwd_bwd(self.imgs, self.out, self.w, self.grads, ctx=self.ctx)
+        if ev:
+            ev[1].record()
+
+    def algorithmic_bytes(self):
+        px = self.W * self.H
+        return {"composite_alpha_fwd_bwd": 2 * self.units * self.bpp + px * 16 + px * self.bpp}
+
+    def setup_e2e(self):
+        super().setup_e2e()
+        self.h_w = self.w.cpu().pin_memory()
+        self.h2d += self.h_w.numel() * 4
+
+    def e2e_step(self):
+        self.lay.copy_(self.h_lay, non_blocking=True)
+        self.w.copy_(self.h_w, non_blocking=True)
+        self.step()
+        self.h_out.copy_(self.out, non_blocking=True)
+
+
 class BatchedTiles:
     """cfg4: 1000 uneven tiles (w, h log-uniform in [16, 1024], 2..64 layers, half
     depth RGBA8+Z32 at 30% box coverage, half alpha FP32 with a <= 0.3), all in
@@ -480,6 +517,12 @@ def make_workload(name, device):
         return AlphaForward(3, 32, 2048, 2048, 0.3, torch.float32, device)
     if name == "cfg3h":
         return AlphaForward(3, 32, 2048, 2048, 0.3, torch.float16, device)
+    if name == "cfg3fused":
+        return AlphaFused(3, 32, 2048, 2048, 0.3, torch.float32, device)
+    if name == "cfg3hfused":
+        return AlphaFused(3, 32, 2048, 2048, 0.3, torch.float16, device)
+    if name == "cfg5afused":
+        return AlphaFused(5, 128, 3840, 2160, 0.1, torch.float16, device)
     if name == "cfg5a":
         return AlphaForward(5, 128, 3840, 2160, 0.1, torch.float16, device)
     raise SystemExit(f"unknown workload {name}")
@@ -606,7 +649,7 @@ def run_ec(args):
         cfg["rle_raw_bytes_per_step"] = 8 * wl.stored_px
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": max(3, args.warmup), "ms_per_step": ms, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "rgba8+f32" if isinstance(wl, DepthPipeline) else "f32",
+            "scaling": "weak", "vs_baseline": None, "dtype": "rgba8+f32" if isinstance(wl, (DepthPipeline, BatchedTiles)) else "f32",
             "data": "synthetic (seeded boxes / layers shaped like the thesis's workloads)",
             "config": cfg, "roofline": roof, "kernels": kern,
             "e2e": {"value": world * wl.units / (e2e_ms * 1e-3) / 1e9, "unit": UNIT,
