@@ -267,8 +267,8 @@ ec_status ec_rle_compress(ec_ctx* ctx, const void* src, int32_t w, int32_t h,
                           int32_t pitch, uint32_t mode, void* dst, size_t dst_capacity,
                           uint64_t* d_size, ec_stream_t s);
 
-/* Decompress a stream of src_size bytes into dst (w x h elements, row pitch
- * `pitch`).  The header must name the same w and h.  Malformed input records
+/* Decompress a stream of src_size bytes (src 4-byte aligned) into dst (w x h
+ * elements, row pitch `pitch`).  The header must name the same w and h.  Malformed input records
  * EC_ERR_CORRUPT in the status word; the kernel never reads past src_size nor
  * writes outside the w x h elements of dst. */
 ec_status ec_rle_decompress(ec_ctx* ctx, const void* src, size_t src_size, void* dst,

@@ -301,7 +301,7 @@ static ec_status rle_job_desc(const ec_rle_job& j, bool compress, RleJobDesc* d)
         d->d_size = j.d_size;
         d->vec = aligned16(j.src) && j.w % 4 == 0 && j.pitch % 4 == 0;
     } else {
-        if (!j.src) return EC_ERR_INVALID_ARG;
+        if (!j.src || (reinterpret_cast<uintptr_t>(j.src) & 3u)) return EC_ERR_INVALID_ARG;
         if (n > 0 && (reinterpret_cast<uintptr_t>(j.dst) & 3u)) return EC_ERR_INVALID_ARG;
         d->capacity = j.capacity;
         d->vec = aligned16(j.dst) && j.w % 4 == 0 && j.pitch % 4 == 0;

@@ -22,11 +22,15 @@
 //   6. The stage is copied out with word stores; chunk 0 writes the header,
 //      every chunk its four end-table entries, the last chunk the size.
 //
-// Decompress: one CTA per chunk.  The header and the chunk's end-table entries
-// are validated, the chunk's compressed bytes are staged in shared memory, one
-// walker thread per plane parses token headers into a list (bounds-checked,
-// in rounds of kTok tokens) while all warps expand the listed tokens, and the
-// four planes are transposed back into elements with byte permutes.
+// Decompress: one CTA of four warps per chunk.  The header and the chunk's
+// end-table entries are fetched in one round trip and validated.  Warp p
+// decodes plane p in windows of 32 stream bytes, one byte per lane: each lane
+// computes where a token starting at its byte would end, the chain of real
+// token starts inside the window is followed with one shuffle per token
+// (instead of one dependent memory access per token), a warp scan gives each
+// token its output position, every token is checked against its stream and
+// chunk bounds, and the whole warp expands it (word stores for runs).  The
+// four planes are then transposed back into elements with byte permutes.
 #include "ec_internal.cuh"
 
 namespace ec {
@@ -40,7 +44,6 @@ constexpr int kStage = 4 * kPlaneCap;                // 16512
 constexpr uint32_t kMagic = 0x31524345u;             // "ECR1"
 constexpr uint64_t kAgg = 1ull << 62, kInc = 2ull << 62, kVal = (1ull << 62) - 1;
 constexpr int kSpinLimit = 1 << 22;
-constexpr int kTok = 256;                            // tokens per plane per round
 
 // Bit-swizzle: byte k of the result gathers bit pair (7-2k, 6-2k) of the four
 // components, component 0 (R) in the top pair.  This is a transpose of the 4x4
@@ -224,21 +227,36 @@ k_rle_compress(const __grid_constant__ RleJobList<N> J, uint64_t* flags, uint32_
 
     // 1. load, swizzle (mode 2) and split into byte planes
     if (jb.vec) {
+        // the chunk's 1024 groups of 4 elements, 4 per thread: all four
+        // 16-byte loads are issued before any of them is used
         const bool dense = jb.pitch == jb.w;       // element q at src + q
-        for (int g = tid; 4 * g < len; g += kT) {
-            const uint32_t q = q0 + 4u * g;
-            size_t e = q;
-            if (!dense) {
-                const uint32_t y = q / w;
-                e = (size_t)y * jb.pitch + (q - y * w);
+        constexpr int kG = kChunk / 4 / kT;
+        uint4 v[kG];
+#pragma unroll
+        for (int k = 0; k < kG; ++k) {
+            const int g = tid + k * kT;
+            if (4 * g < len) {
+                const uint32_t q = q0 + 4u * g;
+                size_t e = q;
+                if (!dense) {
+                    const uint32_t y = q / w;
+                    e = (size_t)y * jb.pitch + (q - y * w);
+                }
+                v[k] = ld_stream(reinterpret_cast<const uint4*>(jb.src + e));
             }
-            uint4 v = ld_stream(reinterpret_cast<const uint4*>(jb.src + e));
-            if (jb.mode == 2) { v.x = swizzle(v.x); v.y = swizzle(v.y); v.z = swizzle(v.z); v.w = swizzle(v.w); }
-            const uint4 t = transpose4(v.x, v.y, v.z, v.w);
-            *reinterpret_cast<uint32_t*>(&pl[0][16 + 4 * g]) = t.x;
-            *reinterpret_cast<uint32_t*>(&pl[1][16 + 4 * g]) = t.y;
-            *reinterpret_cast<uint32_t*>(&pl[2][16 + 4 * g]) = t.z;
-            *reinterpret_cast<uint32_t*>(&pl[3][16 + 4 * g]) = t.w;
+        }
+#pragma unroll
+        for (int k = 0; k < kG; ++k) {
+            const int g = tid + k * kT;
+            if (4 * g < len) {
+                uint4 x = v[k];
+                if (jb.mode == 2) { x.x = swizzle(x.x); x.y = swizzle(x.y); x.z = swizzle(x.z); x.w = swizzle(x.w); }
+                const uint4 t = transpose4(x.x, x.y, x.z, x.w);
+                *reinterpret_cast<uint32_t*>(&pl[0][16 + 4 * g]) = t.x;
+                *reinterpret_cast<uint32_t*>(&pl[1][16 + 4 * g]) = t.y;
+                *reinterpret_cast<uint32_t*>(&pl[2][16 + 4 * g]) = t.z;
+                *reinterpret_cast<uint32_t*>(&pl[3][16 + 4 * g]) = t.w;
+            }
         }
     } else {
         for (int t = tid; t < len; t += kT) {
@@ -434,16 +452,17 @@ k_rle_compress(const __grid_constant__ RleJobList<N> J, uint64_t* flags, uint32_
 
 // ----------------------------------------------------------- decompress ----
 
+constexpr int kDT = 128;        // decoder CTA: one warp per byte plane
+
+__device__ __forceinline__ uint32_t bcast8(uint32_t w) { return 0x01010101u * (w & 0xFFu); }
+
 template <int N>
-__global__ void __launch_bounds__(kT)
+__global__ void __launch_bounds__(kDT)
 k_rle_decompress(const __grid_constant__ RleJobList<N> J, uint32_t* status)
 {
-    __shared__ __align__(16) uint8_t sbuf[kStage + 16];
     __shared__ __align__(16) uint8_t planes[4][kChunk];
-    __shared__ uint2 toks[4][kTok];
-    __shared__ int ntok[4], pref[5];
     __shared__ uint32_t s_beg[5];
-    __shared__ int s_fail, s_mode, s_live;
+    __shared__ int s_fail, s_mode;
     __shared__ uint8_t s_hdr[52];
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -502,104 +521,94 @@ k_rle_decompress(const __grid_constant__ RleJobList<N> J, uint32_t* status)
     const uint32_t q0 = c * (uint32_t)kChunk;
     const int len = (int)min((uint32_t)kChunk, n - q0);
     const uint8_t* payload = src + 32 + 16ull * nc;
-    const uint32_t b0 = s_beg[0], nbytes = s_beg[4] - b0;
-    for (uint32_t i = tid; i < nbytes; i += kT) sbuf[i] = payload[b0 + i];
 
-    // token walk (lane 0 of warps 0..3, one plane each) + cooperative expansion
-    int in = 0, in_end = 0, outp = 0;
-    bool done = true;
-    if (lane == 0 && warp < 4) {
-        in = (int)(s_beg[warp] - b0);
-        in_end = (int)(s_beg[warp + 1] - b0);
-        done = false;
+    // decode plane `warp`: windows of 32 stream bytes, one per lane.  A lane
+    // knows where a token starting at its byte would end (next) and how many
+    // bytes it would emit (olen); the real chain of token starts is followed
+    // with one shuffle per token, output positions come from a warp scan, and
+    // every token is expanded by the whole warp.
+    {
+        const int p = warp;
+        const int in_end = (int)s_beg[p + 1];
+        int cur = (int)s_beg[p], outp = 0, bad = 0;
+        uint8_t* plane = planes[p];
+        while (cur < in_end) {
+            const int i = cur + lane;
+            const uint32_t b = i < in_end ? (uint32_t)__ldg(payload + i) : 0u;
+            const uint32_t b1 = i + 1 < in_end ? (uint32_t)__ldg(payload + i + 1) : 0u;
+            const bool rep = b >= 128u;
+            const int next = rep ? i + 2 : i + 2 + (int)b;
+            const int olen = rep ? (int)b - 127 : (int)b + 1;
+            uint32_t starts = 0u;
+            int sl = 0;
+            while (sl < 32 && cur + sl < in_end) {
+                starts |= 1u << sl;
+                sl = __shfl_sync(0xffffffffu, next, sl) - cur;
+            }
+            const bool st = (starts >> lane) & 1u;
+            int incl = st ? olen : 0;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += y;
+            }
+            const int total = __shfl_sync(0xffffffffu, incl, 31);
+            const int obeg = outp + incl - (st ? olen : 0);
+            if (__any_sync(0xffffffffu, st && (next > in_end || outp + incl > len))) {
+                bad = 1;                                  // a token runs past its stream or chunk
+                break;
+            }
+            // expand every token of the window with all 32 lanes
+            for (uint32_t m = starts; m; m &= m - 1u) {
+                const int l = __ffs(m) - 1;
+                const int o = __shfl_sync(0xffffffffu, obeg, l);
+                const int mlen = __shfl_sync(0xffffffffu, olen, l);
+                const bool r = __shfl_sync(0xffffffffu, (int)rep, l) != 0;
+                const int s0 = cur + l + 1;                  // first byte after the control
+                if (r) {
+                    const uint32_t v = __shfl_sync(0xffffffffu, b1, l);
+                    const int head = min(mlen, (4 - (o & 3)) & 3);
+                    const int body = (mlen - head) >> 2, tail = (mlen - head) & 3;
+                    if (lane < head) plane[o + lane] = (uint8_t)v;
+                    if (lane < body) reinterpret_cast<uint32_t*>(plane + o + head)[lane] = 0x01010101u * v;
+                    if (lane < tail) plane[o + head + 4 * body + lane] = (uint8_t)v;
+                } else {
+                    for (int k = lane; k < mlen; k += 32) plane[o + k] = __ldg(payload + s0 + k);
+                }
+            }
+            outp += total;
+            cur += sl;
+        }
+        if (!bad && outp != len) bad = 1;
+        if (bad && lane == 0) s_fail = 1;
     }
-    if (tid == 0) s_live = 4;
     __syncthreads();
-    for (;;) {
-        if (lane == 0 && warp < 4) {
-            int cnt = 0;
-            if (!done) {
-                int last_rep = -1;           // list index of a repeat this token may extend
-                int last_val = -1;
-                while (cnt < kTok && in < in_end) {
-                    const int ctl = sbuf[in];
-                    if (ctl < 128) {
-                        const int m = ctl + 1, next = in + 1 + m;
-                        if (next > in_end || outp + m > len) { s_fail = 1; break; }
-                        toks[warp][cnt++] = make_uint2((uint32_t)outp | ((uint32_t)m << 16), (uint32_t)(in + 1));
-                        last_rep = -1;
-                        outp += m;
-                        in = next;
-                    } else {
-                        const int m = ctl - 127, next = in + 2;
-                        if (next > in_end || outp + m > len) { s_fail = 1; break; }
-                        const int v = sbuf[in + 1];
-                        if (last_rep >= 0 && v == last_val) {
-                            toks[warp][last_rep].x += (uint32_t)m << 16;     // one longer run
-                        } else {
-                            toks[warp][cnt] = make_uint2((uint32_t)outp | ((uint32_t)m << 16),
-                                                         (uint32_t)(in + 1) | (1u << 31));
-                            last_rep = cnt++;
-                            last_val = v;
-                        }
-                        outp += m;
-                        in = next;
-                    }
-                }
-                if (in >= in_end && !s_fail) {
-                    done = true;
-                    if (outp != len) s_fail = 1;
-                    atomicSub(&s_live, 1);
-                }
-            }
-            ntok[warp] = cnt;
-        }
-        __syncthreads();
-        if (s_fail) {
-            if (tid == 0) set_status(status, EC_ERR_CORRUPT);
-            return;
-        }
-        if (tid == 0) {
-            pref[0] = 0;
-            for (int p = 0; p < 4; ++p) pref[p + 1] = pref[p] + ntok[p];
-        }
-        __syncthreads();
-        for (int t = warp; t < pref[4]; t += kT / 32) {
-            const int p = t < pref[1] ? 0 : t < pref[2] ? 1 : t < pref[3] ? 2 : 3;
-            const uint2 tk = toks[p][t - pref[p]];
-            const int o = (int)(tk.x & 0xFFFFu), m = (int)(tk.x >> 16);
-            const int s0 = (int)(tk.y & 0xFFFFu);
-            uint8_t* d = &planes[p][o];
-            if (tk.y >> 31) {                    // run: head bytes, 32-bit words, tail bytes
-                const uint8_t v = sbuf[s0];
-                const int head = min(m, (4 - (o & 3)) & 3);
-                const int body = (m - head) >> 2, tail = (m - head) & 3;
-                if (lane < head) d[lane] = v;
-                uint32_t* wd = reinterpret_cast<uint32_t*>(d + head);
-                const uint32_t word = 0x01010101u * v;
-                for (int i = lane; i < body; i += 32) wd[i] = word;
-                if (lane < tail) d[head + 4 * body + lane] = v;
-            } else {
-                for (int i = lane; i < m; i += 32) d[i] = sbuf[s0 + i];
-            }
-        }
-        __syncthreads();
-        if (s_live == 0) break;
+    if (s_fail) {
+        if (tid == 0) set_status(status, EC_ERR_CORRUPT);
+        return;
     }
 
-    // transpose planes back into elements
+    // transpose planes back into elements; groups of four equal elements
+    // (each plane word one repeated byte) are un-swizzled once
     uint32_t* dstp = reinterpret_cast<uint32_t*>(jb.dst);
     const uint32_t w = (uint32_t)jb.w;
     const bool sw = s_mode == 2;
     if (jb.vec) {
         const bool dense = jb.pitch == jb.w;
-        for (int g = tid; 4 * g < len; g += kT) {
+        for (int g = tid; 4 * g < len; g += kDT) {
             const uint32_t A = *reinterpret_cast<const uint32_t*>(&planes[0][4 * g]);
             const uint32_t B = *reinterpret_cast<const uint32_t*>(&planes[1][4 * g]);
             const uint32_t C = *reinterpret_cast<const uint32_t*>(&planes[2][4 * g]);
             const uint32_t D = *reinterpret_cast<const uint32_t*>(&planes[3][4 * g]);
-            uint4 v = transpose4(A, B, C, D);                 // planes -> elements
-            if (sw) { v.x = swizzle(v.x); v.y = swizzle(v.y); v.z = swizzle(v.z); v.w = swizzle(v.w); }
+            uint4 v;
+            if (A == bcast8(A) && B == bcast8(B) && C == bcast8(C) && D == bcast8(D)) {
+                uint32_t e = __byte_perm(__byte_perm(A, B, 0x0040), __byte_perm(C, D, 0x0040), 0x5410);
+                if (sw) e = swizzle(e);
+                v = make_uint4(e, e, e, e);
+            } else {
+                v = transpose4(A, B, C, D);                 // planes -> elements
+                if (sw) { v.x = swizzle(v.x); v.y = swizzle(v.y); v.z = swizzle(v.z); v.w = swizzle(v.w); }
+            }
             const uint32_t q = q0 + 4u * g;
             size_t e = q;
             if (!dense) {
@@ -609,7 +618,7 @@ k_rle_decompress(const __grid_constant__ RleJobList<N> J, uint32_t* status)
             st_stream(reinterpret_cast<uint4*>(dstp + e), v);
         }
     } else {
-        for (int t = tid; t < len; t += kT) {
+        for (int t = tid; t < len; t += kDT) {
             uint32_t v = (uint32_t)planes[0][t] | ((uint32_t)planes[1][t] << 8) |
                          ((uint32_t)planes[2][t] << 16) | ((uint32_t)planes[3][t] << 24);
             if (sw) v = swizzle(v);
@@ -650,9 +659,9 @@ cudaError_t launch_rle_decompress(const RleJobDesc* jobs, int n, uint32_t total_
                                   uint32_t* status, cudaStream_t s)
 {
     if (n <= 0 || total_units == 0) return cudaSuccess;
-    if (n <= 8) k_rle_decompress<8><<<total_units, kT, 0, s>>>(make_jobs<8>(jobs, n, total_units), status);
-    else if (n <= 64) k_rle_decompress<64><<<total_units, kT, 0, s>>>(make_jobs<64>(jobs, n, total_units), status);
-    else k_rle_decompress<kRleJobsPerLaunch><<<total_units, kT, 0, s>>>(make_jobs<kRleJobsPerLaunch>(jobs, n, total_units), status);
+    if (n <= 8) k_rle_decompress<8><<<total_units, kDT, 0, s>>>(make_jobs<8>(jobs, n, total_units), status);
+    else if (n <= 64) k_rle_decompress<64><<<total_units, kDT, 0, s>>>(make_jobs<64>(jobs, n, total_units), status);
+    else k_rle_decompress<kRleJobsPerLaunch><<<total_units, kDT, 0, s>>>(make_jobs<kRleJobsPerLaunch>(jobs, n, total_units), status);
     return cudaGetLastError();
 }
 

@@ -144,6 +144,9 @@ def _adversarial_images():
     imgs["lit_run_mix"] = np.array(
         sum(([int(v)] * int(k) for v, k in zip(r.integers(0, 4, 3000), r.integers(1, 6, 3000))), []),
         np.uint32)[:8192].reshape(64, 128)
+    # runs of exactly 3 alternating values: ~1365 repeat runs per plane and chunk
+    imgs["runs_of_3"] = np.repeat(np.arange(2800, dtype=np.uint32) % 2 * np.uint32(0x01010101) + 7,
+                                  3).reshape(6, 1400)
     imgs["boxes"] = S.depth_source(200, 90, 0.4, 42, 0).color.numpy()
     imgs["depth_bits"] = S.depth_source(200, 90, 0.4, 42, 0).depth.numpy().view(np.uint32)
     imgs["smooth"] = S.smooth_image(160, 120)
