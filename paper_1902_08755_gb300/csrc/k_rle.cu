@@ -33,6 +33,9 @@
 // four planes are then transposed back into elements with byte permutes.
 #include "ec_internal.cuh"
 
+#include <algorithm>
+#include <atomic>
+
 namespace ec {
 namespace {
 
@@ -55,18 +58,6 @@ __device__ __forceinline__ uint32_t swizzle(uint32_t x)
     t = ((x >> 10) ^ x) & 0x00330033u;
     x ^= t ^ (t << 10);
     return x;
-}
-
-__device__ __forceinline__ void st_release(uint64_t* p, uint64_t v)
-{
-    asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
-}
-
-__device__ __forceinline__ uint64_t ld_acquire(const uint64_t* p)
-{
-    uint64_t v;
-    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
-    return v;
 }
 
 template <int N>
@@ -190,88 +181,243 @@ __device__ __forceinline__ uint64_t warp_sum(uint64_t v)
     return v;
 }
 
-constexpr int kPlaneStride = kChunk + 32;   // 16 bytes of slack before and after
+constexpr int kSparseMax = 1024;              // most segments (all planes) the sparse path takes
+constexpr int kSegPerThread = kSparseMax / kT;
+constexpr int kCPerSM = 4;                    // resident compress CTAs per SM
+// Element buffer: 4096 elements; the dense path later reuses it for the plane-
+// major copy and then as its output stage (<= kStage bytes + 16 of slack).
+constexpr int kRawBytes = kStage + 16;
+// Sparse region: the segment list, later the sparse output (at most
+// 3 * kSparseMax + 4 * kChunk / 64 bytes, see sparse_chunk) + 16 of slack.
+constexpr int kSpBytes = 3 * kSparseMax + 4 * kChunk / 64 + 128;
+constexpr size_t kCompressSmem = 3ull * kRawBytes + 2ull * kSpBytes;
+constexpr uint32_t kNone = 0xFFFFFFFFu;
+static_assert(kRawBytes % 16 == 0 && kSpBytes % 16 == 0, "16-byte aligned regions");
+static_assert(2 * (kSparseMax + 8) <= kSpBytes, "segment list fits");
 
-template <int N>
-__global__ void __launch_bounds__(kT, 4)
-k_rle_compress(const __grid_constant__ RleJobList<N> J, uint64_t* flags, uint32_t* ticket,
-               uint32_t* status)
+// Element q of a chunk sits at word raw_idx(q) of its buffer.  The 16-byte
+// groups are permuted inside every 128 bytes (XOR with bits 3..5 of the group
+// index), so that a quarter warp reading 16 consecutive elements per thread
+// touches all 32 banks.
+__device__ __forceinline__ int raw_idx(int q) { return (((q >> 2) ^ ((q >> 5) & 7)) << 2) | (q & 3); }
+
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem)
 {
-    // plane-major copy of the chunk: pl[b][16 + q] = plane b of element q
-    __shared__ __align__(16) uint8_t pl[4][kPlaneStride];
-    __shared__ __align__(16) uint8_t stage[kStage + 16];
-    __shared__ P4 wt_max[kT / 32], wt_sum[kT / 32];
-    __shared__ uint32_t s_unit;
-    __shared__ uint64_t s_off;
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s), "l"(gmem) : "memory");
+}
 
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    if (tid == 0) s_unit = atomicAdd(ticket, 1u);
-    __syncthreads();
-    const uint32_t unit = s_unit;
-    if (unit >= J.total_units) return;               // cannot happen: one ticket per CTA
-    const RleJobDesc& jb = J.j[find_job(J, unit)];
-    uint8_t* dst = reinterpret_cast<uint8_t*>(jb.dst);
-    const uint32_t nc = jb.n_chunks;
-    if (nc == 0) {                                   // empty image: header only
-        if (tid == 0) {
-            write_header(dst, jb);
-            *jb.d_size = 32u;
-        }
-        return;
-    }
+__device__ __forceinline__ void cp_async4(void* smem, const void* gmem)
+{
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(s), "l"(gmem) : "memory");
+}
+
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+
+template <int K>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(K) : "memory"); }
+
+// The chunk-size flags carry their own value, so relaxed accesses suffice.
+__device__ __forceinline__ void st_flag(uint64_t* p, uint64_t v)
+{
+    asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+__device__ __forceinline__ uint64_t ld_flag(const uint64_t* p)
+{
+    uint64_t v;
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// Start the copy of work unit `unit`'s elements into `raw` (positions past the
+// chunk's end are left as they are and never used).
+__device__ void load_chunk(const RleJobDesc& jb, uint32_t unit, uint32_t* raw)
+{
     const uint32_t c = unit - jb.first_unit;
-    const uint32_t n = (uint32_t)jb.w * (uint32_t)jb.h;
-    const uint32_t q0 = c * (uint32_t)kChunk;
+    if (c >= jb.n_chunks) return;                     // empty image
+    const uint32_t n = (uint32_t)jb.w * (uint32_t)jb.h, q0 = c * (uint32_t)kChunk;
     const int len = (int)min((uint32_t)kChunk, n - q0);
     const uint32_t w = (uint32_t)jb.w;
-
-    // 1. load, swizzle (mode 2) and split into byte planes
-    if (jb.vec) {
-        // the chunk's 1024 groups of 4 elements, 4 per thread: all four
-        // 16-byte loads are issued before any of them is used
-        const bool dense = jb.pitch == jb.w;       // element q at src + q
-        constexpr int kG = kChunk / 4 / kT;
-        uint4 v[kG];
+    const int tid = threadIdx.x;
+    if (jb.vec) {                                     // groups of 4 never straddle a row
+        const bool dense = jb.pitch == jb.w;
 #pragma unroll
-        for (int k = 0; k < kG; ++k) {
-            const int g = tid + k * kT;
-            if (4 * g < len) {
-                const uint32_t q = q0 + 4u * g;
-                size_t e = q;
+        for (int k = 0; k < kChunk / 4 / kT; ++k) {
+            const int q = 4 * (tid + k * kT);
+            if (q < len) {
+                size_t e = q0 + q;
                 if (!dense) {
-                    const uint32_t y = q / w;
-                    e = (size_t)y * jb.pitch + (q - y * w);
+                    const uint32_t y = (q0 + q) / w;
+                    e = (size_t)y * jb.pitch + (q0 + q - y * w);
                 }
-                v[k] = ld_stream(reinterpret_cast<const uint4*>(jb.src + e));
-            }
-        }
-#pragma unroll
-        for (int k = 0; k < kG; ++k) {
-            const int g = tid + k * kT;
-            if (4 * g < len) {
-                uint4 x = v[k];
-                if (jb.mode == 2) { x.x = swizzle(x.x); x.y = swizzle(x.y); x.z = swizzle(x.z); x.w = swizzle(x.w); }
-                const uint4 t = transpose4(x.x, x.y, x.z, x.w);
-                *reinterpret_cast<uint32_t*>(&pl[0][16 + 4 * g]) = t.x;
-                *reinterpret_cast<uint32_t*>(&pl[1][16 + 4 * g]) = t.y;
-                *reinterpret_cast<uint32_t*>(&pl[2][16 + 4 * g]) = t.z;
-                *reinterpret_cast<uint32_t*>(&pl[3][16 + 4 * g]) = t.w;
+                cp_async16(raw + raw_idx(q), jb.src + e);
             }
         }
     } else {
         for (int t = tid; t < len; t += kT) {
-            const uint32_t q = q0 + t, y = q / w, x = q - y * w;
-            uint32_t v = __ldcs(jb.src + (size_t)y * jb.pitch + x);
-            if (jb.mode == 2) v = swizzle(v);
-            pl[0][16 + t] = (uint8_t)v;
-            pl[1][16 + t] = (uint8_t)(v >> 8);
-            pl[2][16 + t] = (uint8_t)(v >> 16);
-            pl[3][16 + t] = (uint8_t)(v >> 24);
+            const uint32_t q = q0 + t, y = q / w;
+            cp_async4(raw + raw_idx(t), jb.src + (size_t)y * jb.pitch + (q - y * w));
         }
     }
-    __syncthreads();
+}
 
-    // 2. classify this thread's 16 positions of every plane with bit masks.
+// Exclusive prefix of work unit `unit`'s output inside its job's payload: the
+// sizes of the preceding chunks of the job, summed 32 flags at a time back to
+// one that holds its inclusive prefix; then this chunk's inclusive prefix is
+// published.  Run by one warp; every wait is bounded.
+__device__ uint64_t look_back(uint64_t* flags, uint32_t unit, uint32_t first_unit, uint64_t total,
+                              uint32_t* status)
+{
+    const int lane = threadIdx.x & 31;
+    if (unit == first_unit) return 0;                 // published inclusive when coded
+    uint64_t acc = 0;
+    int64_t hi = (int64_t)unit - 1;
+    int spins = 0;
+    for (;;) {
+        const int64_t k = hi - lane;
+        const uint64_t v = k >= (int64_t)first_unit ? ld_flag(flags + k) : kInc;
+        const uint32_t st = (uint32_t)(v >> 62);
+        const uint32_t incm = __ballot_sync(0xffffffffu, st == 2u);
+        const uint32_t zerom = __ballot_sync(0xffffffffu, st == 0u);
+        const uint32_t upto = incm ? ((incm & (0u - incm)) << 1) - 1u : 0xffffffffu;
+        if (zerom & upto) {
+            if (++spins > kSpinLimit) {
+                if (lane == 0) set_status(status, EC_ERR_TIMEOUT);
+                break;
+            }
+            __nanosleep(64);
+            continue;
+        }
+        acc += warp_sum(((upto >> lane) & 1u) ? (v & kVal) : 0ull);
+        if (incm) break;
+        hi -= 32;
+    }
+    if (lane == 0) st_flag(flags + unit, kInc | (acc + total));
+    return acc;
+}
+
+// What the finishing step needs of a coded chunk.
+struct ChunkMeta {
+    uint32_t unit, job, total, dense;
+    uint32_t pend[4];        // end of plane p's stream inside the chunk's output
+};
+
+// Shared state of one compress CTA.
+struct CState {
+    P4 wt_a[kT / 32], wt_b[kT / 32];
+    uint32_t tk[3], tj[3];   // ticket ring: work unit and its job
+    ChunkMeta meta[2];
+    uint64_t off;
+};
+
+// Publish the chunk's size: inclusive for the job's first chunk, else an
+// aggregate that the look-back of later chunks may sum.
+__device__ __forceinline__ void publish(uint64_t* flags, uint32_t unit, uint32_t first_unit, uint32_t total)
+{
+    st_flag(flags + unit, (unit == first_unit ? kInc : kAgg) | (uint64_t)total);
+}
+
+// Sparse path: the chunk has few segments (maximal runs of one byte value in a
+// plane), listed by start position, planes one after another.  Each thread
+// takes kSegPerThread consecutive segments: runs of three or more become
+// repeat tokens, and the first short run of a literal span codes the span.
+// The output is at most 2 bytes per repeat segment plus 2 per 128 of its
+// length, and 3 bytes per short run, i.e. 3 * kSparseMax + 4 * kChunk / 64.
+// The stage may overlay the segment list: every list read precedes the scan.
+__device__ void sparse_chunk(const uint32_t* raw, const uint16_t* seg, uint8_t* stage, CState& S,
+                             ChunkMeta& M, const uint32_t nb[4], int len, bool sw,
+                             uint64_t* flags, uint32_t unit, uint32_t first_unit)
+{
+    const int tid = threadIdx.x;
+    const uint32_t nseg = nb[3];
+    // segment: start s (12 bits), length (13), plane (2), kind (1 repeat, 2 literal span)
+    uint32_t info[kSegPerThread], cost[kSegPerThread];
+    uint32_t mine = 0;
+#pragma unroll
+    for (int k = 0; k < kSegPerThread; ++k) {
+        const uint32_t i = kSegPerThread * tid + k;
+        info[k] = 0u;
+        cost[k] = 0u;
+        if (i < nseg) {
+            const uint32_t p = (i >= nb[0]) + (i >= nb[1]) + (i >= nb[2]);
+            const uint32_t pb = i >= nb[2] ? nb[2] : i >= nb[1] ? nb[1] : i >= nb[0] ? nb[0] : 0u;
+            const uint32_t pe = i >= nb[2] ? nb[3] : i >= nb[1] ? nb[2] : i >= nb[0] ? nb[1] : nb[0];
+            const int s = seg[i];
+            const int e = i + 1 < pe ? (int)seg[i + 1] : len;
+            const int L = e - s;
+            if (L >= 3) {
+                info[k] = (uint32_t)s | ((uint32_t)L << 12) | (p << 25) | (1u << 27);
+                cost[k] = 2u * (uint32_t)((L + 127) >> 7);
+            } else if (i == pb || s - (int)seg[i - 1] >= 3) {
+                // first short run of a literal span: walk to the span's end
+                int end = e;
+                for (uint32_t j = i + 1; j < pe; ++j) {
+                    const int en = j + 1 < pe ? (int)seg[j + 1] : len;
+                    if (en - end >= 3) break;
+                    end = en;
+                }
+                const int Ls = end - s;
+                info[k] = (uint32_t)s | ((uint32_t)Ls << 12) | (p << 25) | (2u << 27);
+                cost[k] = (uint32_t)(Ls + ((Ls + 127) >> 7));
+            }
+            mine += cost[k];
+        }
+    }
+    P4 tot;
+    const P4 ex = block_scan<false>(P4{mine, 0u}, S.wt_b, &tot);   // (barrier inside)
+    const uint32_t total = tot.a;
+    if (tid == 0) {
+        publish(flags, unit, first_unit, total);
+        M.total = total;
+        M.dense = 0u;
+    }
+    uint32_t o = ex.a;
+#pragma unroll
+    for (int k = 0; k < kSegPerThread; ++k) {
+        const uint32_t i = kSegPerThread * tid + k;
+        const uint32_t kind = info[k] >> 27;
+        const uint32_t p = (info[k] >> 25) & 3u;
+        const int s = (int)(info[k] & 0xFFFu), L = (int)((info[k] >> 12) & 0x1FFFu);
+        const int sh = 8 * (int)p;
+        if (kind == 1u) {
+            uint32_t e = raw[raw_idx(s)];
+            if (sw) e = swizzle(e);
+            const uint8_t v = (uint8_t)(e >> sh);
+            uint32_t oo = o;
+            for (int r = L; r > 0; r -= 128) {
+                stage[oo] = (uint8_t)(127 + min(r, 128));
+                stage[oo + 1] = v;
+                oo += 2;
+            }
+        } else if (kind == 2u) {
+            uint32_t oo = o;
+            for (int d = 0; d < L; d += 128) {
+                const int m = min(L - d, 128);
+                stage[oo++] = (uint8_t)(m - 1);
+                for (int t = 0; t < m; ++t) {
+                    uint32_t e = raw[raw_idx(s + d + t)];
+                    if (sw) e = swizzle(e);
+                    stage[oo++] = (uint8_t)(e >> sh);
+                }
+            }
+        }
+        o += cost[k];
+        if (i < nseg && (i + 1 == nb[0] || i + 1 == nb[1] || i + 1 == nb[2] || i + 1 == nb[3]))
+            M.pend[(i + 1 == nb[0]) ? 0 : (i + 1 == nb[1]) ? 1 : (i + 1 == nb[2]) ? 2 : 3] = o;
+    }
+}
+
+// Dense path: every position is classified with byte-SIMD bit masks on a
+// plane-major copy of the chunk (pl[b * kChunk + q] = plane b of element q),
+// which lies in the element buffer; once classified, that buffer becomes the
+// stage.
+__device__ void dense_chunk(uint8_t* pl, CState& S, ChunkMeta& M, int len,
+                            uint64_t* flags, uint32_t unit, uint32_t first_unit)
+{
+    const int tid = threadIdx.x;
+    // classify this thread's 16 positions of every plane with bit masks.
     // Bit i of the 24-bit masks stands for position P0 - 4 + i.
     const int P0 = tid * kPer;
     const uint32_t VQ = bit_range(4 - P0, len - P0 + 4);          // 0 <= q < len
@@ -282,10 +428,11 @@ k_rle_compress(const __grid_constant__ RleJobList<N> J, uint64_t* flags, uint32_
     uint4 bytes[4];
 #pragma unroll
     for (int b = 0; b < 4; ++b) {
-        const uint8_t* base = &pl[b][16 + P0];
+        const uint8_t* base = pl + b * kChunk + P0;
         const uint4 v = *reinterpret_cast<const uint4*>(base);
-        const uint32_t wm = *reinterpret_cast<const uint32_t*>(base - 4);
-        const uint32_t wp = *reinterpret_cast<const uint32_t*>(base + 16);
+        // neighbours outside the chunk only feed masked-off bits
+        const uint32_t wm = P0 > 0 ? *reinterpret_cast<const uint32_t*>(base - 4) : 0u;
+        const uint32_t wp = P0 + kPer < kChunk ? *reinterpret_cast<const uint32_t*>(base + 16) : 0u;
         bytes[b] = v;
         // eq bit i: byte at position P0-4+i equals its predecessor
         uint32_t EQ = eq_bytes(wm, wm << 8);
@@ -297,13 +444,13 @@ k_rle_compress(const __grid_constant__ RleJobList<N> J, uint64_t* flags, uint32_
         EQ &= VEQ & ~1u;                                          // bit 0 has no predecessor here
         const uint32_t T3 = EQ & (EQ << 1);                       // positions i-2, i-1, i equal
         const uint32_t R = (T3 | (T3 >> 1) | (T3 >> 2)) & VQ;     // byte lies in a run >= 3
-        const uint32_t S = (((R & ~EQ) | (~R & (R << 1))) & VQ) | HIGH | Q0;
+        const uint32_t Sg = (((R & ~EQ) | (~R & (R << 1))) & VQ) | HIGH | Q0;
         REP[b] = (R >> 4) & 0xFFFFu;
-        SEG[b] = (S >> 4) & 0x1FFFFu;                             // bit 16: position P0+16
+        SEG[b] = (Sg >> 4) & 0x1FFFFu;                            // bit 16: position P0+16
     }
     const uint32_t VALID = (VQ >> 4) & 0xFFFFu;
 
-    // 3. last segment start before each thread (max-scan of position + 1)
+    // last segment start before each thread (max-scan of position + 1)
     P4 mine;
     {
         uint32_t l[4];
@@ -316,9 +463,9 @@ k_rle_compress(const __grid_constant__ RleJobList<N> J, uint64_t* flags, uint32_
         mine.b = l[2] | (l[3] << 16);
     }
     P4 tot_max;
-    const P4 before = block_scan<true>(mine, wt_max, &tot_max);
+    const P4 before = block_scan<true>(mine, S.wt_a, &tot_max);   // (barrier inside: pl is dead after it)
 
-    // 4. piece starts (tokens hold <= 128 bytes) and output sizes
+    // piece starts (tokens hold <= 128 bytes) and output sizes
     uint32_t PSV[4], PE[4], LIT[4], cost[4];
     int sbin[4];
 #pragma unroll
@@ -342,50 +489,27 @@ k_rle_compress(const __grid_constant__ RleJobList<N> J, uint64_t* flags, uint32_
     }
     P4 tot;
     const P4 off0 = block_scan<false>(P4{cost[0] | (cost[1] << 16), cost[2] | (cost[3] << 16)},
-                                      wt_sum, &tot);
-    uint32_t ptot[4], pbase[4], total = 0;
+                                      S.wt_b, &tot);
+    uint32_t pbase[4], total = 0;
 #pragma unroll
     for (int b = 0; b < 4; ++b) {
-        ptot[b] = lane16(tot, b);
         pbase[b] = total;
-        total += ptot[b];
+        total += lane16(tot, b);
     }
-
-    // 5. chunk offset: warp-wide decoupled look-back, bounded waits
-    if (warp == 0) {
-        uint64_t* f = flags + unit;
-        uint64_t acc = 0;
-        if (c == 0) {
-            if (lane == 0) st_release(f, kInc | (uint64_t)total);
-        } else {
-            if (lane == 0) st_release(f, kAgg | (uint64_t)total);
-            int64_t hi = (int64_t)unit - 1;
-            int spins = 0;
-            for (;;) {
-                const int64_t k = hi - lane;
-                const uint64_t v = k >= (int64_t)jb.first_unit ? ld_acquire(flags + k) : kInc;
-                const uint32_t st = (uint32_t)(v >> 62);
-                const uint32_t incm = __ballot_sync(0xffffffffu, st == 2u);
-                const uint32_t zerom = __ballot_sync(0xffffffffu, st == 0u);
-                const uint32_t upto = incm ? ((incm & (0u - incm)) << 1) - 1u : 0xffffffffu;
-                if (zerom & upto) {
-                    if (++spins > kSpinLimit) {
-                        if (lane == 0) set_status(status, EC_ERR_TIMEOUT);
-                        break;
-                    }
-                    __nanosleep(64);
-                    continue;
-                }
-                acc += warp_sum(((upto >> lane) & 1u) ? (v & kVal) : 0ull);
-                if (incm) break;
-                hi -= 32;
-            }
-            if (lane == 0) st_release(f, kInc | (acc + total));
-        }
-        if (lane == 0) s_off = acc;
+    if (tid < 4) {
+        uint32_t e = 0;
+#pragma unroll
+        for (int b = 0; b < 4; ++b) e += b <= tid ? lane16(tot, b) : 0u;
+        M.pend[tid] = e;
+    }
+    if (tid == 0) {
+        publish(flags, unit, first_unit, total);
+        M.total = total;
+        M.dense = 1u;
     }
 
     // emit bytes and control codes into the stage
+    uint8_t* stage = pl;
 #pragma unroll
     for (int b = 0; b < 4; ++b) {
         uint8_t* out = stage + pbase[b];
@@ -418,36 +542,194 @@ k_rle_compress(const __grid_constant__ RleJobList<N> J, uint64_t* flags, uint32_
             }
         }
     }
-    __syncthreads();
+}
 
-    // 6. copy out
-    const uint64_t G = s_off;
-    uint8_t* payload = dst + 32 + 16ull * nc;
-    uint8_t* o = payload + G;
-    {
-        const uintptr_t a0 = reinterpret_cast<uintptr_t>(o), a1 = a0 + total;
-        const uintptr_t w0 = (a0 + 3) & ~(uintptr_t)3, w1 = a1 & ~(uintptr_t)3;
-        if (w0 >= w1) {
-            for (uint32_t i = tid; i < total; i += kT) o[i] = stage[i];
-        } else {
-            const uint32_t head = (uint32_t)(w0 - a0), tail0 = (uint32_t)(w1 - a0);
-            if ((uint32_t)tid < head) o[tid] = stage[tid];
-            for (uint32_t i = tail0 + tid; i < total; i += kT) o[i] = stage[i];
-            const uint32_t nw = (uint32_t)((w1 - w0) >> 2);
-            const uint32_t* s32 = reinterpret_cast<const uint32_t*>(stage);
-            const uint32_t sh = 8u * head;
-            uint32_t* o32 = reinterpret_cast<uint32_t*>(w0);
-            for (uint32_t k = tid; k < nw; k += kT) {
-                // stage bytes [head + 4k, head + 4k + 4), head < 4
-                o32[k] = __funnelshift_r(s32[k], s32[k + 1], sh);
-            }
+// Code one chunk into its stage and publish its size: find where every byte
+// plane changes value, count the segments, then take the sparse or the dense
+// path.  `raw` holds the chunk's elements (raw_idx layout).
+__device__ void code_chunk(const RleJobDesc& jb, uint32_t unit, ChunkMeta& M, uint32_t* raw, uint8_t* sp,
+                           CState& S, uint64_t* flags)
+{
+    const int tid = threadIdx.x;
+    const uint32_t nc = jb.n_chunks;
+    if (nc == 0) return;                             // empty image: header only, when finished
+    const uint32_t c = unit - jb.first_unit;
+    const uint32_t n = (uint32_t)jb.w * (uint32_t)jb.h;
+    const int len = (int)min((uint32_t)kChunk, n - c * (uint32_t)kChunk);
+    const bool sw = jb.mode == 2;
+
+    // 1. value changes: bit i of CH[p] is set when plane p of element P0+i
+    // differs from element P0+i-1 (the swizzle permutes bits, so it commutes
+    // with the XOR); position 0 starts a segment in every plane
+    const int P0 = tid * kPer;
+    uint32_t e[kPer];
+#pragma unroll
+    for (int k = 0; k < kPer / 4; ++k) {
+        const uint4 v = *reinterpret_cast<const uint4*>(raw + raw_idx(P0 + 4 * k));
+        e[4 * k] = v.x; e[4 * k + 1] = v.y; e[4 * k + 2] = v.z; e[4 * k + 3] = v.w;
+    }
+    const uint32_t prev = P0 > 0 ? raw[raw_idx(P0 - 1)] : e[0];
+    const int nv = min(max(len - P0, 0), kPer);
+    uint32_t nzm = 0u;
+#pragma unroll
+    for (int i = 0; i < kPer; ++i) nzm |= (e[i] != (i ? e[i - 1] : prev) ? 1u : 0u) << i;
+    nzm &= (1u << nv) - 1u;
+    uint32_t CH[4] = {0u, 0u, 0u, 0u};
+    for (uint32_t m = nzm; m; m &= m - 1u) {
+        const int i = __ffs(m) - 1;
+        uint32_t x = raw[raw_idx(P0 + i)] ^ raw[raw_idx(P0 + i - 1)];
+        if (sw) x = swizzle(x);
+#pragma unroll
+        for (int p = 0; p < 4; ++p) CH[p] |= ((x >> (8 * p)) & 0xFFu ? 1u : 0u) << i;
+    }
+    if (P0 == 0) {
+#pragma unroll
+        for (int p = 0; p < 4; ++p) CH[p] |= 1u;
+    }
+
+    // 2. segment counts per plane
+    P4 tot;
+    const P4 ex = block_scan<false>(P4{(uint32_t)__popc(CH[0]) | ((uint32_t)__popc(CH[1]) << 16),
+                                       (uint32_t)__popc(CH[2]) | ((uint32_t)__popc(CH[3]) << 16)},
+                                    S.wt_a, &tot);
+    uint32_t nb[4];                                  // cumulative segment counts
+    nb[0] = lane16(tot, 0);
+    nb[1] = nb[0] + lane16(tot, 1);
+    nb[2] = nb[1] + lane16(tot, 2);
+    nb[3] = nb[2] + lane16(tot, 3);
+
+    if (nb[3] <= (uint32_t)kSparseMax) {
+        uint16_t* seg = reinterpret_cast<uint16_t*>(sp);
+#pragma unroll
+        for (int p = 0; p < 4; ++p) {
+            uint32_t at = (p ? nb[p - 1] : 0u) + lane16(ex, p);
+            for (uint32_t m = CH[p]; m; m &= m - 1u) seg[at++] = (uint16_t)(P0 + __ffs(m) - 1);
+        }
+        __syncthreads();
+        sparse_chunk(raw, seg, sp, S, M, nb, len, sw, flags, unit, jb.first_unit);
+    } else {
+        // plane-major copy, written over the element buffer
+        uint8_t* pl = reinterpret_cast<uint8_t*>(raw);
+        __syncthreads();                              // every thread has read its elements
+#pragma unroll
+        for (int k = 0; k < kPer / 4; ++k) {
+            uint32_t a = e[4 * k], b = e[4 * k + 1], cc = e[4 * k + 2], d = e[4 * k + 3];
+            if (sw) { a = swizzle(a); b = swizzle(b); cc = swizzle(cc); d = swizzle(d); }
+            const uint4 t = transpose4(a, b, cc, d);
+            *reinterpret_cast<uint32_t*>(pl + 0 * kChunk + P0 + 4 * k) = t.x;
+            *reinterpret_cast<uint32_t*>(pl + 1 * kChunk + P0 + 4 * k) = t.y;
+            *reinterpret_cast<uint32_t*>(pl + 2 * kChunk + P0 + 4 * k) = t.z;
+            *reinterpret_cast<uint32_t*>(pl + 3 * kChunk + P0 + 4 * k) = t.w;
+        }
+        __syncthreads();
+        dense_chunk(pl, S, M, len, flags, unit, jb.first_unit);
+    }
+}
+
+// Place a coded chunk in its stream and copy it out: look back for its
+// offset (warp 0), then write the payload bytes, the chunk's four end-table
+// entries, the header (chunk 0) and the stream size (last chunk).
+__device__ void finish_chunk(const RleJobDesc& jb, const ChunkMeta& M, const uint8_t* stage, CState& S,
+                             uint64_t* flags, uint32_t* status)
+{
+    const int tid = threadIdx.x;
+    uint8_t* dst = reinterpret_cast<uint8_t*>(jb.dst);
+    const uint32_t nc = jb.n_chunks;
+    if (nc == 0) {                                   // empty image: header only
+        if (tid == 0) {
+            write_header(dst, jb);
+            *jb.d_size = 32u;
+        }
+        return;
+    }
+    const uint32_t c = M.unit - jb.first_unit;
+    const uint32_t total = M.total;
+    if (tid < 32) {
+        const uint64_t acc = look_back(flags, M.unit, jb.first_unit, total, status);
+        if (tid == 0) S.off = acc;
+    }
+    __syncthreads();
+    const uint64_t G = S.off;
+    uint8_t* o = dst + 32 + 16ull * nc + G;
+    const uintptr_t a0 = reinterpret_cast<uintptr_t>(o), a1 = a0 + total;
+    const uintptr_t w0 = (a0 + 3) & ~(uintptr_t)3, w1 = a1 & ~(uintptr_t)3;
+    if (w0 >= w1) {
+        for (uint32_t i = tid; i < total; i += kT) o[i] = stage[i];
+    } else {
+        const uint32_t head = (uint32_t)(w0 - a0), tail0 = (uint32_t)(w1 - a0);
+        if ((uint32_t)tid < head) o[tid] = stage[tid];
+        for (uint32_t i = tail0 + tid; i < total; i += kT) o[i] = stage[i];
+        const uint32_t nw = (uint32_t)((w1 - w0) >> 2);
+        const uint32_t* s32 = reinterpret_cast<const uint32_t*>(stage);
+        const uint32_t sh = 8u * head;
+        uint32_t* o32 = reinterpret_cast<uint32_t*>(w0);
+        for (uint32_t k = tid; k < nw; k += kT) {
+            // stage bytes [head + 4k, head + 4k + 4), head < 4
+            o32[k] = __funnelshift_r(s32[k], s32[k + 1], sh);
         }
     }
-    if (tid < 4) put_u32(dst + 32 + 16ull * c + 4u * tid, (uint32_t)(G + pbase[tid] + ptot[tid]));
+    if (tid < 4) put_u32(dst + 32 + 16ull * c + 4u * tid, (uint32_t)(G + M.pend[tid]));
     if (tid == 0) {
         if (c == 0) write_header(dst, jb);
         if (c == nc - 1) *jb.d_size = 32ull + 16ull * nc + G + total;
     }
+}
+
+// Persistent compressor.  Each CTA takes work units (chunks) from an atomic
+// ticket and runs a three-stage pipeline over them: while the copy of chunk
+// j+1 is in flight, it codes chunk j and publishes its size, then looks back
+// for chunk j-1's offset and copies that chunk out.  A chunk's size is thus
+// published before its CTA waits on anything, and a look-back waits only for
+// chunks with lower tickets, whose CTAs code them before any higher one.
+template <int N>
+__global__ void __launch_bounds__(kT, kCPerSM)
+k_rle_compress(const __grid_constant__ RleJobList<N> J, uint64_t* flags, uint32_t* ticket,
+               uint32_t* status)
+{
+    extern __shared__ __align__(16) uint8_t smem[];
+    __shared__ CState S;
+    const int tid = threadIdx.x;
+    const uint32_t T = J.total_units;
+    auto rawb = [&](int j) { return reinterpret_cast<uint32_t*>(smem + (j % 3) * kRawBytes); };
+    auto spb = [&](int j) { return smem + 3 * kRawBytes + (j & 1) * kSpBytes; };
+    auto take = [&](int slot) {                       // thread 0
+        const uint32_t u = atomicAdd(ticket, 1u);
+        S.tk[slot] = u;
+        S.tj[slot] = u < T ? (uint32_t)find_job(J, u) : 0u;
+    };
+
+    if (tid == 0) { take(0); take(1); }
+    __syncthreads();
+    uint32_t cur = S.tk[0], nxt = S.tk[1], prev = kNone;
+    if (cur < T) load_chunk(J.j[S.tj[0]], cur, rawb(0));
+    cp_async_commit();
+    if (nxt < T) load_chunk(J.j[S.tj[1]], nxt, rawb(1));
+    cp_async_commit();
+    for (int j = 0; cur < T || prev != kNone; ++j) {
+        cp_async_wait<1>();                           // this thread's copies of chunk j landed
+        __syncthreads();
+        if (cur < T) {
+            ChunkMeta& M = S.meta[j & 1];
+            const RleJobDesc& jb = J.j[S.tj[j % 3]];
+            if (tid == 0) { M.unit = cur; M.job = S.tj[j % 3]; }
+            code_chunk(jb, cur, M, rawb(j), spb(j), S, flags);
+            __syncthreads();
+        }
+        if (prev != kNone) {
+            const ChunkMeta& M = S.meta[(j + 1) & 1];
+            const uint8_t* stage = M.dense ? reinterpret_cast<const uint8_t*>(rawb(j + 2)) : spb(j + 1);
+            finish_chunk(J.j[M.job], M, stage, S, flags, status);
+        }
+        if (tid == 0) take((j + 2) % 3);
+        __syncthreads();                              // chunk j-1's buffers are free
+        const uint32_t nn = S.tk[(j + 2) % 3];
+        if (nn < T) load_chunk(J.j[S.tj[(j + 2) % 3]], nn, rawb(j + 2));
+        cp_async_commit();
+        prev = cur < T ? cur : kNone;
+        cur = nxt;
+        nxt = nn;
+    }
+    cp_async_wait<0>();
 }
 
 // ----------------------------------------------------------- decompress ----
@@ -641,6 +923,45 @@ RleJobList<N> make_jobs(const RleJobDesc* jobs, int n, uint32_t total)
 
 }  // namespace
 
+namespace {
+
+// Persistent grid: as many compress CTAs as fit on the device at once (the
+// kernel's dynamic shared memory attribute is set on first use per device).
+template <int N>
+cudaError_t compress_grid(int* grid)
+{
+    constexpr int kMaxDev = 64;
+    static std::atomic<int> cache[kMaxDev];
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < kMaxDev && (*grid = cache[dev].load(std::memory_order_relaxed)) > 0) return cudaSuccess;
+    e = cudaFuncSetAttribute(k_rle_compress<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kCompressSmem);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0, sms = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_rle_compress<N>, kT, kCompressSmem);
+    if (e != cudaSuccess) return e;
+    e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    *grid = std::max(1, per_sm) * sms;
+    if (dev < kMaxDev) cache[dev].store(*grid, std::memory_order_relaxed);
+    return cudaSuccess;
+}
+
+template <int N>
+cudaError_t compress_n(const RleJobDesc* jobs, int n, uint32_t total_units, uint64_t* flags,
+                       uint32_t* ticket, uint32_t* status, cudaStream_t s)
+{
+    int grid = 0;
+    const cudaError_t e = compress_grid<N>(&grid);
+    if (e != cudaSuccess) return e;
+    grid = (int)std::min<uint32_t>((uint32_t)grid, total_units);
+    k_rle_compress<N><<<grid, kT, kCompressSmem, s>>>(make_jobs<N>(jobs, n, total_units), flags, ticket, status);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
 cudaError_t launch_rle_compress(const RleJobDesc* jobs, int n, uint32_t total_units,
                                 void* scratch, uint32_t* status, cudaStream_t s)
 {
@@ -649,10 +970,9 @@ cudaError_t launch_rle_compress(const RleJobDesc* jobs, int n, uint32_t total_un
     uint64_t* flags = reinterpret_cast<uint64_t*>(reinterpret_cast<char*>(scratch) + 16);
     cudaError_t e = cudaMemsetAsync(scratch, 0, 16 + 8ull * total_units, s);
     if (e != cudaSuccess) return e;
-    if (n <= 8) k_rle_compress<8><<<total_units, kT, 0, s>>>(make_jobs<8>(jobs, n, total_units), flags, ticket, status);
-    else if (n <= 64) k_rle_compress<64><<<total_units, kT, 0, s>>>(make_jobs<64>(jobs, n, total_units), flags, ticket, status);
-    else k_rle_compress<kRleJobsPerLaunch><<<total_units, kT, 0, s>>>(make_jobs<kRleJobsPerLaunch>(jobs, n, total_units), flags, ticket, status);
-    return cudaGetLastError();
+    if (n <= 8) return compress_n<8>(jobs, n, total_units, flags, ticket, status, s);
+    if (n <= 64) return compress_n<64>(jobs, n, total_units, flags, ticket, status, s);
+    return compress_n<kRleJobsPerLaunch>(jobs, n, total_units, flags, ticket, status, s);
 }
 
 cudaError_t launch_rle_decompress(const RleJobDesc* jobs, int n, uint32_t total_units,
