@@ -181,19 +181,20 @@ __device__ __forceinline__ uint64_t warp_sum(uint64_t v)
     return v;
 }
 
-constexpr int kSparseMax = 1024;              // most segments (all planes) the sparse path takes
-constexpr int kSegPerThread = kSparseMax / kT;
+constexpr int kSparseMax = 512;               // most segments (all planes) the sparse path takes
 constexpr int kCPerSM = 4;                    // resident compress CTAs per SM
 // Element buffer: 4096 elements; the dense path later reuses it for the plane-
 // major copy and then as its output stage (<= kStage bytes + 16 of slack).
 constexpr int kRawBytes = kStage + 16;
-// Sparse region: the segment list, later the sparse output (at most
-// 3 * kSparseMax + 4 * kChunk / 64 bytes, see sparse_chunk) + 16 of slack.
-constexpr int kSpBytes = 3 * kSparseMax + 4 * kChunk / 64 + 128;
-constexpr size_t kCompressSmem = 3ull * kRawBytes + 2ull * kSpBytes;
+// Sparse stage: plane p's stream gets a region of sp_region(n_p) bytes (see
+// sparse_plane), at most 3 * kSparseMax + 4 * (kChunk / 64 + 3) in all, + slack.
+constexpr int kSpBytes = 3 * kSparseMax + 4 * (kChunk / 64) + 64;
+constexpr int kSegBytes = 2 * kSparseMax;     // segment starts of the sparse path
+constexpr int kChmBytes = 4 * kT * 2;         // one 16-bit change mask per thread and plane
+constexpr size_t kCompressSmem = 3ull * kRawBytes + 2ull * kSpBytes + kSegBytes + kChmBytes;
 constexpr uint32_t kNone = 0xFFFFFFFFu;
-static_assert(kRawBytes % 16 == 0 && kSpBytes % 16 == 0, "16-byte aligned regions");
-static_assert(2 * (kSparseMax + 8) <= kSpBytes, "segment list fits");
+static_assert(kRawBytes % 16 == 0 && kSpBytes % 16 == 0 && kSegBytes % 16 == 0, "16-byte aligned regions");
+static_assert(3 * kSparseMax + 4 * (kChunk / 64 + 3) + 16 <= kSpBytes, "sparse stage bound");
 
 // Element q of a chunk sits at word raw_idx(q) of its buffer.  The 16-byte
 // groups are permuted inside every 128 bytes (XOR with bits 3..5 of the group
@@ -302,12 +303,15 @@ __device__ uint64_t look_back(uint64_t* flags, uint32_t unit, uint32_t first_uni
 struct ChunkMeta {
     uint32_t unit, job, total, dense;
     uint32_t pend[4];        // end of plane p's stream inside the chunk's output
+    uint32_t roff[4];        // sparse path: plane p's region in the stage
 };
 
 // Shared state of one compress CTA.
 struct CState {
     P4 wt_a[kT / 32], wt_b[kT / 32];
     uint32_t tk[3], tj[3];   // ticket ring: work unit and its job
+    uint4 wcnt[kT / 32];     // change counts per warp and plane
+    uint32_t ptot[4];        // sparse path: stream size per plane
     ChunkMeta meta[2];
     uint64_t off;
 };
@@ -319,94 +323,92 @@ __device__ __forceinline__ void publish(uint64_t* flags, uint32_t unit, uint32_t
     st_flag(flags + unit, (unit == first_unit ? kInc : kAgg) | (uint64_t)total);
 }
 
-// Sparse path: the chunk has few segments (maximal runs of one byte value in a
-// plane), listed by start position, planes one after another.  Each thread
-// takes kSegPerThread consecutive segments: runs of three or more become
-// repeat tokens, and the first short run of a literal span codes the span.
-// The output is at most 2 bytes per repeat segment plus 2 per 128 of its
-// length, and 3 bytes per short run, i.e. 3 * kSparseMax + 4 * kChunk / 64.
-// The stage may overlay the segment list: every list read precedes the scan.
-__device__ void sparse_chunk(const uint32_t* raw, const uint16_t* seg, uint8_t* stage, CState& S,
-                             ChunkMeta& M, const uint32_t nb[4], int len, bool sw,
-                             uint64_t* flags, uint32_t unit, uint32_t first_unit)
+// Bytes reserved for a plane stream of n segments on the sparse path: a
+// repeat segment of length L codes to 2 * ceil(L / 128) <= 2 + L / 64 bytes
+// and a literal span of k short runs to at most 3k bytes, so a plane codes
+// to at most 3n + kChunk / 64 bytes.
+__device__ __forceinline__ uint32_t sp_region(uint32_t n) { return (3u * n + kChunk / 64 + 3u) & ~3u; }
+
+// Sparse path, one warp per plane: the plane's segments (maximal runs of one
+// byte value) are listed by start position from the change masks, then coded
+// 32 at a time.  Runs of three or more become repeat tokens; the first short
+// run of a literal span walks to the span's end and codes the whole span.
+// Writes the stream to `out` and returns its size.
+__device__ uint32_t sparse_plane(int p, const uint32_t* raw, const uint16_t* chm, uint16_t* seg,
+                                 uint8_t* out, uint32_t n, int len, bool sw)
 {
-    const int tid = threadIdx.x;
-    const uint32_t nseg = nb[3];
-    // segment: start s (12 bits), length (13), plane (2), kind (1 repeat, 2 literal span)
-    uint32_t info[kSegPerThread], cost[kSegPerThread];
-    uint32_t mine = 0;
+    const int lane = threadIdx.x & 31;
+    // masks of threads 8l .. 8l+7 = positions 128l .. 128l+127, 32 per word
+    const uint4 mm = *reinterpret_cast<const uint4*>(chm + p * kT + 8 * lane);
+    const uint32_t c = __popc(mm.x) + __popc(mm.y) + __popc(mm.z) + __popc(mm.w);
+    uint32_t incl = c;
 #pragma unroll
-    for (int k = 0; k < kSegPerThread; ++k) {
-        const uint32_t i = kSegPerThread * tid + k;
-        info[k] = 0u;
-        cost[k] = 0u;
-        if (i < nseg) {
-            const uint32_t p = (i >= nb[0]) + (i >= nb[1]) + (i >= nb[2]);
-            const uint32_t pb = i >= nb[2] ? nb[2] : i >= nb[1] ? nb[1] : i >= nb[0] ? nb[0] : 0u;
-            const uint32_t pe = i >= nb[2] ? nb[3] : i >= nb[1] ? nb[2] : i >= nb[0] ? nb[1] : nb[0];
-            const int s = seg[i];
-            const int e = i + 1 < pe ? (int)seg[i + 1] : len;
-            const int L = e - s;
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+    }
+    uint32_t at = incl - c;
+    const uint32_t wd[4] = {mm.x, mm.y, mm.z, mm.w};
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+        for (uint32_t m = wd[k]; m; m &= m - 1u) seg[at++] = (uint16_t)(128 * lane + 32 * k + __ffs(m) - 1);
+    __syncwarp();
+
+    const int sh = 8 * p;
+    uint32_t carry = 0;
+    for (uint32_t r = 0; r < n; r += 32) {
+        const uint32_t i = r + lane;
+        uint32_t cost = 0, kind = 0;
+        int s = 0, L = 0;
+        if (i < n) {
+            s = seg[i];
+            const int e = i + 1 < n ? (int)seg[i + 1] : len;
+            L = e - s;
             if (L >= 3) {
-                info[k] = (uint32_t)s | ((uint32_t)L << 12) | (p << 25) | (1u << 27);
-                cost[k] = 2u * (uint32_t)((L + 127) >> 7);
-            } else if (i == pb || s - (int)seg[i - 1] >= 3) {
-                // first short run of a literal span: walk to the span's end
-                int end = e;
-                for (uint32_t j = i + 1; j < pe; ++j) {
-                    const int en = j + 1 < pe ? (int)seg[j + 1] : len;
+                kind = 1;
+                cost = 2u * (uint32_t)((L + 127) >> 7);
+            } else if (i == 0 || s - (int)seg[i - 1] >= 3) {
+                int end = e;                              // first short run: find the span's end
+                for (uint32_t j = i + 1; j < n; ++j) {
+                    const int en = j + 1 < n ? (int)seg[j + 1] : len;
                     if (en - end >= 3) break;
                     end = en;
                 }
-                const int Ls = end - s;
-                info[k] = (uint32_t)s | ((uint32_t)Ls << 12) | (p << 25) | (2u << 27);
-                cost[k] = (uint32_t)(Ls + ((Ls + 127) >> 7));
+                L = end - s;
+                kind = 2;
+                cost = (uint32_t)(L + ((L + 127) >> 7));
             }
-            mine += cost[k];
         }
-    }
-    P4 tot;
-    const P4 ex = block_scan<false>(P4{mine, 0u}, S.wt_b, &tot);   // (barrier inside)
-    const uint32_t total = tot.a;
-    if (tid == 0) {
-        publish(flags, unit, first_unit, total);
-        M.total = total;
-        M.dense = 0u;
-    }
-    uint32_t o = ex.a;
+        uint32_t inc = cost;
 #pragma unroll
-    for (int k = 0; k < kSegPerThread; ++k) {
-        const uint32_t i = kSegPerThread * tid + k;
-        const uint32_t kind = info[k] >> 27;
-        const uint32_t p = (info[k] >> 25) & 3u;
-        const int s = (int)(info[k] & 0xFFFu), L = (int)((info[k] >> 12) & 0x1FFFu);
-        const int sh = 8 * (int)p;
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= o) inc += y;
+        }
+        uint32_t o = carry + inc - cost;
+        carry += __shfl_sync(0xffffffffu, inc, 31);
         if (kind == 1u) {
             uint32_t e = raw[raw_idx(s)];
             if (sw) e = swizzle(e);
             const uint8_t v = (uint8_t)(e >> sh);
-            uint32_t oo = o;
-            for (int r = L; r > 0; r -= 128) {
-                stage[oo] = (uint8_t)(127 + min(r, 128));
-                stage[oo + 1] = v;
-                oo += 2;
+            for (int rr = L; rr > 0; rr -= 128) {
+                out[o] = (uint8_t)(127 + min(rr, 128));
+                out[o + 1] = v;
+                o += 2;
             }
         } else if (kind == 2u) {
-            uint32_t oo = o;
             for (int d = 0; d < L; d += 128) {
                 const int m = min(L - d, 128);
-                stage[oo++] = (uint8_t)(m - 1);
+                out[o++] = (uint8_t)(m - 1);
                 for (int t = 0; t < m; ++t) {
                     uint32_t e = raw[raw_idx(s + d + t)];
                     if (sw) e = swizzle(e);
-                    stage[oo++] = (uint8_t)(e >> sh);
+                    out[o++] = (uint8_t)(e >> sh);
                 }
             }
         }
-        o += cost[k];
-        if (i < nseg && (i + 1 == nb[0] || i + 1 == nb[1] || i + 1 == nb[2] || i + 1 == nb[3]))
-            M.pend[(i + 1 == nb[0]) ? 0 : (i + 1 == nb[1]) ? 1 : (i + 1 == nb[2]) ? 2 : 3] = o;
     }
+    return carry;
 }
 
 // Dense path: every position is classified with byte-SIMD bit masks on a
@@ -548,7 +550,7 @@ __device__ void dense_chunk(uint8_t* pl, CState& S, ChunkMeta& M, int len,
 // plane changes value, count the segments, then take the sparse or the dense
 // path.  `raw` holds the chunk's elements (raw_idx layout).
 __device__ void code_chunk(const RleJobDesc& jb, uint32_t unit, ChunkMeta& M, uint32_t* raw, uint8_t* sp,
-                           CState& S, uint64_t* flags)
+                           uint16_t* seg, uint16_t* chm, CState& S, uint64_t* flags)
 {
     const int tid = threadIdx.x;
     const uint32_t nc = jb.n_chunks;
@@ -587,30 +589,45 @@ __device__ void code_chunk(const RleJobDesc& jb, uint32_t unit, ChunkMeta& M, ui
         for (int p = 0; p < 4; ++p) CH[p] |= 1u;
     }
 
-    // 2. segment counts per plane
-    P4 tot;
-    const P4 ex = block_scan<false>(P4{(uint32_t)__popc(CH[0]) | ((uint32_t)__popc(CH[1]) << 16),
-                                       (uint32_t)__popc(CH[2]) | ((uint32_t)__popc(CH[3]) << 16)},
-                                    S.wt_a, &tot);
-    uint32_t nb[4];                                  // cumulative segment counts
-    nb[0] = lane16(tot, 0);
-    nb[1] = nb[0] + lane16(tot, 1);
-    nb[2] = nb[1] + lane16(tot, 2);
-    nb[3] = nb[2] + lane16(tot, 3);
-
-    if (nb[3] <= (uint32_t)kSparseMax) {
-        uint16_t* seg = reinterpret_cast<uint16_t*>(sp);
+    // 2. segment counts per plane; masks to shared memory for the sparse path
+    const int lane = tid & 31, warp = tid >> 5;
+    uint32_t wc[4];
 #pragma unroll
-        for (int p = 0; p < 4; ++p) {
-            uint32_t at = (p ? nb[p - 1] : 0u) + lane16(ex, p);
-            for (uint32_t m = CH[p]; m; m &= m - 1u) seg[at++] = (uint16_t)(P0 + __ffs(m) - 1);
+    for (int p = 0; p < 4; ++p) {
+        chm[p * kT + tid] = (uint16_t)CH[p];
+        wc[p] = __reduce_add_sync(0xffffffffu, (uint32_t)__popc(CH[p]));
+    }
+    if (lane == 0) S.wcnt[warp] = make_uint4(wc[0], wc[1], wc[2], wc[3]);
+    __syncthreads();                                 // (also: every thread has read its elements)
+    uint32_t n0 = 0, n1 = 0, n2 = 0, n3 = 0;
+#pragma unroll
+    for (int w = 0; w < kT / 32; ++w) {
+        const uint4 v = S.wcnt[w];
+        n0 += v.x; n1 += v.y; n2 += v.z; n3 += v.w;
+    }
+
+    if (n0 + n1 + n2 + n3 <= (uint32_t)kSparseMax) {
+        // plane p: segments at seg[lb_p ..), stream at sp + ro_p
+        const uint32_t r0 = 0, r1 = sp_region(n0), r2 = r1 + sp_region(n1), r3 = r2 + sp_region(n2);
+        if (warp < 4) {
+            const uint32_t np = warp == 0 ? n0 : warp == 1 ? n1 : warp == 2 ? n2 : n3;
+            const uint32_t lb = warp == 0 ? 0u : warp == 1 ? n0 : warp == 2 ? n0 + n1 : n0 + n1 + n2;
+            const uint32_t ro = warp == 0 ? r0 : warp == 1 ? r1 : warp == 2 ? r2 : r3;
+            const uint32_t t = sparse_plane(warp, raw, chm, seg + lb, sp + ro, np, len, sw);
+            if (lane == 0) S.ptot[warp] = t;
         }
         __syncthreads();
-        sparse_chunk(raw, seg, sp, S, M, nb, len, sw, flags, unit, jb.first_unit);
+        if (tid == 0) {
+            const uint32_t e0 = S.ptot[0], e1 = e0 + S.ptot[1], e2 = e1 + S.ptot[2], e3 = e2 + S.ptot[3];
+            publish(flags, unit, jb.first_unit, e3);
+            M.total = e3;
+            M.dense = 0u;
+            M.pend[0] = e0; M.pend[1] = e1; M.pend[2] = e2; M.pend[3] = e3;
+            M.roff[0] = r0; M.roff[1] = r1; M.roff[2] = r2; M.roff[3] = r3;
+        }
     } else {
         // plane-major copy, written over the element buffer
         uint8_t* pl = reinterpret_cast<uint8_t*>(raw);
-        __syncthreads();                              // every thread has read its elements
 #pragma unroll
         for (int k = 0; k < kPer / 4; ++k) {
             uint32_t a = e[4 * k], b = e[4 * k + 1], cc = e[4 * k + 2], d = e[4 * k + 3];
@@ -623,6 +640,30 @@ __device__ void code_chunk(const RleJobDesc& jb, uint32_t unit, ChunkMeta& M, ui
         }
         __syncthreads();
         dense_chunk(pl, S, M, len, flags, unit, jb.first_unit);
+    }
+}
+
+// Copy n stage bytes (src 4-byte aligned) to o, threads t, t+nt, ...: byte
+// stores up to o's first word boundary and after its last, word stores of
+// funnel-shifted stage words between.
+__device__ __forceinline__ void copy_out(uint8_t* o, const uint8_t* src, uint32_t n, uint32_t t, uint32_t nt)
+{
+    const uintptr_t a0 = reinterpret_cast<uintptr_t>(o), a1 = a0 + n;
+    const uintptr_t w0 = (a0 + 3) & ~(uintptr_t)3, w1 = a1 & ~(uintptr_t)3;
+    if (w0 >= w1) {
+        for (uint32_t i = t; i < n; i += nt) o[i] = src[i];
+        return;
+    }
+    const uint32_t head = (uint32_t)(w0 - a0), tail0 = (uint32_t)(w1 - a0);
+    if (t < head) o[t] = src[t];
+    for (uint32_t i = tail0 + t; i < n; i += nt) o[i] = src[i];
+    const uint32_t nw = (uint32_t)((w1 - w0) >> 2);
+    const uint32_t* s32 = reinterpret_cast<const uint32_t*>(src);
+    const uint32_t sh = 8u * head;
+    uint32_t* o32 = reinterpret_cast<uint32_t*>(w0);
+    for (uint32_t k = t; k < nw; k += nt) {
+        // bytes [head + 4k, head + 4k + 4), head < 4
+        o32[k] = __funnelshift_r(s32[k], s32[k + 1], sh);
     }
 }
 
@@ -651,22 +692,12 @@ __device__ void finish_chunk(const RleJobDesc& jb, const ChunkMeta& M, const uin
     __syncthreads();
     const uint64_t G = S.off;
     uint8_t* o = dst + 32 + 16ull * nc + G;
-    const uintptr_t a0 = reinterpret_cast<uintptr_t>(o), a1 = a0 + total;
-    const uintptr_t w0 = (a0 + 3) & ~(uintptr_t)3, w1 = a1 & ~(uintptr_t)3;
-    if (w0 >= w1) {
-        for (uint32_t i = tid; i < total; i += kT) o[i] = stage[i];
-    } else {
-        const uint32_t head = (uint32_t)(w0 - a0), tail0 = (uint32_t)(w1 - a0);
-        if ((uint32_t)tid < head) o[tid] = stage[tid];
-        for (uint32_t i = tail0 + tid; i < total; i += kT) o[i] = stage[i];
-        const uint32_t nw = (uint32_t)((w1 - w0) >> 2);
-        const uint32_t* s32 = reinterpret_cast<const uint32_t*>(stage);
-        const uint32_t sh = 8u * head;
-        uint32_t* o32 = reinterpret_cast<uint32_t*>(w0);
-        for (uint32_t k = tid; k < nw; k += kT) {
-            // stage bytes [head + 4k, head + 4k + 4), head < 4
-            o32[k] = __funnelshift_r(s32[k], s32[k + 1], sh);
-        }
+    if (M.dense) {
+        copy_out(o, stage, total, tid, kT);
+    } else if (tid < 128) {                           // one warp per plane
+        const int p = tid >> 5;
+        const uint32_t b = p ? M.pend[p - 1] : 0u;
+        copy_out(o + b, stage + M.roff[p], M.pend[p] - b, tid & 31, 32);
     }
     if (tid < 4) put_u32(dst + 32 + 16ull * c + 4u * tid, (uint32_t)(G + M.pend[tid]));
     if (tid == 0) {
@@ -690,8 +721,12 @@ k_rle_compress(const __grid_constant__ RleJobList<N> J, uint64_t* flags, uint32_
     __shared__ CState S;
     const int tid = threadIdx.x;
     const uint32_t T = J.total_units;
+    // dynamic shared memory: three element buffers, two sparse stages, the
+    // sparse segment list and the change masks
     auto rawb = [&](int j) { return reinterpret_cast<uint32_t*>(smem + (j % 3) * kRawBytes); };
     auto spb = [&](int j) { return smem + 3 * kRawBytes + (j & 1) * kSpBytes; };
+    uint16_t* seg = reinterpret_cast<uint16_t*>(smem + 3 * kRawBytes + 2 * kSpBytes);
+    uint16_t* chm = reinterpret_cast<uint16_t*>(smem + 3 * kRawBytes + 2 * kSpBytes + kSegBytes);
     auto take = [&](int slot) {                       // thread 0
         const uint32_t u = atomicAdd(ticket, 1u);
         S.tk[slot] = u;
@@ -712,7 +747,7 @@ k_rle_compress(const __grid_constant__ RleJobList<N> J, uint64_t* flags, uint32_
             ChunkMeta& M = S.meta[j & 1];
             const RleJobDesc& jb = J.j[S.tj[j % 3]];
             if (tid == 0) { M.unit = cur; M.job = S.tj[j % 3]; }
-            code_chunk(jb, cur, M, rawb(j), spb(j), S, flags);
+            code_chunk(jb, cur, M, rawb(j), spb(j), seg, chm, S, flags);
             __syncthreads();
         }
         if (prev != kNone) {
