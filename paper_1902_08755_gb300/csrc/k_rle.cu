@@ -839,59 +839,79 @@ k_rle_decompress(const __grid_constant__ RleJobList<N> J, uint32_t* status)
     const int len = (int)min((uint32_t)kChunk, n - q0);
     const uint8_t* payload = src + 32 + 16ull * nc;
 
-    // decode plane `warp`: windows of 32 stream bytes, one per lane.  A lane
-    // knows where a token starting at its byte would end (next) and how many
-    // bytes it would emit (olen); the real chain of token starts is followed
-    // with one shuffle per token, output positions come from a warp scan, and
-    // every token is expanded by the whole warp.
+    // decode plane `warp` in windows of 32 stream bytes, one per lane.  Lane
+    // l knows where a token starting at its byte would be followed by the
+    // next one; composing these jumps by doubling (5 levels) gives every lane
+    // t the start of the window's t-th token, so lanes hold tokens in order.
+    // A warp scan places them; each lane writes the unaligned head and tail
+    // bytes of its own repeat token, the whole warp the aligned body words of
+    // one token per store, and literal tokens are copied by the whole warp.
     {
         const int p = warp;
         const int in_end = (int)s_beg[p + 1];
         int cur = (int)s_beg[p], outp = 0, bad = 0;
         uint8_t* plane = planes[p];
+        uint32_t* p32 = reinterpret_cast<uint32_t*>(plane);
         while (cur < in_end) {
             const int i = cur + lane;
             const uint32_t b = i < in_end ? (uint32_t)__ldg(payload + i) : 0u;
             const uint32_t b1 = i + 1 < in_end ? (uint32_t)__ldg(payload + i + 1) : 0u;
-            const bool rep = b >= 128u;
-            const int next = rep ? i + 2 : i + 2 + (int)b;
-            const int olen = rep ? (int)b - 127 : (int)b + 1;
-            uint32_t starts = 0u;
-            int sl = 0;
-            while (sl < 32 && cur + sl < in_end) {
-                starts |= 1u << sl;
-                sl = __shfl_sync(0xffffffffu, next, sl) - cur;
+            int J = lane + (b >= 128u ? 2 : 2 + (int)b);   // next^(2^k), relative to cur
+            int pos = 0;                                   // start of token #lane
+#pragma unroll
+            for (int k = 0; k < 5; ++k) {
+                const int y = __shfl_sync(0xffffffffu, J, min(pos, 31));
+                if (((lane >> k) & 1) && pos < 32) pos = y;
+                if (k < 4) {
+                    const int z = __shfl_sync(0xffffffffu, J, min(J, 31));
+                    if (J < 32) J = z;
+                }
             }
-            const bool st = (starts >> lane) & 1u;
-            int incl = st ? olen : 0;
+            // tokens take >= 2 bytes: at most 16 start in the window, and the
+            // position after the last one (lane ntok) is exact
+            const bool valid = pos < min(32, in_end - cur);
+            const int ntok = __popc(__ballot_sync(0xffffffffu, valid));
+            const int sl = __shfl_sync(0xffffffffu, pos, ntok);
+            const int ps = min(pos, 31);
+            const uint32_t tb = __shfl_sync(0xffffffffu, b, ps);
+            const uint32_t tv = __shfl_sync(0xffffffffu, b1, ps);
+            const bool trep = tb >= 128u;
+            const int olen = valid ? (trep ? (int)tb - 127 : (int)tb + 1) : 0;
+            const int tnext = pos + (trep ? 2 : 2 + (int)tb);
+            int incl = olen;
 #pragma unroll
             for (int o = 1; o < 32; o <<= 1) {
                 const int y = __shfl_up_sync(0xffffffffu, incl, o);
                 if (lane >= o) incl += y;
             }
             const int total = __shfl_sync(0xffffffffu, incl, 31);
-            const int obeg = outp + incl - (st ? olen : 0);
-            if (__any_sync(0xffffffffu, st && (next > in_end || outp + incl > len))) {
+            const int o = outp + incl - olen;
+            if (__any_sync(0xffffffffu, valid && (cur + tnext > in_end || o + olen > len))) {
                 bad = 1;                                  // a token runs past its stream or chunk
                 break;
             }
-            // expand every token of the window with all 32 lanes
-            for (uint32_t m = starts; m; m &= m - 1u) {
-                const int l = __ffs(m) - 1;
-                const int o = __shfl_sync(0xffffffffu, obeg, l);
-                const int mlen = __shfl_sync(0xffffffffu, olen, l);
-                const bool r = __shfl_sync(0xffffffffu, (int)rep, l) != 0;
-                const int s0 = cur + l + 1;                  // first byte after the control
-                if (r) {
-                    const uint32_t v = __shfl_sync(0xffffffffu, b1, l);
-                    const int head = min(mlen, (4 - (o & 3)) & 3);
-                    const int body = (mlen - head) >> 2, tail = (mlen - head) & 3;
-                    if (lane < head) plane[o + lane] = (uint8_t)v;
-                    if (lane < body) reinterpret_cast<uint32_t*>(plane + o + head)[lane] = 0x01010101u * v;
-                    if (lane < tail) plane[o + head + 4 * body + lane] = (uint8_t)v;
-                } else {
-                    for (int k = lane; k < mlen; k += 32) plane[o + k] = __ldg(payload + s0 + k);
-                }
+            int head = 0, nw = 0;
+            if (valid && trep) {
+                head = min(olen, (4 - (o & 3)) & 3);
+                nw = (olen - head) >> 2;
+                const int tail = olen - head - 4 * nw;
+                for (int k = 0; k < head; ++k) plane[o + k] = (uint8_t)tv;
+                for (int k = 0; k < tail; ++k) plane[o + head + 4 * nw + k] = (uint8_t)tv;
+            }
+            const uint32_t pk = (uint32_t)((o + head) >> 2) | ((uint32_t)nw << 16);
+            const uint32_t wv = 0x01010101u * (tv & 0xFFu);
+            for (uint32_t m = __ballot_sync(0xffffffffu, nw > 0); m; m &= m - 1u) {
+                const int t = __ffs(m) - 1;
+                const uint32_t q = __shfl_sync(0xffffffffu, pk, t);
+                const uint32_t x = __shfl_sync(0xffffffffu, wv, t);
+                if ((uint32_t)lane < (q >> 16)) p32[(q & 0xFFFFu) + lane] = x;
+            }
+            for (uint32_t m = __ballot_sync(0xffffffffu, valid && !trep); m; m &= m - 1u) {
+                const int t = __ffs(m) - 1;
+                const int oo = __shfl_sync(0xffffffffu, o, t);
+                const int ml = __shfl_sync(0xffffffffu, olen, t);
+                const int s0 = cur + __shfl_sync(0xffffffffu, pos, t) + 1;   // after the control
+                for (int k = lane; k < ml; k += 32) plane[oo + k] = __ldg(payload + s0 + k);
             }
             outp += total;
             cur += sl;
@@ -905,34 +925,42 @@ k_rle_decompress(const __grid_constant__ RleJobList<N> J, uint32_t* status)
         return;
     }
 
-    // transpose planes back into elements; groups of four equal elements
-    // (each plane word one repeated byte) are un-swizzled once
+    // transpose planes back into elements, 16 per thread; groups of four
+    // equal elements (each plane word one repeated byte) are un-swizzled once
     uint32_t* dstp = reinterpret_cast<uint32_t*>(jb.dst);
     const uint32_t w = (uint32_t)jb.w;
     const bool sw = s_mode == 2;
     if (jb.vec) {
         const bool dense = jb.pitch == jb.w;
-        for (int g = tid; 4 * g < len; g += kDT) {
-            const uint32_t A = *reinterpret_cast<const uint32_t*>(&planes[0][4 * g]);
-            const uint32_t B = *reinterpret_cast<const uint32_t*>(&planes[1][4 * g]);
-            const uint32_t C = *reinterpret_cast<const uint32_t*>(&planes[2][4 * g]);
-            const uint32_t D = *reinterpret_cast<const uint32_t*>(&planes[3][4 * g]);
-            uint4 v;
-            if (A == bcast8(A) && B == bcast8(B) && C == bcast8(C) && D == bcast8(D)) {
-                uint32_t e = __byte_perm(__byte_perm(A, B, 0x0040), __byte_perm(C, D, 0x0040), 0x5410);
-                if (sw) e = swizzle(e);
-                v = make_uint4(e, e, e, e);
-            } else {
-                v = transpose4(A, B, C, D);                 // planes -> elements
-                if (sw) { v.x = swizzle(v.x); v.y = swizzle(v.y); v.z = swizzle(v.z); v.w = swizzle(v.w); }
+        for (int g16 = tid; 16 * g16 < len; g16 += kDT) {
+            const uint4 A = *reinterpret_cast<const uint4*>(&planes[0][16 * g16]);
+            const uint4 B = *reinterpret_cast<const uint4*>(&planes[1][16 * g16]);
+            const uint4 C = *reinterpret_cast<const uint4*>(&planes[2][16 * g16]);
+            const uint4 D = *reinterpret_cast<const uint4*>(&planes[3][16 * g16]);
+            const uint32_t a4[4] = {A.x, A.y, A.z, A.w}, b4[4] = {B.x, B.y, B.z, B.w};
+            const uint32_t c4[4] = {C.x, C.y, C.z, C.w}, d4[4] = {D.x, D.y, D.z, D.w};
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const int g = 4 * g16 + k;
+                if (4 * g >= len) break;
+                const uint32_t a = a4[k], bb = b4[k], c = c4[k], d = d4[k];
+                uint4 v;
+                if (a == bcast8(a) && bb == bcast8(bb) && c == bcast8(c) && d == bcast8(d)) {
+                    uint32_t e = __byte_perm(__byte_perm(a, bb, 0x0040), __byte_perm(c, d, 0x0040), 0x5410);
+                    if (sw) e = swizzle(e);
+                    v = make_uint4(e, e, e, e);
+                } else {
+                    v = transpose4(a, bb, c, d);              // planes -> elements
+                    if (sw) { v.x = swizzle(v.x); v.y = swizzle(v.y); v.z = swizzle(v.z); v.w = swizzle(v.w); }
+                }
+                const uint32_t q = q0 + 4u * g;
+                size_t e = q;
+                if (!dense) {
+                    const uint32_t y = q / w;
+                    e = (size_t)y * jb.pitch + (q - y * w);
+                }
+                st_stream(reinterpret_cast<uint4*>(dstp + e), v);
             }
-            const uint32_t q = q0 + 4u * g;
-            size_t e = q;
-            if (!dense) {
-                const uint32_t y = q / w;
-                e = (size_t)y * jb.pitch + (q - y * w);
-            }
-            st_stream(reinterpret_cast<uint4*>(dstp + e), v);
         }
     } else {
         for (int t = tid; t < len; t += kDT) {
