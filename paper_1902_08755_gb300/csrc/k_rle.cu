@@ -1,36 +1,38 @@
 // k_rle.cu -- run-length pixel codec kernels for sm_103a (thesis 5.5.1:
 // per-component RLE, bit-swizzle preconditioner, data decomposition).
 //
-// Compress: one CTA per 4096-element chunk, single pass over the input.
-//   1. 16-byte loads of the chunk into shared memory (swizzled in registers for
-//      mode 2).  The layout pads 4 words after every 32 so that each thread's
-//      16 consecutive words read back without bank conflicts.
-//   2. Each thread classifies its 16 positions for all four byte planes at once
-//      with byte-SIMD compares (one 32-bit word = the four planes of an
-//      element): a byte is part of a repeat iff one of the three windows of 3
-//      around it is constant, which needs only +-2 neighbours.
-//   3. Token boundaries need each position's offset inside its run or literal
-//      span (tokens hold at most 128 bytes): a block-wide max-scan of segment
-//      starts, two planes per word as 16-bit lanes (__vmaxu2).
-//   4. A block-wide sum-scan of per-position output sizes (again 16-bit lanes)
-//      gives every byte its output offset; bytes and control codes are
-//      scattered into a shared-memory stage.
-//   5. The chunk's offset inside the stream comes from a decoupled look-back
-//      over preceding chunks (chunk order from an atomic ticket, so every
-//      chunk waited on belongs to a CTA that is already running); every wait
-//      is bounded and records EC_ERR_TIMEOUT if it gives up.
-//   6. The stage is copied out with word stores; chunk 0 writes the header,
-//      every chunk its four end-table entries, the last chunk the size.
+// Compress: persistent CTAs (four per SM) take 4096-element chunks from an
+// atomic ticket and pipeline them: while chunk j+1 is copied in (cp.async),
+// chunk j is coded and its size published, then chunk j-1's offset is found
+// by a decoupled look-back and its bytes are copied out.
+//   1. Changes: every thread compares its 16 elements with their predecessors
+//      (one XOR per element; the swizzle is a bit permutation, so it commutes
+//      with the XOR) and records, per byte plane, which positions start a new
+//      run of equal bytes.
+//   2. Sparse path (at most 512 runs in the chunk, the common case for frames
+//      with flat regions): warp p lists plane p's run starts from the change
+//      masks with a warp scan and codes them 32 at a time: runs of three or
+//      more become repeat tokens, the first short run of a literal span codes
+//      the whole span; each plane is written to its own stage region.
+//   3. Dense path: each thread classifies its 16 positions for all four planes
+//      with byte-SIMD compares on a plane-major copy (a byte is part of a
+//      repeat iff one of the three windows of 3 around it is constant); a
+//      block max-scan of segment starts splits tokens at 128 bytes and a block
+//      sum-scan of per-position output sizes places every byte.
+//   4. The chunk's offset inside the stream comes from the look-back over the
+//      job's preceding chunks; a chunk waits only for lower tickets, which
+//      running CTAs code before any higher one, and every wait is bounded
+//      (EC_ERR_TIMEOUT).  Chunk 0 writes the header, every chunk its four
+//      end-table entries, the last chunk the stream size.
 //
 // Decompress: one CTA of four warps per chunk.  The header and the chunk's
 // end-table entries are fetched in one round trip and validated.  Warp p
-// decodes plane p in windows of 32 stream bytes, one byte per lane: each lane
-// computes where a token starting at its byte would end, the chain of real
-// token starts inside the window is followed with one shuffle per token
-// (instead of one dependent memory access per token), a warp scan gives each
-// token its output position, every token is checked against its stream and
-// chunk bounds, and the whole warp expands it (word stores for runs).  The
-// four planes are then transposed back into elements with byte permutes.
+// decodes plane p in windows of 32 stream bytes: the jump from each byte to
+// the token after one starting there is composed by doubling, so lane t holds
+// the window's t-th token; a warp scan places the tokens, each is checked
+// against its stream and chunk bounds, lanes write the unaligned ends of their
+// repeat tokens and the warp one token's aligned body per store.  The four
+// planes are then transposed back into elements with byte permutes.
 #include "ec_internal.cuh"
 
 #include <algorithm>
