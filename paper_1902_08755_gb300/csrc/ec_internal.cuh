@@ -123,7 +123,7 @@ cudaError_t launch_batch(const BatchJob* jobs, const SrcDesc* srcs, const BatchI
                          cudaStream_t s);
 
 // ---- launchers (defined in the kernel translation units) -------------------
-int alpha_bwd_chunk(int n, bool f16);
+
 cudaError_t launch_alpha_bwd(const BwdDesc* d, int n, bool f16, bool g16, bool fused,
                              const DstDesc& dst, const float* g, cudaStream_t s);
 cudaError_t launch_depth_bwd(const BwdDesc* d, int n, int W, int H, const int16_t* winner,

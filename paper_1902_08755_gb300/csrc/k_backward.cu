@@ -4,14 +4,20 @@
 // back recurrence C += T c_k, T *= (1 - a_k):
 //   dL/dc_k^{RGB} = g^{RGB} T_k,   dL/da_k = T_k (g^A - R_k),
 //   R_{n-1} = 0,  R_{k-1} = g.c_k + (1 - a_k) R_k      (reverse "behind" scan).
-// Nothing per layer is kept from the forward: a CTA stages the layer stack of
-// its 64-pixel row segment in shared memory with cp.async (16/8/4-byte copies,
-// zero-filled outside a layer's ROI, which is exactly a transparent layer),
-// runs the forward scan (recording T_k in shared memory), then the reverse
-// scan, and writes every layer's gradient.  Layers are read from HBM once.
-// Stacks larger than the shared-memory budget are processed in chunks: the
-// forward keeps T at each chunk start, and the reverse reloads the chunks in
-// reverse order (all but the last are then read twice).
+// Nothing per layer is kept from the forward.  A CTA owns 32 pixels (one per
+// lane) of kRows rows; its warps split the tile's layer stack into contiguous
+// segments of at most kMaxSeg layers.  A warp loads its layers' pixels
+// straight into registers (zero outside a layer's ROI, which is exactly a
+// transparent layer), runs its segment's forward, and keeps per layer only
+// T', g.c and a.  Both recurrences split exactly across segments:
+//   forward  T_k = T_start(s) * T'_k, T'_k the transmittance inside segment s,
+//            T_start(s) = prod over earlier segments of P_u = prod (1 - a);
+//   reverse  R entering segment s from behind = sum_{t>s} A_t prod_{s<u<t} P_u
+//            with A_t = sum_{j in t} T'_j (g.c_j), evaluated Horner-style,
+// so after one exchange of (P, A) through shared memory every warp runs the
+// exact reverse recurrence over its own layers and writes their gradients.
+// Layers are read from HBM once; per-layer tile records (addresses, clipped
+// ranges) are built once per CTA in shared memory and read as broadcasts.
 //
 // The fused variant takes the loss weights w up front (L = sum w * out, so
 // the upstream gradient is w) and also writes out and T_final.
@@ -25,24 +31,11 @@
 namespace ec {
 namespace {
 
-constexpr int kP = 64;            // pixels (= threads) per alpha-backward CTA
-constexpr int kMaxChunks = 16;
-
-__device__ __forceinline__ void cp_async(void* smem, const void* gmem, int bytes, int src_bytes)
-{
-    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
-    if (bytes == 16)
-        asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(s), "l"(gmem), "r"(src_bytes) : "memory");
-    else if (bytes == 8)
-        asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(s), "l"(gmem), "r"(src_bytes) : "memory");
-    else
-        asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(s), "l"(gmem), "r"(src_bytes) : "memory");
-}
-
-__device__ __forceinline__ void cp_async_wait_all()
-{
-    asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;" ::: "memory");
-}
+constexpr int kTP = 32;           // pixels per alpha-backward CTA (one per lane)
+constexpr int kRows = 4;          // rows per alpha-backward CTA
+constexpr int kMaxSeg = 8;        // layers per warp (segment)
+constexpr int kMaxWarps = 32;     // segments per CTA
+static_assert(kMaxSeg * kMaxWarps >= kMaxBwdLayers, "every stack fits one CTA");
 
 __device__ __forceinline__ float4 h4_to_f4(uint2 v)
 {
@@ -60,90 +53,63 @@ __device__ __forceinline__ uint2 f4_to_h4(float4 f)
     return v;
 }
 
-template <int N>
-__device__ __forceinline__ int active_grad_layers(const BwdList<N>& L, int tx0, int tx1, int y,
-                                                  int16_t* act, int* nact)
-{
-    const int lane = threadIdx.x & 31;
-    if (threadIdx.x < 32) {
-        int base = 0;
-        for (int i0 = 0; i0 < L.n; i0 += 32) {
-            const int i = i0 + lane;
-            bool hit = false;
-            if (i < L.n) {
-                const BwdDesc& d = L.d[i];
-                hit = d.gx0 < tx1 && d.gx1 > tx0 && d.gy0 <= y && d.gy1 > y;
-            }
-            const unsigned m = __ballot_sync(0xffffffffu, hit);
-            if (hit) act[base + __popc(m & ((1u << lane) - 1u))] = (int16_t)i;
-            base += __popc(m);
-        }
-        if (lane == 0) *nact = base;
-    }
-    __syncthreads();
-    return *nact;
-}
-
-// What a CTA needs of one layer for its 64-pixel row segment, built once per
-// CTA: addresses of the segment's first pixel in the colour and gradient
-// buffers (only offset by columns that lie inside the ROI / pvp before use)
-// and the clipped column ranges relative to the segment start.
-struct LayerTile {
-    uintptr_t src;          // colour address of pixel (tx0, y)
-    uintptr_t grad;         // gradient address of pixel (tx0, y)
-    int16_t rx0, rx1;       // ROI columns [rx0, rx1) (empty if row y is outside)
-    int16_t gx0, gx1;       // gradient columns [gx0, gx1) (empty if row y is outside)
+// What a CTA needs of one layer for its 32 x kRows tile, built once per CTA:
+// addresses of pixel (tx0, ty0) in the colour and gradient buffers (offset
+// only by rows and columns that lie inside the ROI / pvp before use), the
+// pitch, and the ROI and gradient ranges (columns relative to tx0).
+struct BandTile {
+    uintptr_t src;
+    uintptr_t grad;
+    int32_t pitch;
+    int32_t ry0, ry1, gy0, gy1;
+    int16_t rx0, rx1, gx0, gx1;
     int16_t cls, gvec;
-    int32_t pad;
 };
-static_assert(sizeof(LayerTile) == 32, "tile record");
+static_assert(sizeof(BandTile) == 48, "tile record");
 
 template <bool F16, bool G16>
-__device__ __forceinline__ LayerTile make_tile(const BwdDesc& d, int tx0, int y)
+__device__ __forceinline__ BandTile make_band_tile(const BwdDesc& d, int tx0, int ty0)
 {
     constexpr int S = F16 ? 8 : 16, GS = G16 ? 8 : 16;
-    LayerTile t;
-    const int64_t e = (int64_t)(y - d.oy) * d.pitch + (int64_t)(tx0 - d.ox);
+    BandTile t;
+    const int64_t e = (int64_t)(ty0 - d.oy) * d.pitch + (int64_t)(tx0 - d.ox);
     t.src = reinterpret_cast<uintptr_t>(d.color) + (uintptr_t)(e * S);
     t.grad = reinterpret_cast<uintptr_t>(d.grad) + (uintptr_t)(e * GS);
-    const bool rrow = y >= d.y0 && y < d.y1, grow = y >= d.gy0 && y < d.gy1;
-    t.rx0 = (int16_t)(rrow ? max(d.x0 - tx0, 0) : 0);
-    t.rx1 = (int16_t)(rrow ? min(d.x1 - tx0, kP) : 0);
-    t.gx0 = (int16_t)(grow ? max(d.gx0 - tx0, 0) : 0);
-    t.gx1 = (int16_t)(grow ? min(d.gx1 - tx0, kP) : 0);
+    t.pitch = d.pitch;
+    t.ry0 = d.y0; t.ry1 = d.y1;
+    t.gy0 = d.gy0; t.gy1 = d.gy1;
+    t.rx0 = (int16_t)max(min(d.x0 - tx0, kTP), 0);
+    t.rx1 = (int16_t)max(min(d.x1 - tx0, kTP), 0);
+    t.gx0 = (int16_t)max(min(d.gx0 - tx0, kTP), 0);
+    t.gx1 = (int16_t)max(min(d.gx1 - tx0, kTP), 0);
     t.cls = d.cls;
     t.gvec = d.gvec;
-    t.pad = 0;
     return t;
 }
 
-// Stage this thread's pixel of one layer into its slot (zero outside the ROI;
-// `dummy` is any valid global address, never read when zero-filling).
-template <bool F16>
-__device__ __forceinline__ void stage_px(uint8_t* slot, const LayerTile& t, int tid, const void* dummy)
+// One pixel of a layer as stored (FP16: 8 bytes, FP32: 16), read with the
+// widest loads its alignment class allows.
+template <bool F16> struct Px;
+template <> struct Px<true> { using T = uint2; };
+template <> struct Px<false> { using T = float4; };
+
+__device__ __forceinline__ uint2 load_px16(uintptr_t a, int cls)
 {
-    constexpr int S = F16 ? 8 : 16;
-    const bool in = tid >= t.rx0 && tid < t.rx1;
-    const uint8_t* src = in ? reinterpret_cast<const uint8_t*>(t.src) + tid * S
-                            : reinterpret_cast<const uint8_t*>(dummy);
-    if (t.cls >= S) {
-        cp_async(slot, src, S, in ? S : 0);
-    } else if (t.cls >= 4) {
-#pragma unroll
-        for (int o = 0; o < S; o += 4) cp_async(slot + o, in ? src + o : src, 4, in ? 4 : 0);
-    } else {                          // 2-byte aligned half data: synchronous copy
-        const unsigned short* h = reinterpret_cast<const unsigned short*>(src);
-        unsigned short* d = reinterpret_cast<unsigned short*>(slot);
-#pragma unroll
-        for (int o = 0; o < S / 2; ++o) d[o] = in ? h[o] : (unsigned short)0;
+    if (cls >= 8) return __ldcs(reinterpret_cast<const uint2*>(a));
+    if (cls >= 4) {
+        const uint32_t* p = reinterpret_cast<const uint32_t*>(a);
+        return make_uint2(__ldcs(p), __ldcs(p + 1));
     }
+    const unsigned short* h = reinterpret_cast<const unsigned short*>(a);
+    return make_uint2((uint32_t)__ldcs(h) | ((uint32_t)__ldcs(h + 1) << 16),
+                      (uint32_t)__ldcs(h + 2) | ((uint32_t)__ldcs(h + 3) << 16));
 }
 
-template <bool F16>
-__device__ __forceinline__ float4 read_slot(const uint8_t* slot)
+__device__ __forceinline__ float4 load_px32(uintptr_t a, int cls)
 {
-    if constexpr (F16) return h4_to_f4(*reinterpret_cast<const uint2*>(slot));
-    else return *reinterpret_cast<const float4*>(slot);
+    if (cls >= 16) return __ldcs(reinterpret_cast<const float4*>(a));
+    const float* f = reinterpret_cast<const float*>(a);
+    return make_float4(__ldcs(f), __ldcs(f + 1), __ldcs(f + 2), __ldcs(f + 3));
 }
 
 template <bool G16>
@@ -173,211 +139,145 @@ __device__ __forceinline__ void store_grad(const BwdDesc& d, int x, int y, float
     store_grad_at<G16>(a, d.gvec != 0, v);
 }
 
+// Alpha backward (and fused forward + backward) for one 32 x kRows tile.
+// blockDim.x = 32 * NS: warp s owns segment s of the tile's active layers.
 template <int N, bool F16, bool G16, bool FUSED>
-__global__ void __launch_bounds__(kP)
+__global__ void __launch_bounds__(kTP * kMaxWarps, 1)
 k_alpha_bwd(const __grid_constant__ BwdList<N> L, const __grid_constant__ DstDesc D,
-            const float4* __restrict__ g, int chunk)
+            const float4* __restrict__ g, int cap)
 {
     constexpr int S = F16 ? 8 : 16, GS = G16 ? 8 : 16;
+    using RawPx = typename Px<F16>::T;
     extern __shared__ __align__(16) uint8_t smem[];
     __shared__ int16_t act[N];
-    __shared__ LayerTile tiles[N];
     __shared__ int nact_s;
-    __shared__ float Tc[kMaxChunks][kP];
-    uint8_t* stage = smem;                                             // [chunk][kP][S]
-    float* Ts = reinterpret_cast<float*>(smem + (size_t)chunk * kP * S);  // [chunk][kP]
+    BandTile* tiles = reinterpret_cast<BandTile*>(smem);                    // [cap]
+    const int NS = (int)(blockDim.x / kTP);
+    float* Ps = reinterpret_cast<float*>(smem + (size_t)cap * sizeof(BandTile));   // [NS][32]
+    float* As = Ps + NS * kTP;                                                       // [NS][32]
+    float4* Cs = reinterpret_cast<float4*>(As + NS * kTP);                           // [NS][32] (fused)
 
-    const int tid = threadIdx.x;
-    const int tx0 = blockIdx.x * kP, y = blockIdx.y;
-    const int nact = active_grad_layers(L, tx0, min(tx0 + kP, D.W), y, act, &nact_s);
-    for (int k = tid; k < nact; k += kP) tiles[k] = make_tile<F16, G16>(L.d[act[k]], tx0, y);
+    const int p = threadIdx.x & (kTP - 1), sg = threadIdx.x / kTP;
+    const int tx0 = blockIdx.x * kTP, ty0 = blockIdx.y * kRows;
+    const int tx1 = min(tx0 + kTP, D.W), ty1 = min(ty0 + kRows, D.H);
+
+    // layers whose gradient rectangle meets the tile, in compositing order
+    if (threadIdx.x < 32) {
+        int base = 0;
+        for (int i0 = 0; i0 < L.n; i0 += 32) {
+            const int i = i0 + p;
+            bool hit = false;
+            if (i < L.n) {
+                const BwdDesc& d = L.d[i];
+                hit = d.gx0 < tx1 && d.gx1 > tx0 && d.gy0 < ty1 && d.gy1 > ty0;
+            }
+            const unsigned m = __ballot_sync(0xffffffffu, hit);
+            if (hit) act[base + __popc(m & ((1u << p) - 1u))] = (int16_t)i;
+            base += __popc(m);
+        }
+        if (p == 0) nact_s = base;
+    }
     __syncthreads();
-    const int x = tx0 + tid;
-    if (x >= D.W) return;                      // no block-wide barrier follows
-
-    const float4* gpix = g + (size_t)y * D.W + x;
-    const float4 gp = __ldcs(gpix);
-    const int nchunks = (nact + chunk - 1) / chunk;
-    float T = 1.0f;
-    float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
-    uint8_t* myslot = stage + (size_t)tid * S;
-    float* myT = Ts + tid;
-
-    // forward: T_k for every layer, and (fused) the composite
-    for (int ch = 0; ch < nchunks; ++ch) {
-        const int k0 = ch * chunk, k1 = min(nact, k0 + chunk);
-        asm volatile("" ::: "memory");        // reads of the previous chunk come first
-        for (int k = k0; k < k1; ++k) stage_px<F16>(myslot + (size_t)(k - k0) * kP * S, tiles[k], tid, gpix);
-        cp_async_wait_all();
-        Tc[ch][tid] = T;
-#pragma unroll 4
-        for (int k = k0; k < k1; ++k) {
-            const float4 c = read_slot<F16>(myslot + (size_t)(k - k0) * kP * S);
-            myT[(k - k0) * kP] = T;
-            if (FUSED) {
-                acc.x = fmaf(T, c.x, acc.x);
-                acc.y = fmaf(T, c.y, acc.y);
-                acc.z = fmaf(T, c.z, acc.z);
-                acc.w = fmaf(T, c.w, acc.w);
-            }
-            T = fmaf(-T, c.w, T);
-        }
-    }
-    if (FUSED) {
-        const size_t o = (size_t)y * (size_t)D.pitch + (size_t)x;
-        if constexpr (F16) {
-            const uint2 h = f4_to_h4(acc);
-            unsigned short* hp = reinterpret_cast<unsigned short*>(reinterpret_cast<uint2*>(D.color) + o);
-            if (D.vec) __stcs(reinterpret_cast<uint2*>(hp), h);
-            else { hp[0] = (unsigned short)h.x; hp[1] = (unsigned short)(h.x >> 16); hp[2] = (unsigned short)h.y; hp[3] = (unsigned short)(h.y >> 16); }
-        } else {
-            float4* op = reinterpret_cast<float4*>(D.color) + o;
-            if (D.vec) __stcs(op, acc);
-            else { float* f = reinterpret_cast<float*>(op); f[0] = acc.x; f[1] = acc.y; f[2] = acc.z; f[3] = acc.w; }
-        }
-        if (D.tfinal) D.tfinal[(size_t)y * D.W + x] = T;
-    }
-
-    // reverse: R_k and the gradients, back to front
-    float R = 0.0f;
-    for (int ch = nchunks - 1; ch >= 0; --ch) {
-        const int k0 = ch * chunk, k1 = min(nact, k0 + chunk);
-        if (ch != nchunks - 1) {               // reload and recompute T inside the chunk
-            asm volatile("" ::: "memory");
-            for (int k = k0; k < k1; ++k) stage_px<F16>(myslot + (size_t)(k - k0) * kP * S, tiles[k], tid, gpix);
-            cp_async_wait_all();
-            float t = Tc[ch][tid];
-            for (int k = k0; k < k1; ++k) {
-                const float4 c = read_slot<F16>(myslot + (size_t)(k - k0) * kP * S);
-                myT[(k - k0) * kP] = t;
-                t = fmaf(-t, c.w, t);
-            }
-        }
-#pragma unroll 4
-        for (int k = k1 - 1; k >= k0; --k) {
-            const LayerTile& t = tiles[k];
-            const float4 c = read_slot<F16>(myslot + (size_t)(k - k0) * kP * S);
-            const float Tk = myT[(k - k0) * kP];
-            if (tid >= t.gx0 && tid < t.gx1) {
-                const bool in = tid >= t.rx0 && tid < t.rx1;
-                const float4 gr = in ? make_float4(gp.x * Tk, gp.y * Tk, gp.z * Tk, Tk * (gp.w - R))
-                                     : make_float4(0.f, 0.f, 0.f, 0.f);
-                store_grad_at<G16>(t.grad + (uintptr_t)tid * GS, t.gvec != 0, gr);
-            }
-            const float gc = fmaf(gp.x, c.x, fmaf(gp.y, c.y, fmaf(gp.z, c.z, gp.w * c.w)));
-            R = fmaf(1.0f - c.w, R, gc);
-        }
-    }
-}
-
-// Segmented variant for stacks that fit in shared memory: NS threads share a
-// pixel, each owning a contiguous segment of its layers (threads p, p+64, ...
-// of the CTA).  Both recurrences split exactly across segments:
-//   forward  T_k = T_start(s) * T'_k, T'_k the transmittance inside segment s,
-//            T_start(s) = prod over earlier segments of P_u = prod (1 - a);
-//   reverse  R entering segment s from behind = sum_{t>s} A_t prod_{s<u<t} P_u
-//            with A_t = sum_{j in t} T'_j (g.c_j), evaluated Horner-style,
-// after which every segment runs the exact reverse recurrence over its own
-// layers.  NS times more threads per pixel hide the shared-memory latency
-// that a one-thread-per-pixel scan exposes at this occupancy.
-template <int N, bool F16, bool G16, bool FUSED, int NS>
-__global__ void __launch_bounds__(kP * NS)
-k_alpha_bwd_seg(const __grid_constant__ BwdList<N> L, const __grid_constant__ DstDesc D,
-                const float4* __restrict__ g, int cap)
-{
-    constexpr int S = F16 ? 8 : 16, GS = G16 ? 8 : 16;
-    extern __shared__ __align__(16) uint8_t smem[];
-    __shared__ int16_t act[N];
-    __shared__ LayerTile tiles[N];
-    __shared__ int nact_s;
-    __shared__ float Pseg[NS][kP], Aseg[NS][kP];
-    __shared__ float4 Cseg[FUSED ? NS : 1][kP];
-    uint8_t* stage = smem;                                          // [cap][kP][S]
-    float* Tl = reinterpret_cast<float*>(smem + (size_t)cap * kP * S);  // [cap][kP]
-
-    const int tid = threadIdx.x, p = tid % kP, sg = tid / kP;
-    const int tx0 = blockIdx.x * kP, y = blockIdx.y;
-    const int nact = active_grad_layers(L, tx0, min(tx0 + kP, D.W), y, act, &nact_s);
-    for (int k = tid; k < nact; k += kP * NS) tiles[k] = make_tile<F16, G16>(L.d[act[k]], tx0, y);
+    const int nact = nact_s;
+    for (int k = threadIdx.x; k < nact; k += blockDim.x) tiles[k] = make_band_tile<F16, G16>(L.d[act[k]], tx0, ty0);
     __syncthreads();
+
+    const int k0 = (sg * nact) / NS, cnt = ((sg + 1) * nact) / NS - k0;   // cnt <= kMaxSeg
     const int x = tx0 + p;
-    const bool valid = x < D.W;                // every thread reaches the barrier below
-    const int k0 = (sg * nact) / NS, k1 = ((sg + 1) * nact) / NS;
-    const float4* gpix = g + (size_t)y * D.W + (valid ? x : 0);
-    const float4 gp = valid ? __ldcs(gpix) : make_float4(0.f, 0.f, 0.f, 0.f);
-    uint8_t* myslot = stage + (size_t)p * S;
-    float* myT = Tl + p;
-
-    // local forward over this segment
-    if (valid)
-        for (int k = k0; k < k1; ++k) stage_px<F16>(myslot + (size_t)k * kP * S, tiles[k], p, gpix);
-    cp_async_wait_all();
-    float Tp = 1.0f, A = 0.0f;
-    float4 Cl = make_float4(0.f, 0.f, 0.f, 0.f);
-#pragma unroll 4
-    for (int k = k0; k < k1; ++k) {
-        const float4 c = valid ? read_slot<F16>(myslot + (size_t)k * kP * S) : make_float4(0.f, 0.f, 0.f, 0.f);
-        myT[k * kP] = Tp;
-        if (FUSED) {
-            Cl.x = fmaf(Tp, c.x, Cl.x);
-            Cl.y = fmaf(Tp, c.y, Cl.y);
-            Cl.z = fmaf(Tp, c.z, Cl.z);
-            Cl.w = fmaf(Tp, c.w, Cl.w);
+    const bool valid = x < D.W;
+    for (int y = ty0; y < ty1; ++y) {
+        const float4 gp = valid ? __ldcs(g + (size_t)y * D.W + x) : make_float4(0.f, 0.f, 0.f, 0.f);
+        // this segment's pixels, all loads in flight before any is used
+        RawPx raw[kMaxSeg];
+#pragma unroll
+        for (int j = 0; j < kMaxSeg; ++j) {
+            if constexpr (F16) raw[j] = make_uint2(0u, 0u);
+            else raw[j] = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (j < cnt) {
+                const BandTile& t = tiles[k0 + j];
+                if (valid && y >= t.ry0 && y < t.ry1 && p >= t.rx0 && p < t.rx1) {
+                    const uintptr_t a = t.src + (uintptr_t)(((int64_t)(y - ty0) * t.pitch + p) * S);
+                    if constexpr (F16) raw[j] = load_px16(a, t.cls);
+                    else raw[j] = load_px32(a, t.cls);
+                }
+            }
         }
-        const float gc = fmaf(gp.x, c.x, fmaf(gp.y, c.y, fmaf(gp.z, c.z, gp.w * c.w)));
-        A = fmaf(Tp, gc, A);
-        Tp = fmaf(-Tp, c.w, Tp);
-    }
-    Pseg[sg][p] = Tp;
-    Aseg[sg][p] = A;
-    if (FUSED) Cseg[sg][p] = Cl;
-    __syncthreads();
-    if (!valid) return;
-
-    float Tstart = 1.0f;
-    for (int u = 0; u < sg; ++u) Tstart *= Pseg[u][p];
-    float R = 0.0f;
-    for (int t = NS - 1; t > sg; --t) R = fmaf(Pseg[t][p], R, Aseg[t][p]);
-
-    if (FUSED && sg == 0) {
-        float Tacc = 1.0f;
-        float4 out = make_float4(0.f, 0.f, 0.f, 0.f);
-        for (int u = 0; u < NS; ++u) {
-            const float4 c = Cseg[u][p];
-            out.x = fmaf(Tacc, c.x, out.x);
-            out.y = fmaf(Tacc, c.y, out.y);
-            out.z = fmaf(Tacc, c.z, out.z);
-            out.w = fmaf(Tacc, c.w, out.w);
-            Tacc *= Pseg[u][p];
+        // local forward; keep T', g.c and a per layer
+        float Tl[kMaxSeg], gcl[kMaxSeg], al[kMaxSeg];
+        float Tp = 1.0f, A = 0.0f;
+        float4 Cl = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+        for (int j = 0; j < kMaxSeg; ++j) {
+            float4 c;
+            if constexpr (F16) c = h4_to_f4(raw[j]);
+            else c = raw[j];
+            const float gc = fmaf(gp.x, c.x, fmaf(gp.y, c.y, fmaf(gp.z, c.z, gp.w * c.w)));
+            Tl[j] = Tp;
+            gcl[j] = gc;
+            al[j] = c.w;
+            if (j < cnt) {
+                if (FUSED) {
+                    Cl.x = fmaf(Tp, c.x, Cl.x);
+                    Cl.y = fmaf(Tp, c.y, Cl.y);
+                    Cl.z = fmaf(Tp, c.z, Cl.z);
+                    Cl.w = fmaf(Tp, c.w, Cl.w);
+                }
+                A = fmaf(Tp, gc, A);
+                Tp = fmaf(-Tp, c.w, Tp);
+            }
         }
-        const size_t o = (size_t)y * (size_t)D.pitch + (size_t)x;
-        if constexpr (F16) {
-            const uint2 h = f4_to_h4(out);
-            unsigned short* hp = reinterpret_cast<unsigned short*>(reinterpret_cast<uint2*>(D.color) + o);
-            if (D.vec) __stcs(reinterpret_cast<uint2*>(hp), h);
-            else { hp[0] = (unsigned short)h.x; hp[1] = (unsigned short)(h.x >> 16); hp[2] = (unsigned short)h.y; hp[3] = (unsigned short)(h.y >> 16); }
-        } else {
-            float4* op = reinterpret_cast<float4*>(D.color) + o;
-            if (D.vec) __stcs(op, out);
-            else { float* f = reinterpret_cast<float*>(op); f[0] = out.x; f[1] = out.y; f[2] = out.z; f[3] = out.w; }
-        }
-        if (D.tfinal) D.tfinal[(size_t)y * D.W + x] = Tacc;
-    }
+        Ps[sg * kTP + p] = Tp;
+        As[sg * kTP + p] = A;
+        if (FUSED) Cs[sg * kTP + p] = Cl;
+        __syncthreads();
 
-    // reverse over this segment, entering with the R of the layers behind it
-#pragma unroll 4
-    for (int k = k1 - 1; k >= k0; --k) {
-        const LayerTile& t = tiles[k];
-        const float4 c = read_slot<F16>(myslot + (size_t)k * kP * S);
-        const float Tk = Tstart * myT[k * kP];
-        if (p >= t.gx0 && p < t.gx1) {
-            const bool in = p >= t.rx0 && p < t.rx1;
-            const float4 gr = in ? make_float4(gp.x * Tk, gp.y * Tk, gp.z * Tk, Tk * (gp.w - R))
-                                 : make_float4(0.f, 0.f, 0.f, 0.f);
-            store_grad_at<G16>(t.grad + (uintptr_t)p * GS, t.gvec != 0, gr);
+        float Tstart = 1.0f;
+        for (int u = 0; u < sg; ++u) Tstart *= Ps[u * kTP + p];
+        float R = 0.0f;
+        for (int u = NS - 1; u > sg; --u) R = fmaf(Ps[u * kTP + p], R, As[u * kTP + p]);
+
+        if (FUSED && sg == 0 && valid) {
+            float Tacc = 1.0f;
+            float4 out = make_float4(0.f, 0.f, 0.f, 0.f);
+            for (int u = 0; u < NS; ++u) {
+                const float4 c = Cs[u * kTP + p];
+                out.x = fmaf(Tacc, c.x, out.x);
+                out.y = fmaf(Tacc, c.y, out.y);
+                out.z = fmaf(Tacc, c.z, out.z);
+                out.w = fmaf(Tacc, c.w, out.w);
+                Tacc *= Ps[u * kTP + p];
+            }
+            const size_t o = (size_t)y * (size_t)D.pitch + (size_t)x;
+            if constexpr (F16) {
+                const uint2 h = f4_to_h4(out);
+                unsigned short* hp = reinterpret_cast<unsigned short*>(reinterpret_cast<uint2*>(D.color) + o);
+                if (D.vec) __stcs(reinterpret_cast<uint2*>(hp), h);
+                else { hp[0] = (unsigned short)h.x; hp[1] = (unsigned short)(h.x >> 16); hp[2] = (unsigned short)h.y; hp[3] = (unsigned short)(h.y >> 16); }
+            } else {
+                float4* op = reinterpret_cast<float4*>(D.color) + o;
+                if (D.vec) __stcs(op, out);
+                else { float* f = reinterpret_cast<float*>(op); f[0] = out.x; f[1] = out.y; f[2] = out.z; f[3] = out.w; }
+            }
+            if (D.tfinal) D.tfinal[(size_t)y * D.W + x] = Tacc;
         }
-        const float gc = fmaf(gp.x, c.x, fmaf(gp.y, c.y, fmaf(gp.z, c.z, gp.w * c.w)));
-        R = fmaf(1.0f - c.w, R, gc);
+
+        // reverse over this segment, entering with the R of the layers behind it
+#pragma unroll
+        for (int j = kMaxSeg - 1; j >= 0; --j) {
+            if (j < cnt) {
+                const BandTile& t = tiles[k0 + j];
+                if (valid && y >= t.gy0 && y < t.gy1 && p >= t.gx0 && p < t.gx1) {
+                    const float Tk = Tstart * Tl[j];
+                    const bool in = y >= t.ry0 && y < t.ry1 && p >= t.rx0 && p < t.rx1;
+                    const float4 gr = in ? make_float4(gp.x * Tk, gp.y * Tk, gp.z * Tk, Tk * (gp.w - R))
+                                         : make_float4(0.f, 0.f, 0.f, 0.f);
+                    store_grad_at<G16>(t.grad + (uintptr_t)(((int64_t)(y - ty0) * t.pitch + p) * GS),
+                                       t.gvec != 0, gr);
+                }
+                R = fmaf(1.0f - al[j], R, gcl[j]);
+            }
+        }
+        __syncthreads();                      // Ps / As / Cs are rewritten for the next row
     }
 }
 
@@ -444,76 +344,55 @@ BwdList<N> make_bwd(const BwdDesc* d, int n)
     return L;
 }
 
-template <int N, bool F16, bool G16, bool FUSED, int NS>
-cudaError_t alpha_bwd_seg_n(const BwdDesc* d, int n, const DstDesc& D, const float4* g,
-                            cudaStream_t s)
+// Warps (segments) per alpha-backward CTA for a stack of n layers: enough for
+// kMaxSeg layers each, and at least four (or n) so that short stacks still
+// split their scans.
+int alpha_bwd_warps(int n)
 {
-    const int cap = std::max(n, 1);
-    const size_t smem = (size_t)cap * kP * ((F16 ? 8 : 16) + 4);
-    auto kern = k_alpha_bwd_seg<N, F16, G16, FUSED, NS>;
-    // static + dynamic shared memory may pass the default 48 KB window
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    const dim3 grid(ceil_div(D.W, kP), D.H);
-    kern<<<grid, kP * NS, smem, s>>>(make_bwd<N>(d, n), D, g, cap);
-    return cudaGetLastError();
+    const int need = (n + kMaxSeg - 1) / kMaxSeg;
+    return std::max(1, std::min(kMaxWarps, std::max(need, std::min(n, 4))));
 }
 
 template <int N, bool F16, bool G16, bool FUSED>
-cudaError_t alpha_bwd_n(const BwdDesc* d, int n, const DstDesc& D, const float4* g, int chunk,
-                        cudaStream_t s)
+cudaError_t alpha_bwd_n(const BwdDesc* d, int n, const DstDesc& D, const float4* g, cudaStream_t s)
 {
-    if (chunk >= n) {                          // whole stack fits: segmented kernel
-        if (n >= 32) return alpha_bwd_seg_n<N, F16, G16, FUSED, 8>(d, n, D, g, s);
-        if (n >= 16) return alpha_bwd_seg_n<N, F16, G16, FUSED, 4>(d, n, D, g, s);
-        if (n >= 8) return alpha_bwd_seg_n<N, F16, G16, FUSED, 2>(d, n, D, g, s);
-        return alpha_bwd_seg_n<N, F16, G16, FUSED, 1>(d, n, D, g, s);
-    }
-    const size_t smem = (size_t)chunk * kP * ((F16 ? 8 : 16) + 4);
+    const int ns = alpha_bwd_warps(n), cap = std::max(n, 1);
+    const size_t smem = (size_t)cap * sizeof(BandTile) + (size_t)ns * kTP * (8 + (FUSED ? 16 : 0));
     auto kern = k_alpha_bwd<N, F16, G16, FUSED>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    const dim3 grid(ceil_div(D.W, kP), D.H);
-    kern<<<grid, kP, smem, s>>>(make_bwd<N>(d, n), D, g, chunk);
+    const dim3 grid(ceil_div(D.W, kTP), ceil_div(D.H, kRows));
+    kern<<<grid, kTP * ns, smem, s>>>(make_bwd<N>(d, n), D, g, cap);
     return cudaGetLastError();
 }
 
 template <int N>
 cudaError_t alpha_bwd_dispatch(const BwdDesc* d, int n, bool f16, bool g16, bool fused,
-                               const DstDesc& D, const float4* g, int chunk, cudaStream_t s)
+                               const DstDesc& D, const float4* g, cudaStream_t s)
 {
     if (f16) {
-        if (g16) return fused ? alpha_bwd_n<N, true, true, true>(d, n, D, g, chunk, s)
-                              : alpha_bwd_n<N, true, true, false>(d, n, D, g, chunk, s);
-        return fused ? alpha_bwd_n<N, true, false, true>(d, n, D, g, chunk, s)
-                     : alpha_bwd_n<N, true, false, false>(d, n, D, g, chunk, s);
+        if (g16) return fused ? alpha_bwd_n<N, true, true, true>(d, n, D, g, s)
+                              : alpha_bwd_n<N, true, true, false>(d, n, D, g, s);
+        return fused ? alpha_bwd_n<N, true, false, true>(d, n, D, g, s)
+                     : alpha_bwd_n<N, true, false, false>(d, n, D, g, s);
     }
-    if (g16) return fused ? alpha_bwd_n<N, false, true, true>(d, n, D, g, chunk, s)
-                          : alpha_bwd_n<N, false, true, false>(d, n, D, g, chunk, s);
-    return fused ? alpha_bwd_n<N, false, false, true>(d, n, D, g, chunk, s)
-                 : alpha_bwd_n<N, false, false, false>(d, n, D, g, chunk, s);
+    if (g16) return fused ? alpha_bwd_n<N, false, true, true>(d, n, D, g, s)
+                          : alpha_bwd_n<N, false, true, false>(d, n, D, g, s);
+    return fused ? alpha_bwd_n<N, false, false, true>(d, n, D, g, s)
+                 : alpha_bwd_n<N, false, false, false>(d, n, D, g, s);
 }
 
 }  // namespace
-
-int alpha_bwd_chunk(int n, bool f16)
-{
-    // shared-memory budget per CTA: ~96 KB leaves room for two CTAs per SM
-    const int per_layer = kP * ((f16 ? 8 : 16) + 4);
-    const int cap = (100 * 1024) / per_layer;
-    const int need = (n + kMaxChunks - 1) / kMaxChunks;
-    return std::max(1, std::max(std::min(n, cap), need));
-}
 
 cudaError_t launch_alpha_bwd(const BwdDesc* d, int n, bool f16, bool g16, bool fused,
                              const DstDesc& D, const float* g, cudaStream_t s)
 {
     if (D.W <= 0 || D.H <= 0) return cudaSuccess;
-    const int chunk = alpha_bwd_chunk(n, f16);
+    if (n > kMaxBwdLayers) return cudaErrorInvalidValue;
     const float4* g4 = reinterpret_cast<const float4*>(g);
-    if (n <= 16) return alpha_bwd_dispatch<16>(d, n, f16, g16, fused, D, g4, chunk, s);
-    if (n <= 64) return alpha_bwd_dispatch<64>(d, n, f16, g16, fused, D, g4, chunk, s);
-    return alpha_bwd_dispatch<kMaxBwdLayers>(d, n, f16, g16, fused, D, g4, chunk, s);
+    if (n <= 16) return alpha_bwd_dispatch<16>(d, n, f16, g16, fused, D, g4, s);
+    if (n <= 64) return alpha_bwd_dispatch<64>(d, n, f16, g16, fused, D, g4, s);
+    return alpha_bwd_dispatch<kMaxBwdLayers>(d, n, f16, g16, fused, D, g4, s);
 }
 
 cudaError_t launch_depth_bwd(const BwdDesc* d, int n, int W, int H, const int16_t* winner,
