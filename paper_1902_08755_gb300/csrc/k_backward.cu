@@ -4,12 +4,14 @@
 // back recurrence C += T c_k, T *= (1 - a_k):
 //   dL/dc_k^{RGB} = g^{RGB} T_k,   dL/da_k = T_k (g^A - R_k),
 //   R_{n-1} = 0,  R_{k-1} = g.c_k + (1 - a_k) R_k      (reverse "behind" scan).
-// Nothing per layer is kept from the forward.  A CTA owns 32 pixels (one per
-// lane) of kRows rows; its warps split the tile's layer stack into contiguous
-// segments of at most kMaxSeg layers.  A warp loads its layers' pixels
-// straight into registers (zero outside a layer's ROI, which is exactly a
-// transparent layer), runs its segment's forward, and keeps per layer only
-// T', g.c and a.  Both recurrences split exactly across segments:
+// Nothing per layer is kept from the forward.  A CTA owns a tile of 32 lanes
+// by kRows rows (FP16 stacks of up to 64 layers: two adjacent pixels per lane,
+// read and written as one 16-byte word where aligned; otherwise one pixel per
+// lane); its warps split the tile's layer stack into contiguous segments of
+// at most 4 (two pixels per lane) or 8 layers.  A warp loads its layers'
+// pixels straight into registers (zero outside a layer's ROI, which is
+// exactly a transparent layer), runs its segment's forward, and keeps per
+// layer only T', g.c and a.  Both recurrences split exactly across segments:
 //   forward  T_k = T_start(s) * T'_k, T'_k the transmittance inside segment s,
 //            T_start(s) = prod over earlier segments of P_u = prod (1 - a);
 //   reverse  R entering segment s from behind = sum_{t>s} A_t prod_{s<u<t} P_u
@@ -25,17 +27,16 @@
 // Depth compositing (thesis 5.2.1) copies the winner's colour, so its
 // gradient routes grad_out to the winning input and writes zero elsewhere.
 #include <algorithm>
+#include <type_traits>
 
 #include "ec_internal.cuh"
 
 namespace ec {
 namespace {
 
-constexpr int kTP = 32;           // pixels per alpha-backward CTA (one per lane)
-constexpr int kRows = 4;          // rows per alpha-backward CTA
-constexpr int kMaxSeg = 8;        // layers per warp (segment)
-constexpr int kMaxWarps = 32;     // segments per CTA
-static_assert(kMaxSeg * kMaxWarps >= kMaxBwdLayers, "every stack fits one CTA");
+constexpr int kRows = 16;         // rows per alpha-backward CTA
+constexpr int kMaxWarps = 32;     // segments (warps) per CTA
+static_assert(8 * kMaxWarps >= kMaxBwdLayers, "every stack fits one CTA");
 
 __device__ __forceinline__ float4 h4_to_f4(uint2 v)
 {
@@ -53,21 +54,24 @@ __device__ __forceinline__ uint2 f4_to_h4(float4 f)
     return v;
 }
 
-// What a CTA needs of one layer for its 32 x kRows tile, built once per CTA:
-// addresses of pixel (tx0, ty0) in the colour and gradient buffers (offset
-// only by rows and columns that lie inside the ROI / pvp before use), the
-// pitch, and the ROI and gradient ranges (columns relative to tx0).
+// What a CTA needs of one layer for its tile (TW columns by kRows rows),
+// built once per CTA: addresses of pixel (tx0, ty0) in the colour and
+// gradient buffers (offset only by rows and columns that lie inside the ROI /
+// pvp before use), the pitch, the ROI and gradient ranges (columns relative
+// to tx0), the colour alignment class, and whether pixel pairs starting at an
+// even column may be read (wide) or their gradients written (gwide) as one
+// 16-byte word.
 struct BandTile {
     uintptr_t src;
     uintptr_t grad;
     int32_t pitch;
     int32_t ry0, ry1, gy0, gy1;
     int16_t rx0, rx1, gx0, gx1;
-    int16_t cls, gvec;
+    int8_t cls, gvec, wide, gwide;
 };
 static_assert(sizeof(BandTile) == 48, "tile record");
 
-template <bool F16, bool G16>
+template <bool F16, bool G16, int TW>
 __device__ __forceinline__ BandTile make_band_tile(const BwdDesc& d, int tx0, int ty0)
 {
     constexpr int S = F16 ? 8 : 16, GS = G16 ? 8 : 16;
@@ -78,12 +82,15 @@ __device__ __forceinline__ BandTile make_band_tile(const BwdDesc& d, int tx0, in
     t.pitch = d.pitch;
     t.ry0 = d.y0; t.ry1 = d.y1;
     t.gy0 = d.gy0; t.gy1 = d.gy1;
-    t.rx0 = (int16_t)max(min(d.x0 - tx0, kTP), 0);
-    t.rx1 = (int16_t)max(min(d.x1 - tx0, kTP), 0);
-    t.gx0 = (int16_t)max(min(d.gx0 - tx0, kTP), 0);
-    t.gx1 = (int16_t)max(min(d.gx1 - tx0, kTP), 0);
-    t.cls = d.cls;
-    t.gvec = d.gvec;
+    t.rx0 = (int16_t)max(min(d.x0 - tx0, TW), 0);
+    t.rx1 = (int16_t)max(min(d.x1 - tx0, TW), 0);
+    t.gx0 = (int16_t)max(min(d.gx0 - tx0, TW), 0);
+    t.gx1 = (int16_t)max(min(d.gx1 - tx0, TW), 0);
+    t.cls = (int8_t)d.cls;
+    t.gvec = (int8_t)d.gvec;
+    const bool even = (d.pitch & 1) == 0;
+    t.wide = (int8_t)(F16 && even && d.cls >= 8 && (t.src & 15u) == 0);
+    t.gwide = (int8_t)(G16 && even && d.gvec && (t.grad & 15u) == 0);
     return t;
 }
 
@@ -139,145 +146,227 @@ __device__ __forceinline__ void store_grad(const BwdDesc& d, int x, int y, float
     store_grad_at<G16>(a, d.gvec != 0, v);
 }
 
-// Alpha backward (and fused forward + backward) for one 32 x kRows tile.
-// blockDim.x = 32 * NS: warp s owns segment s of the tile's active layers.
-template <int N, bool F16, bool G16, bool FUSED>
-__global__ void __launch_bounds__(kTP * kMaxWarps, 1)
+// Alpha backward (and fused forward + backward) for one tile of 32 * PX
+// pixels (PX per lane, adjacent) by kRows rows.  blockDim.x = 32 * NS: warp s
+// owns segment s of the tile's active layers, at most MS of them.  Tiles that
+// every active layer covers entirely (ROI and gradient rectangle) skip the
+// per-row range checks.
+template <int N, bool F16, bool G16, bool FUSED, int PX, int MS>
+__global__ void __launch_bounds__(32 * kMaxWarps, 1)
 k_alpha_bwd(const __grid_constant__ BwdList<N> L, const __grid_constant__ DstDesc D,
             const float4* __restrict__ g, int cap)
 {
-    constexpr int S = F16 ? 8 : 16, GS = G16 ? 8 : 16;
+    constexpr int S = F16 ? 8 : 16, GS = G16 ? 8 : 16, TW = 32 * PX;
     using RawPx = typename Px<F16>::T;
     extern __shared__ __align__(16) uint8_t smem[];
     __shared__ int16_t act[N];
     __shared__ int nact_s;
     BandTile* tiles = reinterpret_cast<BandTile*>(smem);                    // [cap]
-    const int NS = (int)(blockDim.x / kTP);
-    float* Ps = reinterpret_cast<float*>(smem + (size_t)cap * sizeof(BandTile));   // [NS][32]
-    float* As = Ps + NS * kTP;                                                       // [NS][32]
-    float4* Cs = reinterpret_cast<float4*>(As + NS * kTP);                           // [NS][32] (fused)
+    const int NS = (int)(blockDim.x / 32);
+    // per segment and pixel: [NS][PX][32], pixel (lane, q) at q * 32 + lane
+    float* Ps = reinterpret_cast<float*>(smem + (size_t)cap * sizeof(BandTile));
+    float* As = Ps + NS * TW;
+    float4* Cs = reinterpret_cast<float4*>(As + NS * TW);                   // (fused)
 
-    const int p = threadIdx.x & (kTP - 1), sg = threadIdx.x / kTP;
-    const int tx0 = blockIdx.x * kTP, ty0 = blockIdx.y * kRows;
-    const int tx1 = min(tx0 + kTP, D.W), ty1 = min(ty0 + kRows, D.H);
+    const int lane = threadIdx.x & 31, sg = threadIdx.x / 32;
+    const int tx0 = blockIdx.x * TW, ty0 = blockIdx.y * kRows;
+    const int tx1 = min(tx0 + TW, D.W), ty1 = min(ty0 + kRows, D.H);
 
     // layers whose gradient rectangle meets the tile, in compositing order
     if (threadIdx.x < 32) {
         int base = 0;
         for (int i0 = 0; i0 < L.n; i0 += 32) {
-            const int i = i0 + p;
+            const int i = i0 + lane;
             bool hit = false;
             if (i < L.n) {
                 const BwdDesc& d = L.d[i];
                 hit = d.gx0 < tx1 && d.gx1 > tx0 && d.gy0 < ty1 && d.gy1 > ty0;
             }
             const unsigned m = __ballot_sync(0xffffffffu, hit);
-            if (hit) act[base + __popc(m & ((1u << p) - 1u))] = (int16_t)i;
+            if (hit) act[base + __popc(m & ((1u << lane) - 1u))] = (int16_t)i;
             base += __popc(m);
         }
-        if (p == 0) nact_s = base;
+        if (lane == 0) nact_s = base;
     }
     __syncthreads();
     const int nact = nact_s;
-    for (int k = threadIdx.x; k < nact; k += blockDim.x) tiles[k] = make_band_tile<F16, G16>(L.d[act[k]], tx0, ty0);
-    __syncthreads();
+    bool covers = true;
+    for (int k = threadIdx.x; k < nact; k += blockDim.x) {
+        const BandTile t = make_band_tile<F16, G16, TW>(L.d[act[k]], tx0, ty0);
+        tiles[k] = t;
+        covers = covers && t.rx0 == 0 && t.rx1 >= tx1 - tx0 && t.ry0 <= ty0 && t.ry1 >= ty1 &&
+                 t.gx0 == 0 && t.gx1 >= tx1 - tx0 && t.gy0 <= ty0 && t.gy1 >= ty1;
+    }
+    const bool full = __syncthreads_and(covers);
 
-    const int k0 = (sg * nact) / NS, cnt = ((sg + 1) * nact) / NS - k0;   // cnt <= kMaxSeg
-    const int x = tx0 + p;
-    const bool valid = x < D.W;
-    for (int y = ty0; y < ty1; ++y) {
-        const float4 gp = valid ? __ldcs(g + (size_t)y * D.W + x) : make_float4(0.f, 0.f, 0.f, 0.f);
-        // this segment's pixels, all loads in flight before any is used
-        RawPx raw[kMaxSeg];
+    const int k0 = (sg * nact) / NS, cnt = ((sg + 1) * nact) / NS - k0;   // cnt <= MS
+    const int c0 = PX * lane;                                              // first column of this lane
+    bool valid[PX];
 #pragma unroll
-        for (int j = 0; j < kMaxSeg; ++j) {
-            if constexpr (F16) raw[j] = make_uint2(0u, 0u);
-            else raw[j] = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int q = 0; q < PX; ++q) valid[q] = tx0 + c0 + q < D.W;
+
+    auto row_pass = [&](auto full_c, int y) {
+        constexpr bool FULL = decltype(full_c)::value;
+        float4 gp[PX];
+#pragma unroll
+        for (int q = 0; q < PX; ++q)
+            gp[q] = valid[q] ? __ldcs(g + (size_t)y * D.W + tx0 + c0 + q) : make_float4(0.f, 0.f, 0.f, 0.f);
+        // this segment's pixels, all loads in flight before any is used
+        RawPx raw[MS][PX];
+#pragma unroll
+        for (int j = 0; j < MS; ++j) {
+#pragma unroll
+            for (int q = 0; q < PX; ++q) {
+                if constexpr (F16) raw[j][q] = make_uint2(0u, 0u);
+                else raw[j][q] = make_float4(0.f, 0.f, 0.f, 0.f);
+            }
             if (j < cnt) {
                 const BandTile& t = tiles[k0 + j];
-                if (valid && y >= t.ry0 && y < t.ry1 && p >= t.rx0 && p < t.rx1) {
-                    const uintptr_t a = t.src + (uintptr_t)(((int64_t)(y - ty0) * t.pitch + p) * S);
-                    if constexpr (F16) raw[j] = load_px16(a, t.cls);
-                    else raw[j] = load_px32(a, t.cls);
-                }
-            }
-        }
-        // local forward; keep T', g.c and a per layer
-        float Tl[kMaxSeg], gcl[kMaxSeg], al[kMaxSeg];
-        float Tp = 1.0f, A = 0.0f;
-        float4 Cl = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (FULL || (y >= t.ry0 && y < t.ry1)) {
+                    const uintptr_t a = t.src + (uintptr_t)(((int64_t)(y - ty0) * t.pitch + c0) * S);
+                    bool in[PX];
 #pragma unroll
-        for (int j = 0; j < kMaxSeg; ++j) {
-            float4 c;
-            if constexpr (F16) c = h4_to_f4(raw[j]);
-            else c = raw[j];
-            const float gc = fmaf(gp.x, c.x, fmaf(gp.y, c.y, fmaf(gp.z, c.z, gp.w * c.w)));
-            Tl[j] = Tp;
-            gcl[j] = gc;
-            al[j] = c.w;
-            if (j < cnt) {
-                if (FUSED) {
-                    Cl.x = fmaf(Tp, c.x, Cl.x);
-                    Cl.y = fmaf(Tp, c.y, Cl.y);
-                    Cl.z = fmaf(Tp, c.z, Cl.z);
-                    Cl.w = fmaf(Tp, c.w, Cl.w);
+                    for (int q = 0; q < PX; ++q)
+                        in[q] = valid[q] && (FULL || (c0 + q >= t.rx0 && c0 + q < t.rx1));
+                    bool done = false;
+                    if constexpr (PX == 2) {
+                        if (t.wide && in[0] && in[1]) {
+                            const uint4 v = __ldcs(reinterpret_cast<const uint4*>(a));
+                            raw[j][0] = make_uint2(v.x, v.y);
+                            raw[j][1] = make_uint2(v.z, v.w);
+                            done = true;
+                        }
+                    }
+                    if (!done) {
+#pragma unroll
+                        for (int q = 0; q < PX; ++q) {
+                            if (!in[q]) continue;
+                            if constexpr (F16) raw[j][q] = load_px16(a + q * S, t.cls);
+                            else raw[j][q] = load_px32(a + q * S, t.cls);
+                        }
+                    }
                 }
-                A = fmaf(Tp, gc, A);
-                Tp = fmaf(-Tp, c.w, Tp);
             }
         }
-        Ps[sg * kTP + p] = Tp;
-        As[sg * kTP + p] = A;
-        if (FUSED) Cs[sg * kTP + p] = Cl;
+        // local forward; keep T', g.c and a per layer and pixel
+        float Tl[MS][PX], gcl[MS][PX], al[MS][PX];
+        float Tp[PX], A[PX];
+        float4 Cl[PX];
+#pragma unroll
+        for (int q = 0; q < PX; ++q) { Tp[q] = 1.0f; A[q] = 0.0f; Cl[q] = make_float4(0.f, 0.f, 0.f, 0.f); }
+#pragma unroll
+        for (int j = 0; j < MS; ++j) {
+#pragma unroll
+            for (int q = 0; q < PX; ++q) {
+                float4 c;
+                if constexpr (F16) c = h4_to_f4(raw[j][q]);
+                else c = raw[j][q];
+                const float gc = fmaf(gp[q].x, c.x, fmaf(gp[q].y, c.y, fmaf(gp[q].z, c.z, gp[q].w * c.w)));
+                Tl[j][q] = Tp[q];
+                gcl[j][q] = gc;
+                al[j][q] = c.w;
+                if (j < cnt) {
+                    if (FUSED) {
+                        Cl[q].x = fmaf(Tp[q], c.x, Cl[q].x);
+                        Cl[q].y = fmaf(Tp[q], c.y, Cl[q].y);
+                        Cl[q].z = fmaf(Tp[q], c.z, Cl[q].z);
+                        Cl[q].w = fmaf(Tp[q], c.w, Cl[q].w);
+                    }
+                    A[q] = fmaf(Tp[q], gc, A[q]);
+                    Tp[q] = fmaf(-Tp[q], c.w, Tp[q]);
+                }
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < PX; ++q) {
+            Ps[sg * TW + q * 32 + lane] = Tp[q];
+            As[sg * TW + q * 32 + lane] = A[q];
+            if (FUSED) Cs[sg * TW + q * 32 + lane] = Cl[q];
+        }
         __syncthreads();
 
-        float Tstart = 1.0f;
-        for (int u = 0; u < sg; ++u) Tstart *= Ps[u * kTP + p];
-        float R = 0.0f;
-        for (int u = NS - 1; u > sg; --u) R = fmaf(Ps[u * kTP + p], R, As[u * kTP + p]);
+        float Tstart[PX], R[PX];
+#pragma unroll
+        for (int q = 0; q < PX; ++q) {
+            Tstart[q] = 1.0f;
+            for (int u = 0; u < sg; ++u) Tstart[q] *= Ps[u * TW + q * 32 + lane];
+            R[q] = 0.0f;
+            for (int u = NS - 1; u > sg; --u) R[q] = fmaf(Ps[u * TW + q * 32 + lane], R[q], As[u * TW + q * 32 + lane]);
+        }
 
-        if (FUSED && sg == 0 && valid) {
-            float Tacc = 1.0f;
-            float4 out = make_float4(0.f, 0.f, 0.f, 0.f);
-            for (int u = 0; u < NS; ++u) {
-                const float4 c = Cs[u * kTP + p];
-                out.x = fmaf(Tacc, c.x, out.x);
-                out.y = fmaf(Tacc, c.y, out.y);
-                out.z = fmaf(Tacc, c.z, out.z);
-                out.w = fmaf(Tacc, c.w, out.w);
-                Tacc *= Ps[u * kTP + p];
+        if (FUSED && sg == 0) {
+#pragma unroll
+            for (int q = 0; q < PX; ++q) {
+                if (!valid[q]) continue;
+                float Tacc = 1.0f;
+                float4 out = make_float4(0.f, 0.f, 0.f, 0.f);
+                for (int u = 0; u < NS; ++u) {
+                    const float4 c = Cs[u * TW + q * 32 + lane];
+                    out.x = fmaf(Tacc, c.x, out.x);
+                    out.y = fmaf(Tacc, c.y, out.y);
+                    out.z = fmaf(Tacc, c.z, out.z);
+                    out.w = fmaf(Tacc, c.w, out.w);
+                    Tacc *= Ps[u * TW + q * 32 + lane];
+                }
+                const int x = tx0 + c0 + q;
+                const size_t o = (size_t)y * (size_t)D.pitch + (size_t)x;
+                if constexpr (F16) {
+                    const uint2 h = f4_to_h4(out);
+                    unsigned short* hp = reinterpret_cast<unsigned short*>(reinterpret_cast<uint2*>(D.color) + o);
+                    if (D.vec) __stcs(reinterpret_cast<uint2*>(hp), h);
+                    else { hp[0] = (unsigned short)h.x; hp[1] = (unsigned short)(h.x >> 16); hp[2] = (unsigned short)h.y; hp[3] = (unsigned short)(h.y >> 16); }
+                } else {
+                    float4* op = reinterpret_cast<float4*>(D.color) + o;
+                    if (D.vec) __stcs(op, out);
+                    else { float* f = reinterpret_cast<float*>(op); f[0] = out.x; f[1] = out.y; f[2] = out.z; f[3] = out.w; }
+                }
+                if (D.tfinal) D.tfinal[(size_t)y * D.W + x] = Tacc;
             }
-            const size_t o = (size_t)y * (size_t)D.pitch + (size_t)x;
-            if constexpr (F16) {
-                const uint2 h = f4_to_h4(out);
-                unsigned short* hp = reinterpret_cast<unsigned short*>(reinterpret_cast<uint2*>(D.color) + o);
-                if (D.vec) __stcs(reinterpret_cast<uint2*>(hp), h);
-                else { hp[0] = (unsigned short)h.x; hp[1] = (unsigned short)(h.x >> 16); hp[2] = (unsigned short)h.y; hp[3] = (unsigned short)(h.y >> 16); }
-            } else {
-                float4* op = reinterpret_cast<float4*>(D.color) + o;
-                if (D.vec) __stcs(op, out);
-                else { float* f = reinterpret_cast<float*>(op); f[0] = out.x; f[1] = out.y; f[2] = out.z; f[3] = out.w; }
-            }
-            if (D.tfinal) D.tfinal[(size_t)y * D.W + x] = Tacc;
         }
 
         // reverse over this segment, entering with the R of the layers behind it
 #pragma unroll
-        for (int j = kMaxSeg - 1; j >= 0; --j) {
+        for (int j = MS - 1; j >= 0; --j) {
             if (j < cnt) {
                 const BandTile& t = tiles[k0 + j];
-                if (valid && y >= t.gy0 && y < t.gy1 && p >= t.gx0 && p < t.gx1) {
-                    const float Tk = Tstart * Tl[j];
-                    const bool in = y >= t.ry0 && y < t.ry1 && p >= t.rx0 && p < t.rx1;
-                    const float4 gr = in ? make_float4(gp.x * Tk, gp.y * Tk, gp.z * Tk, Tk * (gp.w - R))
-                                         : make_float4(0.f, 0.f, 0.f, 0.f);
-                    store_grad_at<G16>(t.grad + (uintptr_t)(((int64_t)(y - ty0) * t.pitch + p) * GS),
-                                       t.gvec != 0, gr);
+                if (FULL || (y >= t.gy0 && y < t.gy1)) {
+                    const bool rrow = FULL || (y >= t.ry0 && y < t.ry1);
+                    float4 gr[PX];
+                    bool gin[PX];
+#pragma unroll
+                    for (int q = 0; q < PX; ++q) {
+                        const int c = c0 + q;
+                        gin[q] = valid[q] && (FULL || (c >= t.gx0 && c < t.gx1));
+                        const float Tk = Tstart[q] * Tl[j][q];
+                        const bool in = FULL || (rrow && c >= t.rx0 && c < t.rx1);
+                        gr[q] = in ? make_float4(gp[q].x * Tk, gp[q].y * Tk, gp[q].z * Tk, Tk * (gp[q].w - R[q]))
+                                   : make_float4(0.f, 0.f, 0.f, 0.f);
+                    }
+                    const uintptr_t ga = t.grad + (uintptr_t)(((int64_t)(y - ty0) * t.pitch + c0) * GS);
+                    bool done = false;
+                    if constexpr (PX == 2 && G16) {
+                        if (t.gwide && gin[0] && gin[1]) {
+                            const uint2 h0 = f4_to_h4(gr[0]), h1 = f4_to_h4(gr[1]);
+                            __stcs(reinterpret_cast<uint4*>(ga), make_uint4(h0.x, h0.y, h1.x, h1.y));
+                            done = true;
+                        }
+                    }
+                    if (!done) {
+#pragma unroll
+                        for (int q = 0; q < PX; ++q)
+                            if (gin[q]) store_grad_at<G16>(ga + q * GS, t.gvec != 0, gr[q]);
+                    }
                 }
-                R = fmaf(1.0f - al[j], R, gcl[j]);
+#pragma unroll
+                for (int q = 0; q < PX; ++q) R[q] = fmaf(1.0f - al[j][q], R[q], gcl[j][q]);
             }
         }
         __syncthreads();                      // Ps / As / Cs are rewritten for the next row
+    };
+    if (full) {
+        for (int y = ty0; y < ty1; ++y) row_pass(std::true_type{}, y);
+    } else {
+        for (int y = ty0; y < ty1; ++y) row_pass(std::false_type{}, y);
     }
 }
 
@@ -345,25 +434,39 @@ BwdList<N> make_bwd(const BwdDesc* d, int n)
 }
 
 // Warps (segments) per alpha-backward CTA for a stack of n layers: enough for
-// kMaxSeg layers each, and at least four (or n) so that short stacks still
-// split their scans.
-int alpha_bwd_warps(int n)
+// ms layers each, and at least four (or n) so that short stacks still split
+// their scans.
+int alpha_bwd_warps(int n, int ms)
 {
-    const int need = (n + kMaxSeg - 1) / kMaxSeg;
+    const int need = (n + ms - 1) / ms;
     return std::max(1, std::min(kMaxWarps, std::max(need, std::min(n, 4))));
 }
 
-template <int N, bool F16, bool G16, bool FUSED>
+template <int N, bool F16, bool G16, bool FUSED, int PX, int MS>
 cudaError_t alpha_bwd_n(const BwdDesc* d, int n, const DstDesc& D, const float4* g, cudaStream_t s)
 {
-    const int ns = alpha_bwd_warps(n), cap = std::max(n, 1);
-    const size_t smem = (size_t)cap * sizeof(BandTile) + (size_t)ns * kTP * (8 + (FUSED ? 16 : 0));
-    auto kern = k_alpha_bwd<N, F16, G16, FUSED>;
+    const int ns = alpha_bwd_warps(n, MS), cap = std::max(n, 1), tw = 32 * PX;
+    const size_t smem = (size_t)cap * sizeof(BandTile) + (size_t)ns * tw * (8 + (FUSED ? 16 : 0));
+    auto kern = k_alpha_bwd<N, F16, G16, FUSED, PX, MS>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    const dim3 grid(ceil_div(D.W, kTP), ceil_div(D.H, kRows));
-    kern<<<grid, kTP * ns, smem, s>>>(make_bwd<N>(d, n), D, g, cap);
+    const dim3 grid(ceil_div(D.W, tw), ceil_div(D.H, kRows));
+    kern<<<grid, 32 * ns, smem, s>>>(make_bwd<N>(d, n), D, g, cap);
     return cudaGetLastError();
+}
+
+// FP16 stacks of up to 64 layers: two pixels per lane (one 16-byte word),
+// four layers per warp; deeper FP16 stacks and FP32: one pixel, eight layers.
+template <int N, bool F16, bool G16, bool FUSED>
+cudaError_t alpha_bwd_px(const BwdDesc* d, int n, const DstDesc& D, const float4* g, cudaStream_t s)
+{
+    if constexpr (F16) {
+        if (n <= 64) return alpha_bwd_n<N, F16, G16, FUSED, 2, 4>(d, n, D, g, s);
+        if constexpr (N > 64) return alpha_bwd_n<N, F16, G16, FUSED, 1, 8>(d, n, D, g, s);
+        return cudaErrorInvalidValue;
+    } else {
+        return alpha_bwd_n<N, F16, G16, FUSED, 1, 8>(d, n, D, g, s);
+    }
 }
 
 template <int N>
@@ -371,15 +474,15 @@ cudaError_t alpha_bwd_dispatch(const BwdDesc* d, int n, bool f16, bool g16, bool
                                const DstDesc& D, const float4* g, cudaStream_t s)
 {
     if (f16) {
-        if (g16) return fused ? alpha_bwd_n<N, true, true, true>(d, n, D, g, s)
-                              : alpha_bwd_n<N, true, true, false>(d, n, D, g, s);
-        return fused ? alpha_bwd_n<N, true, false, true>(d, n, D, g, s)
-                     : alpha_bwd_n<N, true, false, false>(d, n, D, g, s);
+        if (g16) return fused ? alpha_bwd_px<N, true, true, true>(d, n, D, g, s)
+                              : alpha_bwd_px<N, true, true, false>(d, n, D, g, s);
+        return fused ? alpha_bwd_px<N, true, false, true>(d, n, D, g, s)
+                     : alpha_bwd_px<N, true, false, false>(d, n, D, g, s);
     }
-    if (g16) return fused ? alpha_bwd_n<N, false, true, true>(d, n, D, g, s)
-                          : alpha_bwd_n<N, false, true, false>(d, n, D, g, s);
-    return fused ? alpha_bwd_n<N, false, false, true>(d, n, D, g, s)
-                 : alpha_bwd_n<N, false, false, false>(d, n, D, g, s);
+    if (g16) return fused ? alpha_bwd_px<N, false, true, true>(d, n, D, g, s)
+                          : alpha_bwd_px<N, false, true, false>(d, n, D, g, s);
+    return fused ? alpha_bwd_px<N, false, false, true>(d, n, D, g, s)
+                 : alpha_bwd_px<N, false, false, false>(d, n, D, g, s);
 }
 
 }  // namespace
