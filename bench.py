@@ -98,6 +98,12 @@ def max_over_ranks(x: float, world: int) -> float:
     return float(t.item())
 
 
+def whole_job_value(units_per_rank: float, ms_slowest: float, world: int) -> float:
+    """Throughput of the whole job in G units/s: every rank processes
+    units_per_rank per step, and a step lasts as long as the slowest rank."""
+    return world * units_per_rank / (ms_slowest * 1e-3) / 1e9
+
+
 def hbm_peak():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -623,7 +629,7 @@ def run_ec(args):
     step_ms = [sum(per_kernel[i][k] for i in range(nk)) for k in range(args.steps)]
     ms = statistics.mean(step_ms)
     ms = max_over_ranks(ms, world)
-    value = world * wl.units / (ms * 1e-3) / 1e9
+    value = whole_job_value(wl.units, ms, world)
 
     # end to end through the public API, host buffers in pinned memory
     wl.setup_e2e()
@@ -667,7 +673,7 @@ def run_ec(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "rgba8+f32" if isinstance(wl, (DepthPipeline, BatchedTiles)) else "f32",
             "data": "synthetic (seeded boxes / layers shaped like the thesis's workloads)",
             "config": cfg, "roofline": roof, "kernels": kern,
-            "e2e": {"value": world * wl.units / (e2e_ms * 1e-3) / 1e9, "unit": UNIT,
+            "e2e": {"value": whole_job_value(wl.units, e2e_ms, world), "unit": UNIT,
                     "ms_per_step": e2e_ms, "h2d_bytes_per_step": wl.h2d, "d2h_bytes_per_step": wl.d2h},
             "gpu_launches": wl.launches_per_step() * args.steps,
             "clocks": clk, "wall_s_timed_loop": t_wall}
