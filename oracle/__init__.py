@@ -78,6 +78,9 @@ def lib():
         L.orc_composite_depth_backward.restype = C.c_int
         L.orc_composite_depth_backward.argtypes = [C.c_void_p, Rect, C.c_void_p, C.c_int32,
                                                    C.c_void_p, C.c_void_p, C.c_void_p]
+        L.orc_detect_roi.restype = C.c_int
+        L.orc_detect_roi.argtypes = [Rect, Rect, C.c_int32, C.c_int32, C.c_void_p, C.c_void_p,
+                                     C.c_int32, C.c_void_p, C.POINTER(Rect)]
         L.orc_rle_max_size.restype = C.c_size_t
         L.orc_rle_max_size.argtypes = [C.c_int32, C.c_int32]
         L.orc_swizzle.restype = C.c_uint32
@@ -229,6 +232,24 @@ def composite_depth_backward(winner: np.ndarray, out_pvp, g: np.ndarray, pvps, p
     if rc:
         raise OracleError(rc, "composite_depth_backward")
     return grads
+
+
+def detect_roi(pvp, search, pitch: int, fmt: int, color: Optional[np.ndarray] = None,
+               depth: Optional[np.ndarray] = None, tile: int = 64):
+    """Automatic ROI (thesis 5.3): bounding box of the data pixels of the
+    examined region, and the tile occupancy grid.  color: [pvp.h][pitch] uint32
+    (RGBA8), [..][4] float32 or [..][4] uint16 half bits; depth: float32."""
+    gw, gh = -(-max(pvp[2], 0) // tile), -(-max(pvp[3], 0) // tile)
+    occ = np.zeros((gh, gw), dtype=np.uint8)
+    c = None if color is None else np.ascontiguousarray(color)
+    d = None if depth is None else np.ascontiguousarray(depth, dtype=np.float32)
+    out = Rect()
+    rc = lib().orc_detect_roi(_rect(pvp), _rect(search), int(pitch), int(fmt),
+                              None if c is None else _ptr(c), None if d is None else _ptr(d),
+                              int(tile), _ptr(occ) if occ.size else None, C.byref(out))
+    if rc:
+        raise OracleError(rc, "detect_roi")
+    return (out.x, out.y, out.w, out.h), occ
 
 
 def rle_max_size(w: int, h: int) -> int:

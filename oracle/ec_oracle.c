@@ -529,3 +529,56 @@ int orc_rle_decompress(const uint8_t* src, size_t size, uint32_t* dst,
     }
     return ORC_OK;
 }
+
+/* ---- automatic region of interest (thesis 5.3) ------------------------- */
+
+static int holds_data(int32_t format, const void* color, const float* depth, size_t e)
+{
+    if (depth) return depth[e] < 1.0f;
+    if (format == 0) return ((const uint32_t*)color)[e] != 0u;
+    if (format == 1) {
+        const float* f = (const float*)color + 4 * e;
+        return f[0] != 0.0f || f[1] != 0.0f || f[2] != 0.0f || f[3] != 0.0f;
+    }
+    const uint16_t* h = (const uint16_t*)color + 4 * e;
+    return (h[0] & 0x7FFFu) || (h[1] & 0x7FFFu) || (h[2] & 0x7FFFu) || (h[3] & 0x7FFFu);
+}
+
+int orc_detect_roi(orc_rect pvp, orc_rect search, int32_t pitch, int32_t format,
+                   const void* color, const float* depth, int32_t tile, uint8_t* occ,
+                   orc_rect* roi)
+{
+    if (pvp.w < 0 || pvp.h < 0 || pitch < pvp.w || tile < 1 || !roi) return ORC_EINVAL;
+    if (!depth && (format < 0 || format > 2)) return ORC_EINVAL;
+    int64_t gw = (pvp.w + tile - 1) / tile, gh = (pvp.h + tile - 1) / tile;
+    if (occ) memset(occ, 0, (size_t)(gw * gh));
+    /* the examined pixels: search clipped to pvp, relative to the pvp origin */
+    int64_t x0 = (int64_t)search.x - pvp.x, y0 = (int64_t)search.y - pvp.y;
+    int64_t x1 = x0 + search.w, y1 = y0 + search.h;
+    if (x0 < 0) x0 = 0;
+    if (y0 < 0) y0 = 0;
+    if (x1 > pvp.w) x1 = pvp.w;
+    if (y1 > pvp.h) y1 = pvp.h;
+    int have = 0;
+    int64_t bx0 = 0, by0 = 0, bx1 = 0, by1 = 0;
+    for (int64_t y = y0; y < y1; ++y) {
+        for (int64_t x = x0; x < x1; ++x) {
+            if (!holds_data(format, color, depth, (size_t)(y * pitch + x))) continue;
+            if (!have) { bx0 = bx1 = x; by0 = by1 = y; have = 1; }
+            if (x < bx0) bx0 = x;
+            if (x > bx1) bx1 = x;
+            if (y < by0) by0 = y;
+            if (y > by1) by1 = y;
+            if (occ) occ[(y / tile) * gw + x / tile] = 1;
+        }
+    }
+    if (!have) {
+        roi->x = roi->y = roi->w = roi->h = 0;
+        return ORC_OK;
+    }
+    roi->x = (int32_t)(pvp.x + bx0);
+    roi->y = (int32_t)(pvp.y + by0);
+    roi->w = (int32_t)(bx1 - bx0 + 1);
+    roi->h = (int32_t)(by1 - by0 + 1);
+    return ORC_OK;
+}

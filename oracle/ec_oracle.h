@@ -87,6 +87,25 @@ int orc_composite_depth_backward(const int16_t* winner, orc_rect out_pvp,
                                  const float* g, int32_t n, const orc_rect* pvps,
                                  const int32_t* pitches, float* const* grad);
 
+/* ---- automatic region of interest (thesis 5.3) ---------------------------
+ * The ROI found by scanning a frame buffer instead of being supplied by the
+ * application: the bounding box of the pixels that hold rendered data, plus a
+ * grid of tiles telling which tiles hold any (holes are the empty tiles).
+ * A pixel holds data when
+ *   depth != NULL:          its depth is below 1.0, the cleared background
+ *                           depth (a NaN depth is background);
+ *   else colour format 0 (RGBA8):    its 32-bit word is not 0;
+ *        format 1 (RGBA32F):         one of its four floats is not 0 (-0 is 0);
+ *        format 2 (RGBA16F, bits):   one of its four halves is not +-0.
+ * Only pixels of search (clipped to pvp) are examined.  *roi receives the
+ * bounding box in destination coordinates, {0,0,0,0} when no pixel holds
+ * data.  occ, when not NULL, receives ceil(pvp.h/tile) rows of
+ * ceil(pvp.w/tile) bytes: tile (i, j) covers pvp pixels [j*tile, (j+1)*tile)
+ * x [i*tile, (i+1)*tile) and is 1 iff one of its examined pixels holds data. */
+int orc_detect_roi(orc_rect pvp, orc_rect search, int32_t pitch, int32_t format,
+                   const void* color, const float* depth, int32_t tile, uint8_t* occ,
+                   orc_rect* roi);
+
 /* ---- run-length codec (thesis 5.5.1), container "ECR1" ------------------
  * The image is w*h four-byte elements read row-major (pitch ignored in the
  * logical order).  Mode 1 splits each element into its four bytes (one stream

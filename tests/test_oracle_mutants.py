@@ -18,6 +18,7 @@ import test_oracle_alpha as TA
 import test_oracle_depth as TD
 import test_oracle_depth_grad as TG
 import test_oracle_rle as TR
+import test_oracle_roi as TO
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 ORACLE = os.path.join(ROOT, "oracle")
@@ -41,6 +42,11 @@ MUTANTS = {
     "swizzle_component_order": ("s |= ((b >> (6 - 2 * k)) & 3u) << (6 - 2 * j);",
                                 "s |= ((b >> (6 - 2 * k)) & 3u) << (2 * j);"),
     "decoder_no_length_check": ("if (o != len) return ORC_ECORRUPT;", ""),
+    "roi_depth_le": ("if (depth) return depth[e] < 1.0f;", "if (depth) return depth[e] <= 1.0f;"),
+    "roi_half_sign": ("return (h[0] & 0x7FFFu) || (h[1] & 0x7FFFu)", "return (h[0] & 0xFFFFu) || (h[1] & 0x7FFFu)"),
+    "roi_max_x_dropped": ("if (x > bx1) bx1 = x;", ""),
+    "roi_occ_transposed": ("occ[(y / tile) * gw + x / tile] = 1;", "occ[(x / tile) * gw + y / tile] = 1;"),
+    "roi_search_not_clipped": ("if (x1 > pvp.w) x1 = pvp.w;", ""),
 }
 
 
@@ -80,6 +86,9 @@ def _pins(orc):
     yield lambda: [TR.test_streams_decode_and_have_canonical_size(orc, n, 1)
                    for n in ("run_lengths", "lit_run_mix", "boxes")]
     yield lambda: TR.test_decoder_rejects_corrupt_streams(orc)
+    yield lambda: [TO.test_matches_numpy_reductions(orc, f, s) for f in ("depth", 0, 1, 2) for s in range(4)]
+    yield lambda: TO.test_search_region_limits_the_scan(orc)
+    yield lambda: TO.test_special_values(orc)
 
 
 def _caught(orc):
