@@ -230,6 +230,34 @@ ec_status ec_batch_get_config(const ec_batch* plan, ec_batch_config* cfg, int32_
                               int32_t* grid);
 void ec_batch_free(ec_batch* plan);
 
+/* ------------------------------------------------- automatic region of interest
+ * Thesis 5.3: instead of the application supplying each frame's ROI, it can be
+ * computed by analysing the frame buffer, which also detects holes.
+ *
+ * ec_detect_roi: for every image, the bounding box of the pixels of its roi
+ * (the region searched; roi must lie inside pvp) that hold rendered data, and
+ * optionally which tiles of its pvp hold any.  A pixel holds data when
+ *   depth != NULL: its depth is below 1.0, the cleared depth (NaN is
+ *                  background); only the depth buffer is read;
+ *   otherwise:     its colour is not all zero: an RGBA8 word != 0, or one of
+ *                  the four float / half channels != +-0 (colour is read).
+ * in:        host array of n images (pvp, roi, pitch, format, color, depth;
+ *            color may be NULL when depth is given).  Elements must be
+ *            naturally aligned; 16-byte aligned buffers with pitch*bytes a
+ *            multiple of 16 are read with 16-byte loads.
+ * tile:      occupancy tile edge in pixels: 8, 16, 32 or 64.
+ * occupancy: NULL, or a host array of n device pointers (entries may be
+ *            NULL) to ceil(pvp.h/tile) rows of ceil(pvp.w/tile) bytes; tile
+ *            (i, j) covers pvp pixels [j*tile, (j+1)*tile) x [i*tile, (i+1)*tile)
+ *            and is written 1 if one of its searched pixels holds data, else 0.
+ * d_rois:    device array of n ec_rect, written in destination coordinates;
+ *            {0,0,0,0} when no searched pixel holds data.
+ * Asynchronous on s; argument errors (bad rectangles, tile, alignment of
+ * d_rois to 4 bytes, n > EC_MAX_SOURCES) are returned synchronously.  Uses
+ * context scratch: calls on one context must not overlap on the device. */
+ec_status ec_detect_roi(ec_ctx* ctx, const ec_image* in, int32_t n, int32_t tile,
+                        uint8_t* const* occupancy, ec_rect* d_rois, ec_stream_t s);
+
 /* ------------------------------------------------------------ run-length codec
  * Thesis 5.5.1 (enhanced RLE): the image is coded as four independent byte
  * streams, one per component (mode 1), optionally after regrouping the 32 bits

@@ -31,6 +31,7 @@ from .api import (  # noqa: F401
     composite_depth,
     composite_depth_backward,
     default_context,
+    detect_roi,
     pixel_layout,
     rle_compress,
     rle_compress_batch,

@@ -248,6 +248,48 @@ def composite_alpha_fwd_bwd(layers: Sequence[Image], out: torch.Tensor, w: torch
     return roi.tup()
 
 
+def detect_roi(images: Sequence[Image], tile: int = 64, occupancy: bool = True,
+               ctx: Optional[Context] = None, stream=None):
+    """ec_detect_roi: bounding box of each image's data pixels inside its roi
+    (depth < 1.0 when a depth buffer is given, else a non-zero colour), and
+    optionally its tile occupancy grid (holes are the 0 tiles).
+
+    Returns (rois, grids): rois is an int32 [n][4] device tensor of (x, y, w, h)
+    in destination coordinates ((0,0,0,0) when nothing is found); grids is a list
+    of uint8 [ceil(pvp.h/tile)][ceil(pvp.w/tile)] device tensors, or None."""
+    n = len(images)
+    dev = (ctx.device if ctx else (images[0].color.device.index if n else torch.cuda.current_device()))
+    ctx = ctx or default_context(dev)
+    dev = ctx.device
+    structs = []
+    for im in images:
+        fmt, pitch, w, h = pixel_layout(im.color)
+        _on_device(im.color, dev, "colour")
+        pvp = tuple(im.pvp) if im.pvp is not None else (0, 0, w, h)
+        roi = tuple(im.roi) if im.roi is not None else pvp
+        if pvp[2] > w or pvp[3] > h:
+            raise ValueError("pvp larger than the colour tensor")
+        dptr = None
+        if im.depth is not None:
+            _on_device(im.depth, dev, "depth")
+            dd = im.depth
+            if dd.dtype != torch.float32 or dd.dim() != 2 or dd.stride(1) != 1 or dd.stride(0) != pitch \
+                    or dd.shape[0] < pvp[3] or dd.shape[1] < pvp[2]:
+                raise ValueError("depth must be float32 [h][pitch] with the colour's pitch")
+            dptr = dd.data_ptr()
+        structs.append(ec_image(_rect(pvp), _rect(roi), pitch, fmt, im.color.data_ptr(), dptr))
+    arr = (ec_image * max(1, n))(*structs)
+    rois = torch.zeros((max(n, 1), 4), dtype=torch.int32, device=f"cuda:{dev}")[:n]
+    grids, occ = None, None
+    if occupancy:
+        grids = [torch.empty((-(-s.pvp.h // tile), -(-s.pvp.w // tile)), dtype=torch.uint8, device=f"cuda:{dev}")
+                 for s in structs]
+        occ = (C.c_void_p * max(1, n))(*[g.data_ptr() if g.numel() else None for g in grids])
+    check(_lib().ec_detect_roi(ctx.h, arr, n, int(tile), occ, rois.data_ptr() if n else None,
+                               _stream_handle(stream)), "ec_detect_roi")
+    return rois, grids
+
+
 def composite_depth_backward(winner: torch.Tensor, out_pvp: Rect, grad_out: torch.Tensor,
                              images: Sequence[Image], grads: Sequence[torch.Tensor],
                              ctx: Optional[Context] = None, stream=None):

@@ -138,6 +138,18 @@ ec_status ensure_scratch(ec_ctx* ctx, size_t bytes)
     return EC_OK;
 }
 
+ec_status ensure_roi_scratch(ec_ctx* ctx, size_t bytes)
+{
+    if (ctx->roi_scratch_bytes >= bytes) return EC_OK;
+    if (ctx->roi_scratch) cudaFree(ctx->roi_scratch);
+    ctx->roi_scratch = nullptr;
+    ctx->roi_scratch_bytes = 0;
+    bytes = std::max<size_t>(bytes, 16 * 1024);
+    if (cudaMalloc(&ctx->roi_scratch, bytes) != cudaSuccess) return EC_ERR_CUDA;
+    ctx->roi_scratch_bytes = bytes;
+    return EC_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -183,6 +195,7 @@ void ec_destroy(ec_ctx* ctx)
     DeviceGuard g(ctx->device);
     if (ctx->d_status) cudaFree(ctx->d_status);
     if (ctx->scratch) cudaFree(ctx->scratch);
+    if (ctx->roi_scratch) cudaFree(ctx->roi_scratch);
     delete ctx;
 }
 
@@ -266,6 +279,71 @@ ec_status ec_composite_alpha(ec_ctx* ctx, const ec_image* in, const int32_t* ord
     DeviceGuard g(ctx->device);
     if (!g.ok) return EC_ERR_CUDA;
     return cuda_status(launch_alpha_fwd(d.data(), n, f16, D, (cudaStream_t)s));
+}
+
+ec_status ec_detect_roi(ec_ctx* ctx, const ec_image* in, int32_t n, int32_t tile,
+                        uint8_t* const* occupancy, ec_rect* d_rois, ec_stream_t s)
+{
+    if (!ctx || n < 0 || (n > 0 && (!in || !d_rois))) return EC_ERR_INVALID_ARG;
+    if (tile != 8 && tile != 16 && tile != 32 && tile != 64) return EC_ERR_INVALID_ARG;
+    if (n > EC_MAX_SOURCES) return EC_ERR_UNSUPPORTED;
+    if (reinterpret_cast<uintptr_t>(d_rois) & 3u) return EC_ERR_INVALID_ARG;
+    std::vector<RoiDesc> d((size_t)std::max(n, 1));
+    std::vector<uint64_t> nblocks((size_t)std::max(n, 1));
+    for (int i = 0; i < n; ++i) {
+        const ec_image& im = in[i];
+        if (!rect_ok(im.pvp) || !rect_ok(im.roi) || im.pitch < im.pvp.w || im.pitch < 0 ||
+            !rect_inside(im.roi, im.pvp))
+            return EC_ERR_INVALID_ARG;
+        int kind;
+        if (im.depth) kind = 0;
+        else if (im.format == EC_RGBA8) kind = 1;
+        else if (im.format == EC_RGBA32F) kind = 2;
+        else if (im.format == EC_RGBA16F) kind = 3;
+        else return EC_ERR_INVALID_ARG;
+        const void* data = im.depth ? static_cast<const void*>(im.depth) : im.color;
+        const bool search = !rect_empty(im.roi);
+        const uintptr_t align = kind == 3 ? 2u : 4u;
+        if (search && (!data || (reinterpret_cast<uintptr_t>(data) & (align - 1)))) return EC_ERR_INVALID_ARG;
+        const int bpp = kind == 2 ? 16 : kind == 3 ? 8 : 4;
+        RoiDesc& r = d[i];
+        memset(&r, 0, sizeof(r));
+        if (search) {
+            r.x0 = im.roi.x - im.pvp.x;
+            r.y0 = im.roi.y - im.pvp.y;
+            r.x1 = r.x0 + im.roi.w;
+            r.y1 = r.y0 + im.roi.h;
+        }
+        r.ox = im.pvp.x;
+        r.oy = im.pvp.y;
+        r.pitch = im.pitch;
+        r.gw = (im.pvp.w + tile - 1) / tile;
+        r.gh = (im.pvp.h + tile - 1) / tile;
+        r.bw = (im.pvp.w + 63) / 64;
+        nblocks[i] = (uint64_t)r.bw * (uint64_t)((im.pvp.h + 63) / 64);
+        r.kind = (int16_t)kind;
+        r.vec = (int16_t)(aligned16(data) && ((int64_t)im.pitch * bpp) % 16 == 0);
+        r.data = data;
+        r.occ = occupancy ? occupancy[i] : nullptr;
+    }
+    DeviceGuard g(ctx->device);
+    if (!g.ok) return EC_ERR_CUDA;
+    for (int b = 0; b < n; b += kRoiPerLaunch) {
+        const int cnt = std::min(kRoiPerLaunch, n - b);
+        uint64_t blocks = 0;
+        for (int i = 0; i < cnt; ++i) {
+            d[b + i].first_block = (uint32_t)blocks;
+            blocks += nblocks[b + i];
+        }
+        if (blocks >= (1ull << 31)) return EC_ERR_UNSUPPORTED;
+        const ec_status st = ensure_roi_scratch(ctx, (4ull * cnt + 1) * sizeof(uint32_t));
+        if (st != EC_OK) return st;
+        const cudaError_t e = launch_detect_roi(&d[b], cnt, tile, (uint32_t)blocks,
+                                                reinterpret_cast<uint32_t*>(ctx->roi_scratch), d_rois + b,
+                                                (cudaStream_t)s);
+        if (e != cudaSuccess) return EC_ERR_CUDA;
+    }
+    return EC_OK;
 }
 
 size_t ec_rle_max_size(int32_t w, int32_t h)

@@ -16,6 +16,8 @@ struct ec_ctx {
     uint32_t* d_status = nullptr;   // first device-side error (0 = none)
     void* scratch = nullptr;        // codec look-back flags + ticket counter
     size_t scratch_bytes = 0;
+    void* roi_scratch = nullptr;    // ROI detection: per-image box accumulators + done counter
+    size_t roi_scratch_bytes = 0;
     int sm_count = 0;
 };
 
@@ -164,5 +166,39 @@ cudaError_t launch_rle_compress(const RleJobDesc* jobs, int n, uint32_t total_un
                                 void* scratch, uint32_t* status, cudaStream_t s);
 cudaError_t launch_rle_decompress(const RleJobDesc* jobs, int n, uint32_t total_units,
                                   uint32_t* status, cudaStream_t s);
+
+// ---- automatic region of interest -------------------------------------------
+
+// One image of an ROI detection launch (64 bytes).  The image is scanned in
+// 64 x 64 blocks aligned to its pvp origin; [x0,x1) x [y0,y1) are the searched
+// pixels relative to that origin.
+struct RoiDesc {
+    int32_t x0, y0, x1, y1;
+    int32_t ox, oy;            // pvp origin in destination coordinates
+    int32_t pitch;
+    int32_t gw, gh;            // occupancy grid (tiles)
+    int32_t bw;                // 64-pixel blocks along x
+    uint32_t first_block;      // first CTA of this image
+    int16_t kind;              // 0 depth, 1 RGBA8, 2 RGBA32F, 3 RGBA16F
+    int16_t vec;               // 16-byte loads allowed
+    const void* data;          // depth or colour, pvp pixel (0, 0)
+    uint8_t* occ;              // occupancy grid or null
+};
+static_assert(sizeof(RoiDesc) == 64, "roi descriptor layout");
+
+constexpr int kRoiPerLaunch = 256;
+
+template <int N>
+struct RoiList {
+    int32_t n;
+    uint32_t blocks;           // CTAs with work (the launch may have one more)
+    int32_t tile;
+    int32_t pad;
+    RoiDesc d[N];
+};
+
+// scratch: 4 box accumulators per image, then one done counter (all zeroed)
+cudaError_t launch_detect_roi(const RoiDesc* d, int n, int tile, uint32_t blocks, uint32_t* scratch,
+                              ec_rect* out, cudaStream_t s);
 
 }  // namespace ec
