@@ -11,7 +11,7 @@ its size is written, then another 2x its size is read, so that the timed step
 neither finds its inputs in L2 nor pays for writing back the flush's lines.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ec|reference]
-                    [--workload cfg2|cfg1|cfg3|cfg3h|cfg3fused|cfg3hfused|cfg4|cfg5d|cfg5a|cfg5afused]
+                    [--workload cfg2|cfg1|cfg3|cfg3h|cfg3fused|cfg3hfused|cfg4|cfg5d|cfg5a|cfg5afused|roi2]
 
 Prints ONE JSON line (rank 0).  Metric: composited Gpixel-layers/s (sum over
 sources of |roi_i ∩ frame| per step, divided by the step time).  With N > 1
@@ -386,6 +386,76 @@ class AlphaFused(AlphaForward):
         self.h_out.copy_(self.out, non_blocking=True)
 
 
+class RoiDetect:
+    """roi2: automatic ROI (thesis 5.3) of the 16 uncropped 1920x1080 sources of
+    the depth pipeline: every depth buffer is scanned for pixels below the
+    cleared depth, giving each source's bounding box and 64-px tile occupancy
+    grid (holes), all in one launch."""
+
+    def __init__(self, cfg, n, W, H, coverage, device, tile=64):
+        import ctypes as C
+
+        import paper_1902_08755_gb300 as ec
+        from paper_1902_08755_gb300 import _abi as A
+        import synthetic as S
+        self.ec = ec
+        self.W, self.H, self.n, self.tile = W, H, n, tile
+        self.desc = (f"{n} uncropped sources {W}x{H} (~{int(coverage * 100)}% coverage, clustered): "
+                     f"bounding box of depth < 1 and {tile}-px occupancy grids, one launch")
+        self.srcs = S.depth_sources(cfg, n, W, H, coverage, clustered=True, device=device)
+        self.units = n * W * H
+        self.kernels = ["detect_roi"]
+        self.gw, self.gh = -(-W // tile), -(-H // tile)
+        if torch.device(device).type != "cuda":
+            return
+        self.ctx = ec.default_context(torch.device(device).index or 0)
+        self.rois = torch.zeros((n, 4), dtype=torch.int32, device=device)
+        self.grids = [torch.empty((self.gh, self.gw), dtype=torch.uint8, device=device) for _ in range(n)]
+        # the C entry point with arguments marshalled once
+        self._arr = (A.ec_image * n)(*[A.ec_image(A.ec_rect(0, 0, W, H), A.ec_rect(0, 0, W, H), W, A.EC_RGBA8,
+                                                  s.color.data_ptr(), s.depth.data_ptr()) for s in self.srcs])
+        self._occ = (C.c_void_p * n)(*[g.data_ptr() for g in self.grids])
+        self._fn = A.load().ec_detect_roi
+
+    def step(self, ev=None):
+        if ev:
+            ev[0].record()
+        rc = self._fn(self.ctx.h, self._arr, self.n, self.tile, self._occ, self.rois.data_ptr(),
+                      torch.cuda.current_stream().cuda_stream)
+        if rc:
+            raise SystemExit(f"ec_detect_roi failed: {rc}")
+        if ev:
+            ev[1].record()
+
+    def launches_per_step(self):
+        return 1
+
+    def algorithmic_bytes(self):
+        return {"detect_roi": 4 * self.units + self.n * (self.gw * self.gh + 16)}
+
+    def setup_e2e(self):
+        self.h_depth = [s.depth.cpu().pin_memory() for s in self.srcs]
+        self.h_rois = torch.empty((self.n, 4), dtype=torch.int32).pin_memory()
+        self.h2d = 4 * self.units
+        self.d2h = self.n * 16
+
+    def e2e_step(self):
+        for s, h in zip(self.srcs, self.h_depth):
+            s.depth.copy_(h, non_blocking=True)
+        self.step()
+        self.h_rois.copy_(self.rois, non_blocking=True)
+
+    def oracle_step(self, pool, cores):
+        import oracle
+        host = [s.depth.cpu().numpy() for s in self.srcs[:min(self.n, cores)]]
+        t0 = time.perf_counter()
+        full = (0, 0, self.W, self.H)
+        list(pool.map(lambda d: oracle.detect_roi(full, full, self.W, 0, depth=d, tile=self.tile), host))
+        self.sample_fraction = len(host) / self.n
+        self.sample_desc = f"{len(host)} of the {self.n} sources"
+        return (time.perf_counter() - t0) / self.sample_fraction
+
+
 class BatchedTiles:
     """cfg4: 1000 uneven tiles (w, h log-uniform in [16, 1024], 2..64 layers, half
     depth RGBA8+Z32 at 30% box coverage, half alpha FP32 with a <= 0.3), all in
@@ -534,6 +604,8 @@ def make_workload(name, device):
         return DepthPipeline(5, 64, 7680, 4320, 0.25, True, True, device)
     if name == "cfg4":
         return BatchedTiles(device)
+    if name == "roi2":
+        return RoiDetect(2, 16, 1920, 1080, 0.3, device)
     if name == "cfg3":
         return AlphaForward(3, 32, 2048, 2048, 0.3, torch.float32, device)
     if name == "cfg3h":
@@ -562,7 +634,8 @@ def cpu_baseline(wl, budget_s=12.0, max_reps=20):
     t = statistics.median(times)
     frac = getattr(wl, "sample_fraction", 1.0)
     sample = (f"{len(times)} full steps of the workload" if frac == 1.0 else
-              f"{len(times)} x the first {frac:.4f} of each frame's rows, scaled to a full step")
+              f"{len(times)} x " + getattr(wl, "sample_desc", f"the first {frac:.4f} of each frame's rows") +
+              ", scaled to a full step")
     return {"value": wl.units / t / 1e9, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": sample, "ms_per_step": t * 1e3}
 
@@ -585,7 +658,8 @@ def run_reference(args):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "rgba8+f32",
             "data": "synthetic", "config": {"workload": f"{args.workload}: {wl.desc}"},
             "cpu_baseline": {"value": val, "unit": UNIT, "cores": cores, "kind": "oracle",
-                             "sample": "full steps" if frac == 1.0 else f"first {frac:.4f} of rows, scaled"},
+                             "sample": "full steps" if frac == 1.0 else
+                             getattr(wl, "sample_desc", f"first {frac:.4f} of rows") + ", scaled"},
             "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -670,7 +744,7 @@ def run_ec(args):
         cfg["rle_raw_bytes_per_step"] = 8 * wl.stored_px
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": max(3, args.warmup), "ms_per_step": ms, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "rgba8+f32" if isinstance(wl, (DepthPipeline, BatchedTiles)) else "f32",
+            "scaling": "weak", "vs_baseline": None, "dtype": "rgba8+f32" if isinstance(wl, (DepthPipeline, BatchedTiles, RoiDetect)) else "f32",
             "data": "synthetic (seeded boxes / layers shaped like the thesis's workloads)",
             "config": cfg, "roofline": roof, "kernels": kern,
             "e2e": {"value": whole_job_value(wl.units, e2e_ms, world), "unit": UNIT,

@@ -146,6 +146,8 @@ ec_status ensure_roi_scratch(ec_ctx* ctx, size_t bytes)
     ctx->roi_scratch_bytes = 0;
     bytes = std::max<size_t>(bytes, 16 * 1024);
     if (cudaMalloc(&ctx->roi_scratch, bytes) != cudaSuccess) return EC_ERR_CUDA;
+    // the accumulators start at zero; every launch leaves them zero
+    if (cudaMemset(ctx->roi_scratch, 0, bytes) != cudaSuccess) return EC_ERR_CUDA;
     ctx->roi_scratch_bytes = bytes;
     return EC_OK;
 }
@@ -290,6 +292,7 @@ ec_status ec_detect_roi(ec_ctx* ctx, const ec_image* in, int32_t n, int32_t tile
     if (reinterpret_cast<uintptr_t>(d_rois) & 3u) return EC_ERR_INVALID_ARG;
     std::vector<RoiDesc> d((size_t)std::max(n, 1));
     std::vector<uint64_t> nblocks((size_t)std::max(n, 1));
+    std::vector<int> kinds((size_t)std::max(n, 1));
     for (int i = 0; i < n; ++i) {
         const ec_image& im = in[i];
         if (!rect_ok(im.pvp) || !rect_ok(im.roi) || im.pitch < im.pvp.w || im.pitch < 0 ||
@@ -319,9 +322,9 @@ ec_status ec_detect_roi(ec_ctx* ctx, const ec_image* in, int32_t n, int32_t tile
         r.pitch = im.pitch;
         r.gw = (im.pvp.w + tile - 1) / tile;
         r.gh = (im.pvp.h + tile - 1) / tile;
-        r.bw = (im.pvp.w + 63) / 64;
-        nblocks[i] = (uint64_t)r.bw * (uint64_t)((im.pvp.h + 63) / 64);
-        r.kind = (int16_t)kind;
+        r.bw = (im.pvp.w + kRoiBlkW - 1) / kRoiBlkW;
+        nblocks[i] = (uint64_t)r.bw * (uint64_t)((im.pvp.h + kRoiBlkH - 1) / kRoiBlkH);
+        kinds[i] = kind;
         r.vec = (int16_t)(aligned16(data) && ((int64_t)im.pitch * bpp) % 16 == 0);
         r.data = data;
         r.occ = occupancy ? occupancy[i] : nullptr;
@@ -331,14 +334,16 @@ ec_status ec_detect_roi(ec_ctx* ctx, const ec_image* in, int32_t n, int32_t tile
     for (int b = 0; b < n; b += kRoiPerLaunch) {
         const int cnt = std::min(kRoiPerLaunch, n - b);
         uint64_t blocks = 0;
+        std::vector<uint32_t> nb((size_t)cnt);
         for (int i = 0; i < cnt; ++i) {
-            d[b + i].first_block = (uint32_t)blocks;
+            d[b + i].idx = (int16_t)i;
+            nb[i] = (uint32_t)nblocks[b + i];
             blocks += nblocks[b + i];
         }
         if (blocks >= (1ull << 31)) return EC_ERR_UNSUPPORTED;
-        const ec_status st = ensure_roi_scratch(ctx, (4ull * cnt + 1) * sizeof(uint32_t));
+        const ec_status st = ensure_roi_scratch(ctx, 4ull * cnt * sizeof(uint32_t));
         if (st != EC_OK) return st;
-        const cudaError_t e = launch_detect_roi(&d[b], cnt, tile, (uint32_t)blocks,
+        const cudaError_t e = launch_detect_roi(&d[b], &kinds[b], nb.data(), cnt, tile,
                                                 reinterpret_cast<uint32_t*>(ctx->roi_scratch), d_rois + b,
                                                 (cudaStream_t)s);
         if (e != cudaSuccess) return EC_ERR_CUDA;

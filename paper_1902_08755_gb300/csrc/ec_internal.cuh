@@ -170,16 +170,16 @@ cudaError_t launch_rle_decompress(const RleJobDesc* jobs, int n, uint32_t total_
 // ---- automatic region of interest -------------------------------------------
 
 // One image of an ROI detection launch (64 bytes).  The image is scanned in
-// 64 x 64 blocks aligned to its pvp origin; [x0,x1) x [y0,y1) are the searched
-// pixels relative to that origin.
+// kRoiBlkW x kRoiBlkH blocks aligned to its pvp origin; [x0,x1) x [y0,y1) are
+// the searched pixels relative to that origin.
 struct RoiDesc {
     int32_t x0, y0, x1, y1;
     int32_t ox, oy;            // pvp origin in destination coordinates
     int32_t pitch;
     int32_t gw, gh;            // occupancy grid (tiles)
-    int32_t bw;                // 64-pixel blocks along x
-    uint32_t first_block;      // first CTA of this image
-    int16_t kind;              // 0 depth, 1 RGBA8, 2 RGBA32F, 3 RGBA16F
+    int32_t bw;                // blocks along x
+    uint32_t first_block;      // first CTA of this image (within its kind's launch)
+    int16_t idx;               // image index within the call (accumulators, output)
     int16_t vec;               // 16-byte loads allowed
     const void* data;          // depth or colour, pvp pixel (0, 0)
     uint8_t* occ;              // occupancy grid or null
@@ -187,6 +187,7 @@ struct RoiDesc {
 static_assert(sizeof(RoiDesc) == 64, "roi descriptor layout");
 
 constexpr int kRoiPerLaunch = 256;
+constexpr int kRoiBlkW = 64, kRoiBlkH = 128;    // pixels one CTA scans
 
 template <int N>
 struct RoiList {
@@ -197,8 +198,10 @@ struct RoiList {
     RoiDesc d[N];
 };
 
-// scratch: 4 box accumulators per image, then one done counter (all zeroed)
-cudaError_t launch_detect_roi(const RoiDesc* d, int n, int tile, uint32_t blocks, uint32_t* scratch,
-                              ec_rect* out, cudaStream_t s);
+// Images of one call: kinds[i] is 0 depth, 1 RGBA8, 2 RGBA32F, 3 RGBA16F;
+// nblocks[i] the image's blocks.  scratch holds 4 box accumulators per image,
+// 16-byte aligned; they must be zero on entry and are zero again on exit.
+cudaError_t launch_detect_roi(RoiDesc* d, const int* kinds, const uint32_t* nblocks, int n, int tile,
+                              uint32_t* scratch, ec_rect* out, cudaStream_t s);
 
 }  // namespace ec
