@@ -78,6 +78,13 @@ def lib():
         L.orc_composite_depth_backward.restype = C.c_int
         L.orc_composite_depth_backward.argtypes = [C.c_void_p, Rect, C.c_void_p, C.c_int32,
                                                    C.c_void_p, C.c_void_p, C.c_void_p]
+        L.orc_assemble_tiles.restype = C.c_int
+        L.orc_assemble_tiles.argtypes = [C.c_void_p, C.c_int32, C.c_int32, Rect, C.c_int32, C.c_void_p]
+        L.orc_assemble_pixels.restype = C.c_int
+        L.orc_assemble_pixels.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32,
+                                          C.c_int32, C.c_int32, C.c_int32, Rect, C.c_int32, C.c_void_p]
+        L.orc_average.restype = C.c_int
+        L.orc_average.argtypes = [C.c_void_p, C.c_int32, C.c_int32, Rect, C.c_int32, C.c_void_p]
         L.orc_detect_roi.restype = C.c_int
         L.orc_detect_roi.argtypes = [Rect, Rect, C.c_int32, C.c_int32, C.c_void_p, C.c_void_p,
                                      C.c_int32, C.c_void_p, C.POINTER(Rect)]
@@ -232,6 +239,63 @@ def composite_depth_backward(winner: np.ndarray, out_pvp, g: np.ndarray, pvps, p
     if rc:
         raise OracleError(rc, "composite_depth_backward")
     return grads
+
+
+def _pixel_bytes(a: np.ndarray) -> int:
+    return a.itemsize * int(np.prod(a.shape[2:], dtype=np.int64))
+
+
+def assemble_tiles(images: Sequence[Image], out: np.ndarray, out_pvp) -> np.ndarray:
+    """Sort-first / tile assembly: copy every image's roi (clipped to out_pvp) into
+    a copy of out ([h][pitch](...)), in order; returns the assembled array."""
+    out = np.ascontiguousarray(out).copy()
+    bpp = _pixel_bytes(out)
+    arr = (_Layer * max(1, len(images)))()
+    for i, im in enumerate(images):
+        _check_c(im.color, "color")
+        if _pixel_bytes(im.color) != bpp:
+            raise ValueError("pixel size differs from the output's")
+        arr[i] = _Layer(_rect(im.pvp), _rect(im.roi), im.pitch, _ptr(im.color))
+    rc = lib().orc_assemble_tiles(arr, len(images), bpp, _rect(out_pvp), out.shape[1] if out.ndim > 1 else 0,
+                                  _ptr(out) if out.size else None)
+    if rc:
+        raise OracleError(rc, "assemble_tiles")
+    return out
+
+
+def assemble_pixels(srcs: Sequence[np.ndarray], offsets, kernel, out: np.ndarray, out_pvp) -> np.ndarray:
+    """Pixel-compound assembly: source k ([h_k][pitch_k](...)) holds the destination
+    pixels at offsets (kx + i*nx, ky + j*ny); returns the assembled copy of out."""
+    out = np.ascontiguousarray(out).copy()
+    bpp = _pixel_bytes(out)
+    n = len(srcs)
+    for a in srcs:
+        _check_c(a, "source")
+    ptrs = (C.c_void_p * max(1, n))(*[_ptr(a) for a in srcs])
+    pitches = (C.c_int32 * max(1, n))(*[int(a.shape[1]) for a in srcs])
+    kx = (C.c_int32 * max(1, n))(*[int(o[0]) for o in offsets])
+    ky = (C.c_int32 * max(1, n))(*[int(o[1]) for o in offsets])
+    rc = lib().orc_assemble_pixels(ptrs, pitches, kx, ky, n, int(kernel[0]), int(kernel[1]), bpp,
+                                   _rect(out_pvp), out.shape[1], _ptr(out) if out.size else None)
+    if rc:
+        raise OracleError(rc, "assemble_pixels")
+    return out
+
+
+def average(images: Sequence[Image], out_pvp, fmt: int) -> np.ndarray:
+    """Subpixel-compound assembly: per-pixel average of the sources whose roi holds
+    it.  fmt 0 (RGBA8): uint32 [h][w] with integer rounding; fmt 1/2 (float32 /
+    float16 storage): float64 [h][w][4]."""
+    W, H = max(out_pvp[2], 0), max(out_pvp[3], 0)
+    arr = (_Layer * max(1, len(images)))()
+    for i, im in enumerate(images):
+        _check_c(im.color, "color")
+        arr[i] = _Layer(_rect(im.pvp), _rect(im.roi), im.pitch, _ptr(im.color))
+    out = np.zeros((H, W), dtype=np.uint32) if fmt == 0 else np.zeros((H, W, 4), dtype=np.float64)
+    rc = lib().orc_average(arr, len(images), int(fmt), _rect(out_pvp), W, _ptr(out) if out.size else None)
+    if rc:
+        raise OracleError(rc, "average")
+    return out
 
 
 def detect_roi(pvp, search, pitch: int, fmt: int, color: Optional[np.ndarray] = None,

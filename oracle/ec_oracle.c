@@ -582,3 +582,87 @@ int orc_detect_roi(orc_rect pvp, orc_rect search, int32_t pitch, int32_t format,
     roi->h = (int32_t)(by1 - by0 + 1);
     return ORC_OK;
 }
+
+/* ---- assembly of the other compound modes (thesis 4.2) ----------------- */
+
+static int in_rect(orc_rect r, int64_t x, int64_t y)
+{
+    return x >= r.x && x < (int64_t)r.x + r.w && y >= r.y && y < (int64_t)r.y + r.h;
+}
+
+int orc_assemble_tiles(const orc_layer* src, int32_t n, int32_t bpp, orc_rect out_pvp,
+                       int32_t out_pitch, void* out)
+{
+    if (n < 0 || (bpp != 4 && bpp != 8 && bpp != 16) || out_pitch < out_pvp.w) return ORC_EINVAL;
+    uint8_t* o = (uint8_t*)out;
+    for (int32_t i = 0; i < n; ++i) {
+        const orc_layer* s = &src[i];
+        for (int64_t py = out_pvp.y; py < (int64_t)out_pvp.y + out_pvp.h; ++py) {
+            for (int64_t px = out_pvp.x; px < (int64_t)out_pvp.x + out_pvp.w; ++px) {
+                if (!in_rect(s->roi, px, py) || !in_rect(s->pvp, px, py)) continue;
+                const size_t e = (size_t)((py - s->pvp.y) * s->pitch + (px - s->pvp.x));
+                const size_t d = (size_t)((py - out_pvp.y) * out_pitch + (px - out_pvp.x));
+                memcpy(o + d * bpp, (const uint8_t*)s->color + e * bpp, (size_t)bpp);
+            }
+        }
+    }
+    return ORC_OK;
+}
+
+int orc_assemble_pixels(const void* const* src, const int32_t* pitch, const int32_t* kx,
+                        const int32_t* ky, int32_t n, int32_t nx, int32_t ny, int32_t bpp,
+                        orc_rect out_pvp, int32_t out_pitch, void* out)
+{
+    if (n < 0 || nx < 1 || ny < 1 || (bpp != 4 && bpp != 8 && bpp != 16) || out_pitch < out_pvp.w)
+        return ORC_EINVAL;
+    uint8_t* o = (uint8_t*)out;
+    for (int32_t k = 0; k < n; ++k) {
+        if (kx[k] < 0 || kx[k] >= nx || ky[k] < 0 || ky[k] >= ny) return ORC_EINVAL;
+        const int64_t w = out_pvp.w > kx[k] ? (out_pvp.w - kx[k] + nx - 1) / nx : 0;
+        const int64_t h = out_pvp.h > ky[k] ? (out_pvp.h - ky[k] + ny - 1) / ny : 0;
+        if (pitch[k] < w) return ORC_EINVAL;
+        for (int64_t j = 0; j < h; ++j) {
+            for (int64_t i = 0; i < w; ++i) {
+                const int64_t dx = kx[k] + i * nx, dy = ky[k] + j * ny;
+                memcpy(o + (size_t)(dy * out_pitch + dx) * bpp,
+                       (const uint8_t*)src[k] + (size_t)(j * pitch[k] + i) * bpp, (size_t)bpp);
+            }
+        }
+    }
+    return ORC_OK;
+}
+
+int orc_average(const orc_layer* src, int32_t n, int32_t format, orc_rect out_pvp,
+                int32_t out_pitch, void* out)
+{
+    if (n < 0 || (format != 0 && format != ORC_F32 && format != ORC_F16) || out_pitch < out_pvp.w)
+        return ORC_EINVAL;
+    for (int64_t py = out_pvp.y; py < (int64_t)out_pvp.y + out_pvp.h; ++py) {
+        for (int64_t px = out_pvp.x; px < (int64_t)out_pvp.x + out_pvp.w; ++px) {
+            const size_t d = (size_t)((py - out_pvp.y) * out_pitch + (px - out_pvp.x));
+            uint64_t isum[4] = {0, 0, 0, 0};
+            double fsum[4] = {0.0, 0.0, 0.0, 0.0};
+            int64_t count = 0;
+            for (int32_t i = 0; i < n; ++i) {
+                const orc_layer* s = &src[i];
+                if (!in_rect(s->roi, px, py) || !in_rect(s->pvp, px, py)) continue;
+                const size_t e = (size_t)((py - s->pvp.y) * s->pitch + (px - s->pvp.x));
+                ++count;
+                for (int ch = 0; ch < 4; ++ch) {
+                    if (format == 0) isum[ch] += (((const uint32_t*)s->color)[e] >> (8 * ch)) & 0xFFu;
+                    else if (format == ORC_F32) fsum[ch] += ((const float*)s->color)[4 * e + ch];
+                    else fsum[ch] += half_to_double(((const uint16_t*)s->color)[4 * e + ch]);
+                }
+            }
+            if (format == 0) {
+                uint32_t v = 0;
+                for (int ch = 0; ch < 4; ++ch)
+                    if (count) v |= (uint32_t)((isum[ch] + (uint64_t)count / 2) / (uint64_t)count) << (8 * ch);
+                ((uint32_t*)out)[d] = v;
+            } else {
+                for (int ch = 0; ch < 4; ++ch) ((double*)out)[4 * d + ch] = count ? fsum[ch] / (double)count : 0.0;
+            }
+        }
+    }
+    return ORC_OK;
+}

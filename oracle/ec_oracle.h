@@ -87,6 +87,34 @@ int orc_composite_depth_backward(const int16_t* winner, orc_rect out_pvp,
                                  const float* g, int32_t n, const orc_rect* pvps,
                                  const int32_t* pitches, float* const* grad);
 
+/* ---- assembly of the other compound modes (thesis 4.2) -------------------
+ * Tile assembly (sort-first and tile compounds): the roi of every source,
+ * clipped to out_pvp, is copied bit for bit (bpp = 4, 8 or 16 bytes per pixel)
+ * to the same destination pixels, sources in ascending order, so a later one
+ * overwrites an earlier one where they overlap.  Output pixels no roi covers
+ * are left unchanged. */
+int orc_assemble_tiles(const orc_layer* src, int32_t n, int32_t bpp, orc_rect out_pvp,
+                       int32_t out_pitch, void* out);
+
+/* Pixel compound: the destination is interleaved over an nx x ny pixel
+ * kernel.  Source k owns the pixels at offsets (kx[k] + i*nx, ky[k] + j*ny)
+ * from the out_pvp origin, 0 <= kx[k] < nx, 0 <= ky[k] < ny, and stores them
+ * densely: its element j*pitch[k] + i is destination offset (kx[k] + i*nx,
+ * ky[k] + j*ny), for i < ceil((out_pvp.w - kx[k]) / nx) and
+ * j < ceil((out_pvp.h - ky[k]) / ny).  Pixels are copied bit for bit, sources
+ * in ascending order; destination pixels no source owns are left unchanged. */
+int orc_assemble_pixels(const void* const* src, const int32_t* pitch, const int32_t* kx,
+                        const int32_t* ky, int32_t n, int32_t nx, int32_t ny, int32_t bpp,
+                        orc_rect out_pvp, int32_t out_pitch, void* out);
+
+/* Subpixel compound: every output pixel is the average of the sources whose
+ * roi holds it, channel by channel.  format 0 (RGBA8): per 8-bit channel the
+ * integer (sum + count/2) / count, written to out as uint32 pixels; ORC_F32 /
+ * ORC_F16 sources: the exact average, written to out as doubles (4 per pixel).
+ * Pixels no roi holds become 0.  out is [out_pvp.h][out_pitch] pixels. */
+int orc_average(const orc_layer* src, int32_t n, int32_t format, orc_rect out_pvp,
+                int32_t out_pitch, void* out);
+
 /* ---- automatic region of interest (thesis 5.3) ---------------------------
  * The ROI found by scanning a frame buffer instead of being supplied by the
  * application: the bounding box of the pixels that hold rendered data, plus a

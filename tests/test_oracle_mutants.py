@@ -19,6 +19,7 @@ import test_oracle_depth as TD
 import test_oracle_depth_grad as TG
 import test_oracle_rle as TR
 import test_oracle_roi as TO
+import test_oracle_assemble as TS
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 ORACLE = os.path.join(ROOT, "oracle")
@@ -47,6 +48,11 @@ MUTANTS = {
     "roi_max_x_dropped": ("if (x > bx1) bx1 = x;", ""),
     "roi_occ_transposed": ("occ[(y / tile) * gw + x / tile] = 1;", "occ[(x / tile) * gw + y / tile] = 1;"),
     "roi_search_not_clipped": ("if (x1 > pvp.w) x1 = pvp.w;", ""),
+    "tiles_ignore_roi": ("if (!in_rect(s->roi, px, py) || !in_rect(s->pvp, px, py)) continue;\n                const size_t e = (size_t)((py - s->pvp.y) * s->pitch + (px - s->pvp.x));\n                const size_t d",
+                         "if (!in_rect(s->pvp, px, py)) continue;\n                const size_t e = (size_t)((py - s->pvp.y) * s->pitch + (px - s->pvp.x));\n                const size_t d"),
+    "pixels_drop_offset": ("const int64_t dx = kx[k] + i * nx, dy = ky[k] + j * ny;", "const int64_t dx = i * nx, dy = ky[k] + j * ny;"),
+    "average_no_rounding": ("((isum[ch] + (uint64_t)count / 2) / (uint64_t)count)", "((isum[ch]) / (uint64_t)count)"),
+    "average_counts_all": ("                ++count;\n", ""),
 }
 
 
@@ -89,6 +95,10 @@ def _pins(orc):
     yield lambda: [TO.test_matches_numpy_reductions(orc, f, s) for f in ("depth", 0, 1, 2) for s in range(4)]
     yield lambda: TO.test_search_region_limits_the_scan(orc)
     yield lambda: TO.test_special_values(orc)
+    yield lambda: TS.test_tile_order_roi_and_untouched_pixels(orc)
+    yield lambda: [TS.test_pixel_decomposition_reassembles(orc, "rgba8", k) for k in ((2, 2), (4, 3))]
+    yield lambda: TS.test_rgba8_average_rounding_and_coverage(orc)
+    yield lambda: TS.test_float_average_matches_numpy_mean(orc, "f32", 1)
 
 
 def _caught(orc):
