@@ -230,6 +230,38 @@ ec_status ec_batch_get_config(const ec_batch* plan, ec_batch_config* cfg, int32_
                               int32_t* grid);
 void ec_batch_free(ec_batch* plan);
 
+/* ------------------------------------------ assembly of the other compound modes
+ * Thesis 4.2: sort-first and tile compounds compute complete pixels per source
+ * and copy them into place; pixel compounds interleave the destination's
+ * pixels over a pixel kernel; subpixel compounds average the samples every
+ * source computed for a pixel.  Inputs and output share one colour format
+ * (RGBA8, RGBA32F or RGBA16F); depth is neither read nor written.
+ *
+ * ec_assemble_tiles: the roi of every input, clipped to out->pvp, is copied
+ * bit for bit to the same destination pixels, inputs in ascending order (a
+ * later input overwrites an earlier one where they overlap).  Output pixels
+ * no roi covers are left unchanged.  n <= EC_MAX_SOURCES. */
+ec_status ec_assemble_tiles(ec_ctx* ctx, const ec_image* in, int32_t n, const ec_target* out,
+                            ec_stream_t s);
+
+/* ec_assemble_pixels: the destination is interleaved over an nx x ny pixel
+ * kernel (1 <= nx, ny <= 16).  Input k owns the pixels at offsets
+ * (kx[k] + i*nx, ky[k] + j*ny) from out->pvp's origin (0 <= kx[k] < nx,
+ * 0 <= ky[k] < ny; host arrays) and stores them densely: its pixel (i, j) is
+ * element j*pitch + i of in[k].color, an image of ceil((out.w - kx)/nx) x
+ * ceil((out.h - ky)/ny) pixels (in[k].pvp and roi are not used).  Later inputs
+ * overwrite earlier ones; pixels no input owns are left unchanged.
+ * n <= 256. */
+ec_status ec_assemble_pixels(ec_ctx* ctx, const ec_image* in, const int32_t* kx, const int32_t* ky,
+                             int32_t n, int32_t nx, int32_t ny, const ec_target* out, ec_stream_t s);
+
+/* ec_average: every pixel of out->pvp becomes the average of the inputs whose
+ * roi holds it, channel by channel: RGBA8 (sum + count/2) / count in
+ * integers; RGBA32F and RGBA16F the FP32 sum in input order divided by the
+ * count, stored in the output type.  Pixels no roi holds become 0.
+ * n <= EC_MAX_SOURCES. */
+ec_status ec_average(ec_ctx* ctx, const ec_image* in, int32_t n, const ec_target* out, ec_stream_t s);
+
 /* ------------------------------------------------- automatic region of interest
  * Thesis 5.3: instead of the application supplying each frame's ROI, it can be
  * computed by analysing the frame buffer, which also detects holes.

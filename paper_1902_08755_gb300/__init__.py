@@ -25,6 +25,9 @@ from .api import (  # noqa: F401
     Context,
     Job,
     Image,
+    assemble_pixels,
+    assemble_tiles,
+    average,
     composite_alpha,
     composite_alpha_backward,
     composite_alpha_fwd_bwd,

@@ -86,6 +86,9 @@ SIGNATURES = {
     "ec_composite_alpha_fwd_bwd": (_S, [_P, _P, _P, _I, _P, _P, _P, _P, _I, C.POINTER(ec_rect), _P]),
     "ec_composite_depth_backward": (_S, [_P, _P, _R, _P, _I, _P, _P, _P, _P]),
     "ec_detect_roi": (_S, [_P, _P, _I, _I, _P, _P, _P]),
+    "ec_assemble_tiles": (_S, [_P, _P, _I, _P, _P]),
+    "ec_assemble_pixels": (_S, [_P, _P, _P, _P, _I, _I, _I, _P, _P]),
+    "ec_average": (_S, [_P, _P, _I, _P, _P]),
     "ec_rle_max_size": (C.c_size_t, [_I, _I]),
     "ec_rle_compress": (_S, [_P, _P, _I, _I, _I, C.c_uint32, _P, C.c_size_t, _P, _P]),
     "ec_rle_decompress": (_S, [_P, _P, C.c_size_t, _P, _I, _I, _I, _P]),

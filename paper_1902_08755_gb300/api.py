@@ -248,6 +248,47 @@ def composite_alpha_fwd_bwd(layers: Sequence[Image], out: torch.Tensor, w: torch
     return roi.tup()
 
 
+def assemble_tiles(images: Sequence[Image], out: torch.Tensor, out_pvp: Optional[Rect] = None,
+                   ctx: Optional[Context] = None, stream=None):
+    """ec_assemble_tiles: copy every image's roi into out (later images win)."""
+    ctx = ctx or default_context(out.device.index)
+    dev = ctx.device
+    n = len(images)
+    arr = (ec_image * max(1, n))(*[_image_struct(im, dev, False) for im in images])
+    tgt = _target(out, None, out_pvp, dev)
+    check(_lib().ec_assemble_tiles(ctx.h, arr, n, C.byref(tgt), _stream_handle(stream)), "ec_assemble_tiles")
+
+
+def average(images: Sequence[Image], out: torch.Tensor, out_pvp: Optional[Rect] = None,
+            ctx: Optional[Context] = None, stream=None):
+    """ec_average: per-pixel average of the images whose roi holds the pixel."""
+    ctx = ctx or default_context(out.device.index)
+    dev = ctx.device
+    n = len(images)
+    arr = (ec_image * max(1, n))(*[_image_struct(im, dev, False) for im in images])
+    tgt = _target(out, None, out_pvp, dev)
+    check(_lib().ec_average(ctx.h, arr, n, C.byref(tgt), _stream_handle(stream)), "ec_average")
+
+
+def assemble_pixels(sources: Sequence[torch.Tensor], offsets, kernel, out: torch.Tensor,
+                    out_pvp: Optional[Rect] = None, ctx: Optional[Context] = None, stream=None):
+    """ec_assemble_pixels: sources[k] holds the pixels at offsets (kx + i*nx, ky + j*ny)."""
+    ctx = ctx or default_context(out.device.index)
+    dev = ctx.device
+    n = len(sources)
+    structs = []
+    for t in sources:
+        fmt, pitch, w, h = pixel_layout(t)
+        _on_device(t, dev, "source")
+        structs.append(ec_image(_rect((0, 0, w, h)), _rect((0, 0, w, h)), pitch, fmt, t.data_ptr(), None))
+    arr = (ec_image * max(1, n))(*structs)
+    kx = (C.c_int32 * max(1, n))(*[int(o[0]) for o in offsets])
+    ky = (C.c_int32 * max(1, n))(*[int(o[1]) for o in offsets])
+    tgt = _target(out, None, out_pvp, dev)
+    check(_lib().ec_assemble_pixels(ctx.h, arr, kx, ky, n, int(kernel[0]), int(kernel[1]), C.byref(tgt),
+                                    _stream_handle(stream)), "ec_assemble_pixels")
+
+
 def detect_roi(images: Sequence[Image], tile: int = 64, occupancy: bool = True,
                ctx: Optional[Context] = None, stream=None):
     """ec_detect_roi: bounding box of each image's data pixels inside its roi

@@ -283,6 +283,102 @@ ec_status ec_composite_alpha(ec_ctx* ctx, const ec_image* in, const int32_t* ord
     return cuda_status(launch_alpha_fwd(d.data(), n, f16, D, (cudaStream_t)s));
 }
 
+// Target of an assembly call: any colour format, 4-byte aligned pixels.
+static ec_status check_assembly_target(const ec_target* out)
+{
+    if (!out || bytes_per_px(out->format) == 0) return EC_ERR_INVALID_ARG;
+    const ec_status st = check_target(out, out->format, out->format);
+    if (st != EC_OK) return st;
+    if (!rect_empty(out->pvp) && (reinterpret_cast<uintptr_t>(out->color) & 3u)) return EC_ERR_INVALID_ARG;
+    return EC_OK;
+}
+
+// Inputs of an assembly call: same colour format as the target, descriptors
+// relative to out->pvp.
+static ec_status assembly_descs(const ec_image* in, int32_t n, const ec_target* out, std::vector<SrcDesc>& d)
+{
+    const int bpp = bytes_per_px(out->format);
+    d.assign((size_t)std::max(n, 1), SrcDesc{});
+    for (int i = 0; i < n; ++i) {
+        if (in[i].format != out->format) return EC_ERR_INVALID_ARG;
+        const ec_status st = make_desc(in[i], out->pvp, 16 / bpp, false, &d[i]);
+        if (st != EC_OK) return st;
+        if (d[i].x1 > d[i].x0 && (reinterpret_cast<uintptr_t>(in[i].color) & 3u)) return EC_ERR_INVALID_ARG;
+    }
+    return EC_OK;
+}
+
+static DstDesc assembly_target(const ec_target* out)
+{
+    const int bpp = bytes_per_px(out->format);
+    DstDesc D;
+    memset(&D, 0, sizeof(D));
+    D.W = out->pvp.w;
+    D.H = out->pvp.h;
+    D.pitch = out->pitch;
+    D.vec = aligned16(out->color) && ((int64_t)out->pitch * bpp) % 16 == 0;
+    D.color = out->color;
+    return D;
+}
+
+ec_status ec_assemble_tiles(ec_ctx* ctx, const ec_image* in, int32_t n, const ec_target* out, ec_stream_t s)
+{
+    if (!ctx || n < 0 || (n > 0 && !in)) return EC_ERR_INVALID_ARG;
+    if (n > EC_MAX_SOURCES) return EC_ERR_UNSUPPORTED;
+    ec_status st = check_assembly_target(out);
+    if (st != EC_OK) return st;
+    std::vector<SrcDesc> d;
+    st = assembly_descs(in, n, out, d);
+    if (st != EC_OK) return st;
+    DeviceGuard g(ctx->device);
+    if (!g.ok) return EC_ERR_CUDA;
+    return cuda_status(launch_assemble_tiles(d.data(), n, bytes_per_px(out->format), assembly_target(out),
+                                             (cudaStream_t)s));
+}
+
+ec_status ec_average(ec_ctx* ctx, const ec_image* in, int32_t n, const ec_target* out, ec_stream_t s)
+{
+    if (!ctx || n < 0 || (n > 0 && !in)) return EC_ERR_INVALID_ARG;
+    if (n > EC_MAX_SOURCES) return EC_ERR_UNSUPPORTED;
+    ec_status st = check_assembly_target(out);
+    if (st != EC_OK) return st;
+    std::vector<SrcDesc> d;
+    st = assembly_descs(in, n, out, d);
+    if (st != EC_OK) return st;
+    const int fmt = out->format == EC_RGBA8 ? 0 : out->format == EC_RGBA32F ? 1 : 2;
+    DeviceGuard g(ctx->device);
+    if (!g.ok) return EC_ERR_CUDA;
+    return cuda_status(launch_average(d.data(), n, fmt, assembly_target(out), (cudaStream_t)s));
+}
+
+ec_status ec_assemble_pixels(ec_ctx* ctx, const ec_image* in, const int32_t* kx, const int32_t* ky,
+                             int32_t n, int32_t nx, int32_t ny, const ec_target* out, ec_stream_t s)
+{
+    if (!ctx || n < 0 || (n > 0 && (!in || !kx || !ky))) return EC_ERR_INVALID_ARG;
+    if (nx < 1 || ny < 1 || nx > kPixMaxKernel || ny > kPixMaxKernel) return EC_ERR_INVALID_ARG;
+    if (n > kPixMaxSources) return EC_ERR_UNSUPPORTED;
+    ec_status st = check_assembly_target(out);
+    if (st != EC_OK) return st;
+    std::vector<PixSrc> src((size_t)std::max(n, 1));
+    std::vector<int16_t> owner((size_t)nx * ny, (int16_t)-1);
+    for (int k = 0; k < n; ++k) {
+        if (in[k].format != out->format || kx[k] < 0 || kx[k] >= nx || ky[k] < 0 || ky[k] >= ny)
+            return EC_ERR_INVALID_ARG;
+        const int64_t w = out->pvp.w > kx[k] ? (out->pvp.w - kx[k] + nx - 1) / nx : 0;
+        const int64_t h = out->pvp.h > ky[k] ? (out->pvp.h - ky[k] + ny - 1) / ny : 0;
+        if (in[k].pitch < w || (w > 0 && h > 0 && (!in[k].color || (reinterpret_cast<uintptr_t>(in[k].color) & 3u))))
+            return EC_ERR_INVALID_ARG;
+        src[k].color = in[k].color;
+        src[k].pitch = in[k].pitch;
+        src[k].pad = 0;
+        owner[(size_t)ky[k] * nx + kx[k]] = (int16_t)k;    // later inputs overwrite earlier ones
+    }
+    DeviceGuard g(ctx->device);
+    if (!g.ok) return EC_ERR_CUDA;
+    return cuda_status(launch_assemble_pixels(src.data(), owner.data(), n, nx, ny, bytes_per_px(out->format),
+                                              assembly_target(out), (cudaStream_t)s));
+}
+
 ec_status ec_detect_roi(ec_ctx* ctx, const ec_image* in, int32_t n, int32_t tile,
                         uint8_t* const* occupancy, ec_rect* d_rois, ec_stream_t s)
 {

@@ -167,6 +167,31 @@ cudaError_t launch_rle_compress(const RleJobDesc* jobs, int n, uint32_t total_un
 cudaError_t launch_rle_decompress(const RleJobDesc* jobs, int n, uint32_t total_units,
                                   uint32_t* status, cudaStream_t s);
 
+// ---- assembly of the other compound modes ------------------------------------
+
+cudaError_t launch_assemble_tiles(const SrcDesc* src, int n, int bpp, const DstDesc& D, cudaStream_t s);
+// fmt: 0 RGBA8, 1 RGBA32F, 2 RGBA16F
+cudaError_t launch_average(const SrcDesc* src, int n, int fmt, const DstDesc& D, cudaStream_t s);
+
+// Pixel compound source: densely stored interleaved pixels.
+struct PixSrc {
+    const void* color;
+    int32_t pitch;
+    int32_t pad;
+};
+static_assert(sizeof(PixSrc) == 16, "pixel source layout");
+constexpr int kPixMaxSources = 256, kPixMaxKernel = 16;   // kernel edge <= 16 pixels
+
+template <int N>
+struct PixList {
+    int32_t n, nx, ny, pad;
+    PixSrc s[N];
+    int16_t owner[kPixMaxKernel * kPixMaxKernel];   // source owning offset (x % nx, y % ny), or -1
+};
+
+cudaError_t launch_assemble_pixels(const PixSrc* src, const int16_t* owner, int n, int nx, int ny, int bpp,
+                                   const DstDesc& D, cudaStream_t s);
+
 // ---- automatic region of interest -------------------------------------------
 
 // One image of an ROI detection launch (64 bytes).  The image is scanned in

@@ -1,0 +1,334 @@
+// k_assemble.cu -- assembly of the compound modes other than sort-last
+// (thesis 4.2): sort-first and tile compounds copy complete pixels into place,
+// pixel compounds interleave the sources' pixels over a pixel kernel, and
+// subpixel compounds average every pixel's samples.
+//
+// All three are streaming copies / reductions: every thread owns one 16-byte
+// group of output pixels (4 RGBA8, 2 RGBA16F or 1 RGBA32F pixels) of a
+// 32-group x 8-row tile, reads each contributing source pixel once (16-byte
+// loads where the layout allows) and writes the group once.  HBM-bound.
+#include "composite_body.cuh"
+
+namespace ec {
+namespace {
+
+constexpr int kAT = 256;
+constexpr int kARows = kAT / 32;
+
+template <int BPP> struct Grp;                 // one 16-byte group of pixels
+template <> struct Grp<4> { static constexpr int PX = 4; };
+template <> struct Grp<8> { static constexpr int PX = 2; };
+template <> struct Grp<16> { static constexpr int PX = 1; };
+
+// Pixel j of a 16-byte group as raw 32-bit words (BPP / 4 of them).
+template <int BPP>
+__device__ __forceinline__ void load_px(const uint8_t* p, uint32_t* w)
+{
+    if constexpr (BPP == 4) w[0] = __ldcs(reinterpret_cast<const uint32_t*>(p));
+    else if constexpr (BPP == 8) {
+        const uint2 v = __ldcs(reinterpret_cast<const uint2*>(p));
+        w[0] = v.x; w[1] = v.y;
+    } else {
+        const uint4 v = __ldcs(reinterpret_cast<const uint4*>(p));
+        w[0] = v.x; w[1] = v.y; w[2] = v.z; w[3] = v.w;
+    }
+}
+
+template <int BPP>
+__device__ __forceinline__ void store_px(uint8_t* p, const uint32_t* w)
+{
+    if constexpr (BPP == 4) *reinterpret_cast<uint32_t*>(p) = w[0];
+    else if constexpr (BPP == 8) *reinterpret_cast<uint2*>(p) = make_uint2(w[0], w[1]);
+    else *reinterpret_cast<uint4*>(p) = make_uint4(w[0], w[1], w[2], w[3]);
+}
+
+// Bit j set when pixel x + j of row y lies in the source's clipped roi.
+template <int PX>
+__device__ __forceinline__ uint32_t covered(const SrcDesc& s, int x, int y, int W)
+{
+    if (y < s.y0 || y >= s.y1) return 0u;
+    uint32_t m = 0;
+#pragma unroll
+    for (int j = 0; j < PX; ++j)
+        if (x + j >= s.x0 && x + j < s.x1 && x + j < W) m |= 1u << j;
+    return m;
+}
+
+// ---- sort-first / tile assembly -----------------------------------------
+
+template <int N, int BPP>
+__global__ void __launch_bounds__(kAT)
+k_assemble_tiles(const __grid_constant__ SrcList<N> L, const __grid_constant__ DstDesc D)
+{
+    constexpr int PX = Grp<BPP>::PX, TW = 32 * PX, WPP = BPP / 4;
+    __shared__ int16_t act[N > 0 ? N : 1];
+    __shared__ int nact_s;
+    auto at = [&](int, int i) -> const SrcDesc& { return L.s[i]; };
+    const int lane = threadIdx.x & 31, row = threadIdx.x >> 5;
+    const int tx0 = blockIdx.x * TW, ty0 = blockIdx.y * kARows;
+    build_active(at, L.n, tx0, ty0, min(tx0 + TW, D.W), min(ty0 + kARows, D.H), act, &nact_s);
+    __syncthreads();
+    const int x = tx0 + lane * PX, y = ty0 + row;
+    if (x >= D.W || y >= D.H) return;
+    const uint32_t full = x + PX <= D.W ? (1u << PX) - 1u : (1u << (D.W - x)) - 1u;
+    uint32_t w[PX][WPP];
+    uint32_t have = 0;
+    // the last source covering a pixel wins: walk back until every pixel is set
+    for (int a = nact_s - 1; a >= 0 && have != full; --a) {
+        const SrcDesc& s = L.s[act[a]];
+        const uint32_t m = covered<PX>(s, x, y, D.W) & ~have;
+        if (!m) continue;
+        const size_t e = (size_t)(y - s.oy) * (size_t)s.pitch + (size_t)(x - s.ox);
+        const uint8_t* p = reinterpret_cast<const uint8_t*>(s.color) + e * BPP;
+        if (m == full && s.vec && PX * BPP == 16 && full == (1u << PX) - 1u) {
+            const uint4 v = __ldcs(reinterpret_cast<const uint4*>(p));
+            const uint32_t vv[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+            for (int j = 0; j < PX; ++j)
+#pragma unroll
+                for (int k = 0; k < WPP; ++k) w[j][k] = vv[j * WPP + k];
+        } else {
+#pragma unroll
+            for (int j = 0; j < PX; ++j)
+                if ((m >> j) & 1u) load_px<BPP>(p + j * BPP, w[j]);
+        }
+        have |= m;
+    }
+    if (!have) return;
+    uint8_t* o = reinterpret_cast<uint8_t*>(D.color) + ((size_t)y * (size_t)D.pitch + (size_t)x) * BPP;
+    if (have == (1u << PX) - 1u && D.vec) {
+        uint32_t vv[4];
+#pragma unroll
+        for (int j = 0; j < PX; ++j)
+#pragma unroll
+            for (int k = 0; k < WPP; ++k) vv[j * WPP + k] = w[j][k];
+        __stcs(reinterpret_cast<uint4*>(o), make_uint4(vv[0], vv[1], vv[2], vv[3]));
+    } else {
+#pragma unroll
+        for (int j = 0; j < PX; ++j)
+            if ((have >> j) & 1u) store_px<BPP>(o + j * BPP, w[j]);
+    }
+}
+
+// ---- subpixel average ------------------------------------------------------
+
+// FMT: 0 RGBA8 (integer sums, (sum + count/2) / count), 1 RGBA32F, 2 RGBA16F
+// (FP32 sums in input order, divided by the count).
+template <int N, int FMT>
+__global__ void __launch_bounds__(kAT)
+k_average(const __grid_constant__ SrcList<N> L, const __grid_constant__ DstDesc D)
+{
+    constexpr int BPP = FMT == 0 ? 4 : FMT == 1 ? 16 : 8, PX = Grp<BPP>::PX;
+    __shared__ int16_t act[N > 0 ? N : 1];
+    __shared__ int nact_s;
+    auto at = [&](int, int i) -> const SrcDesc& { return L.s[i]; };
+    const int lane = threadIdx.x & 31, row = threadIdx.x >> 5;
+    const int tx0 = blockIdx.x * (32 * PX), ty0 = blockIdx.y * kARows;
+    build_active(at, L.n, tx0, ty0, min(tx0 + 32 * PX, D.W), min(ty0 + kARows, D.H), act, &nact_s);
+    __syncthreads();
+    const int x = tx0 + lane * PX, y = ty0 + row;
+    if (x >= D.W || y >= D.H) return;
+    uint32_t isum[PX][4];
+    float fsum[PX][4];
+    int cnt[PX];
+#pragma unroll
+    for (int j = 0; j < PX; ++j) {
+        cnt[j] = 0;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) { isum[j][c] = 0u; fsum[j][c] = 0.0f; }
+    }
+    for (int a = 0; a < nact_s; ++a) {
+        const SrcDesc& s = L.s[act[a]];
+        const uint32_t m = covered<PX>(s, x, y, D.W);
+        if (!m) continue;
+        const size_t e = (size_t)(y - s.oy) * (size_t)s.pitch + (size_t)(x - s.ox);
+        const uint8_t* p = reinterpret_cast<const uint8_t*>(s.color) + e * BPP;
+        uint32_t w[PX][BPP / 4];
+        if (m == (1u << PX) - 1u && s.vec) {
+            const uint4 v = __ldcs(reinterpret_cast<const uint4*>(p));
+            const uint32_t vv[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+            for (int j = 0; j < PX; ++j)
+#pragma unroll
+                for (int k = 0; k < BPP / 4; ++k) w[j][k] = vv[j * (BPP / 4) + k];
+        } else {
+#pragma unroll
+            for (int j = 0; j < PX; ++j)
+                if ((m >> j) & 1u) load_px<BPP>(p + j * BPP, w[j]);
+        }
+#pragma unroll
+        for (int j = 0; j < PX; ++j) {
+            if (!((m >> j) & 1u)) continue;
+            ++cnt[j];
+            if constexpr (FMT == 0) {
+#pragma unroll
+                for (int c = 0; c < 4; ++c) isum[j][c] += (w[j][0] >> (8 * c)) & 0xFFu;
+            } else if constexpr (FMT == 1) {
+#pragma unroll
+                for (int c = 0; c < 4; ++c) fsum[j][c] += __uint_as_float(w[j][c]);
+            } else {
+                const float4 f = half4_to_float4(make_uint2(w[j][0], w[j][1]));
+                fsum[j][0] += f.x; fsum[j][1] += f.y; fsum[j][2] += f.z; fsum[j][3] += f.w;
+            }
+        }
+    }
+    uint32_t out[PX][BPP / 4];
+#pragma unroll
+    for (int j = 0; j < PX; ++j) {
+        const int n = cnt[j];
+        if constexpr (FMT == 0) {
+            uint32_t v = 0;
+            if (n)
+#pragma unroll
+                for (int c = 0; c < 4; ++c) v |= ((isum[j][c] + (uint32_t)n / 2u) / (uint32_t)n) << (8 * c);
+            out[j][0] = v;
+        } else {
+            float4 f = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (n) {
+                const float fn = (float)n;
+                f = make_float4(fsum[j][0] / fn, fsum[j][1] / fn, fsum[j][2] / fn, fsum[j][3] / fn);
+            }
+            if constexpr (FMT == 1) {
+                out[j][0] = __float_as_uint(f.x); out[j][1] = __float_as_uint(f.y);
+                out[j][2] = __float_as_uint(f.z); out[j][3] = __float_as_uint(f.w);
+            } else {
+                const uint2 h = float4_to_half4(f);
+                out[j][0] = h.x; out[j][1] = h.y;
+            }
+        }
+    }
+    uint8_t* o = reinterpret_cast<uint8_t*>(D.color) + ((size_t)y * (size_t)D.pitch + (size_t)x) * BPP;
+    if (x + PX <= D.W && D.vec) {
+        uint32_t vv[4];
+#pragma unroll
+        for (int j = 0; j < PX; ++j)
+#pragma unroll
+            for (int k = 0; k < BPP / 4; ++k) vv[j * (BPP / 4) + k] = out[j][k];
+        __stcs(reinterpret_cast<uint4*>(o), make_uint4(vv[0], vv[1], vv[2], vv[3]));
+    } else {
+#pragma unroll
+        for (int j = 0; j < PX; ++j)
+            if (x + j < D.W) store_px<BPP>(o + j * BPP, out[j]);
+    }
+}
+
+// ---- pixel compound --------------------------------------------------------
+
+template <int N, int BPP>
+__global__ void __launch_bounds__(kAT)
+k_assemble_pixels(const __grid_constant__ PixList<N> P, const __grid_constant__ DstDesc D)
+{
+    constexpr int PX = Grp<BPP>::PX;
+    const int lane = threadIdx.x & 31, row = threadIdx.x >> 5;
+    const int x = blockIdx.x * (32 * PX) + lane * PX, y = blockIdx.y * kARows + row;
+    if (x >= D.W || y >= D.H) return;
+    const int ry = y % P.ny, j0 = y / P.ny;
+    uint32_t w[PX][BPP / 4];
+    uint32_t have = 0;
+#pragma unroll
+    for (int j = 0; j < PX; ++j) {
+        const int xj = x + j;
+        if (xj >= D.W) continue;
+        const int k = P.owner[ry * P.nx + xj % P.nx];
+        if (k < 0) continue;
+        const PixSrc& s = P.s[k];
+        const size_t e = (size_t)j0 * (size_t)s.pitch + (size_t)(xj / P.nx);
+        load_px<BPP>(reinterpret_cast<const uint8_t*>(s.color) + e * BPP, w[j]);
+        have |= 1u << j;
+    }
+    if (!have) return;
+    uint8_t* o = reinterpret_cast<uint8_t*>(D.color) + ((size_t)y * (size_t)D.pitch + (size_t)x) * BPP;
+    if (have == (1u << PX) - 1u && D.vec) {
+        uint32_t vv[4];
+#pragma unroll
+        for (int j = 0; j < PX; ++j)
+#pragma unroll
+            for (int k = 0; k < BPP / 4; ++k) vv[j * (BPP / 4) + k] = w[j][k];
+        __stcs(reinterpret_cast<uint4*>(o), make_uint4(vv[0], vv[1], vv[2], vv[3]));
+    } else {
+#pragma unroll
+        for (int j = 0; j < PX; ++j)
+            if ((have >> j) & 1u) store_px<BPP>(o + j * BPP, w[j]);
+    }
+}
+
+template <int N>
+SrcList<N> make_src_list(const SrcDesc* src, int n)
+{
+    SrcList<N> L;
+    L.n = n;
+    L.pad[0] = L.pad[1] = L.pad[2] = 0;
+    for (int i = 0; i < n; ++i) L.s[i] = src[i];
+    return L;
+}
+
+template <int N>
+cudaError_t tiles_n(const SrcDesc* src, int n, int bpp, const DstDesc& D, cudaStream_t s)
+{
+    const SrcList<N> L = make_src_list<N>(src, n);
+    const int px = 16 / bpp;
+    const dim3 grid(ceil_div(D.W, 32 * px), ceil_div(D.H, kARows));
+    if (bpp == 4) k_assemble_tiles<N, 4><<<grid, kAT, 0, s>>>(L, D);
+    else if (bpp == 8) k_assemble_tiles<N, 8><<<grid, kAT, 0, s>>>(L, D);
+    else k_assemble_tiles<N, 16><<<grid, kAT, 0, s>>>(L, D);
+    return cudaGetLastError();
+}
+
+template <int N>
+cudaError_t average_n(const SrcDesc* src, int n, int fmt, const DstDesc& D, cudaStream_t s)
+{
+    const SrcList<N> L = make_src_list<N>(src, n);
+    const int px = fmt == 0 ? 4 : fmt == 1 ? 1 : 2;
+    const dim3 grid(ceil_div(D.W, 32 * px), ceil_div(D.H, kARows));
+    if (fmt == 0) k_average<N, 0><<<grid, kAT, 0, s>>>(L, D);
+    else if (fmt == 1) k_average<N, 1><<<grid, kAT, 0, s>>>(L, D);
+    else k_average<N, 2><<<grid, kAT, 0, s>>>(L, D);
+    return cudaGetLastError();
+}
+
+template <int N>
+cudaError_t pixels_n(const PixSrc* src, const int16_t* owner, int n, int nx, int ny, int bpp,
+                     const DstDesc& D, cudaStream_t s)
+{
+    PixList<N> P;
+    P.n = n;
+    P.nx = nx;
+    P.ny = ny;
+    P.pad = 0;
+    for (int i = 0; i < n; ++i) P.s[i] = src[i];
+    for (int i = 0; i < nx * ny; ++i) P.owner[i] = owner[i];
+    const int px = 16 / bpp;
+    const dim3 grid(ceil_div(D.W, 32 * px), ceil_div(D.H, kARows));
+    if (bpp == 4) k_assemble_pixels<N, 4><<<grid, kAT, 0, s>>>(P, D);
+    else if (bpp == 8) k_assemble_pixels<N, 8><<<grid, kAT, 0, s>>>(P, D);
+    else k_assemble_pixels<N, 16><<<grid, kAT, 0, s>>>(P, D);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_assemble_tiles(const SrcDesc* src, int n, int bpp, const DstDesc& D, cudaStream_t s)
+{
+    if (D.W <= 0 || D.H <= 0 || n <= 0) return cudaSuccess;
+    if (n <= 16) return tiles_n<16>(src, n, bpp, D, s);
+    if (n <= 64) return tiles_n<64>(src, n, bpp, D, s);
+    return tiles_n<EC_MAX_SOURCES>(src, n, bpp, D, s);
+}
+
+cudaError_t launch_average(const SrcDesc* src, int n, int fmt, const DstDesc& D, cudaStream_t s)
+{
+    if (D.W <= 0 || D.H <= 0) return cudaSuccess;
+    if (n <= 16) return average_n<16>(src, n, fmt, D, s);
+    if (n <= 64) return average_n<64>(src, n, fmt, D, s);
+    return average_n<EC_MAX_SOURCES>(src, n, fmt, D, s);
+}
+
+cudaError_t launch_assemble_pixels(const PixSrc* src, const int16_t* owner, int n, int nx, int ny, int bpp,
+                                   const DstDesc& D, cudaStream_t s)
+{
+    if (D.W <= 0 || D.H <= 0 || n <= 0) return cudaSuccess;
+    if (n <= 16) return pixels_n<16>(src, owner, n, nx, ny, bpp, D, s);
+    return pixels_n<kPixMaxSources>(src, owner, n, nx, ny, bpp, D, s);
+}
+
+}  // namespace ec
