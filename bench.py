@@ -11,7 +11,7 @@ its size is written, then another 2x its size is read, so that the timed step
 neither finds its inputs in L2 nor pays for writing back the flush's lines.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ec|reference]
-                    [--workload cfg2|cfg1|cfg3|cfg3h|cfg3fused|cfg3hfused|cfg4|cfg5d|cfg5a|cfg5afused|roi2]
+                    [--workload cfg2|cfg1|cfg3|cfg3h|cfg3fused|cfg3hfused|cfg4|cfg5d|cfg5a|cfg5afused|roi2|asm4k]
 
 Prints ONE JSON line (rank 0).  Metric: composited Gpixel-layers/s (sum over
 sources of |roi_i ∩ frame| per step, divided by the step time).  With N > 1
@@ -456,6 +456,104 @@ class RoiDetect:
         return (time.perf_counter() - t0) / self.sample_fraction
 
 
+class Assembly:
+    """asm4k: the assembly steps of the other compound modes (thesis 4.2) on a
+    3840x2160 RGBA8 frame: a sort-first frame from 8 x 8 tiles, a 2 x 2 pixel
+    compound from 4 interleaved sources, and the average of 8 subpixel samples."""
+
+    def __init__(self, W, H, device, nt=8, kern=(2, 2), ns=8):
+        import ctypes as C
+
+        import paper_1902_08755_gb300 as ec
+        from paper_1902_08755_gb300 import _abi as A
+        from paper_1902_08755_gb300 import api
+        self.ec = ec
+        self.W, self.H = W, H
+        self.desc = (f"{W}x{H} RGBA8: sort-first frame from {nt}x{nt} tiles, {kern[0]}x{kern[1]} pixel "
+                     f"compound, average of {ns} subpixel samples")
+        self.kernels = ["assemble_tiles", "assemble_pixels", "average"]
+        self.units = W * H * (2 + ns)                   # source pixels read per step
+        self.bytes = {"assemble_tiles": 8 * W * H, "assemble_pixels": 8 * W * H, "average": 4 * W * H * (ns + 1)}
+        if torch.device(device).type != "cuda":
+            return
+        g = torch.Generator(device=device)
+        g.manual_seed(190208755)
+        rnd = lambda h, w: torch.randint(-2 ** 31, 2 ** 31 - 1, (h, w), generator=g, dtype=torch.int32,
+                                         device=device).view(torch.uint32)
+        self.ctx = ec.default_context(torch.device(device).index or 0)
+        dev = self.ctx.device
+        self.out = [torch.empty((H, W), dtype=torch.int32, device=device).view(torch.uint32) for _ in range(3)]
+        tw, th = -(-W // nt), -(-H // nt)
+        tiles = []
+        for j in range(nt):
+            for i in range(nt):
+                r = (i * tw, j * th, min(tw, W - i * tw), min(th, H - j * th))
+                tiles.append(ec.Image(color=rnd(r[3], r[2]), pvp=r, roi=r))
+        nx, ny = kern
+        pix = [rnd(-(-(H - ky) // ny), -(-(W - kx) // nx)) for ky in range(ny) for kx in range(nx)]
+        offs = [(kx, ky) for ky in range(ny) for kx in range(nx)]
+        samples = [ec.Image(color=rnd(H, W)) for _ in range(ns)]
+        self._keep = (tiles, pix, samples)
+        lib = A.load()
+        arr_t = (A.ec_image * len(tiles))(*[api._image_struct(im, dev, False) for im in tiles])
+        arr_p = (A.ec_image * len(pix))(*[A.ec_image(A.ec_rect(0, 0, t.shape[1], t.shape[0]),
+                                                     A.ec_rect(0, 0, t.shape[1], t.shape[0]), t.shape[1],
+                                                     A.EC_RGBA8, t.data_ptr(), None) for t in pix])
+        kx = (C.c_int32 * len(offs))(*[o[0] for o in offs])
+        ky = (C.c_int32 * len(offs))(*[o[1] for o in offs])
+        arr_s = (A.ec_image * ns)(*[api._image_struct(im, dev, False) for im in samples])
+        tg = [api._target(o, None, None, dev) for o in self.out]
+        self._calls = [(lib.ec_assemble_tiles, (self.ctx.h, arr_t, len(tiles), C.byref(tg[0]))),
+                       (lib.ec_assemble_pixels, (self.ctx.h, arr_p, kx, ky, len(pix), nx, ny, C.byref(tg[1]))),
+                       (lib.ec_average, (self.ctx.h, arr_s, ns, C.byref(tg[2])))]
+        self._args = (arr_t, arr_p, arr_s, kx, ky, tg)
+
+    def step(self, ev=None):
+        st = torch.cuda.current_stream().cuda_stream
+        for i, (fn, args) in enumerate(self._calls):
+            if ev:
+                ev[i].record()
+            rc = fn(*args, st)
+            if rc:
+                raise SystemExit(f"assembly call {i} failed: {rc}")
+        if ev:
+            ev[len(self._calls)].record()
+
+    def launches_per_step(self):
+        return 3
+
+    def algorithmic_bytes(self):
+        return dict(self.bytes)
+
+    def setup_e2e(self):
+        tiles, pix, samples = self._keep
+        self._dev_in = [im.color for im in tiles] + list(pix) + [im.color for im in samples]
+        self._host_in = [t.cpu().pin_memory() for t in self._dev_in]
+        self._host_out = [o.cpu().pin_memory() for o in self.out]
+        self.h2d = sum(t.numel() * 4 for t in self._dev_in)
+        self.d2h = sum(o.numel() * 4 for o in self.out)
+
+    def e2e_step(self):
+        for d, h in zip(self._dev_in, self._host_in):
+            d.copy_(h, non_blocking=True)
+        self.step()
+        for h, o in zip(self._host_out, self.out):
+            h.copy_(o, non_blocking=True)
+
+    def oracle_step(self, pool, cores):
+        import oracle
+        rows, ns = 16, 8                                 # bounded sample: a 16-row band of the average
+        r = np.random.default_rng(190208755)
+        band = [oracle.Image((0, 0, self.W, rows), (0, 0, self.W, rows),
+                             r.integers(0, 2 ** 32, (rows, self.W), dtype=np.uint64).astype(np.uint32))
+                for _ in range(ns)]
+        t0 = time.perf_counter()
+        oracle.average(band, (0, 0, self.W, rows), 0)
+        self.sample_fraction = rows / self.H * (ns / (ns + 2))
+        self.sample_desc = f"a {rows}-row band of the average"
+        return (time.perf_counter() - t0) / self.sample_fraction
+
+
 class BatchedTiles:
     """cfg4: 1000 uneven tiles (w, h log-uniform in [16, 1024], 2..64 layers, half
     depth RGBA8+Z32 at 30% box coverage, half alpha FP32 with a <= 0.3), all in
@@ -606,6 +704,8 @@ def make_workload(name, device):
         return BatchedTiles(device)
     if name == "roi2":
         return RoiDetect(2, 16, 1920, 1080, 0.3, device)
+    if name == "asm4k":
+        return Assembly(3840, 2160, device)
     if name == "cfg3":
         return AlphaForward(3, 32, 2048, 2048, 0.3, torch.float32, device)
     if name == "cfg3h":
@@ -744,7 +844,7 @@ def run_ec(args):
         cfg["rle_raw_bytes_per_step"] = 8 * wl.stored_px
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": max(3, args.warmup), "ms_per_step": ms, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "rgba8+f32" if isinstance(wl, (DepthPipeline, BatchedTiles, RoiDetect)) else "f32",
+            "scaling": "weak", "vs_baseline": None, "dtype": "rgba8+f32" if isinstance(wl, (DepthPipeline, BatchedTiles, RoiDetect)) else "u8" if isinstance(wl, Assembly) else "f32",
             "data": "synthetic (seeded boxes / layers shaped like the thesis's workloads)",
             "config": cfg, "roofline": roof, "kernels": kern,
             "e2e": {"value": whole_job_value(wl.units, e2e_ms, world), "unit": UNIT,

@@ -13,7 +13,8 @@ namespace ec {
 namespace {
 
 constexpr int kAT = 256;
-constexpr int kARows = kAT / 32;
+constexpr int kARows = kAT / 32;          // rows a CTA covers at once
+constexpr int kAPasses = 4;                 // row passes per CTA (tile and average kernels)
 
 template <int BPP> struct Grp;                 // one 16-byte group of pixels
 template <> struct Grp<4> { static constexpr int PX = 4; };
@@ -65,12 +66,15 @@ k_assemble_tiles(const __grid_constant__ SrcList<N> L, const __grid_constant__ D
     __shared__ int nact_s;
     auto at = [&](int, int i) -> const SrcDesc& { return L.s[i]; };
     const int lane = threadIdx.x & 31, row = threadIdx.x >> 5;
-    const int tx0 = blockIdx.x * TW, ty0 = blockIdx.y * kARows;
-    build_active(at, L.n, tx0, ty0, min(tx0 + TW, D.W), min(ty0 + kARows, D.H), act, &nact_s);
+    const int tx0 = blockIdx.x * TW, ty0 = blockIdx.y * (kARows * kAPasses);
+    build_active(at, L.n, tx0, ty0, min(tx0 + TW, D.W), min(ty0 + kARows * kAPasses, D.H), act, &nact_s);
     __syncthreads();
-    const int x = tx0 + lane * PX, y = ty0 + row;
-    if (x >= D.W || y >= D.H) return;
+    const int x = tx0 + lane * PX;
+    if (x >= D.W) return;
     const uint32_t full = x + PX <= D.W ? (1u << PX) - 1u : (1u << (D.W - x)) - 1u;
+    for (int pass = 0; pass < kAPasses; ++pass) {
+    const int y = ty0 + pass * kARows + row;
+    if (y >= D.H) break;
     uint32_t w[PX][WPP];
     uint32_t have = 0;
     // the last source covering a pixel wins: walk back until every pixel is set
@@ -94,7 +98,7 @@ k_assemble_tiles(const __grid_constant__ SrcList<N> L, const __grid_constant__ D
         }
         have |= m;
     }
-    if (!have) return;
+    if (!have) continue;
     uint8_t* o = reinterpret_cast<uint8_t*>(D.color) + ((size_t)y * (size_t)D.pitch + (size_t)x) * BPP;
     if (have == (1u << PX) - 1u && D.vec) {
         uint32_t vv[4];
@@ -108,107 +112,154 @@ k_assemble_tiles(const __grid_constant__ SrcList<N> L, const __grid_constant__ D
         for (int j = 0; j < PX; ++j)
             if ((have >> j) & 1u) store_px<BPP>(o + j * BPP, w[j]);
     }
+    }
 }
 
 // ---- subpixel average ------------------------------------------------------
 
 // FMT: 0 RGBA8 (integer sums, (sum + count/2) / count), 1 RGBA32F, 2 RGBA16F
-// (FP32 sums in input order, divided by the count).
+// (FP32 sums in input order, divided by the count).  Sources are read four
+// at a time, all four groups in flight before any is added.
 template <int N, int FMT>
 __global__ void __launch_bounds__(kAT)
 k_average(const __grid_constant__ SrcList<N> L, const __grid_constant__ DstDesc D)
 {
-    constexpr int BPP = FMT == 0 ? 4 : FMT == 1 ? 16 : 8, PX = Grp<BPP>::PX;
+    constexpr int BPP = FMT == 0 ? 4 : FMT == 1 ? 16 : 8, PX = Grp<BPP>::PX, WPP = BPP / 4, B = 4;
     __shared__ int16_t act[N > 0 ? N : 1];
     __shared__ int nact_s;
     auto at = [&](int, int i) -> const SrcDesc& { return L.s[i]; };
     const int lane = threadIdx.x & 31, row = threadIdx.x >> 5;
-    const int tx0 = blockIdx.x * (32 * PX), ty0 = blockIdx.y * kARows;
-    build_active(at, L.n, tx0, ty0, min(tx0 + 32 * PX, D.W), min(ty0 + kARows, D.H), act, &nact_s);
+    const int tx0 = blockIdx.x * (32 * PX), ty0 = blockIdx.y * (kARows * kAPasses);
+    const int tx1 = min(tx0 + 32 * PX, D.W), ty1 = min(ty0 + kARows * kAPasses, D.H);
+    build_active(at, L.n, tx0, ty0, tx1, ty1, act, &nact_s);
     __syncthreads();
-    const int x = tx0 + lane * PX, y = ty0 + row;
-    if (x >= D.W || y >= D.H) return;
-    uint32_t isum[PX][4];
-    float fsum[PX][4];
-    int cnt[PX];
-#pragma unroll
-    for (int j = 0; j < PX; ++j) {
-        cnt[j] = 0;
-#pragma unroll
-        for (int c = 0; c < 4; ++c) { isum[j][c] = 0u; fsum[j][c] = 0.0f; }
-    }
-    for (int a = 0; a < nact_s; ++a) {
+    const int nact = nact_s;
+    // every active source covers the whole tile with 16-byte rows: no per-pixel masks
+    bool cov = true;
+    for (int a = threadIdx.x; a < nact; a += kAT) {
         const SrcDesc& s = L.s[act[a]];
-        const uint32_t m = covered<PX>(s, x, y, D.W);
-        if (!m) continue;
-        const size_t e = (size_t)(y - s.oy) * (size_t)s.pitch + (size_t)(x - s.ox);
-        const uint8_t* p = reinterpret_cast<const uint8_t*>(s.color) + e * BPP;
-        uint32_t w[PX][BPP / 4];
-        if (m == (1u << PX) - 1u && s.vec) {
-            const uint4 v = __ldcs(reinterpret_cast<const uint4*>(p));
-            const uint32_t vv[4] = {v.x, v.y, v.z, v.w};
-#pragma unroll
-            for (int j = 0; j < PX; ++j)
-#pragma unroll
-                for (int k = 0; k < BPP / 4; ++k) w[j][k] = vv[j * (BPP / 4) + k];
-        } else {
-#pragma unroll
-            for (int j = 0; j < PX; ++j)
-                if ((m >> j) & 1u) load_px<BPP>(p + j * BPP, w[j]);
-        }
+        cov = cov && s.vec && s.x0 <= tx0 && s.x1 >= tx1 && s.y0 <= ty0 && s.y1 >= ty1;
+    }
+    const bool full = __syncthreads_and(cov) && tx1 - tx0 == 32 * PX;
+    const int x = tx0 + lane * PX;
+    if (x >= D.W) return;
+    for (int pass = 0; pass < kAPasses; ++pass) {
+        const int y = ty0 + pass * kARows + row;
+        if (y >= D.H) break;
+        uint32_t isum[PX][4];
+        uint32_t lo[PX], hi[PX];            // RGBA8: channels 0,2 and 1,3 as 16-bit lanes
+        float fsum[PX][4];
+        int cnt[PX];
 #pragma unroll
         for (int j = 0; j < PX; ++j) {
-            if (!((m >> j) & 1u)) continue;
-            ++cnt[j];
+            cnt[j] = 0;
+            lo[j] = hi[j] = 0u;
+#pragma unroll
+            for (int c = 0; c < 4; ++c) { isum[j][c] = 0u; fsum[j][c] = 0.0f; }
+        }
+        auto fold = [&]() {                 // 16-bit lanes into the 32-bit sums
+#pragma unroll
+            for (int j = 0; j < PX; ++j) {
+                isum[j][0] += lo[j] & 0xFFFFu; isum[j][2] += lo[j] >> 16;
+                isum[j][1] += hi[j] & 0xFFFFu; isum[j][3] += hi[j] >> 16;
+                lo[j] = hi[j] = 0u;
+            }
+        };
+        for (int a0 = 0; a0 < nact; a0 += B) {
+            if (FMT == 0 && a0 % 256 == 0 && a0) fold();   // at most 256 * 255 per lane
+            uint32_t w[B][PX][WPP];
+            uint32_t m[B];
+#pragma unroll
+            for (int b = 0; b < B; ++b) {
+                m[b] = 0u;
+                if (a0 + b >= nact) continue;
+                const SrcDesc& s = L.s[act[a0 + b]];
+                m[b] = full ? (1u << PX) - 1u : covered<PX>(s, x, y, D.W);
+                if (!m[b]) continue;
+                const size_t e = (size_t)(y - s.oy) * (size_t)s.pitch + (size_t)(x - s.ox);
+                const uint8_t* p = reinterpret_cast<const uint8_t*>(s.color) + e * BPP;
+                if (m[b] == (1u << PX) - 1u && s.vec) {
+                    const uint4 v = __ldcs(reinterpret_cast<const uint4*>(p));
+                    const uint32_t vv[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+                    for (int j = 0; j < PX; ++j)
+#pragma unroll
+                        for (int k = 0; k < WPP; ++k) w[b][j][k] = vv[j * WPP + k];
+                } else {
+#pragma unroll
+                    for (int j = 0; j < PX; ++j)
+                        if ((m[b] >> j) & 1u) load_px<BPP>(p + j * BPP, w[b][j]);
+                }
+            }
+#pragma unroll
+            for (int b = 0; b < B; ++b) {
+#pragma unroll
+                for (int j = 0; j < PX; ++j) {
+                    if (!((m[b] >> j) & 1u)) continue;
+                    ++cnt[j];
+                    if constexpr (FMT == 0) {
+                        lo[j] += w[b][j][0] & 0x00FF00FFu;
+                        hi[j] += (w[b][j][0] >> 8) & 0x00FF00FFu;
+                    } else if constexpr (FMT == 1) {
+#pragma unroll
+                        for (int c = 0; c < 4; ++c) fsum[j][c] += __uint_as_float(w[b][j][c]);
+                    } else {
+                        const float4 f = half4_to_float4(make_uint2(w[b][j][0], w[b][j][1]));
+                        fsum[j][0] += f.x; fsum[j][1] += f.y; fsum[j][2] += f.z; fsum[j][3] += f.w;
+                    }
+                }
+            }
+        }
+        if (FMT == 0) fold();
+        uint32_t out[PX][WPP];
+#pragma unroll
+        for (int j = 0; j < PX; ++j) {
+            const int n = cnt[j];
             if constexpr (FMT == 0) {
+                uint32_t v = 0;
+                if (n) {
+                    // (sum + n/2) / n: a float estimate, exact after a +-1 correction
+                    // (the numerator is < 2^18, so the estimate is off by < 1e-4)
+                    const uint32_t un = (uint32_t)n;
+                    const float r = 1.0f / (float)n;
 #pragma unroll
-                for (int c = 0; c < 4; ++c) isum[j][c] += (w[j][0] >> (8 * c)) & 0xFFu;
-            } else if constexpr (FMT == 1) {
-#pragma unroll
-                for (int c = 0; c < 4; ++c) fsum[j][c] += __uint_as_float(w[j][c]);
+                    for (int c = 0; c < 4; ++c) {
+                        const uint32_t x = isum[j][c] + un / 2u;
+                        uint32_t q = (uint32_t)((float)x * r);
+                        if (q * un > x) --q;
+                        else if ((q + 1u) * un <= x) ++q;
+                        v |= q << (8 * c);
+                    }
+                }
+                out[j][0] = v;
             } else {
-                const float4 f = half4_to_float4(make_uint2(w[j][0], w[j][1]));
-                fsum[j][0] += f.x; fsum[j][1] += f.y; fsum[j][2] += f.z; fsum[j][3] += f.w;
+                float4 f = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (n) {
+                    const float fn = (float)n;
+                    f = make_float4(fsum[j][0] / fn, fsum[j][1] / fn, fsum[j][2] / fn, fsum[j][3] / fn);
+                }
+                if constexpr (FMT == 1) {
+                    out[j][0] = __float_as_uint(f.x); out[j][1] = __float_as_uint(f.y);
+                    out[j][2] = __float_as_uint(f.z); out[j][3] = __float_as_uint(f.w);
+                } else {
+                    const uint2 h = float4_to_half4(f);
+                    out[j][0] = h.x; out[j][1] = h.y;
+                }
             }
         }
-    }
-    uint32_t out[PX][BPP / 4];
+        uint8_t* o = reinterpret_cast<uint8_t*>(D.color) + ((size_t)y * (size_t)D.pitch + (size_t)x) * BPP;
+        if (x + PX <= D.W && D.vec) {
+            uint32_t vv[4];
 #pragma unroll
-    for (int j = 0; j < PX; ++j) {
-        const int n = cnt[j];
-        if constexpr (FMT == 0) {
-            uint32_t v = 0;
-            if (n)
+            for (int j = 0; j < PX; ++j)
 #pragma unroll
-                for (int c = 0; c < 4; ++c) v |= ((isum[j][c] + (uint32_t)n / 2u) / (uint32_t)n) << (8 * c);
-            out[j][0] = v;
+                for (int k = 0; k < WPP; ++k) vv[j * WPP + k] = out[j][k];
+            __stcs(reinterpret_cast<uint4*>(o), make_uint4(vv[0], vv[1], vv[2], vv[3]));
         } else {
-            float4 f = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (n) {
-                const float fn = (float)n;
-                f = make_float4(fsum[j][0] / fn, fsum[j][1] / fn, fsum[j][2] / fn, fsum[j][3] / fn);
-            }
-            if constexpr (FMT == 1) {
-                out[j][0] = __float_as_uint(f.x); out[j][1] = __float_as_uint(f.y);
-                out[j][2] = __float_as_uint(f.z); out[j][3] = __float_as_uint(f.w);
-            } else {
-                const uint2 h = float4_to_half4(f);
-                out[j][0] = h.x; out[j][1] = h.y;
-            }
+#pragma unroll
+            for (int j = 0; j < PX; ++j)
+                if (x + j < D.W) store_px<BPP>(o + j * BPP, out[j]);
         }
-    }
-    uint8_t* o = reinterpret_cast<uint8_t*>(D.color) + ((size_t)y * (size_t)D.pitch + (size_t)x) * BPP;
-    if (x + PX <= D.W && D.vec) {
-        uint32_t vv[4];
-#pragma unroll
-        for (int j = 0; j < PX; ++j)
-#pragma unroll
-            for (int k = 0; k < BPP / 4; ++k) vv[j * (BPP / 4) + k] = out[j][k];
-        __stcs(reinterpret_cast<uint4*>(o), make_uint4(vv[0], vv[1], vv[2], vv[3]));
-    } else {
-#pragma unroll
-        for (int j = 0; j < PX; ++j)
-            if (x + j < D.W) store_px<BPP>(o + j * BPP, out[j]);
     }
 }
 
@@ -223,18 +274,20 @@ k_assemble_pixels(const __grid_constant__ PixList<N> P, const __grid_constant__ 
     const int x = blockIdx.x * (32 * PX) + lane * PX, y = blockIdx.y * kARows + row;
     if (x >= D.W || y >= D.H) return;
     const int ry = y % P.ny, j0 = y / P.ny;
+    int rx = x % P.nx, i0 = x / P.nx;                   // one division; then step the residue
     uint32_t w[PX][BPP / 4];
     uint32_t have = 0;
 #pragma unroll
     for (int j = 0; j < PX; ++j) {
         const int xj = x + j;
-        if (xj >= D.W) continue;
-        const int k = P.owner[ry * P.nx + xj % P.nx];
-        if (k < 0) continue;
-        const PixSrc& s = P.s[k];
-        const size_t e = (size_t)j0 * (size_t)s.pitch + (size_t)(xj / P.nx);
-        load_px<BPP>(reinterpret_cast<const uint8_t*>(s.color) + e * BPP, w[j]);
-        have |= 1u << j;
+        const int k = xj < D.W ? P.owner[ry * P.nx + rx] : -1;
+        if (k >= 0) {
+            const PixSrc& s = P.s[k];
+            const size_t e = (size_t)j0 * (size_t)s.pitch + (size_t)i0;
+            load_px<BPP>(reinterpret_cast<const uint8_t*>(s.color) + e * BPP, w[j]);
+            have |= 1u << j;
+        }
+        if (++rx == P.nx) { rx = 0; ++i0; }
     }
     if (!have) return;
     uint8_t* o = reinterpret_cast<uint8_t*>(D.color) + ((size_t)y * (size_t)D.pitch + (size_t)x) * BPP;
@@ -267,7 +320,7 @@ cudaError_t tiles_n(const SrcDesc* src, int n, int bpp, const DstDesc& D, cudaSt
 {
     const SrcList<N> L = make_src_list<N>(src, n);
     const int px = 16 / bpp;
-    const dim3 grid(ceil_div(D.W, 32 * px), ceil_div(D.H, kARows));
+    const dim3 grid(ceil_div(D.W, 32 * px), ceil_div(D.H, kARows * kAPasses));
     if (bpp == 4) k_assemble_tiles<N, 4><<<grid, kAT, 0, s>>>(L, D);
     else if (bpp == 8) k_assemble_tiles<N, 8><<<grid, kAT, 0, s>>>(L, D);
     else k_assemble_tiles<N, 16><<<grid, kAT, 0, s>>>(L, D);
@@ -279,7 +332,7 @@ cudaError_t average_n(const SrcDesc* src, int n, int fmt, const DstDesc& D, cuda
 {
     const SrcList<N> L = make_src_list<N>(src, n);
     const int px = fmt == 0 ? 4 : fmt == 1 ? 1 : 2;
-    const dim3 grid(ceil_div(D.W, 32 * px), ceil_div(D.H, kARows));
+    const dim3 grid(ceil_div(D.W, 32 * px), ceil_div(D.H, kARows * kAPasses));
     if (fmt == 0) k_average<N, 0><<<grid, kAT, 0, s>>>(L, D);
     else if (fmt == 1) k_average<N, 1><<<grid, kAT, 0, s>>>(L, D);
     else k_average<N, 2><<<grid, kAT, 0, s>>>(L, D);

@@ -148,3 +148,22 @@ def test_bad_arguments():
         ec.assemble_pixels([out[:4, :4]], [(2, 0)], (2, 2), out)   # offset outside the kernel
     with pytest.raises(ec.EcError):
         ec.assemble_pixels([out], [(0, 0)], (17, 1), out)     # kernel larger than 16
+
+
+def test_rgba8_average_of_many_bright_samples():
+    """300 samples with channels near 255 (the 16-bit lane sums are folded every
+    256 sources) and per-pixel counts from 1 to 300: exact integer rounding."""
+    require_gpu()
+    r = np.random.default_rng(17)
+    W, H = 37, 9
+    imgs_o, imgs_g = [], []
+    for i in range(300):
+        w = int(r.integers(1, W + 1))
+        pvp = (0, 0, w, H)                                 # pixel x is held by every sample wider than x
+        a = (0xFFFFFFFF - r.integers(0, 0x03030303, (H, w), dtype=np.uint64)).astype(np.uint32)
+        imgs_o.append(oracle.Image(pvp, pvp, a))
+        imgs_g.append(ec.Image(color=_dev(a), pvp=pvp, roi=pvp))
+    out = torch.empty((H, W), dtype=torch.int32, device="cuda").view(torch.uint32)
+    ec.average(imgs_g, out)
+    ec.default_context().check_status()
+    assert np.array_equal(np_of(out), oracle.average(imgs_o, (0, 0, W, H), 0))
