@@ -10,6 +10,7 @@ import os
 import shutil
 import subprocess
 import sys
+import types
 
 import numpy as np
 import pytest
@@ -20,6 +21,7 @@ import test_oracle_depth_grad as TG
 import test_oracle_rle as TR
 import test_oracle_roi as TO
 import test_oracle_assemble as TS
+import test_oracle_schedules as TSC
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 ORACLE = os.path.join(ROOT, "oracle")
@@ -119,3 +121,57 @@ def test_pins_catch_mutant(tmp_path, name):
 
 def test_real_oracle_passes_all_pins(orc):
     assert not _caught(orc)
+
+
+# ---- schedule planner and executor (oracle/schedules.py, Python) ----------
+
+SCHED_MUTANTS = {
+    "sched_units_reversed": ("            for u in group:\n                for m in u:\n                    p = intersect",
+                             "            for u in reversed(group):\n                for m in u:\n                    p = intersect"),
+    "sched_chain_front_back": ("[[[l], [l + 1]]]", "[[[l + 1], [l]]]"),
+    "sched_bands_ceil": ("a, b = y + (j * h) // k, y + ((j + 1) * h) // k",
+                         "a, b = y + (j * h) // k, y + ((j + 1) * h + k - 1) // k"),
+    "sched_self_messages": ("if m != r:\n                        lv.messages.append",
+                            "if True:\n                        lv.messages.append"),
+    "sched_intersect_short": ("x1, y1 = min(a[0] + a[2], b[0] + b[2]), min(",
+                              "x1, y1 = min(a[0] + a[2], b[0] + b[2]) - 1, min("),
+    "sched_halves_overlap": ("return (x, y, w, m), (x, y + m, w, h - m)", "return (x, y, w, m + 1), (x, y + m, w, h - m)"),
+}
+
+
+def _load_sched_mutant(name, old, new):
+    src = open(os.path.join(ORACLE, "schedules.py")).read()
+    assert src.count(old) == 1, f"mutant {name}: pattern must occur exactly once"
+    mod = types.ModuleType(f"oracle._sched_mutant_{name}")
+    mod.__package__ = "oracle"
+    sys.modules[mod.__name__] = mod
+    exec(compile(src.replace(old, new), f"schedules_{name}.py", "exec"), mod.__dict__)
+    return mod
+
+
+def _sched_caught(mod, monkeypatch):
+    monkeypatch.setattr(TSC, "S", mod)
+    pins = [
+        lambda: [TSC.test_schedule_equals_single_pass(a, True) for a in TSC.ALGOS],
+        lambda: [TSC.test_final_regions_partition_the_frame(a) for a in TSC.ALGOS],
+        lambda: [TSC.test_full_frame_transfers(a, c) for a, c in TSC.FULL_FRAME_COUNTS],
+        lambda: TSC.test_two_three_swap_of_three_is_direct_send(),
+        lambda: TSC.test_direct_send_moves_only_roi_pixels(),
+    ]
+    for pin in pins:
+        try:
+            pin()
+        except (AssertionError, RuntimeError, ValueError, IndexError):
+            return True
+    return False
+
+
+@pytest.mark.parametrize("name", sorted(SCHED_MUTANTS))
+def test_schedule_pins_catch_mutant(name, monkeypatch):
+    mod = _load_sched_mutant(name, *SCHED_MUTANTS[name])
+    assert _sched_caught(mod, monkeypatch), f"mutant {name} survived every schedule pin"
+
+
+def test_real_schedule_oracle_passes_all_pins(monkeypatch):
+    from oracle import schedules
+    assert not _sched_caught(schedules, monkeypatch)
