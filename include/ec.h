@@ -230,6 +230,97 @@ ec_status ec_batch_get_config(const ec_batch* plan, ec_batch_config* cfg, int32_
                               int32_t* grid);
 void ec_batch_free(ec_batch* plan);
 
+/* ------------------------------------------------ multi-stage compositing schedules
+ * Thesis 5.2.2 (direct send, binary swap, 2-3 swap) and 5.2.3 (streaming
+ * sort-last compositing).  The n inputs stand for n rendering resources.  In
+ * stages, resources send parts of their partial frames to others; a receiver
+ * composites what it holds with what it receives, source by source in index
+ * order (depth: ec_composite_depth's merge and tie rule; alpha: front-to-back
+ * "over" in the order given).  At the end each resource owns a part of the
+ * frame and writes it into out (the stream's last resource owns all of it).
+ * A transfer carries only the sender's ROI inside the region sent (thesis
+ * 5.3).  The result equals ec_composite_depth of all inputs bit for bit; for
+ * alpha it equals ec_composite_alpha up to the rounding of the partials.
+ *
+ * Geometry (all in out->pvp coordinates; a rectangle R cut into k row bands
+ * gives band j the rows [R.y + floor(j R.h / k), R.y + floor((j+1) R.h / k))):
+ *   EC_SCHED_STREAM        stage l (l = 0..n-2): resource l sends its whole
+ *                          partial frame to l+1, which composites it in front
+ *                          of its own image.
+ *   EC_SCHED_DIRECT_SEND   one stage: resource i owns row band i of n and
+ *                          receives every other resource's pixels there.
+ *   EC_SCHED_BINARY_SWAP   n a power of two; stage l pairs u = a + j with
+ *                          u + 2^l (a a multiple of 2^(l+1)); their common
+ *                          region is halved across its longer side (rows when
+ *                          h >= w, the first half floor(len/2)); u keeps the
+ *                          first half, u + 2^l the second.
+ *   EC_SCHED_TWO_THREE_SWAP  any n: the current units (first the single
+ *                          resources) are grouped consecutively in pairs, the
+ *                          last group a triple if their count is odd; a
+ *                          group's resources, ordered by the first row of the
+ *                          region they hold and then by unit, get the frame's
+ *                          row bands in that order and receive from every
+ *                          group member the part of their band it holds.
+ * A receiver's new ROI is the bounding box of the pieces it composites.
+ *
+ * flags:
+ *   EC_SCHED_RLE    transfers are RLE-compressed by the sender and decoded by
+ *                   the receiver (depth mode with EC_RGBA8 only: colour mode 2,
+ *                   depth mode 1).  Without it transfers are read in place.
+ *   EC_SCHED_FUSED  with EC_SCHED_RLE: stages that merge the receiver's own
+ *                   image with the pieces of one other unit (every stage of
+ *                   the stream and of binary swap) decode inside the
+ *                   composite, never writing the decoded pieces.
+ */
+typedef enum {
+    EC_SCHED_STREAM = 0,
+    EC_SCHED_DIRECT_SEND = 1,
+    EC_SCHED_BINARY_SWAP = 2,
+    EC_SCHED_TWO_THREE_SWAP = 3
+} ec_sched_algorithm;
+
+#define EC_SCHED_RLE 1u
+#define EC_SCHED_FUSED 2u
+
+typedef struct {
+    int32_t level;      /* stage of the schedule, from 0                      */
+    int32_t sender;     /* resource index (alpha: position in the order)      */
+    int32_t receiver;
+    int32_t fused;      /* 1 if the receiver decodes it inside the composite   */
+    ec_rect piece;      /* pixels carried, out->pvp coordinates                */
+} ec_sched_message;
+
+typedef struct ec_schedule ec_schedule;
+
+/* Plan a schedule of n inputs into out.
+ *   mode    EC_JOB_DEPTH (inputs and out EC_RGBA8 or EC_RGBA32F with depth;
+ *           out->depth required) or EC_JOB_ALPHA (EC_RGBA32F / EC_RGBA16F).
+ *   order   alpha: host array of n distinct indices, order[0] in front
+ *           (resource i holds input order[i]); NULL means 0..n-1.  Ignored
+ *           for depth.
+ * The plan allocates one device arena for every intermediate partial, stream
+ * and decoded piece, and captures the schedule's launches in a CUDA graph.
+ * It refers to the inputs and out by address: they must stay in place until
+ * ec_schedule_free.  Partial results depend only on the inputs' ROIs, which
+ * are read now.  Errors: EC_ERR_INVALID_ARG (bad geometry, format, flags;
+ * binary swap with n not a power of two), EC_ERR_UNSUPPORTED (RLE for alpha
+ * or RGBA32F, n > EC_MAX_SOURCES, a composite of more than
+ * EC_MAX_BATCH_INPUTS pieces). */
+ec_status ec_schedule_plan(ec_ctx* ctx, int32_t mode, int32_t algorithm, const ec_image* in,
+                           int32_t n, const int32_t* order, const ec_target* out, uint32_t flags,
+                           ec_schedule** plan);
+/* Enqueue the captured schedule on stream s. */
+ec_status ec_schedule_run(ec_schedule* plan, ec_stream_t s);
+/* Stages, transfers, kernel launches per run and arena bytes (host pointers, any may be NULL). */
+ec_status ec_schedule_info(const ec_schedule* plan, int32_t* n_levels, int32_t* n_messages,
+                           int32_t* n_launches, uint64_t* arena_bytes);
+/* The transfers, in stage order (cap entries of host memory; EC_ERR_CAPACITY if too few). */
+ec_status ec_schedule_messages(const ec_schedule* plan, ec_sched_message* msgs, int32_t cap);
+/* Wait for s, then copy the colour and depth stream sizes of every transfer of
+ * the last run (2 per message, host memory).  EC_ERR_UNSUPPORTED without RLE. */
+ec_status ec_schedule_stream_sizes(ec_schedule* plan, uint64_t* sizes, int32_t cap, ec_stream_t s);
+void ec_schedule_free(ec_schedule* plan);
+
 /* ------------------------------------------ assembly of the other compound modes
  * Thesis 4.2: sort-first and tile compounds compute complete pixels per source
  * and copy them into place; pixel compounds interleave the destination's

@@ -21,7 +21,9 @@ from ._abi import (  # noqa: F401
     load,
 )
 from .api import (  # noqa: F401
+    SCHEDULES,
     Batch,
+    Schedule,
     Context,
     Job,
     Image,

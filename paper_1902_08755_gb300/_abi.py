@@ -66,6 +66,13 @@ class ec_batch_config(C.Structure):
 
 
 EC_JOB_DEPTH, EC_JOB_ALPHA = 0, 1
+EC_SCHED_STREAM, EC_SCHED_DIRECT_SEND, EC_SCHED_BINARY_SWAP, EC_SCHED_TWO_THREE_SWAP = 0, 1, 2, 3
+EC_SCHED_RLE, EC_SCHED_FUSED = 1, 2
+
+
+class ec_sched_message(C.Structure):
+    _fields_ = [("level", C.c_int32), ("sender", C.c_int32), ("receiver", C.c_int32),
+                ("fused", C.c_int32), ("piece", ec_rect)]
 assert C.sizeof(ec_job) == 80 and C.sizeof(ec_batch_config) == 28
 assert C.sizeof(ec_image) == 56 and C.sizeof(ec_target) == 40 and C.sizeof(ec_rle_job) == 48
 
@@ -98,6 +105,12 @@ SIGNATURES = {
     "ec_batch_run": (_S, [_P, _P]),
     "ec_batch_get_config": (_S, [_P, _P, _P, _P]),
     "ec_batch_free": (None, [_P]),
+    "ec_schedule_plan": (_S, [_P, _I, _I, _P, _I, _P, _P, C.c_uint32, C.POINTER(C.c_void_p)]),
+    "ec_schedule_run": (_S, [_P, _P]),
+    "ec_schedule_info": (_S, [_P, _P, _P, _P, _P]),
+    "ec_schedule_messages": (_S, [_P, _P, _I]),
+    "ec_schedule_stream_sizes": (_S, [_P, _P, _I, _P]),
+    "ec_schedule_free": (None, [_P]),
     "ec_rle_compress_noalloc": (_S, [_P, _I, _I, _I, C.c_uint32, _P, C.c_size_t, _P, _P, _P]),
 }
 

@@ -511,3 +511,75 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+SCHEDULES = {"stream": A.EC_SCHED_STREAM, "direct_send": A.EC_SCHED_DIRECT_SEND,
+             "binary_swap": A.EC_SCHED_BINARY_SWAP, "two_three_swap": A.EC_SCHED_TWO_THREE_SWAP}
+
+
+class Schedule:
+    """ec_schedule: a multi-stage compositing schedule (thesis 5.2.2, 5.2.3)
+    captured in a CUDA graph.
+
+    ``mode`` is 'depth' or 'alpha'; ``algorithm`` one of SCHEDULES.  With
+    ``rle`` the transfers travel RLE-compressed (depth, RGBA8); ``fused`` lets
+    binary stages decode inside the composite.  The tensors must stay alive and
+    in place while the schedule exists."""
+
+    def __init__(self, mode: str, algorithm: str, images: Sequence[Image], out_color: torch.Tensor,
+                 out_depth: Optional[torch.Tensor] = None, out_pvp: Optional[Rect] = None,
+                 order=None, rle: bool = True, fused: bool = True, ctx: Optional[Context] = None):
+        self.ctx = ctx or default_context(out_color.device.index)
+        dev = self.ctx.device
+        depth = mode == "depth"
+        if not depth and mode != "alpha":
+            raise ValueError("mode must be 'depth' or 'alpha'")
+        imgs = (ec_image * max(1, len(images)))(*[_image_struct(im, dev, depth) for im in images])
+        o = None if depth else _order(order, len(images))
+        tgt = _target(out_color, out_depth if depth else None, out_pvp, dev)
+        self._keep = [imgs, o, list(images), out_color, out_depth]
+        flags = (A.EC_SCHED_RLE if rle else 0) | (A.EC_SCHED_FUSED if fused else 0)
+        h = C.c_void_p()
+        check(_lib().ec_schedule_plan(self.ctx.h, A.EC_JOB_DEPTH if depth else A.EC_JOB_ALPHA,
+                                      SCHEDULES[algorithm], imgs, len(images),
+                                      None if o is None else C.cast(o, C.c_void_p), C.byref(tgt), flags,
+                                      C.byref(h)), "ec_schedule_plan")
+        self.h = h
+        self.rle = rle
+
+    def run(self, stream=None):
+        check(_lib().ec_schedule_run(self.h, _stream_handle(stream)), "ec_schedule_run")
+
+    def info(self) -> dict:
+        lv, nm, nl = C.c_int32(), C.c_int32(), C.c_int32()
+        ab = C.c_uint64()
+        check(_lib().ec_schedule_info(self.h, C.byref(lv), C.byref(nm), C.byref(nl), C.byref(ab)),
+              "ec_schedule_info")
+        return {"levels": lv.value, "messages": nm.value, "launches": nl.value, "arena_bytes": ab.value}
+
+    def messages(self):
+        """[(level, sender, receiver, fused, (x, y, w, h))] in stage order."""
+        n = self.info()["messages"]
+        arr = (A.ec_sched_message * max(1, n))()
+        check(_lib().ec_schedule_messages(self.h, arr, n), "ec_schedule_messages")
+        return [(m.level, m.sender, m.receiver, m.fused, (m.piece.x, m.piece.y, m.piece.w, m.piece.h))
+                for m in arr[:n]]
+
+    def stream_sizes(self, stream=None):
+        """[(colour bytes, depth bytes)] of every transfer of the last run."""
+        n = self.info()["messages"]
+        arr = (C.c_uint64 * max(2, 2 * n))()
+        check(_lib().ec_schedule_stream_sizes(self.h, arr, 2 * n, _stream_handle(stream)),
+              "ec_schedule_stream_sizes")
+        return [(int(arr[2 * i]), int(arr[2 * i + 1])) for i in range(n)]
+
+    def close(self):
+        if getattr(self, "h", None) is not None and self.h.value:
+            _lib().ec_schedule_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

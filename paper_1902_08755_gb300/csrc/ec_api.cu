@@ -12,23 +12,6 @@ using namespace ec;
 
 namespace {
 
-// Makes ctx->device current for the duration of a call, then restores the
-// caller's device.
-struct DeviceGuard {
-    int prev = -1;
-    bool ok = true;
-    explicit DeviceGuard(int dev)
-    {
-        if (cudaGetDevice(&prev) != cudaSuccess) { ok = false; return; }
-        if (prev != dev && cudaSetDevice(dev) != cudaSuccess) ok = false;
-    }
-    ~DeviceGuard()
-    {
-        int cur = -1;
-        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
-    }
-};
-
 bool rect_ok(const ec_rect& r)
 {
     return r.w >= 0 && r.h >= 0 && (int64_t)r.x + r.w <= INT32_MAX && (int64_t)r.y + r.h <= INT32_MAX;
@@ -70,7 +53,6 @@ ec_rect merged_roi(const ec_image* in, int n, const ec_rect& pvp)
     return ec_rect{(int32_t)x0, (int32_t)y0, (int32_t)(x1 - x0), (int32_t)(y1 - y0)};
 }
 
-bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
 
 int mod_pos(int64_t a, int m) { return (int)(((a % m) + m) % m); }
 
@@ -458,7 +440,9 @@ size_t ec_rle_max_size(int32_t w, int32_t h)
     return (size_t)size;
 }
 
-static ec_status rle_job_desc(const ec_rle_job& j, bool compress, RleJobDesc* d)
+}  // extern "C"
+
+ec_status rle_job_desc(const ec_rle_job& j, bool compress, RleJobDesc* d)
 {
     if (j.w < 0 || j.h < 0 || j.pitch < j.w) return EC_ERR_INVALID_ARG;
     const uint64_t n = (uint64_t)j.w * (uint64_t)j.h;
@@ -487,6 +471,8 @@ static ec_status rle_job_desc(const ec_rle_job& j, bool compress, RleJobDesc* d)
     }
     return EC_OK;
 }
+
+extern "C" {
 
 static ec_status rle_batch(ec_ctx* ctx, const ec_rle_job* jobs, int32_t njobs, bool compress,
                            ec_stream_t s)
@@ -997,6 +983,15 @@ ec_status ec_batch_plan(ec_ctx* ctx, const ec_job* jobs, int32_t njobs, const ec
     *plan = b;
     return EC_OK;
 }
+
+}  // extern "C"
+
+cudaError_t ec::batch_enqueue(const ec_batch* b, cudaStream_t s)
+{
+    return launch_batch(b->d_jobs, b->d_srcs, b->d_items, b->n_items, b->d_head, b->shape, b->grid, s);
+}
+
+extern "C" {
 
 ec_status ec_batch_run(ec_batch* b, ec_stream_t s)
 {

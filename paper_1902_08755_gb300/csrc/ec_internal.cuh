@@ -11,6 +11,25 @@
 
 #include "../../include/ec.h"
 
+// Makes a device current for the duration of a call, then restores the
+// caller's device.
+struct DeviceGuard {
+    int prev = -1;
+    bool ok = true;
+    explicit DeviceGuard(int dev)
+    {
+        if (cudaGetDevice(&prev) != cudaSuccess) { ok = false; return; }
+        if (prev != dev && cudaSetDevice(dev) != cudaSuccess) ok = false;
+    }
+    ~DeviceGuard()
+    {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+inline bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
 struct ec_ctx {
     int device = 0;
     uint32_t* d_status = nullptr;   // first device-side error (0 = none)
@@ -228,5 +247,53 @@ struct RoiList {
 // 16-byte aligned; they must be zero on entry and are zero again on exit.
 cudaError_t launch_detect_roi(RoiDesc* d, const int* kinds, const uint32_t* nblocks, int n, int tile,
                               uint32_t* scratch, ec_rect* out, cudaStream_t s);
+
+// ---- fused decode-and-composite (stages of multi-stage schedules) ---------
+// One receiver's binary depth merge: a plain local input and RLE-coded pieces
+// of one other unit, all in frame coordinates.  Buffers are [rows][pitch]
+// uint32 colour + float depth; element [0][0] sits at frame (ox, oy) / (lx, ly).
+struct FusedStage {
+    uint32_t* oc;
+    float* od;
+    const uint32_t* lc;
+    const float* ld;
+    int32_t opitch, ox, oy;
+    int32_t lpitch, lx, ly;
+    int32_t r0x, r0y, r1x, r1y;   // local ROI [r0, r1); empty if r0x >= r1x
+    int32_t front;                // 1: the pieces are in front of the local input
+    int32_t ovec, lvec;           // 16-byte aligned bases and pitches (multiples of 4)
+    int32_t pad;
+};
+static_assert(sizeof(FusedStage) == 88, "fused stage layout");
+
+// A work unit: chunk `chunk` (4096 elements, row-major) of a rectangle.  With
+// streams (cs, ds non-null) the rectangle is a coded piece and the unit
+// decodes and merges it; without, it is a part of the output no piece covers
+// and the unit writes the local input there (or the background).
+struct FusedUnit {
+    const uint8_t* cs;
+    const uint8_t* ds;
+    const uint64_t* csize;        // stream sizes written by the compressor
+    const uint64_t* dsize;
+    int32_t stage;
+    int32_t x, y, w, h;
+    uint32_t chunk;
+    int32_t pad[2];
+};
+static_assert(sizeof(FusedUnit) == 64, "fused unit layout");
+
+}  // namespace ec
+
+// Validate a codec job and turn it into a descriptor (first_unit left 0).
+ec_status rle_job_desc(const ec_rle_job& j, bool compress, ec::RleJobDesc* d);
+
+namespace ec {
+
+cudaError_t launch_fused_depth(const FusedStage* stages, const FusedUnit* units, int n_units,
+                               uint32_t* status, cudaStream_t s);
+
+// Enqueue a batch plan's persistent launch directly (no graph), for callers
+// that capture their own graph.
+cudaError_t batch_enqueue(const ec_batch* b, cudaStream_t s);
 
 }  // namespace ec

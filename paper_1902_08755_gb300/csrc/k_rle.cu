@@ -34,6 +34,7 @@
 // repeat tokens and the warp one token's aligned body per store.  The four
 // planes are then transposed back into elements with byte permutes.
 #include "ec_internal.cuh"
+#include "rle_codec.cuh"
 
 #include <algorithm>
 #include <atomic>
@@ -50,17 +51,10 @@ constexpr uint32_t kMagic = 0x31524345u;             // "ECR1"
 constexpr uint64_t kAgg = 1ull << 62, kInc = 2ull << 62, kVal = (1ull << 62) - 1;
 constexpr int kSpinLimit = 1 << 22;
 
-// Bit-swizzle: byte k of the result gathers bit pair (7-2k, 6-2k) of the four
-// components, component 0 (R) in the top pair.  This is a transpose of the 4x4
-// matrix of 2-bit cells, done as two delta swaps; it is its own inverse.
-__device__ __forceinline__ uint32_t swizzle(uint32_t x)
-{
-    uint32_t t = ((x >> 20) ^ x) & 0x00000F0Fu;
-    x ^= t ^ (t << 20);
-    t = ((x >> 10) ^ x) & 0x00330033u;
-    x ^= t ^ (t << 10);
-    return x;
-}
+using rlec::swizzle;
+using rlec::get_u32;
+using rlec::transpose4;
+using rlec::bcast8;
 
 template <int N>
 __device__ __forceinline__ int find_job(const RleJobList<N>& J, uint32_t unit)
@@ -79,10 +73,6 @@ __device__ __forceinline__ void put_u32(uint8_t* p, uint32_t v)
     p[0] = (uint8_t)v; p[1] = (uint8_t)(v >> 8); p[2] = (uint8_t)(v >> 16); p[3] = (uint8_t)(v >> 24);
 }
 
-__device__ __forceinline__ uint32_t get_u32(const uint8_t* p)
-{
-    return (uint32_t)p[0] | ((uint32_t)p[1] << 8) | ((uint32_t)p[2] << 16) | ((uint32_t)p[3] << 24);
-}
 
 __device__ void write_header(uint8_t* d, const RleJobDesc& jb)
 {
@@ -159,14 +149,6 @@ __device__ __forceinline__ uint32_t eq_bytes(uint32_t a, uint32_t b)
     return byte_msbs(t);
 }
 
-// 4x4 byte transpose: word b of the result holds byte b of e0..e3 (e0 lowest).
-__device__ __forceinline__ uint4 transpose4(uint32_t e0, uint32_t e1, uint32_t e2, uint32_t e3)
-{
-    const uint32_t lo01 = __byte_perm(e0, e1, 0x5140), lo23 = __byte_perm(e2, e3, 0x5140);
-    const uint32_t hi01 = __byte_perm(e0, e1, 0x7362), hi23 = __byte_perm(e2, e3, 0x7362);
-    return make_uint4(__byte_perm(lo01, lo23, 0x5410), __byte_perm(lo01, lo23, 0x7632),
-                      __byte_perm(hi01, hi23, 0x5410), __byte_perm(hi01, hi23, 0x7632));
-}
 
 // Bits [lo, hi) set (0 <= lo, hi <= 31).
 __device__ __forceinline__ uint32_t bit_range(int lo, int hi)
@@ -773,8 +755,6 @@ k_rle_compress(const __grid_constant__ RleJobList<N> J, uint64_t* flags, uint32_
 
 constexpr int kDT = 128;        // decoder CTA: one warp per byte plane
 
-__device__ __forceinline__ uint32_t bcast8(uint32_t w) { return 0x01010101u * (w & 0xFFu); }
-
 template <int N>
 __global__ void __launch_bounds__(kDT)
 k_rle_decompress(const __grid_constant__ RleJobList<N> J, uint32_t* status)
@@ -782,7 +762,7 @@ k_rle_decompress(const __grid_constant__ RleJobList<N> J, uint32_t* status)
     __shared__ __align__(16) uint8_t planes[4][kChunk];
     __shared__ uint32_t s_beg[5];
     __shared__ int s_fail, s_mode;
-    __shared__ uint8_t s_hdr[52];
+    __shared__ uint8_t s_hdr[rlec::kHdrBytes];
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const uint32_t unit = blockIdx.x;
@@ -794,42 +774,10 @@ k_rle_decompress(const __grid_constant__ RleJobList<N> J, uint32_t* status)
 
     // header (32 bytes) and this chunk's end-table entries 4c-1 .. 4c+3 (20 bytes),
     // fetched in one round trip by 52 threads
-    const bool has_hdr = size >= 32, has_tab = nc > 0 && size >= 32ull + 16ull * nc;
-    if (tid < 32) {
-        s_hdr[tid] = has_hdr ? src[tid] : 0;
-    } else if (tid < 52) {
-        const int i = tid - 32;
-        s_hdr[tid] = (has_tab && !(c == 0 && i < 4)) ? src[32 + 16ull * c - 4 + i] : 0;
-    }
+    if (tid < rlec::kHdrBytes) s_hdr[tid] = rlec::header_byte(src, size, nc, c, tid);
     __syncthreads();
     if (tid == 0) {
-        int bad = 0;
-        if (!has_hdr) bad = 1;
-        else {
-            const uint8_t* h = s_hdr;
-            const uint32_t mode = (uint32_t)h[6] | ((uint32_t)h[7] << 8);
-            bad |= get_u32(h) != kMagic;
-            bad |= (h[4] | (h[5] << 8)) != 1;
-            bad |= mode != 1u && mode != 2u;
-            bad |= get_u32(h + 8) != (uint32_t)jb.w || get_u32(h + 12) != (uint32_t)jb.h;
-            bad |= get_u32(h + 16) != 4u || get_u32(h + 20) != (uint32_t)kChunk;
-            bad |= get_u32(h + 24) != nc || get_u32(h + 28) != 4u;
-            s_mode = (int)mode;
-            if (!bad && nc > 0 && !has_tab) bad = 1;
-            if (!bad && nc > 0) {
-                const uint64_t psize = size - 32ull - 16ull * nc;
-                const uint32_t n = (uint32_t)jb.w * (uint32_t)jb.h;
-                const uint32_t clen = min((uint32_t)kChunk, n - c * (uint32_t)kChunk);
-                const uint32_t cap = clen + (clen + 127u) / 128u;   // all-literal coding
-                s_beg[0] = get_u32(h + 32);                         // 0 for chunk 0
-                for (int p = 0; p < 4; ++p) {
-                    s_beg[p + 1] = get_u32(h + 36 + 4 * p);
-                    bad |= s_beg[p + 1] < s_beg[p];
-                    bad |= s_beg[p + 1] - s_beg[p] > cap;   // longer than any valid stream
-                }
-                bad |= (uint64_t)s_beg[4] > psize;
-            }
-        }
+        const int bad = rlec::check_header(s_hdr, size, (uint32_t)jb.w, (uint32_t)jb.h, nc, c, s_beg, &s_mode);
         s_fail = bad;
         if (bad) set_status(status, EC_ERR_CORRUPT);
     }
@@ -841,86 +789,10 @@ k_rle_decompress(const __grid_constant__ RleJobList<N> J, uint32_t* status)
     const int len = (int)min((uint32_t)kChunk, n - q0);
     const uint8_t* payload = src + 32 + 16ull * nc;
 
-    // decode plane `warp` in windows of 32 stream bytes, one per lane.  Lane
-    // l knows where a token starting at its byte would be followed by the
-    // next one; composing these jumps by doubling (5 levels) gives every lane
-    // t the start of the window's t-th token, so lanes hold tokens in order.
-    // A warp scan places them; each lane writes the unaligned head and tail
-    // bytes of its own repeat token, the whole warp the aligned body words of
-    // one token per store, and literal tokens are copied by the whole warp.
-    {
-        const int p = warp;
-        const int in_end = (int)s_beg[p + 1];
-        int cur = (int)s_beg[p], outp = 0, bad = 0;
-        uint8_t* plane = planes[p];
-        uint32_t* p32 = reinterpret_cast<uint32_t*>(plane);
-        while (cur < in_end) {
-            const int i = cur + lane;
-            const uint32_t b = i < in_end ? (uint32_t)__ldg(payload + i) : 0u;
-            const uint32_t b1 = i + 1 < in_end ? (uint32_t)__ldg(payload + i + 1) : 0u;
-            int J = lane + (b >= 128u ? 2 : 2 + (int)b);   // next^(2^k), relative to cur
-            int pos = 0;                                   // start of token #lane
-#pragma unroll
-            for (int k = 0; k < 5; ++k) {
-                const int y = __shfl_sync(0xffffffffu, J, min(pos, 31));
-                if (((lane >> k) & 1) && pos < 32) pos = y;
-                if (k < 4) {
-                    const int z = __shfl_sync(0xffffffffu, J, min(J, 31));
-                    if (J < 32) J = z;
-                }
-            }
-            // tokens take >= 2 bytes: at most 16 start in the window, and the
-            // position after the last one (lane ntok) is exact
-            const bool valid = pos < min(32, in_end - cur);
-            const int ntok = __popc(__ballot_sync(0xffffffffu, valid));
-            const int sl = __shfl_sync(0xffffffffu, pos, ntok);
-            const int ps = min(pos, 31);
-            const uint32_t tb = __shfl_sync(0xffffffffu, b, ps);
-            const uint32_t tv = __shfl_sync(0xffffffffu, b1, ps);
-            const bool trep = tb >= 128u;
-            const int olen = valid ? (trep ? (int)tb - 127 : (int)tb + 1) : 0;
-            const int tnext = pos + (trep ? 2 : 2 + (int)tb);
-            int incl = olen;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const int y = __shfl_up_sync(0xffffffffu, incl, o);
-                if (lane >= o) incl += y;
-            }
-            const int total = __shfl_sync(0xffffffffu, incl, 31);
-            const int o = outp + incl - olen;
-            if (__any_sync(0xffffffffu, valid && (cur + tnext > in_end || o + olen > len))) {
-                bad = 1;                                  // a token runs past its stream or chunk
-                break;
-            }
-            int head = 0, nw = 0;
-            if (valid && trep) {
-                head = min(olen, (4 - (o & 3)) & 3);
-                nw = (olen - head) >> 2;
-                const int tail = olen - head - 4 * nw;
-                for (int k = 0; k < head; ++k) plane[o + k] = (uint8_t)tv;
-                for (int k = 0; k < tail; ++k) plane[o + head + 4 * nw + k] = (uint8_t)tv;
-            }
-            const uint32_t pk = (uint32_t)((o + head) >> 2) | ((uint32_t)nw << 16);
-            const uint32_t wv = 0x01010101u * (tv & 0xFFu);
-            for (uint32_t m = __ballot_sync(0xffffffffu, nw > 0); m; m &= m - 1u) {
-                const int t = __ffs(m) - 1;
-                const uint32_t q = __shfl_sync(0xffffffffu, pk, t);
-                const uint32_t x = __shfl_sync(0xffffffffu, wv, t);
-                if ((uint32_t)lane < (q >> 16)) p32[(q & 0xFFFFu) + lane] = x;
-            }
-            for (uint32_t m = __ballot_sync(0xffffffffu, valid && !trep); m; m &= m - 1u) {
-                const int t = __ffs(m) - 1;
-                const int oo = __shfl_sync(0xffffffffu, o, t);
-                const int ml = __shfl_sync(0xffffffffu, olen, t);
-                const int s0 = cur + __shfl_sync(0xffffffffu, pos, t) + 1;   // after the control
-                for (int k = lane; k < ml; k += 32) plane[oo + k] = __ldg(payload + s0 + k);
-            }
-            outp += total;
-            cur += sl;
-        }
-        if (!bad && outp != len) bad = 1;
-        if (bad && lane == 0) s_fail = 1;
-    }
+    // warp p decodes byte plane p
+    if (rlec::decode_plane(payload, (int)s_beg[warp], (int)s_beg[warp + 1], len, planes[warp], lane) &&
+        lane == 0)
+        s_fail = 1;
     __syncthreads();
     if (s_fail) {
         if (tid == 0) set_status(status, EC_ERR_CORRUPT);

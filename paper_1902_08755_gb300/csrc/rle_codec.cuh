@@ -1,0 +1,170 @@
+// rle_codec.cuh -- device pieces of the RLE container (thesis 5.5.1) shared by
+// the decoder kernel and the fused decode-and-composite kernel: the swizzle,
+// byte transposes, header and end-table validation, and the warp-wide decoder
+// of one byte-plane stream.
+#pragma once
+
+#include "ec_internal.cuh"
+
+namespace ec {
+namespace rlec {
+
+constexpr int kChunk = EC_RLE_CHUNK;                 // 4096 elements
+constexpr uint32_t kMagic = 0x31524345u;             // "ECR1"
+constexpr int kHdrBytes = 52;                        // header + 5 end-table entries
+
+// Bit-swizzle: byte k of the result gathers bit pair (7-2k, 6-2k) of the four
+// components, component 0 (R) in the top pair.  This is a transpose of the 4x4
+// matrix of 2-bit cells, done as two delta swaps; it is its own inverse.
+__device__ __forceinline__ uint32_t swizzle(uint32_t x)
+{
+    uint32_t t = ((x >> 20) ^ x) & 0x00000F0Fu;
+    x ^= t ^ (t << 20);
+    t = ((x >> 10) ^ x) & 0x00330033u;
+    x ^= t ^ (t << 10);
+    return x;
+}
+
+__device__ __forceinline__ uint32_t get_u32(const uint8_t* p)
+{
+    return (uint32_t)p[0] | ((uint32_t)p[1] << 8) | ((uint32_t)p[2] << 16) | ((uint32_t)p[3] << 24);
+}
+
+// 4x4 byte transpose: word b of the result holds byte b of e0..e3 (e0 lowest).
+__device__ __forceinline__ uint4 transpose4(uint32_t e0, uint32_t e1, uint32_t e2, uint32_t e3)
+{
+    const uint32_t lo01 = __byte_perm(e0, e1, 0x5140), lo23 = __byte_perm(e2, e3, 0x5140);
+    const uint32_t hi01 = __byte_perm(e0, e1, 0x7362), hi23 = __byte_perm(e2, e3, 0x7362);
+    return make_uint4(__byte_perm(lo01, lo23, 0x5410), __byte_perm(lo01, lo23, 0x7632),
+                      __byte_perm(hi01, hi23, 0x5410), __byte_perm(hi01, hi23, 0x7632));
+}
+
+__device__ __forceinline__ uint32_t bcast8(uint32_t w) { return 0x01010101u * (w & 0xFFu); }
+
+// Byte i (0 <= i < 52) of what the validator reads for chunk c: the 32-byte
+// header, then end-table entries 4c-1 .. 4c+3 (entry -1 reads as 0).  Bytes
+// past `size` read as 0 and fail validation.
+__device__ __forceinline__ uint8_t header_byte(const uint8_t* src, uint64_t size, uint32_t nc,
+                                               uint32_t c, int i)
+{
+    if (i < 32) return size >= 32 ? src[i] : 0;
+    const int k = i - 32;
+    const bool has_tab = nc > 0 && size >= 32ull + 16ull * nc;
+    return (has_tab && !(c == 0 && k < 4)) ? src[32 + 16ull * c - 4 + k] : 0;
+}
+
+// Validate the header fields against the expected w x h and n_chunks, and
+// chunk c's four stream ends against the payload size and the all-literal
+// bound.  Writes beg[0..4] (stream offsets inside the payload) and *mode.
+// Returns nonzero for a malformed stream.
+__device__ __forceinline__ int check_header(const uint8_t* h, uint64_t size, uint32_t w, uint32_t hgt,
+                                            uint32_t nc, uint32_t c, uint32_t* beg, int* mode)
+{
+    if (size < 32) return 1;
+    int bad = 0;
+    const uint32_t md = (uint32_t)h[6] | ((uint32_t)h[7] << 8);
+    bad |= get_u32(h) != kMagic;
+    bad |= (h[4] | (h[5] << 8)) != 1;
+    bad |= md != 1u && md != 2u;
+    bad |= get_u32(h + 8) != w || get_u32(h + 12) != hgt;
+    bad |= get_u32(h + 16) != 4u || get_u32(h + 20) != (uint32_t)kChunk;
+    bad |= get_u32(h + 24) != nc || get_u32(h + 28) != 4u;
+    *mode = (int)md;
+    if (!bad && nc > 0 && size < 32ull + 16ull * nc) bad = 1;
+    if (!bad && nc > 0) {
+        const uint64_t psize = size - 32ull - 16ull * nc;
+        const uint32_t n = w * hgt;
+        const uint32_t clen = min((uint32_t)kChunk, n - c * (uint32_t)kChunk);
+        const uint32_t cap = clen + (clen + 127u) / 128u;   // all-literal coding
+        beg[0] = get_u32(h + 32);                           // 0 for chunk 0
+        for (int p = 0; p < 4; ++p) {
+            beg[p + 1] = get_u32(h + 36 + 4 * p);
+            bad |= beg[p + 1] < beg[p];
+            bad |= beg[p + 1] - beg[p] > cap;               // longer than any valid stream
+        }
+        bad |= (uint64_t)beg[4] > psize;
+    }
+    return bad;
+}
+
+// One warp decodes the stream payload[beg, end) into plane[0, len).  Windows
+// of 32 stream bytes, one per lane: lane l knows where a token starting at its
+// byte would be followed by the next one; composing these jumps by doubling
+// (5 levels) gives every lane t the start of the window's t-th token, so lanes
+// hold tokens in order.  A warp scan places them; each lane writes the
+// unaligned head and tail bytes of its own repeat token, the whole warp the
+// aligned body words of one token per store, and literal tokens are copied by
+// the whole warp.  Returns nonzero (the same on every lane) when a token runs
+// past its stream or the chunk, or the stream does not yield exactly len bytes.
+// plane must be 4-byte aligned.
+__device__ __forceinline__ int decode_plane(const uint8_t* __restrict__ payload, int beg, int end,
+                                            int len, uint8_t* plane, int lane)
+{
+    uint32_t* p32 = reinterpret_cast<uint32_t*>(plane);
+    int cur = beg, outp = 0;
+    while (cur < end) {
+        const int i = cur + lane;
+        const uint32_t b = i < end ? (uint32_t)__ldg(payload + i) : 0u;
+        const uint32_t b1 = i + 1 < end ? (uint32_t)__ldg(payload + i + 1) : 0u;
+        int J = lane + (b >= 128u ? 2 : 2 + (int)b);   // next^(2^k), relative to cur
+        int pos = 0;                                   // start of token #lane
+#pragma unroll
+        for (int k = 0; k < 5; ++k) {
+            const int y = __shfl_sync(0xffffffffu, J, min(pos, 31));
+            if (((lane >> k) & 1) && pos < 32) pos = y;
+            if (k < 4) {
+                const int z = __shfl_sync(0xffffffffu, J, min(J, 31));
+                if (J < 32) J = z;
+            }
+        }
+        // tokens take >= 2 bytes: at most 16 start in the window, and the
+        // position after the last one (lane ntok) is exact
+        const bool valid = pos < min(32, end - cur);
+        const int ntok = __popc(__ballot_sync(0xffffffffu, valid));
+        const int sl = __shfl_sync(0xffffffffu, pos, ntok);
+        const int ps = min(pos, 31);
+        const uint32_t tb = __shfl_sync(0xffffffffu, b, ps);
+        const uint32_t tv = __shfl_sync(0xffffffffu, b1, ps);
+        const bool trep = tb >= 128u;
+        const int olen = valid ? (trep ? (int)tb - 127 : (int)tb + 1) : 0;
+        const int tnext = pos + (trep ? 2 : 2 + (int)tb);
+        int incl = olen;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += y;
+        }
+        const int total = __shfl_sync(0xffffffffu, incl, 31);
+        const int o = outp + incl - olen;
+        if (__any_sync(0xffffffffu, valid && (cur + tnext > end || o + olen > len))) return 1;
+        int head = 0, nw = 0;
+        if (valid && trep) {
+            head = min(olen, (4 - (o & 3)) & 3);
+            nw = (olen - head) >> 2;
+            const int tail = olen - head - 4 * nw;
+            for (int k = 0; k < head; ++k) plane[o + k] = (uint8_t)tv;
+            for (int k = 0; k < tail; ++k) plane[o + head + 4 * nw + k] = (uint8_t)tv;
+        }
+        const uint32_t pk = (uint32_t)((o + head) >> 2) | ((uint32_t)nw << 16);
+        const uint32_t wv = 0x01010101u * (tv & 0xFFu);
+        for (uint32_t m = __ballot_sync(0xffffffffu, nw > 0); m; m &= m - 1u) {
+            const int t = __ffs(m) - 1;
+            const uint32_t q = __shfl_sync(0xffffffffu, pk, t);
+            const uint32_t x = __shfl_sync(0xffffffffu, wv, t);
+            if ((uint32_t)lane < (q >> 16)) p32[(q & 0xFFFFu) + lane] = x;
+        }
+        for (uint32_t m = __ballot_sync(0xffffffffu, valid && !trep); m; m &= m - 1u) {
+            const int t = __ffs(m) - 1;
+            const int oo = __shfl_sync(0xffffffffu, o, t);
+            const int ml = __shfl_sync(0xffffffffu, olen, t);
+            const int s0 = cur + __shfl_sync(0xffffffffu, pos, t) + 1;   // after the control
+            for (int k = lane; k < ml; k += 32) plane[oo + k] = __ldg(payload + s0 + k);
+        }
+        outp += total;
+        cur += sl;
+    }
+    return outp != len;
+}
+
+}  // namespace rlec
+}  // namespace ec
