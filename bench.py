@@ -11,7 +11,7 @@ its size is written, then another 2x its size is read, so that the timed step
 neither finds its inputs in L2 nor pays for writing back the flush's lines.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ec|reference]
-                    [--workload cfg2|cfg1|cfg3|cfg3h|cfg3fused|cfg3hfused|cfg4|cfg5d|cfg5a|cfg5afused|roi2|asm4k]
+                    [--workload cfg2|cfg1|cfg3|cfg3h|cfg3fused|cfg3hfused|cfg4|cfg5d|cfg5a|cfg5afused|roi2|asm4k|sched2]
 
 Prints ONE JSON line (rank 0).  Metric: composited Gpixel-layers/s (sum over
 sources of |roi_i ∩ frame| per step, divided by the step time).  With N > 1
@@ -554,6 +554,121 @@ class Assembly:
         return (time.perf_counter() - t0) / self.sample_fraction
 
 
+class Schedules:
+    """sched2: a multi-stage compositing schedule (thesis 5.2.2, 5.2.3) over the
+    cfg2 sources (16 x 1920x1080 RGBA8+Z32, cropped): binary swap, transfers
+    RLE-compressed, every stage a fused decode-and-merge; the whole schedule
+    is one CUDA graph.  The other schedules and variants are timed beside it."""
+
+    OTHERS = [("binary_swap", "rle"), ("binary_swap", "raw"), ("direct_send", "rle"),
+              ("direct_send", "raw"), ("two_three_swap", "fused"), ("stream", "fused")]
+    VARIANTS = {"fused": dict(rle=True, fused=True), "rle": dict(rle=True, fused=False),
+                "raw": dict(rle=False, fused=False)}
+
+    def __init__(self, device, algo="binary_swap", variant="fused"):
+        import paper_1902_08755_gb300 as ec
+        import synthetic as S
+        self.ec = ec
+        self.W, self.H, self.n = 1920, 1080, 16
+        self.algo, self.variant = algo, variant
+        self.desc = (f"{self.n} sources {self.W}x{self.H} RGBA8+Z32, ~30% coverage, ROI-cropped; {algo} "
+                     f"schedule, {variant} transfers ({'RLE colour mode 2 / depth mode 1, decoded inside the merge' if variant == 'fused' else variant}); one CUDA graph per step")
+        self.srcs = S.depth_sources(2, self.n, self.W, self.H, 0.3, clustered=True, cropped=True, device=device)
+        self.units = sum(max(0, min(s.roi[2], self.W)) * max(0, min(s.roi[3], self.H)) for s in self.srcs)
+        self.stored_px = sum(s.pvp[2] * s.pvp[3] for s in self.srcs)
+        if torch.device(device).type != "cuda":
+            self.kernels = []
+            return
+        self.ctx = ec.default_context(torch.device(device).index or 0)
+        self.imgs = [ec.Image(color=s.color, depth=s.depth, pvp=s.pvp, roi=s.roi) for s in self.srcs]
+        self.out_c = torch.empty((self.H, self.W), dtype=torch.int32, device=device).view(torch.uint32)
+        self.out_d = torch.empty((self.H, self.W), dtype=torch.float32, device=device)
+        self.sch = self._plan(algo, variant)
+        self.launch_list = self.sch.launches()
+        self.kernels = [f"L{lv}:{kind}" for lv, kind, _ in self.launch_list]
+        self.kind_of = [kind for _, kind, _ in self.launch_list]
+
+    def _plan(self, algo, variant):
+        return self.ec.Schedule("depth", algo, self.imgs, self.out_c, self.out_d, ctx=self.ctx,
+                                **self.VARIANTS[variant])
+
+    def step(self, ev=None):
+        """Launch by launch, an event after each (for the per-kernel times)."""
+        if ev is None:
+            self.sch.run()
+            return
+        ev[0].record()
+        for i in range(len(self.launch_list)):
+            self.sch.run_launch(i)
+            ev[i + 1].record()
+
+    def graph_step(self):
+        self.sch.run()
+
+    def launches_per_step(self):
+        return len(self.launch_list)
+
+    def compressed_bytes(self):
+        if self.variant == "raw":
+            return 0
+        return sum(c + d for c, d in self.sch.stream_sizes())
+
+    def algorithmic_bytes(self):
+        out = {}
+        for _, kind, b in self.launch_list:
+            out[kind] = out.get(kind, 0) + b
+        if self.variant != "raw":
+            for m, (c, d) in zip(self.sch.messages(), self.sch.stream_sizes()):
+                out["rle_compress"] = out.get("rle_compress", 0) + c + d          # streams written
+                k = "fused_depth" if m[3] else "rle_decompress"                  # streams read
+                out[k] = out.get(k, 0) + c + d
+        return out
+
+    def others(self, flush, reps=30):
+        res = {}
+        for algo, variant in [(self.algo, self.variant)] + self.OTHERS:
+            sch = self._plan(algo, variant)
+            ms = _timed(sch.run, flush, reps)
+            info = sch.info()
+            comp = 0 if variant == "raw" else sum(c + d for c, d in sch.stream_sizes())
+            res[f"{algo}/{variant}"] = {"ms": ms, "gpixel_layers_s": self.units / (ms * 1e-3) / 1e9,
+                                        "levels": info["levels"], "transfers": info["messages"],
+                                        "launches": info["launches"], "compressed_bytes": comp}
+            sch.close()
+        return res
+
+    def setup_e2e(self):
+        self.h_c = [s.color.view(torch.int32).cpu().pin_memory() for s in self.srcs]
+        self.h_d = [s.depth.cpu().pin_memory() for s in self.srcs]
+        self.h_out = torch.empty((self.H, self.W), dtype=torch.int32).pin_memory()
+        self.h_outd = torch.empty((self.H, self.W), dtype=torch.float32).pin_memory()
+        self.h2d = sum(t.numel() * 4 for t in self.h_c + self.h_d)
+        self.d2h = self.H * self.W * 8
+
+    def e2e_step(self):
+        for s, hc, hd in zip(self.srcs, self.h_c, self.h_d):
+            s.color.view(torch.int32).copy_(hc, non_blocking=True)
+            s.depth.copy_(hd, non_blocking=True)
+        self.sch.run()
+        self.h_out.copy_(self.out_c.view(torch.int32), non_blocking=True)
+        self.h_outd.copy_(self.out_d, non_blocking=True)
+
+    def oracle_step(self, pool, cores):
+        """The oracle's schedule (plan, RLE transfers, merges), a level's stages
+        spread over the host cores."""
+        import oracle
+        from oracle import schedules as OS
+        if not hasattr(self, "_host"):
+            self._host = [oracle.Image(s.pvp, s.roi, s.color.view(torch.int32).cpu().numpy().view(np.uint32),
+                                       s.depth.cpu().numpy()) for s in self.srcs]
+        algo = {"stream": OS.CHAIN, "direct_send": OS.DIRECT_SEND, "binary_swap": OS.BINARY_SWAP,
+                "two_three_swap": OS.TWO_THREE_SWAP}[self.algo]
+        t0 = time.perf_counter()
+        pl = OS.plan(algo, (0, 0, self.W, self.H), [OS.intersect(tuple(i.roi), tuple(i.pvp)) for i in self._host])
+        OS.run_depth(pl, self._host, compress=self.variant != "raw", map=pool.map)
+        return time.perf_counter() - t0
+
+
 class BatchedTiles:
     """cfg4: 1000 uneven tiles (w, h log-uniform in [16, 1024], 2..64 layers, half
     depth RGBA8+Z32 at 30% box coverage, half alpha FP32 with a <= 0.3), all in
@@ -706,6 +821,8 @@ def make_workload(name, device):
         return RoiDetect(2, 16, 1920, 1080, 0.3, device)
     if name == "asm4k":
         return Assembly(3840, 2160, device)
+    if name == "sched2":
+        return Schedules(device)
     if name == "cfg3":
         return AlphaForward(3, 32, 2048, 2048, 0.3, torch.float32, device)
     if name == "cfg3h":
@@ -801,7 +918,31 @@ def run_ec(args):
         raise SystemExit(f"device status {st} after the timed region")
     per_kernel = [[evs[k][i].elapsed_time(evs[k][i + 1]) for k in range(args.steps)] for i in range(nk)]
     step_ms = [sum(per_kernel[i][k] for i in range(nk)) for k in range(args.steps)]
+    names = list(wl.kernels)
+    launches_of = {n: 1 for n in names}
+    if hasattr(wl, "kind_of"):              # several launches of one kernel per step: sum them
+        agg, cnt = {}, {}
+        for i, kd in enumerate(wl.kind_of):
+            a = agg.setdefault(kd, [0.0] * args.steps)
+            cnt[kd] = cnt.get(kd, 0) + 1
+            for k in range(args.steps):
+                a[k] += per_kernel[i][k]
+        names = list(agg)
+        per_kernel = [agg[n] for n in names]
+        launches_of = cnt
     ms = statistics.mean(step_ms)
+    per_launch_sum_ms = ms
+    if hasattr(wl, "graph_step"):            # the step as users run it: one graph launch
+        g_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                for _ in range(args.steps)]
+        torch.cuda.synchronize()
+        for k in range(args.steps):
+            flush(k)
+            g_ev[k][0].record()
+            wl.graph_step()
+            g_ev[k][1].record()
+        torch.cuda.synchronize()
+        ms = statistics.mean(a.elapsed_time(b) for a, b in g_ev)
     ms = max_over_ranks(ms, world)
     value = whole_job_value(wl.units, ms, world)
 
@@ -826,11 +967,11 @@ def run_ec(args):
     peak, peak_src = hbm_peak()
     algo = wl.algorithmic_bytes()
     kern = {}
-    for i, name in enumerate(wl.kernels):
+    for i, name in enumerate(names):
         kms = statistics.mean(per_kernel[i])
         gbs = algo[name] / (kms * 1e-3) / 1e9
         kern[name] = {"ms": kms, "share": kms / statistics.mean(step_ms), "algorithmic_bytes": algo[name],
-                      "achieved_gbs": gbs, "frac_of_peak": gbs / peak}
+                      "achieved_gbs": gbs, "frac_of_peak": gbs / peak, "launches_per_step": launches_of[name]}
     dom = max(kern, key=lambda k: kern[k]["ms"])
     traffic = measured_traffic(dom, args.workload)
     roof = {"bound": "hbm", "kernel": dom, "achieved": kern[dom]["achieved_gbs"], "peak": peak,
@@ -844,13 +985,17 @@ def run_ec(args):
         cfg["rle_raw_bytes_per_step"] = 8 * wl.stored_px
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": max(3, args.warmup), "ms_per_step": ms, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "rgba8+f32" if isinstance(wl, (DepthPipeline, BatchedTiles, RoiDetect)) else "u8" if isinstance(wl, Assembly) else "f32",
+            "scaling": "weak", "vs_baseline": None, "dtype": "rgba8+f32" if isinstance(wl, (DepthPipeline, BatchedTiles, RoiDetect, Schedules)) else "u8" if isinstance(wl, Assembly) else "f32",
             "data": "synthetic (seeded boxes / layers shaped like the thesis's workloads)",
             "config": cfg, "roofline": roof, "kernels": kern,
             "e2e": {"value": whole_job_value(wl.units, e2e_ms, world), "unit": UNIT,
                     "ms_per_step": e2e_ms, "h2d_bytes_per_step": wl.h2d, "d2h_bytes_per_step": wl.d2h},
             "gpu_launches": wl.launches_per_step() * args.steps,
             "clocks": clk, "wall_s_timed_loop": t_wall}
+    if hasattr(wl, "graph_step"):
+        cfg["per_launch_sum_ms"] = per_launch_sum_ms
+        if not args.no_extras:
+            line["schedules"] = wl.others(flush)
     if isinstance(wl, BatchedTiles):
         pt = _timed(wl.per_tile, flush, 10)
         line["batched_vs_per_tile"] = {"batched_ms": ms, "per_tile_ms": pt, "speedup": pt / ms,

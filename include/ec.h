@@ -316,6 +316,24 @@ ec_status ec_schedule_info(const ec_schedule* plan, int32_t* n_levels, int32_t* 
                            int32_t* n_launches, uint64_t* arena_bytes);
 /* The transfers, in stage order (cap entries of host memory; EC_ERR_CAPACITY if too few). */
 ec_status ec_schedule_messages(const ec_schedule* plan, ec_sched_message* msgs, int32_t cap);
+/* The schedule's kernel launches, in the order a run enqueues them. */
+typedef enum {
+    EC_SCHED_LAUNCH_COMPRESS = 0,   /* RLE compress of a stage's transfers          */
+    EC_SCHED_LAUNCH_DECOMPRESS = 1, /* decode of the transfers of unfused stages    */
+    EC_SCHED_LAUNCH_FUSED = 2,      /* decode-and-merge of the fused stages         */
+    EC_SCHED_LAUNCH_COMPOSITE = 3   /* persistent composite of the other stages     */
+} ec_sched_launch_kind;
+typedef struct {
+    int32_t level;
+    int32_t kind;       /* ec_sched_launch_kind                                    */
+    uint64_t bytes;     /* pixel bytes the launch reads and writes; the RLE
+                           streams it reads or writes are not included          */
+} ec_sched_launch;
+ec_status ec_schedule_launches(const ec_schedule* plan, ec_sched_launch* out, int32_t cap);
+/* Enqueue launch i alone on s (ec_schedule_run enqueues all of them, in
+ * order, as one graph).  Launches must be enqueued in order, 0 first, each
+ * after the previous one completes or on the same stream; for timing. */
+ec_status ec_schedule_run_launch(ec_schedule* plan, int32_t i, ec_stream_t s);
 /* Wait for s, then copy the colour and depth stream sizes of every transfer of
  * the last run (2 per message, host memory).  EC_ERR_UNSUPPORTED without RLE. */
 ec_status ec_schedule_stream_sizes(ec_schedule* plan, uint64_t* sizes, int32_t cap, ec_stream_t s);

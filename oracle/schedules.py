@@ -229,12 +229,14 @@ def _slice(p: _Partial, r: Rect):
             np.ascontiguousarray(p.depth[oy:oy + r[3], ox:ox + r[2]]))
 
 
-def run_depth(pl: Plan, sources: Sequence[Image], compress: bool = True):
+def run_depth(pl: Plan, sources: Sequence[Image], compress: bool = True, map=map):
     """Execute a depth-compositing schedule (RGBA8 colour + float32 depth).
 
     Returns (color [H][W] uint32, depth [H][W] float32, sizes) where sizes maps
     (level, sender, receiver) -> (colour stream bytes, depth stream bytes) of
-    every transfer when ``compress`` (else raw bytes, 8 per pixel)."""
+    every transfer when ``compress`` (else raw bytes, 4 per pixel and stream).
+    ``map`` runs the stages of one level (they are independent); a thread
+    pool's map spreads them over host cores."""
     if len(sources) != pl.n:
         raise ValueError("one source per resource")
     parts: List[Optional[_Partial]] = []
@@ -248,29 +250,31 @@ def run_depth(pl: Plan, sources: Sequence[Image], compress: bool = True):
                               np.ascontiguousarray(s.depth[oy:oy + r[3], ox:ox + r[2]])))
         assert parts[-1].color.dtype == np.uint32 and parts[-1].depth.dtype == np.float32
     sizes: Dict[Tuple[int, int, int], Tuple[int, int]] = {}
+
+    def stage(li, st):
+        imgs, sz = [], {}
+        for m, p in st.pieces:
+            c, d = _slice(parts[m], p)
+            if m != st.receiver:
+                if compress:
+                    cs = rle_compress(c, 2)
+                    ds = rle_compress(d.view(np.uint32), 1)
+                    sz[(li, m, st.receiver)] = (len(cs), len(ds))
+                    c = rle_decompress(cs, p[2], p[3])
+                    d = rle_decompress(ds, p[2], p[3]).view(np.float32)
+                else:
+                    sz[(li, m, st.receiver)] = (4 * p[2] * p[3], 4 * p[2] * p[3])
+            imgs.append(Image(p, p, c, d))
+        if is_empty(st.roi):
+            return st.receiver, None, sz
+        color, depth, _, _ = composite_depth(imgs, st.roi)
+        return st.receiver, _Partial(st.roi, color, depth), sz
+
     for li, lv in enumerate(pl.levels):
-        new: Dict[int, Optional[_Partial]] = {}
-        for st in lv.stages:
-            imgs = []
-            for m, p in st.pieces:
-                c, d = _slice(parts[m], p)
-                if m != st.receiver:
-                    if compress:
-                        cs = rle_compress(c, 2)
-                        ds = rle_compress(d.view(np.uint32), 1)
-                        sizes[(li, m, st.receiver)] = (len(cs), len(ds))
-                        c = rle_decompress(cs, p[2], p[3])
-                        d = rle_decompress(ds, p[2], p[3]).view(np.float32)
-                    else:
-                        sizes[(li, m, st.receiver)] = (4 * p[2] * p[3], 4 * p[2] * p[3])
-                imgs.append(Image(p, p, c, d))
-            if is_empty(st.roi):
-                new[st.receiver] = None
-                continue
-            color, depth, _, _ = composite_depth(imgs, st.roi)
-            new[st.receiver] = _Partial(st.roi, color, depth)
-        for r, v in new.items():
+        done = list(map(lambda st: stage(li, st), lv.stages))
+        for r, v, sz in done:
             parts[r] = v
+            sizes.update(sz)
     fx, fy, W, H = pl.frame
     color = np.zeros((H, W), np.uint32)
     depth = np.ones((H, W), np.float32)

@@ -70,6 +70,13 @@ EC_SCHED_STREAM, EC_SCHED_DIRECT_SEND, EC_SCHED_BINARY_SWAP, EC_SCHED_TWO_THREE_
 EC_SCHED_RLE, EC_SCHED_FUSED = 1, 2
 
 
+EC_SCHED_LAUNCH_KINDS = ("rle_compress", "rle_decompress", "fused_depth", "composite")
+
+
+class ec_sched_launch(C.Structure):
+    _fields_ = [("level", C.c_int32), ("kind", C.c_int32), ("bytes", C.c_uint64)]
+
+
 class ec_sched_message(C.Structure):
     _fields_ = [("level", C.c_int32), ("sender", C.c_int32), ("receiver", C.c_int32),
                 ("fused", C.c_int32), ("piece", ec_rect)]
@@ -109,6 +116,8 @@ SIGNATURES = {
     "ec_schedule_run": (_S, [_P, _P]),
     "ec_schedule_info": (_S, [_P, _P, _P, _P, _P]),
     "ec_schedule_messages": (_S, [_P, _P, _I]),
+    "ec_schedule_launches": (_S, [_P, _P, _I]),
+    "ec_schedule_run_launch": (_S, [_P, _I, _P]),
     "ec_schedule_stream_sizes": (_S, [_P, _P, _I, _P]),
     "ec_schedule_free": (None, [_P]),
     "ec_rle_compress_noalloc": (_S, [_P, _I, _I, _I, C.c_uint32, _P, C.c_size_t, _P, _P, _P]),

@@ -565,6 +565,18 @@ class Schedule:
         return [(m.level, m.sender, m.receiver, m.fused, (m.piece.x, m.piece.y, m.piece.w, m.piece.h))
                 for m in arr[:n]]
 
+    def launches(self):
+        """[(level, kind, pixel bytes)] of the run's kernel launches, in order;
+        kind is one of 'rle_compress', 'rle_decompress', 'fused_depth', 'composite'."""
+        n = self.info()["launches"]
+        arr = (A.ec_sched_launch * max(1, n))()
+        check(_lib().ec_schedule_launches(self.h, arr, n), "ec_schedule_launches")
+        return [(l.level, A.EC_SCHED_LAUNCH_KINDS[l.kind], int(l.bytes)) for l in arr[:n]]
+
+    def run_launch(self, i: int, stream=None):
+        """Enqueue launch i alone (in order, for timing)."""
+        check(_lib().ec_schedule_run_launch(self.h, i, _stream_handle(stream)), "ec_schedule_run_launch")
+
     def stream_sizes(self, stream=None):
         """[(colour bytes, depth bytes)] of every transfer of the last run."""
         n = self.info()["messages"]

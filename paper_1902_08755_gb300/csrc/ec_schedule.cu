@@ -354,8 +354,24 @@ ec_target buf_target(const Buf& b, char* base, const ec_rect& r, int fmt, int bp
 
 }  // namespace
 
+// One kernel launch of a schedule: the graph is captured from these, and
+// ec_schedule_run_launch enqueues one alone.
+struct SchedLaunch {
+    int kind = 0;                        // EC_SCHED_LAUNCH_*
+    int level = 0;
+    std::vector<ec::RleJobDesc> jobs;    // codec launches
+    uint32_t units = 0;
+    const ec::FusedStage* stages = nullptr;
+    const ec::FusedUnit* funits = nullptr;
+    int n_units = 0;
+    ec_batch* batch = nullptr;
+    uint64_t bytes = 0;                  // pixel bytes read and written (streams not counted)
+};
+
 struct ec_schedule {
     ec_ctx* ctx = nullptr;
+    std::vector<SchedLaunch> launches;
+    void* scratch = nullptr;             // the compressor's look-back words, inside the arena
     int mode = 0, algo = 0, n = 0, fmt = 0;
     uint32_t flags = 0;
     char* arena = nullptr;
@@ -368,6 +384,24 @@ struct ec_schedule {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
 };
+
+namespace {
+
+cudaError_t enqueue(ec_schedule* S, const SchedLaunch& r, cudaStream_t s)
+{
+    switch (r.kind) {
+    case EC_SCHED_LAUNCH_COMPRESS:
+        return ec::launch_rle_compress(r.jobs.data(), (int)r.jobs.size(), r.units, S->scratch, S->ctx->d_status, s);
+    case EC_SCHED_LAUNCH_DECOMPRESS:
+        return ec::launch_rle_decompress(r.jobs.data(), (int)r.jobs.size(), r.units, S->ctx->d_status, s);
+    case EC_SCHED_LAUNCH_FUSED:
+        return ec::launch_fused_depth(r.stages, r.funits, r.n_units, S->ctx->d_status, s);
+    default:
+        return ec::batch_enqueue(r.batch, s);
+    }
+}
+
+}  // namespace
 
 extern "C" {
 
@@ -699,51 +733,71 @@ ec_status ec_schedule_plan(ec_ctx* ctx, int32_t mode, int32_t algorithm, const e
         S->batches.push_back(level_batch[0]);
     }
 
-    // ---- phase 3: capture the schedule
+    // ---- phase 3: launch records, then the graph
+    S->scratch = base + scratch_off;
+    const uint64_t pxb = (uint64_t)bpp + (depth ? 4u : 0u);    // bytes per pixel with depth
+    for (size_t li = 0; li < L.size(); ++li) {
+        for (int kind = EC_SCHED_LAUNCH_COMPRESS; kind <= EC_SCHED_LAUNCH_DECOMPRESS; ++kind) {
+            std::vector<RleJobDesc>& jobs = kind == EC_SCHED_LAUNCH_COMPRESS ? cjobs[li] : djobs[li];
+            for (size_t b = 0; b < jobs.size(); b += ec::kRleJobsPerLaunch) {
+                const int cnt = (int)std::min<size_t>(ec::kRleJobsPerLaunch, jobs.size() - b);
+                SchedLaunch r;
+                r.kind = kind;
+                r.level = (int)li;
+                for (int i = 0; i < cnt; ++i) {
+                    RleJobDesc d = jobs[b + i];
+                    d.first_unit = r.units;
+                    r.units += (uint32_t)std::max<uint64_t>(1, chunks(ec_rect{0, 0, d.w, d.h}));
+                    r.bytes += 4ull * (uint64_t)d.w * (uint64_t)d.h;
+                    r.jobs.push_back(d);
+                }
+                S->launches.push_back(std::move(r));
+            }
+        }
+        if (L[li].n_fused_units > 0) {
+            SchedLaunch r;
+            r.kind = EC_SCHED_LAUNCH_FUSED;
+            r.level = (int)li;
+            r.stages = reinterpret_cast<const FusedStage*>(base + L[li].fst_off);
+            r.funits = reinterpret_cast<const FusedUnit*>(base + L[li].fun_off);
+            r.n_units = L[li].n_fused_units;
+            for (const StageRec& sr : L[li].stages) {
+                if (!sr.fused || is_empty(sr.out_rect)) continue;
+                r.bytes += 8ull * sr.out_rect.w * sr.out_rect.h;
+                for (size_t k = 0; k < sr.st.pieces.size(); ++k)
+                    if (sr.xfer[k] < 0) r.bytes += 8ull * sr.st.pieces[k].r.w * sr.st.pieces[k].r.h;
+            }
+            S->launches.push_back(std::move(r));
+        }
+        if (level_batch[li]) {
+            SchedLaunch r;
+            r.kind = EC_SCHED_LAUNCH_COMPOSITE;
+            r.level = (int)li;
+            r.batch = level_batch[li];
+            for (const StageRec& sr : L[li].stages) {
+                if (sr.fused || is_empty(sr.out_rect)) continue;
+                r.bytes += pxb * sr.out_rect.w * sr.out_rect.h;
+                for (const Piece& p : sr.st.pieces) r.bytes += pxb * p.r.w * p.r.h;
+            }
+            S->launches.push_back(std::move(r));
+        }
+    }
+    if (L.empty()) {
+        SchedLaunch r;
+        r.kind = EC_SCHED_LAUNCH_COMPOSITE;
+        r.batch = level_batch[0];
+        const ec_rect c = P.roi[0];
+        r.bytes = pxb * ((uint64_t)out->pvp.w * out->pvp.h + (uint64_t)c.w * c.h);
+        S->launches.push_back(std::move(r));
+    }
+    S->n_launches = (int)S->launches.size();
     if (cudaStreamBeginCapture(S->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return fail(EC_ERR_CUDA);
     cudaError_t e = cudaSuccess;
-    int launches = 0;
-    void* scratch = base + scratch_off;
-    for (size_t li = 0; li < L.size() && e == cudaSuccess; ++li) {
-        for (size_t b = 0; b < cjobs[li].size() && e == cudaSuccess; b += ec::kRleJobsPerLaunch) {
-            const int cnt = (int)std::min<size_t>(ec::kRleJobsPerLaunch, cjobs[li].size() - b);
-            uint32_t units = 0;
-            for (int i = 0; i < cnt; ++i) {
-                cjobs[li][b + i].first_unit = units;
-                units += (uint32_t)std::max<uint64_t>(1, chunks(ec_rect{0, 0, cjobs[li][b + i].w, cjobs[li][b + i].h}));
-            }
-            e = ec::launch_rle_compress(&cjobs[li][b], cnt, units, scratch, ctx->d_status, S->stream);
-            ++launches;
-        }
-        for (size_t b = 0; b < djobs[li].size() && e == cudaSuccess; b += ec::kRleJobsPerLaunch) {
-            const int cnt = (int)std::min<size_t>(ec::kRleJobsPerLaunch, djobs[li].size() - b);
-            uint32_t units = 0;
-            for (int i = 0; i < cnt; ++i) {
-                djobs[li][b + i].first_unit = units;
-                units += (uint32_t)std::max<uint64_t>(1, chunks(ec_rect{0, 0, djobs[li][b + i].w, djobs[li][b + i].h}));
-            }
-            e = ec::launch_rle_decompress(&djobs[li][b], cnt, units, ctx->d_status, S->stream);
-            ++launches;
-        }
-        if (e == cudaSuccess && L[li].n_fused_units > 0) {
-            e = ec::launch_fused_depth(reinterpret_cast<const FusedStage*>(base + L[li].fst_off),
-                                       reinterpret_cast<const FusedUnit*>(base + L[li].fun_off),
-                                       L[li].n_fused_units, ctx->d_status, S->stream);
-            ++launches;
-        }
-        if (e == cudaSuccess && level_batch[li]) {
-            e = ec::batch_enqueue(level_batch[li], S->stream);
-            ++launches;
-        }
-    }
-    if (e == cudaSuccess && L.empty()) {
-        e = ec::batch_enqueue(level_batch[0], S->stream);
-        ++launches;
-    }
+    for (const SchedLaunch& r : S->launches)
+        if (e == cudaSuccess) e = enqueue(S, r, S->stream);
     const cudaError_t e2 = cudaStreamEndCapture(S->stream, &S->graph);
     if (e != cudaSuccess || e2 != cudaSuccess) return fail(EC_ERR_CUDA);
     if (cudaGraphInstantiate(&S->exec, S->graph, 0) != cudaSuccess) return fail(EC_ERR_CUDA);
-    S->n_launches = launches;
     *plan = S;
     return EC_OK;
 }
@@ -765,6 +819,26 @@ ec_status ec_schedule_info(const ec_schedule* S, int32_t* n_levels, int32_t* n_m
     if (n_launches) *n_launches = S->n_launches;
     if (arena_bytes) *arena_bytes = S->arena_bytes;
     return EC_OK;
+}
+
+ec_status ec_schedule_launches(const ec_schedule* S, ec_sched_launch* out, int32_t cap)
+{
+    if (!S || cap < 0 || (cap > 0 && !out)) return EC_ERR_INVALID_ARG;
+    if ((size_t)cap < S->launches.size()) return EC_ERR_CAPACITY;
+    for (size_t i = 0; i < S->launches.size(); ++i) {
+        out[i].level = S->launches[i].level;
+        out[i].kind = S->launches[i].kind;
+        out[i].bytes = S->launches[i].bytes;
+    }
+    return EC_OK;
+}
+
+ec_status ec_schedule_run_launch(ec_schedule* S, int32_t i, ec_stream_t s)
+{
+    if (!S || i < 0 || (size_t)i >= S->launches.size()) return EC_ERR_INVALID_ARG;
+    DeviceGuard g(S->ctx->device);
+    if (!g.ok) return EC_ERR_CUDA;
+    return enqueue(S, S->launches[i], (cudaStream_t)s) == cudaSuccess ? EC_OK : EC_ERR_CUDA;
 }
 
 ec_status ec_schedule_messages(const ec_schedule* S, ec_sched_message* msgs, int32_t cap)
