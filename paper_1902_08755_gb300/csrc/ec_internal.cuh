@@ -266,10 +266,10 @@ struct FusedStage {
 };
 static_assert(sizeof(FusedStage) == 88, "fused stage layout");
 
-// A work unit: chunk `chunk` (4096 elements, row-major) of a rectangle.  With
-// streams (cs, ds non-null) the rectangle is a coded piece and the unit
-// decodes and merges it; without, it is a part of the output no piece covers
-// and the unit writes the local input there (or the background).
+// A work unit.  With streams (cs, ds non-null) it is chunk `chunk` (4096
+// elements, row-major) of a coded piece, which it decodes and merges; without,
+// it is rows [chunk, chunk + nrows) of a part of the output no piece covers,
+// where it writes the local input (or the background).
 struct FusedUnit {
     const uint8_t* cs;
     const uint8_t* ds;
@@ -278,7 +278,8 @@ struct FusedUnit {
     int32_t stage;
     int32_t x, y, w, h;
     uint32_t chunk;
-    int32_t pad[2];
+    int32_t nrows;
+    uint32_t cap;                 // bytes allocated to each stream (>= its size)
 };
 static_assert(sizeof(FusedUnit) == 64, "fused unit layout");
 

@@ -306,6 +306,10 @@ struct LevelRec {
 int32_t round4(int32_t v) { return (v + 3) & ~3; }
 uint64_t chunks(const ec_rect& r) { return ((uint64_t)r.w * r.h + EC_RLE_CHUNK - 1) / EC_RLE_CHUNK; }
 
+// Fill units take whole rows, about one chunk's worth of pixels each.
+int32_t fill_rows(const ec_rect& r) { return std::max<int32_t>(1, EC_RLE_CHUNK / std::max<int32_t>(r.w, 1)); }
+uint64_t fill_units(const ec_rect& r) { return ((uint64_t)r.h + fill_rows(r) - 1) / fill_rows(r); }
+
 struct Arena {
     size_t top = 0;
     size_t take(size_t bytes)
@@ -533,11 +537,13 @@ ec_status ec_schedule_plan(ec_ctx* ctx, int32_t mode, int32_t algorithm, const e
                 if (last) {
                     sr.out = target;
                 } else {
+                    // the buffer starts at a frame column that is a multiple of 4, so
+                    // that four pixels from such a column are one 16-byte access
                     Buf b;
                     b.arena = true;
-                    b.pitch = round4(sr.out_rect.w);
-                    b.ox = sr.out_rect.x;
+                    b.ox = sr.out_rect.x & ~3;
                     b.oy = sr.out_rect.y;
+                    b.pitch = round4(sr.out_rect.x + sr.out_rect.w - b.ox);
                     b.c_off = A.take((size_t)b.pitch * sr.out_rect.h * bpp);
                     if (depth) b.d_off = A.take((size_t)b.pitch * sr.out_rect.h * 4);
                     sr.out = b;
@@ -559,7 +565,7 @@ ec_status ec_schedule_plan(ec_ctx* ctx, int32_t mode, int32_t algorithm, const e
                     holes.push_back(sr.st.pieces[k].r);
                     nu += chunks(sr.st.pieces[k].r);
                 }
-            for (const ec_rect& f : subtract(sr.out_rect, holes)) nu += chunks(f);
+            for (const ec_rect& f : subtract(sr.out_rect, holes)) nu += fill_units(f);
         }
         if (nu > (size_t)INT32_MAX) return fail(EC_ERR_UNSUPPORTED);
         lr.n_fused_units = (int)nu;
@@ -670,6 +676,7 @@ ec_status ec_schedule_plan(ec_ctx* ctx, int32_t mode, int32_t algorithm, const e
                         u.ds = reinterpret_cast<const uint8_t*>(base + x.ds_off);
                         u.csize = reinterpret_cast<const uint64_t*>(base + x.sz_off);
                         u.dsize = u.csize + 1;
+                        u.cap = (uint32_t)x.cap;
                         u.stage = si;
                         u.x = x.piece.x;
                         u.y = x.piece.y;
@@ -680,7 +687,7 @@ ec_status ec_schedule_plan(ec_ctx* ctx, int32_t mode, int32_t algorithm, const e
                     }
                 }
                 for (const ec_rect& f : subtract(sr.out_rect, holes))
-                    for (uint64_t c = 0; c < chunks(f); ++c) {
+                    for (int32_t r0 = 0; r0 < f.h; r0 += fill_rows(f)) {
                         FusedUnit u;
                         memset(&u, 0, sizeof(u));
                         u.stage = si;
@@ -688,7 +695,8 @@ ec_status ec_schedule_plan(ec_ctx* ctx, int32_t mode, int32_t algorithm, const e
                         u.y = f.y;
                         u.w = f.w;
                         u.h = f.h;
-                        u.chunk = (uint32_t)c;
+                        u.chunk = (uint32_t)r0;
+                        u.nrows = std::min(fill_rows(f), f.h - r0);
                         fun[li].push_back(u);
                     }
                 continue;

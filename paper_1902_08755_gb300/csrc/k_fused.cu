@@ -7,10 +7,12 @@
 // One CTA of eight warps per work unit.  A decode unit is one 4096-element
 // chunk of a received piece: warps 0-3 decode the colour stream's four byte
 // planes and warps 4-7 the depth stream's into shared memory (the decoder of
-// the RLE kernels, including its validation), then every thread transposes
-// four elements of each back from planes, reads the local input at the same
-// frame pixels and writes the merge.  A fill unit covers output pixels no
-// piece reaches: the local input (or the background) is written there.
+// the RLE kernels, including its validation); then the threads take the
+// chunk's pixels four at a time (quads aligned to the output's 16-byte
+// boundaries), transpose them back from the planes with funnel shifts, read
+// the local input at the same frame pixels and write the merge.  A fill unit,
+// a band of rows that no piece reaches, writes the local input (or the
+// background) there.
 //
 // The merge of a front and a back partial: the front is first merged with the
 // cleared background (depth not below 1.0, or NaN, gives the background), then
@@ -26,6 +28,7 @@ namespace {
 constexpr int kFT = 256;
 constexpr int kChunk = rlec::kChunk;
 constexpr uint32_t kBgDepth = 0x3F800000u;   // 1.0f
+constexpr int kStageWords = 1024;             // staged stream bytes per stream: 4 KB
 
 __device__ __forceinline__ bool below_one(uint32_t d) { return __uint_as_float(d) < 1.0f; }
 __device__ __forceinline__ bool less(uint32_t a, uint32_t b) { return __uint_as_float(a) < __uint_as_float(b); }
@@ -39,68 +42,144 @@ __device__ __forceinline__ void merge(uint32_t fc, uint32_t fd, uint32_t bc, uin
     od = b ? bd : fd;
 }
 
-// Four consecutive elements of a rectangle of width w starting at element q:
-// frame pixels (x0 + x, y0 + y) with (x, y) stepping along the rows.
-struct Run4 {
-    int x, y;      // frame coordinates of the first element
-    bool row;      // all four in one row
+// Pixels are handled in quads: four horizontally adjacent pixels whose first
+// one sits at a 16-byte boundary of the output buffer (x - ox a multiple of
+// 4), so that a quad inside the unit is one 16-byte store.  A unit covers
+// `nrows` rows of its rectangle from row `ra`; a decode unit only the elements
+// [q0, q0 + len) of its chunk (element q = row * w + column).
+struct Quad {
+    int fx, fy, lo, hi, qa;       // frame position, pixels [lo, hi) inside the unit, element of pixel 0
+    uint32_t lc[4], ld[4];        // the receiver's own image there
 };
 
-__device__ __forceinline__ void local4(const FusedStage& S, const Run4& r, int cnt, uint32_t* lc, uint32_t* ld,
-                                       int w, int x0)
+struct Grid {
+    int qx0, nq, slots;
+    float inv;
+};
+
+template <bool CODED>
+__device__ __forceinline__ bool quad_at(const FusedUnit& u, const Grid& g, int s, int ra, int q0, int len, Quad& Q)
 {
-    const bool in_y = r.y >= S.r0y && r.y < S.r1y;
-    if (r.row && cnt == 4 && in_y && r.x >= S.r0x && r.x + 3 < S.r1x) {
-        const size_t e = (size_t)(r.y - S.ly) * S.lpitch + (r.x - S.lx);
-        if (S.lvec && (e & 3) == 0) {
-            const uint4 c = __ldcs(reinterpret_cast<const uint4*>(S.lc + e));
-            const uint4 d = __ldcs(reinterpret_cast<const uint4*>(S.ld + e));
-            lc[0] = c.x; lc[1] = c.y; lc[2] = c.z; lc[3] = c.w;
-            ld[0] = d.x; ld[1] = d.y; ld[2] = d.z; ld[3] = d.w;
-            return;
-        }
+    int r = (int)((float)s * g.inv);
+    if (r * g.nq > s) --r;
+    else if ((r + 1) * g.nq <= s) ++r;
+    const int row = ra + r;
+    Q.fx = g.qx0 + 4 * (s - r * g.nq);
+    Q.fy = u.y + row;
+    const int xs = Q.fx - u.x;
+    Q.lo = max(0, -xs);
+    Q.hi = min(4, u.w - xs);
+    Q.qa = row * u.w + xs;
+    if (CODED) {
+        Q.lo = max(Q.lo, q0 - Q.qa);
+        Q.hi = min(Q.hi, q0 + len - Q.qa);
     }
-    int x = r.x, y = r.y;
+    return Q.lo < Q.hi;
+}
+
+// The receiver's own image at the quad (background outside its ROI).
+__device__ __forceinline__ void load_local(const FusedStage& S, Quad& Q)
+{
+    const bool in_y = Q.fy >= S.r0y && Q.fy < S.r1y;
+    const size_t le = (size_t)(Q.fy - S.ly) * S.lpitch + (Q.fx - S.lx);
+    if (in_y && Q.fx >= S.r0x && Q.fx + 3 < S.r1x && S.lvec && (le & 3) == 0) {
+        const uint4 c = __ldcs(reinterpret_cast<const uint4*>(S.lc + le));
+        const uint4 d = __ldcs(reinterpret_cast<const uint4*>(S.ld + le));
+        Q.lc[0] = c.x; Q.lc[1] = c.y; Q.lc[2] = c.z; Q.lc[3] = c.w;
+        Q.ld[0] = d.x; Q.ld[1] = d.y; Q.ld[2] = d.z; Q.ld[3] = d.w;
+        return;
+    }
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
-        lc[k] = 0u;
-        ld[k] = kBgDepth;
-        if (k < cnt && y >= S.r0y && y < S.r1y && x >= S.r0x && x < S.r1x) {
-            const size_t e = (size_t)(y - S.ly) * S.lpitch + (x - S.lx);
-            lc[k] = __ldcs(S.lc + e);
-            ld[k] = __ldcs(reinterpret_cast<const uint32_t*>(S.ld) + e);
+        Q.lc[k] = 0u;
+        Q.ld[k] = kBgDepth;
+        if (k >= Q.lo && k < Q.hi && in_y && Q.fx + k >= S.r0x && Q.fx + k < S.r1x) {
+            Q.lc[k] = __ldcs(S.lc + le + k);
+            Q.ld[k] = __ldcs(reinterpret_cast<const uint32_t*>(S.ld) + le + k);
         }
-        if (++x == x0 + w) { x = x0; ++y; }
     }
 }
 
-__device__ __forceinline__ void store4(const FusedStage& S, const Run4& r, int cnt, const uint32_t* oc,
-                                       const uint32_t* od, int w, int x0)
+template <bool CODED>
+__device__ __forceinline__ void finish(const FusedStage& S, const Quad& Q, int q0, const uint8_t (*planes)[kChunk],
+                                       bool csw, bool dsw)
 {
-    if (r.row && cnt == 4) {
-        const size_t e = (size_t)(r.y - S.oy) * S.opitch + (r.x - S.ox);
-        if (S.ovec && (e & 3) == 0) {
-            st_stream(reinterpret_cast<uint4*>(S.oc + e), make_uint4(oc[0], oc[1], oc[2], oc[3]));
-            st_stream(reinterpret_cast<uint4*>(S.od) + e / 4, make_uint4(od[0], od[1], od[2], od[3]));
-            return;
+    uint32_t oc[4], od[4];
+    if (CODED) {
+        // bytes of elements qa - q0 .. +3 of every plane: two words and a funnel shift
+        const int i0 = Q.qa - q0;
+        const int wi = i0 >> 2, sh = 8 * (i0 & 3);
+        const int w0 = max(wi, 0), w1 = min(wi + 1, kChunk / 4 - 1);
+        uint32_t pb[8];
+#pragma unroll
+        for (int p = 0; p < 8; ++p) {
+            const uint32_t* pl = reinterpret_cast<const uint32_t*>(planes[p]);
+            pb[p] = __funnelshift_r(pl[w0], pl[w1], sh);
+        }
+        const uint4 C = rlec::transpose4(pb[0], pb[1], pb[2], pb[3]);
+        const uint4 D = rlec::transpose4(pb[4], pb[5], pb[6], pb[7]);
+        uint32_t ic[4] = {C.x, C.y, C.z, C.w}, id[4] = {D.x, D.y, D.z, D.w};
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            if (csw) ic[k] = rlec::swizzle(ic[k]);
+            if (dsw) id[k] = rlec::swizzle(id[k]);
+            if (S.front) merge(ic[k], id[k], Q.lc[k], Q.ld[k], oc[k], od[k]);
+            else merge(Q.lc[k], Q.ld[k], ic[k], id[k], oc[k], od[k]);
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const bool keep = below_one(Q.ld[k]);
+            oc[k] = keep ? Q.lc[k] : 0u;
+            od[k] = keep ? Q.ld[k] : kBgDepth;
         }
     }
-    int x = r.x, y = r.y;
+    const size_t oe = (size_t)(Q.fy - S.oy) * S.opitch + (Q.fx - S.ox);
+    if (Q.lo == 0 && Q.hi == 4 && S.ovec) {
+        st_stream(reinterpret_cast<uint4*>(S.oc + oe), make_uint4(oc[0], oc[1], oc[2], oc[3]));
+        st_stream(reinterpret_cast<uint4*>(S.od + oe), make_uint4(od[0], od[1], od[2], od[3]));
+    } else {
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
-        if (k < cnt) {
-            const size_t e = (size_t)(y - S.oy) * S.opitch + (x - S.ox);
-            S.oc[e] = oc[k];
-            reinterpret_cast<uint32_t*>(S.od)[e] = od[k];
-        }
-        if (++x == x0 + w) { x = x0; ++y; }
+        for (int k = 0; k < 4; ++k)
+            if (k >= Q.lo && k < Q.hi) {
+                S.oc[oe + k] = oc[k];
+                reinterpret_cast<uint32_t*>(S.od)[oe + k] = od[k];
+            }
     }
 }
 
-__global__ void __launch_bounds__(kFT)
+__device__ __forceinline__ Grid grid_of(const FusedStage& S, const FusedUnit& u, int nrows)
+{
+    Grid g;
+    g.qx0 = u.x - ((u.x - S.ox) & 3);
+    g.nq = (u.x + u.w - g.qx0 + 3) >> 2;
+    g.slots = nrows * g.nq;
+    g.inv = 1.0f / (float)g.nq;
+    return g;
+}
+
+// Two quads per thread at a time: both local loads are in flight together.
+template <bool CODED>
+__device__ __forceinline__ void compose(const FusedStage& S, const FusedUnit& u, int ra, int nrows,
+                                        int q0, int len, const uint8_t (*planes)[kChunk], bool csw, bool dsw)
+{
+    const Grid g = grid_of(S, u, nrows);
+    for (int s = threadIdx.x; s < g.slots; s += 2 * kFT) {
+        Quad A, B;
+        const bool a = quad_at<CODED>(u, g, s, ra, q0, len, A);
+        const bool b = s + kFT < g.slots && quad_at<CODED>(u, g, s + kFT, ra, q0, len, B);
+        if (a) load_local(S, A);
+        if (b) load_local(S, B);
+        if (a) finish<CODED>(S, A, q0, planes, csw, dsw);
+        if (b) finish<CODED>(S, B, q0, planes, csw, dsw);
+    }
+}
+
+__global__ void __launch_bounds__(kFT, 5)
 k_fused_depth(const FusedStage* __restrict__ stages, const FusedUnit* __restrict__ units, uint32_t* status)
 {
     __shared__ __align__(16) uint8_t planes[8][kChunk];
+    __shared__ __align__(16) uint32_t staged[2][kStageWords];
     __shared__ uint8_t s_hdr[2][rlec::kHdrBytes];
     __shared__ uint32_t s_beg[2][5];
     __shared__ int s_mode[2];
@@ -109,81 +188,63 @@ k_fused_depth(const FusedStage* __restrict__ stages, const FusedUnit* __restrict
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const FusedUnit u = units[blockIdx.x];
     const FusedStage S = stages[u.stage];
+
+    if (u.cs == nullptr) {                    // fill: rows [chunk, chunk + nrows) of the rectangle
+        compose<false>(S, u, (int)u.chunk, u.nrows, 0, 0, planes, false, false);
+        return;
+    }
     const uint32_t n = (uint32_t)u.w * (uint32_t)u.h;
     const uint32_t q0 = u.chunk * (uint32_t)kChunk;
     const int len = (int)min((uint32_t)kChunk, n - q0);
-    const bool coded = u.cs != nullptr;
-
-    if (coded) {
-        const uint32_t nc = (n + kChunk - 1) / kChunk;
-        const uint64_t csz = *u.csize, dsz = *u.dsize;
-        if (tid < rlec::kHdrBytes) s_hdr[0][tid] = rlec::header_byte(u.cs, csz, nc, u.chunk, tid);
-        else if (tid >= 64 && tid < 64 + rlec::kHdrBytes)
-            s_hdr[1][tid - 64] = rlec::header_byte(u.ds, dsz, nc, u.chunk, tid - 64);
-        if (tid == 0) s_fail = 0;
-        __syncthreads();
-        if (tid == 0 || tid == 32) {
-            const int k = tid >> 5;
-            if (rlec::check_header(s_hdr[k], k ? dsz : csz, (uint32_t)u.w, (uint32_t)u.h, nc, u.chunk,
-                                   s_beg[k], &s_mode[k]))
-                s_fail = 1;
-        }
-        __syncthreads();
-        if (s_fail) {
-            if (tid == 0) set_status(status, EC_ERR_CORRUPT);
-            return;
-        }
-        const int k = warp >> 2, p = warp & 3;
-        const uint8_t* payload = (k ? u.ds : u.cs) + 32 + 16ull * nc;
-        if (rlec::decode_plane(payload, (int)s_beg[k][p], (int)s_beg[k][p + 1], len, planes[warp], lane) &&
-            lane == 0)
+    const uint32_t nc = (n + kChunk - 1) / kChunk;
+    const int ra = (int)(q0 / (uint32_t)u.w), rb = (int)((q0 + (uint32_t)len - 1u) / (uint32_t)u.w);
+    // header bytes are read within the streams' capacity, in parallel with
+    // their sizes; the validation then uses the sizes
+    const uint64_t csz = *u.csize, dsz = *u.dsize;
+    if (tid < rlec::kHdrBytes) s_hdr[0][tid] = rlec::header_byte(u.cs, (uint64_t)u.cap, nc, u.chunk, tid);
+    else if (tid >= 64 && tid < 64 + rlec::kHdrBytes)
+        s_hdr[1][tid - 64] = rlec::header_byte(u.ds, (uint64_t)u.cap, nc, u.chunk, tid - 64);
+    if (tid == 0) s_fail = 0;
+    __syncthreads();
+    if (tid == 0 || tid == 32) {
+        const int k = tid >> 5;
+        if (rlec::check_header(s_hdr[k], k ? dsz : csz, (uint32_t)u.w, (uint32_t)u.h, nc, u.chunk,
+                               s_beg[k], &s_mode[k]))
             s_fail = 1;
-        __syncthreads();
-        if (s_fail) {
-            if (tid == 0) set_status(status, EC_ERR_CORRUPT);
-            return;
-        }
     }
-
-    const bool csw = coded && s_mode[0] == 2, dsw = coded && s_mode[1] == 2;
-    const int w = u.w;
-    for (int g = tid; 4 * g < len; g += kFT) {
-        const uint32_t q = q0 + 4u * (uint32_t)g;
-        Run4 r;
-        const int yy = (int)(q / (uint32_t)w), xx = (int)(q - (uint32_t)yy * (uint32_t)w);
-        r.x = u.x + xx;
-        r.y = u.y + yy;
-        r.row = xx + 3 < w;
-        const int cnt = min(4, len - 4 * g);
-        uint32_t lc[4], ld[4], oc[4], od[4];
-        local4(S, r, cnt, lc, ld, w, u.x);
-        if (coded) {
-            const uint4 C = rlec::transpose4(reinterpret_cast<const uint32_t*>(planes[0])[g],
-                                             reinterpret_cast<const uint32_t*>(planes[1])[g],
-                                             reinterpret_cast<const uint32_t*>(planes[2])[g],
-                                             reinterpret_cast<const uint32_t*>(planes[3])[g]);
-            const uint4 D = rlec::transpose4(reinterpret_cast<const uint32_t*>(planes[4])[g],
-                                             reinterpret_cast<const uint32_t*>(planes[5])[g],
-                                             reinterpret_cast<const uint32_t*>(planes[6])[g],
-                                             reinterpret_cast<const uint32_t*>(planes[7])[g]);
-            uint32_t ic[4] = {C.x, C.y, C.z, C.w}, id[4] = {D.x, D.y, D.z, D.w};
-#pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                if (csw) ic[k] = rlec::swizzle(ic[k]);
-                if (dsw) id[k] = rlec::swizzle(id[k]);
-                if (S.front) merge(ic[k], id[k], lc[k], ld[k], oc[k], od[k]);
-                else merge(lc[k], ld[k], ic[k], id[k], oc[k], od[k]);
-            }
-        } else {
-#pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                const bool keep = below_one(ld[k]);
-                oc[k] = keep ? lc[k] : 0u;
-                od[k] = keep ? ld[k] : kBgDepth;
-            }
-        }
-        store4(S, r, cnt, oc, od, w, u.x);
+    __syncthreads();
+    if (s_fail) {
+        if (tid == 0) set_status(status, EC_ERR_CORRUPT);
+        return;
     }
+    // stage each stream's bytes of this chunk (its four planes are contiguous)
+    // in shared memory when they fit, so that the decoder's dependent steps wait
+    // on shared memory instead of global memory
+    const uint8_t* cpay = u.cs + 32 + 16ull * nc;
+    const uint8_t* dpay = u.ds + 32 + 16ull * nc;
+    const int cw0 = (int)(s_beg[0][0] >> 2), cnw = (int)((s_beg[0][4] + 3u) >> 2) - cw0;
+    const int dw0 = (int)(s_beg[1][0] >> 2), dnw = (int)((s_beg[1][4] + 3u) >> 2) - dw0;
+    if (cnw <= kStageWords)
+        for (int i = tid; i < cnw; i += kFT) staged[0][i] = __ldg(reinterpret_cast<const uint32_t*>(cpay) + cw0 + i);
+    if (dnw <= kStageWords)
+        for (int i = tid; i < dnw; i += kFT) staged[1][i] = __ldg(reinterpret_cast<const uint32_t*>(dpay) + dw0 + i);
+    __syncthreads();
+    {
+        const int k = warp >> 2, p = warp & 3;
+        const int b = (int)s_beg[k][p], e = (int)s_beg[k][p + 1];
+        const int w0 = k ? dw0 : cw0, nw = k ? dnw : cnw;
+        const int bad = nw <= kStageWords
+            ? rlec::decode_plane(rlec::SharedBytes{reinterpret_cast<const uint8_t*>(staged[k]), 4 * w0},
+                                 b, e, len, planes[warp], lane)
+            : rlec::decode_plane(rlec::GlobalBytes{k ? dpay : cpay}, b, e, len, planes[warp], lane);
+        if (bad && lane == 0) s_fail = 1;
+    }
+    __syncthreads();
+    if (s_fail) {
+        if (tid == 0) set_status(status, EC_ERR_CORRUPT);
+        return;
+    }
+    compose<true>(S, u, ra, rb - ra + 1, (int)q0, len, planes, s_mode[0] == 2, s_mode[1] == 2);
 }
 
 }  // namespace

@@ -31,7 +31,7 @@
 // the token after one starting there is composed by doubling, so lane t holds
 // the window's t-th token; a warp scan places the tokens, each is checked
 // against its stream and chunk bounds, lanes write the unaligned ends of their
-// repeat tokens and the warp one token's aligned body per store.  The four
+// repeat tokens and short aligned bodies, the warp a long body per store.  The four
 // planes are then transposed back into elements with byte permutes.
 #include "ec_internal.cuh"
 #include "rle_codec.cuh"
@@ -790,7 +790,8 @@ k_rle_decompress(const __grid_constant__ RleJobList<N> J, uint32_t* status)
     const uint8_t* payload = src + 32 + 16ull * nc;
 
     // warp p decodes byte plane p
-    if (rlec::decode_plane(payload, (int)s_beg[warp], (int)s_beg[warp + 1], len, planes[warp], lane) &&
+    if (rlec::decode_plane(rlec::GlobalBytes{payload}, (int)s_beg[warp], (int)s_beg[warp + 1], len, planes[warp],
+                           lane) &&
         lane == 0)
         s_fail = 1;
     __syncthreads();

@@ -92,20 +92,30 @@ __device__ __forceinline__ int check_header(const uint8_t* h, uint64_t size, uin
 // byte would be followed by the next one; composing these jumps by doubling
 // (5 levels) gives every lane t the start of the window's t-th token, so lanes
 // hold tokens in order.  A warp scan places them; each lane writes the
-// unaligned head and tail bytes of its own repeat token, the whole warp the
-// aligned body words of one token per store, and literal tokens are copied by
-// the whole warp.  Returns nonzero (the same on every lane) when a token runs
+// unaligned head and tail bytes of its own repeat token and its aligned body
+// words when there are at most eight of them, the whole warp a longer body,
+// one token per store; literal tokens are copied by the whole warp.  Returns nonzero (the same on every lane) when a token runs
 // past its stream or the chunk, or the stream does not yield exactly len bytes.
-// plane must be 4-byte aligned.
-__device__ __forceinline__ int decode_plane(const uint8_t* __restrict__ payload, int beg, int end,
-                                            int len, uint8_t* plane, int lane)
+// plane must be 4-byte aligned.  src(i) returns stream byte i.
+struct GlobalBytes {
+    const uint8_t* __restrict__ p;
+    __device__ __forceinline__ uint32_t operator()(int i) const { return (uint32_t)__ldg(p + i); }
+};
+struct SharedBytes {     // bytes [off, ...) of the payload staged at p
+    const uint8_t* p;
+    int off;
+    __device__ __forceinline__ uint32_t operator()(int i) const { return (uint32_t)p[i - off]; }
+};
+
+template <class Src>
+__device__ __forceinline__ int decode_plane(const Src& src, int beg, int end, int len, uint8_t* plane, int lane)
 {
     uint32_t* p32 = reinterpret_cast<uint32_t*>(plane);
     int cur = beg, outp = 0;
     while (cur < end) {
         const int i = cur + lane;
-        const uint32_t b = i < end ? (uint32_t)__ldg(payload + i) : 0u;
-        const uint32_t b1 = i + 1 < end ? (uint32_t)__ldg(payload + i + 1) : 0u;
+        const uint32_t b = i < end ? src(i) : 0u;
+        const uint32_t b1 = i + 1 < end ? src(i + 1) : 0u;
         int J = lane + (b >= 128u ? 2 : 2 + (int)b);   // next^(2^k), relative to cur
         int pos = 0;                                   // start of token #lane
 #pragma unroll
@@ -147,7 +157,11 @@ __device__ __forceinline__ int decode_plane(const uint8_t* __restrict__ payload,
         }
         const uint32_t pk = (uint32_t)((o + head) >> 2) | ((uint32_t)nw << 16);
         const uint32_t wv = 0x01010101u * (tv & 0xFFu);
-        for (uint32_t m = __ballot_sync(0xffffffffu, nw > 0); m; m &= m - 1u) {
+        // a body of at most 8 words is written by its own lane; longer ones by
+        // the whole warp, one token per store
+        if (nw <= 8)
+            for (int k = 0; k < nw; ++k) p32[((o + head) >> 2) + k] = wv;
+        for (uint32_t m = __ballot_sync(0xffffffffu, nw > 8); m; m &= m - 1u) {
             const int t = __ffs(m) - 1;
             const uint32_t q = __shfl_sync(0xffffffffu, pk, t);
             const uint32_t x = __shfl_sync(0xffffffffu, wv, t);
@@ -158,7 +172,7 @@ __device__ __forceinline__ int decode_plane(const uint8_t* __restrict__ payload,
             const int oo = __shfl_sync(0xffffffffu, o, t);
             const int ml = __shfl_sync(0xffffffffu, olen, t);
             const int s0 = cur + __shfl_sync(0xffffffffu, pos, t) + 1;   // after the control
-            for (int k = lane; k < ml; k += 32) plane[oo + k] = __ldg(payload + s0 + k);
+            for (int k = lane; k < ml; k += 32) plane[oo + k] = (uint8_t)src(s0 + k);
         }
         outp += total;
         cur += sl;
