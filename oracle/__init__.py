@@ -97,6 +97,10 @@ def lib():
         L.orc_rle_compress.restype = C.c_int64
         L.orc_rle_compress.argtypes = [C.c_void_p, C.c_int32, C.c_int32, C.c_int32, C.c_uint32,
                                        C.c_void_p, C.c_size_t]
+        L.orc_yuv_encode.restype = C.c_int
+        L.orc_yuv_encode.argtypes = [C.c_void_p, C.c_int32, C.c_int32, C.c_int32, C.c_void_p]
+        L.orc_yuv_decode.restype = C.c_int
+        L.orc_yuv_decode.argtypes = [C.c_void_p, C.c_int32, C.c_int32, C.c_void_p, C.c_int32]
         L.orc_rle_decompress.restype = C.c_int
         L.orc_rle_decompress.argtypes = [C.c_void_p, C.c_size_t, C.c_void_p, C.c_int32,
                                          C.c_int32, C.c_int32]
@@ -341,6 +345,34 @@ def rle_compress(src: np.ndarray, mode: int, w: Optional[int] = None) -> bytes:
     if n < 0:
         raise OracleError(-n, "rle_compress")
     return dst[:n].tobytes()
+
+
+def yuv_encode(src: np.ndarray, w: Optional[int] = None) -> np.ndarray:
+    """Lossy YUV conversion with 2x2 chroma subsampling (thesis 5.5.3) of a
+    [h][pitch] RGBA8 (uint32) image: returns the packed [2*ceil(h/2)][ceil(w/2)]
+    uint32 image (luma words, then chroma words)."""
+    if src.dtype != np.uint32 or src.ndim != 2:
+        raise ValueError("src must be a [h][pitch] uint32 array")
+    _check_c(src, "src")
+    h, pitch = src.shape
+    w = pitch if w is None else int(w)
+    out = np.zeros((2 * ((h + 1) // 2), (w + 1) // 2), dtype=np.uint32)
+    rc = lib().orc_yuv_encode(_ptr(src), w, h, pitch, _ptr(out))
+    if rc:
+        raise OracleError(rc, "yuv_encode")
+    return out
+
+
+def yuv_decode(packed: np.ndarray, w: int, h: int) -> np.ndarray:
+    """Inverse of yuv_encode up to its loss: a [h][w] RGBA8 (uint32) image."""
+    packed = np.ascontiguousarray(packed, dtype=np.uint32)
+    if packed.shape != (2 * ((h + 1) // 2), (w + 1) // 2):
+        raise ValueError("packed image has the wrong shape")
+    out = np.zeros((h, w), dtype=np.uint32)
+    rc = lib().orc_yuv_decode(_ptr(packed), w, h, _ptr(out), w)
+    if rc:
+        raise OracleError(rc, "yuv_decode")
+    return out
 
 
 def rle_decompress(buf: bytes, w: int, h: int, pitch: Optional[int] = None,

@@ -426,10 +426,60 @@ static size_t encode_stream(const uint8_t* b, size_t n, uint8_t* out)
     return o;
 }
 
+/* Thesis 5.5.1, basic RLE ("mode 0"): 64-bit tokens that compare two RGBA8
+ * pixels at once.  A chunk's elements are taken in pairs (element 2k in the
+ * low four bytes of unit k, 2k+1 in the high four); runs of two or more equal
+ * units become repeat tokens (control 128 + len - 1, then the unit's 8 bytes;
+ * at most 128 units per token, full tokens first); the other units form
+ * maximal literal spans (control len - 1, then len units of 8 bytes; at most
+ * 128 per token, full tokens first).  A chunk of odd length ends with its last
+ * element's 4 bytes after the tokens.  Returns the bytes written. */
+static size_t encode_units(const uint32_t* e, size_t len, uint8_t* out)
+{
+    size_t nu = len / 2, o = 0, i = 0;
+    while (i < nu) {
+        size_t L = 1;
+        while (i + L < nu && e[2 * (i + L)] == e[2 * i] && e[2 * (i + L) + 1] == e[2 * i + 1]) ++L;
+        if (L >= 2) {
+            size_t left = L;
+            while (left > 0) {
+                size_t piece = left >= 128 ? 128 : left;
+                out[o++] = (uint8_t)(128 + piece - 1);
+                put_u32(out + o, e[2 * i]);
+                put_u32(out + o + 4, e[2 * i + 1]);
+                o += 8;
+                left -= piece;
+            }
+            i += L;
+        } else {
+            size_t start = i;
+            /* a unit is literal when it equals neither neighbour */
+            while (i < nu && !(i + 1 < nu && e[2 * (i + 1)] == e[2 * i] && e[2 * (i + 1) + 1] == e[2 * i + 1]))
+                ++i;
+            size_t m = i - start, done = 0;
+            while (done < m) {
+                size_t piece = (m - done) >= 128 ? 128 : (m - done);
+                out[o++] = (uint8_t)(piece - 1);
+                for (size_t k = 0; k < piece; ++k) {
+                    put_u32(out + o, e[2 * (start + done + k)]);
+                    put_u32(out + o + 4, e[2 * (start + done + k) + 1]);
+                    o += 8;
+                }
+                done += piece;
+            }
+        }
+    }
+    if (len & 1) {
+        put_u32(out + o, e[len - 1]);
+        o += 4;
+    }
+    return o;
+}
+
 int64_t orc_rle_compress(const uint32_t* src, int32_t w, int32_t h, int32_t pitch,
                          uint32_t mode, uint8_t* dst, size_t capacity)
 {
-    if (w < 0 || h < 0 || pitch < w || (mode != 1 && mode != 2)) return -ORC_EINVAL;
+    if (w < 0 || h < 0 || pitch < w || mode > 2) return -ORC_EINVAL;
     uint64_t n = (uint64_t)w * (uint64_t)h;
     if (n > ORC_MAX_ELEMS) return -ORC_EINVAL;
     if (capacity < orc_rle_max_size(w, h)) return -ORC_ECAP;
@@ -443,7 +493,25 @@ int64_t orc_rle_compress(const uint32_t* src, int32_t w, int32_t h, int32_t pitc
     put_u32(dst + 16, 4u);
     put_u32(dst + 20, ORC_CHUNK);
     put_u32(dst + 24, (uint32_t)nc);
-    put_u32(dst + 28, 4u);
+    put_u32(dst + 28, mode == 0 ? 1u : 4u);
+
+    if (mode == 0) {                    /* one stream per chunk */
+        uint8_t* table = dst + ORC_HEADER;
+        uint8_t* payload = table + 4u * nc;
+        uint32_t e[ORC_CHUNK];
+        size_t off = 0;
+        for (uint64_t c = 0; c < nc; ++c) {
+            uint64_t q0 = c * ORC_CHUNK;
+            uint64_t len = (q0 + ORC_CHUNK <= n) ? ORC_CHUNK : n - q0;
+            for (uint64_t t = 0; t < len; ++t) {
+                uint64_t q = q0 + t;
+                e[t] = src[(q / (uint64_t)w) * (uint64_t)pitch + q % (uint64_t)w];
+            }
+            off += encode_units(e, (size_t)len, payload + off);
+            put_u32(table + 4u * c, (uint32_t)off);
+        }
+        return (int64_t)(ORC_HEADER + 4u * nc + off);
+    }
 
     uint8_t* table = dst + ORC_HEADER;
     uint8_t* payload = table + 16u * nc;
@@ -474,13 +542,64 @@ int orc_rle_decompress(const uint8_t* src, size_t size, uint32_t* dst,
     if (!src || size < ORC_HEADER) return ORC_ECORRUPT;
     if (get_u32(src) != ORC_MAGIC || get_u16(src + 4) != ORC_VERSION) return ORC_ECORRUPT;
     uint32_t mode = get_u16(src + 6);
-    if (mode != 1 && mode != 2) return ORC_ECORRUPT;
+    if (mode > 2) return ORC_ECORRUPT;
     if (get_u32(src + 8) != (uint32_t)w || get_u32(src + 12) != (uint32_t)h) return ORC_ECORRUPT;
-    if (get_u32(src + 16) != 4u || get_u32(src + 20) != ORC_CHUNK || get_u32(src + 28) != 4u)
+    if (get_u32(src + 16) != 4u || get_u32(src + 20) != ORC_CHUNK || get_u32(src + 28) != (mode == 0 ? 1u : 4u))
         return ORC_ECORRUPT;
     uint64_t n = (uint64_t)w * (uint64_t)h;
     uint64_t nc = n_chunks_of(n);
     if (get_u32(src + 24) != nc) return ORC_ECORRUPT;
+    if (mode == 0) {
+        if (size < ORC_HEADER + 4u * nc) return ORC_ECORRUPT;
+        const uint8_t* table = src + ORC_HEADER;
+        const uint8_t* payload = table + 4u * nc;
+        size_t payload_size = size - (ORC_HEADER + 4u * nc);
+        size_t begin = 0;
+        for (uint64_t c = 0; c < nc; ++c) {
+            uint64_t q0 = c * ORC_CHUNK;
+            size_t len = (size_t)((q0 + ORC_CHUNK <= n) ? ORC_CHUNK : n - q0), nu = len / 2;
+            size_t end = get_u32(table + 4u * c);
+            if (end < begin || end > payload_size) return ORC_ECORRUPT;
+            /* no valid stream is longer than the all-literal coding of its chunk */
+            if (end - begin > 8 * nu + (nu + 127) / 128 + 4 * (len & 1)) return ORC_ECORRUPT;
+            uint32_t e[ORC_CHUNK];
+            size_t i = begin, o = 0;     /* o counts units */
+            while (o < nu) {
+                if (i >= end) return ORC_ECORRUPT;
+                uint32_t ctl = payload[i++];
+                size_t m = ctl < 128 ? ctl + 1 : ctl - 127;
+                if (o + m > nu) return ORC_ECORRUPT;
+                if (ctl < 128) {
+                    if (i + 8 * m > end) return ORC_ECORRUPT;
+                    for (size_t k = 0; k < m; ++k) {
+                        e[2 * (o + k)] = get_u32(payload + i + 8 * k);
+                        e[2 * (o + k) + 1] = get_u32(payload + i + 8 * k + 4);
+                    }
+                    i += 8 * m;
+                } else {
+                    if (i + 8 > end) return ORC_ECORRUPT;
+                    for (size_t k = 0; k < m; ++k) {
+                        e[2 * (o + k)] = get_u32(payload + i);
+                        e[2 * (o + k) + 1] = get_u32(payload + i + 4);
+                    }
+                    i += 8;
+                }
+                o += m;
+            }
+            if (len & 1) {
+                if (i + 4 > end) return ORC_ECORRUPT;
+                e[len - 1] = get_u32(payload + i);
+                i += 4;
+            }
+            if (i != end) return ORC_ECORRUPT;
+            for (size_t t = 0; t < len; ++t) {
+                uint64_t q = q0 + t;
+                dst[(q / (uint64_t)w) * (uint64_t)pitch + q % (uint64_t)w] = e[t];
+            }
+            begin = end;
+        }
+        return ORC_OK;
+    }
     if (size < ORC_HEADER + 16u * nc) return ORC_ECORRUPT;
     const uint8_t* table = src + ORC_HEADER;
     const uint8_t* payload = table + 16u * nc;
@@ -525,6 +644,77 @@ int orc_rle_decompress(const uint8_t* src, size_t size, uint32_t* dst,
             uint64_t q = q0 + t;
             uint64_t y = q / (uint64_t)w, x = q % (uint64_t)w;
             dst[y * (uint64_t)pitch + x] = v;
+        }
+    }
+    return ORC_OK;
+}
+
+/* ---- lossy YUV compressor (thesis 5.5.3) ------------------------------- */
+
+/* Colour-space conversion and chroma subsampling before run-length coding.
+ * The thesis names the steps but prints no formulas; this is the full-range
+ * BT.601 (JFIF) transform in 8-bit fixed point (coefficients x 256):
+ *   Y = (77 R + 150 G + 29 B + 128) / 256
+ *   U = 128 + (-43 R - 85 G + 128 B + 128) / 256      (clamped to 255)
+ *   V = 128 + (128 R - 107 G - 21 B + 128) / 256      (clamped to 255)
+ * with divisions rounding down.  Every 2x2 block keeps its four Y values and
+ * the rounded means of its pixels' U, V and alpha (over the pixels the image
+ * has).  Packed image: ceil(w/2) x 2 ceil(h/2) words; row by of the top half
+ * holds the blocks' luma words (byte k = Y of pixel (2bx + (k & 1),
+ * 2by + (k >> 1)), 0 where the image has no pixel), row ceil(h/2) + by the
+ * chroma words (bytes U, V, A, 0).  Decoding gives every pixel its block's
+ * U, V and alpha:
+ *   R = Y + (359 (V-128) + 128) / 256,  G = Y - (88 (U-128) + 183 (V-128) + 128) / 256,
+ *   B = Y + (454 (U-128) + 128) / 256,  each clamped to [0, 255]. */
+static int32_t floor_div256(int32_t x) { return x >= 0 ? x / 256 : -((-x + 255) / 256); }
+static int32_t clamp255(int32_t v) { return v < 0 ? 0 : (v > 255 ? 255 : v); }
+
+int orc_yuv_encode(const uint32_t* src, int32_t w, int32_t h, int32_t pitch, uint32_t* dst)
+{
+    if (w < 0 || h < 0 || pitch < w) return ORC_EINVAL;
+    int32_t bw = (w + 1) / 2, bh = (h + 1) / 2;
+    for (int32_t by = 0; by < bh; ++by) {
+        for (int32_t bx = 0; bx < bw; ++bx) {
+            uint32_t luma = 0;
+            int32_t su = 0, sv = 0, sa = 0, cnt = 0;
+            for (int k = 0; k < 4; ++k) {
+                int32_t x = 2 * bx + (k & 1), y = 2 * by + (k >> 1);
+                if (x >= w || y >= h) continue;
+                uint32_t v = src[(size_t)y * pitch + x];
+                int32_t R = v & 0xFF, G = (v >> 8) & 0xFF, B = (v >> 16) & 0xFF, A = (int32_t)(v >> 24);
+                int32_t Y = floor_div256(77 * R + 150 * G + 29 * B + 128);
+                int32_t U = clamp255(128 + floor_div256(-43 * R - 85 * G + 128 * B + 128));
+                int32_t V = clamp255(128 + floor_div256(128 * R - 107 * G - 21 * B + 128));
+                luma |= (uint32_t)Y << (8 * k);
+                su += U;
+                sv += V;
+                sa += A;
+                ++cnt;
+            }
+            dst[(size_t)by * bw + bx] = luma;
+            dst[(size_t)(bh + by) * bw + bx] = (uint32_t)((su + cnt / 2) / cnt) |
+                                               ((uint32_t)((sv + cnt / 2) / cnt) << 8) |
+                                               ((uint32_t)((sa + cnt / 2) / cnt) << 16);
+        }
+    }
+    return ORC_OK;
+}
+
+int orc_yuv_decode(const uint32_t* src, int32_t w, int32_t h, uint32_t* dst, int32_t pitch)
+{
+    if (w < 0 || h < 0 || pitch < w) return ORC_EINVAL;
+    int32_t bw = (w + 1) / 2, bh = (h + 1) / 2;
+    for (int32_t y = 0; y < h; ++y) {
+        for (int32_t x = 0; x < w; ++x) {
+            int32_t bx = x / 2, by = y / 2, k = (x & 1) + 2 * (y & 1);
+            uint32_t luma = src[(size_t)by * bw + bx], ch = src[(size_t)(bh + by) * bw + bx];
+            int32_t Y = (luma >> (8 * k)) & 0xFF;
+            int32_t U = (int32_t)(ch & 0xFF) - 128, V = (int32_t)((ch >> 8) & 0xFF) - 128;
+            int32_t A = (ch >> 16) & 0xFF;
+            int32_t R = clamp255(Y + floor_div256(359 * V + 128));
+            int32_t G = clamp255(Y - floor_div256(88 * U + 183 * V + 128));
+            int32_t B = clamp255(Y + floor_div256(454 * U + 128));
+            dst[(size_t)y * pitch + x] = (uint32_t)R | ((uint32_t)G << 8) | ((uint32_t)B << 16) | ((uint32_t)A << 24);
         }
     }
     return ORC_OK;

@@ -140,7 +140,10 @@ int orc_detect_roi(orc_rect pvp, orc_rect search, int32_t pitch, int32_t format,
  * per component); mode 2 first regroups the 32 bits by significance (the
  * swizzle preconditioner).  The element sequence is cut into chunks of 4096
  * elements, each chunk's four byte streams are run-length coded on their
- * own, and the streams are stored chunk-major with an offset table. */
+ * own, and the streams are stored chunk-major with an offset table.  Mode 0
+ * (basic RLE) codes each chunk as one stream of 8-byte units (element pairs),
+ * an odd chunk's last element as 4 raw bytes at its end; its header says one
+ * plane and its table has one entry per chunk. */
 size_t  orc_rle_max_size(int32_t w, int32_t h);
 uint32_t orc_swizzle(uint32_t v);
 uint32_t orc_unswizzle(uint32_t v);
@@ -149,6 +152,13 @@ int64_t orc_rle_compress(const uint32_t* src, int32_t w, int32_t h, int32_t pitc
                          uint32_t mode, uint8_t* dst, size_t capacity);
 int     orc_rle_decompress(const uint8_t* src, size_t size, uint32_t* dst,
                            int32_t w, int32_t h, int32_t pitch);
+
+/* ---- lossy YUV compressor (thesis 5.5.3) --------------------------------
+ * Full-range BT.601 in 8-bit fixed point, chroma and alpha averaged over 2x2
+ * blocks.  Packed image: ceil(w/2) words per row, ceil(h/2) rows of luma words
+ * then ceil(h/2) rows of chroma words (U, V, A, 0). */
+int     orc_yuv_encode(const uint32_t* src, int32_t w, int32_t h, int32_t pitch, uint32_t* dst);
+int     orc_yuv_decode(const uint32_t* src, int32_t w, int32_t h, uint32_t* dst, int32_t pitch);
 
 #ifdef __cplusplus
 }

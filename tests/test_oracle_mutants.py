@@ -22,6 +22,8 @@ import test_oracle_rle as TR
 import test_oracle_roi as TO
 import test_oracle_assemble as TS
 import test_oracle_schedules as TSC
+import test_oracle_rle0 as TR0
+import test_oracle_yuv as TY
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 ORACLE = os.path.join(ROOT, "oracle")
@@ -39,9 +41,12 @@ MUTANTS = {
     "grad_colour_T_next": ("d[0] = gp[0] * T[k];", "d[0] = gp[0] * T[k + 1];"),
     "depth_grad_to_all": ("d[ch] = winner[p] == i ? g[4 * p + ch] : 0.0f;", "d[ch] = g[4 * p + ch];"),
     "rle_repeat_threshold": ("if (L >= 3) {", "if (L >= 2) {"),
-    "rle_repeat_control": ("out[o++] = (uint8_t)(128 + piece - 1);", "out[o++] = (uint8_t)(128 + piece);"),
-    "rle_piece_127": ("size_t piece = left >= 128 ? 128 : left;", "size_t piece = left >= 127 ? 127 : left;"),
-    "rle_literal_control": ("out[o++] = (uint8_t)(piece - 1);", "out[o++] = (uint8_t)(piece);"),
+    "rle_repeat_control": ("out[o++] = (uint8_t)(128 + piece - 1);\n                out[o++] = b[i];",
+                           "out[o++] = (uint8_t)(128 + piece);\n                out[o++] = b[i];"),
+    "rle_piece_127": ("size_t piece = left >= 128 ? 128 : left;\n                out[o++] = (uint8_t)(128 + piece - 1);\n                out[o++] = b[i];",
+                      "size_t piece = left >= 127 ? 127 : left;\n                out[o++] = (uint8_t)(128 + piece - 1);\n                out[o++] = b[i];"),
+    "rle_literal_control": ("out[o++] = (uint8_t)(piece - 1);\n                memcpy(out + o, b + start + done, piece);",
+                            "out[o++] = (uint8_t)(piece);\n                memcpy(out + o, b + start + done, piece);"),
     "swizzle_component_order": ("s |= ((b >> (6 - 2 * k)) & 3u) << (6 - 2 * j);",
                                 "s |= ((b >> (6 - 2 * k)) & 3u) << (2 * j);"),
     "decoder_no_length_check": ("if (o != len) return ORC_ECORRUPT;", ""),
@@ -55,6 +60,16 @@ MUTANTS = {
     "pixels_drop_offset": ("const int64_t dx = kx[k] + i * nx, dy = ky[k] + j * ny;", "const int64_t dx = i * nx, dy = ky[k] + j * ny;"),
     "average_no_rounding": ("((isum[ch] + (uint64_t)count / 2) / (uint64_t)count)", "((isum[ch]) / (uint64_t)count)"),
     "average_counts_all": ("                ++count;\n", ""),
+    "rle0_literal_control": ("                out[o++] = (uint8_t)(piece - 1);\n                for (size_t k = 0; k < piece; ++k) {",
+                             "                out[o++] = (uint8_t)(piece);\n                for (size_t k = 0; k < piece; ++k) {"),
+    "rle0_tail_dropped": ("    if (len & 1) {\n        put_u32(out + o, e[len - 1]);\n        o += 4;\n    }\n", ""),
+    "rle0_unit_halves_swapped": ("                put_u32(out + o, e[2 * i]);\n                put_u32(out + o + 4, e[2 * i + 1]);",
+                                 "                put_u32(out + o, e[2 * i + 1]);\n                put_u32(out + o + 4, e[2 * i]);"),
+    "yuv_luma_no_rounding": ("floor_div256(77 * R + 150 * G + 29 * B + 128)", "floor_div256(77 * R + 150 * G + 29 * B)"),
+    "yuv_chroma_swapped": ("(uint32_t)((su + cnt / 2) / cnt) |\n                                               ((uint32_t)((sv + cnt / 2) / cnt) << 8)",
+                           "(uint32_t)((sv + cnt / 2) / cnt) |\n                                               ((uint32_t)((su + cnt / 2) / cnt) << 8)"),
+    "yuv_average_over_four": ("((uint32_t)((sa + cnt / 2) / cnt) << 16)", "((uint32_t)((sa + 2) / 4) << 16)"),
+    "yuv_inverse_green_sign": ("clamp255(Y - floor_div256(88 * U + 183 * V + 128))", "clamp255(Y + floor_div256(88 * U + 183 * V + 128))"),
 }
 
 
@@ -101,6 +116,12 @@ def _pins(orc):
     yield lambda: [TS.test_pixel_decomposition_reassembles(orc, "rgba8", k) for k in ((2, 2), (4, 3))]
     yield lambda: TS.test_rgba8_average_rounding_and_coverage(orc)
     yield lambda: TS.test_float_average_matches_numpy_mean(orc, "f32", 1)
+    yield lambda: [TR0.test_streams_decode_and_have_canonical_size(orc, n)
+                   for n in ("unit_run_lengths", "straddle_odd", "boxes", "pairs_of_pixels")]
+    yield lambda: TR0.test_incompressible_meets_its_bound(orc)
+    yield lambda: [TY.test_luma_and_chroma_follow_the_float_transform(orc, h, w) for h, w in ((8, 8), (5, 7))]
+    yield lambda: TY.test_grey_round_trips_exactly(orc)
+    yield lambda: TY.test_uniform_blocks_round_trip_within_bound(orc)
 
 
 def _caught(orc):
