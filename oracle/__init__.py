@@ -140,6 +140,14 @@ def _check_c(a: np.ndarray, what: str):
         raise ValueError(f"{what} must be C-contiguous")
 
 
+def _check_covers(im: "Image"):
+    """The arrays must hold the pvp's rows and columns (the C code trusts them)."""
+    w, h = int(im.pvp[2]), int(im.pvp[3])
+    for a in (im.color, im.depth):
+        if a is not None and h > 0 and w > 0 and (a.ndim < 2 or a.shape[0] < h or a.shape[1] < w):
+            raise ValueError("image arrays are smaller than their pvp")
+
+
 def composite_depth(images: Sequence[Image], out_pvp, out_pitch: Optional[int] = None):
     """Depth-test merge (thesis 5.2.1).  Colour is any 4/8/16-byte pixel type copied
     bit for bit.  Returns (color, depth, winner, out_roi)."""
@@ -152,6 +160,7 @@ def composite_depth(images: Sequence[Image], out_pvp, out_pitch: Optional[int] =
     for i, im in enumerate(images):
         _check_c(im.color, "color")
         _check_c(im.depth, "depth")
+        _check_covers(im)
         b = im.color.itemsize * int(np.prod(im.color.shape[2:], dtype=np.int64))
         if cb is None:
             cb, dtype, inner = b, im.color.dtype, im.color.shape[2:]
@@ -176,6 +185,7 @@ def _layers(images: Sequence[Image]):
     fmt = None
     for i, im in enumerate(images):
         _check_c(im.color, "color")
+        _check_covers(im)
         f = F32 if im.color.dtype == np.float32 else F16 if im.color.dtype == np.float16 else None
         if f is None or im.color.shape[2:] != (4,):
             raise ValueError("alpha layers are [h][pitch][4] float32 or float16")
