@@ -318,16 +318,23 @@ def detect_roi(pvp, search, pitch: int, fmt: int, color: Optional[np.ndarray] = 
     examined region, and the tile occupancy grid.  color: [pvp.h][pitch] uint32
     (RGBA8), [..][4] float32 or [..][4] uint16 half bits; depth: float32."""
     gw, gh = -(-max(pvp[2], 0) // tile), -(-max(pvp[3], 0) // tile)
-    occ = np.zeros((gh, gw), dtype=np.uint8)
+    # the grid, then a guard region that must stay zero: the oracle never writes
+    # there, a planted indexing mistake that does is caught instead of
+    # corrupting the process's heap
+    guard = 65536 + gw * max(gw, gh)
+    buf = np.zeros(gh * gw + guard, dtype=np.uint8)
+    occ = buf[:gh * gw].reshape(gh, gw)
     c = None if color is None else np.ascontiguousarray(color)
     d = None if depth is None else np.ascontiguousarray(depth, dtype=np.float32)
     out = Rect()
     rc = lib().orc_detect_roi(_rect(pvp), _rect(search), int(pitch), int(fmt),
                               None if c is None else _ptr(c), None if d is None else _ptr(d),
-                              int(tile), _ptr(occ) if occ.size else None, C.byref(out))
+                              int(tile), _ptr(buf) if occ.size else None, C.byref(out))
     if rc:
         raise OracleError(rc, "detect_roi")
-    return (out.x, out.y, out.w, out.h), occ
+    if buf[gh * gw:].any():
+        raise OracleError(EINVAL, "detect_roi wrote past the occupancy grid")
+    return (out.x, out.y, out.w, out.h), occ.copy()
 
 
 def rle_max_size(w: int, h: int) -> int:
@@ -350,10 +357,15 @@ def rle_compress(src: np.ndarray, mode: int, w: Optional[int] = None) -> bytes:
     h, pitch = src.shape
     w = pitch if w is None else int(w)
     cap = rle_max_size(w, h)
-    dst = np.zeros(max(cap, 1), dtype=np.uint8)
+    # a guard region past the declared capacity: the oracle never writes there,
+    # but a planted mistake that overruns is caught as a wrong size instead of
+    # corrupting the process's heap
+    dst = np.zeros(max(cap, 1) + 65536, dtype=np.uint8)
     n = lib().orc_rle_compress(_ptr(src), w, h, pitch, int(mode), _ptr(dst), cap)
     if n < 0:
         raise OracleError(-n, "rle_compress")
+    if n > cap:
+        raise OracleError(ECAP, "rle_compress wrote past its capacity")
     return dst[:n].tobytes()
 
 
