@@ -421,13 +421,24 @@ ec_status ec_detect_roi(ec_ctx* ctx, const ec_image* in, int32_t n, int32_t tile
  * A decoder accepts any token sequence that yields exactly the chunk's bytes,
  * but rejects a stream longer than len + ceil(len/128) bytes (the all-literal
  * coding of its chunk, the longest the encoder emits).
+ *
+ * Mode 0 (thesis 5.5.1's basic RLE, 64-bit tokens comparing two pixels at
+ * once): each chunk is one stream (header n_planes 1, end table u32
+ * end[n_chunks]) over 8-byte units, unit k holding elements 2k (low four
+ * bytes) and 2k+1.  Runs of >= 2 equal units are repeat tokens (control
+ * 128 + len - 1, then the unit), the other units maximal literal spans
+ * (control len - 1, then the units), at most 128 units per token with full
+ * tokens first; a chunk of odd length ends with its last element's 4 bytes.
+ * The decoder rejects a mode-0 stream longer than 8u + ceil(u/128) (+ 4 for
+ * an odd chunk) bytes, u the chunk's units.  ec_rle_max_size bounds all modes.
  */
 
 /* Upper bound on a stream's size: 32 + 16 n_chunks + sum over streams of
  * (len + ceil(len/128)).  0 for negative sizes. */
 size_t ec_rle_max_size(int32_t w, int32_t h);
 
-/* Compress w x h uint32 elements at src (row pitch `pitch` elements) into dst
+/* Compress w x h uint32 elements at src (row pitch `pitch` elements), mode 0,
+ * 1 or 2, into dst
  * (capacity dst_capacity >= ec_rle_max_size(w, h), else EC_ERR_CAPACITY).
  * The stream's size in bytes is written to *d_size (device uint64) when the
  * kernel finishes.  w * h <= EC_RLE_MAX_ELEMS.  Uses the context's scratch
@@ -457,6 +468,29 @@ ec_status ec_rle_compress_batch(ec_ctx* ctx, const ec_rle_job* jobs, int32_t njo
                                 ec_stream_t s);
 ec_status ec_rle_decompress_batch(ec_ctx* ctx, const ec_rle_job* jobs, int32_t njobs,
                                   ec_stream_t s);
+
+/* ------------------------------------------------------ lossy YUV compressor
+ * Thesis 5.5.3: a colour space conversion with chroma subsampling before the
+ * RLE codec (which then codes the Y, U and V channels), inverted after it.
+ * Full-range BT.601 in 8-bit fixed point, divisions rounding down:
+ *   Y = (77 R + 150 G + 29 B + 128) / 256
+ *   U = min(255, 128 + (-43 R - 85 G + 128 B + 128) / 256)
+ *   V = min(255, 128 + (128 R - 107 G - 21 B + 128) / 256)
+ * Each 2x2 block keeps its four Y and the means of its pixels' U, V and alpha,
+ * rounded half up, over the pixels the image has.  Decoding gives each pixel
+ * its block's U, V, alpha:
+ *   R = Y + (359 (V-128) + 128) / 256,  G = Y - (88 (U-128) + 183 (V-128) + 128) / 256,
+ *   B = Y + (454 (U-128) + 128) / 256,  clamped to [0, 255].
+ * Packed image: 2 * ceil(h/2) rows of ceil(w/2) uint32 words (row pitch
+ * dst_pitch / src_pitch words): rows [0, ceil(h/2)) luma words, byte k the Y
+ * of pixel (2bx + (k & 1), 2by + (k >> 1)) or 0 where the image has none;
+ * then chroma words, bytes U, V, A, 0.  Code it with mode 1.
+ * RGBA8 images are w x h uint32 with row pitch `pitch`; all pointers device,
+ * 4-byte aligned; asynchronous on s. */
+ec_status ec_yuv_encode(ec_ctx* ctx, const void* src, int32_t w, int32_t h, int32_t pitch, void* dst,
+                        int32_t dst_pitch, ec_stream_t s);
+ec_status ec_yuv_decode(ec_ctx* ctx, const void* src, int32_t src_pitch, int32_t w, int32_t h, void* dst,
+                        int32_t pitch, ec_stream_t s);
 
 /* ------------------------------------------------ allocation-free compressor
  * The thesis has no counterpart to this entry point; it exists for callers

@@ -43,5 +43,8 @@ from .api import (  # noqa: F401
     rle_decompress,
     rle_decompress_batch,
     rle_max_size,
+    yuv_decode,
+    yuv_encode,
+    yuv_packed_shape,
 )
 from .autograd import alpha_composite, alpha_composite_fwd_bwd, depth_composite  # noqa: F401,E402

@@ -112,6 +112,8 @@ SIGNATURES = {
     "ec_batch_run": (_S, [_P, _P]),
     "ec_batch_get_config": (_S, [_P, _P, _P, _P]),
     "ec_batch_free": (None, [_P]),
+    "ec_yuv_encode": (_S, [_P, _P, _I, _I, _I, _P, _I, _P]),
+    "ec_yuv_decode": (_S, [_P, _P, _I, _I, _I, _P, _I, _P]),
     "ec_schedule_plan": (_S, [_P, _I, _I, _P, _I, _P, _P, C.c_uint32, C.POINTER(C.c_void_p)]),
     "ec_schedule_run": (_S, [_P, _P]),
     "ec_schedule_info": (_S, [_P, _P, _P, _P, _P]),

@@ -357,6 +357,47 @@ def composite_depth_backward(winner: torch.Tensor, out_pvp: Rect, grad_out: torc
           "ec_composite_depth_backward")
 
 
+def yuv_packed_shape(w: int, h: int) -> Tuple[int, int]:
+    """(rows, words) of the packed image of a w x h frame."""
+    return 2 * ((h + 1) // 2), (w + 1) // 2
+
+
+def yuv_encode(src: torch.Tensor, w: Optional[int] = None, out: Optional[torch.Tensor] = None,
+               ctx: Optional[Context] = None, stream=None) -> torch.Tensor:
+    """ec_yuv_encode: lossy YUV with 2x2 chroma blocks (thesis 5.5.3) of a
+    [h][pitch] RGBA8 (uint32/int32) image; returns the packed uint32 image."""
+    ctx = ctx or default_context(src.device.index)
+    pitch, wt, h = _elem_layout(src)
+    w = wt if w is None else int(w)
+    rows, words = yuv_packed_shape(w, h)
+    if out is None:
+        out = torch.empty((rows, words), dtype=torch.int32, device=src.device).view(torch.uint32)
+    opitch, ow, oh = _elem_layout(out)
+    if ow < words or oh < rows:
+        raise ValueError("packed output too small")
+    check(_lib().ec_yuv_encode(ctx.h, src.data_ptr(), w, h, pitch, out.data_ptr(), opitch,
+                               _stream_handle(stream)), "ec_yuv_encode")
+    return out
+
+
+def yuv_decode(packed: torch.Tensor, w: int, h: int, out: Optional[torch.Tensor] = None,
+               ctx: Optional[Context] = None, stream=None) -> torch.Tensor:
+    """ec_yuv_decode: RGBA8 [h][w] (or into out, any pitch) from a packed image."""
+    ctx = ctx or default_context(packed.device.index)
+    spitch, sw, sh = _elem_layout(packed)
+    rows, words = yuv_packed_shape(w, h)
+    if sw < words or sh < rows:
+        raise ValueError("packed image too small")
+    if out is None:
+        out = torch.empty((h, w), dtype=torch.int32, device=packed.device).view(torch.uint32)
+    pitch, ow, oh = _elem_layout(out)
+    if ow < w or oh < h:
+        raise ValueError("output too small")
+    check(_lib().ec_yuv_decode(ctx.h, packed.data_ptr(), spitch, w, h, out.data_ptr(), pitch,
+                               _stream_handle(stream)), "ec_yuv_decode")
+    return out
+
+
 def rle_max_size(w: int, h: int) -> int:
     return int(_lib().ec_rle_max_size(int(w), int(h)))
 

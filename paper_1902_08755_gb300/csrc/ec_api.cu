@@ -429,6 +429,30 @@ ec_status ec_detect_roi(ec_ctx* ctx, const ec_image* in, int32_t n, int32_t tile
     return EC_OK;
 }
 
+ec_status ec_yuv_encode(ec_ctx* ctx, const void* src, int32_t w, int32_t h, int32_t pitch, void* dst,
+                        int32_t dst_pitch, ec_stream_t s)
+{
+    if (!ctx || w < 0 || h < 0 || pitch < w || dst_pitch < (w + 1) / 2) return EC_ERR_INVALID_ARG;
+    if ((int64_t)w * h > 0 && (!src || !dst)) return EC_ERR_INVALID_ARG;
+    if ((reinterpret_cast<uintptr_t>(src) & 3u) || (reinterpret_cast<uintptr_t>(dst) & 3u)) return EC_ERR_INVALID_ARG;
+    DeviceGuard g(ctx->device);
+    if (!g.ok) return EC_ERR_CUDA;
+    return cuda_status(launch_yuv_encode(static_cast<const uint32_t*>(src), w, h, pitch, static_cast<uint32_t*>(dst),
+                                         dst_pitch, (cudaStream_t)s));
+}
+
+ec_status ec_yuv_decode(ec_ctx* ctx, const void* src, int32_t src_pitch, int32_t w, int32_t h, void* dst,
+                        int32_t pitch, ec_stream_t s)
+{
+    if (!ctx || w < 0 || h < 0 || pitch < w || src_pitch < (w + 1) / 2) return EC_ERR_INVALID_ARG;
+    if ((int64_t)w * h > 0 && (!src || !dst)) return EC_ERR_INVALID_ARG;
+    if ((reinterpret_cast<uintptr_t>(src) & 3u) || (reinterpret_cast<uintptr_t>(dst) & 3u)) return EC_ERR_INVALID_ARG;
+    DeviceGuard g(ctx->device);
+    if (!g.ok) return EC_ERR_CUDA;
+    return cuda_status(launch_yuv_decode(static_cast<const uint32_t*>(src), src_pitch, w, h, static_cast<uint32_t*>(dst),
+                                         pitch, (cudaStream_t)s));
+}
+
 size_t ec_rle_max_size(int32_t w, int32_t h)
 {
     if (w < 0 || h < 0) return 0;
@@ -456,7 +480,7 @@ ec_status rle_job_desc(const ec_rle_job& j, bool compress, RleJobDesc* d)
     d->pitch = j.pitch;
     d->n_chunks = (uint32_t)((n + EC_RLE_CHUNK - 1) / EC_RLE_CHUNK);
     if (compress) {
-        if (j.mode != 1 && j.mode != 2) return EC_ERR_INVALID_ARG;
+        if (j.mode > 2) return EC_ERR_INVALID_ARG;
         if (!j.d_size || (reinterpret_cast<uintptr_t>(j.d_size) & 7u)) return EC_ERR_INVALID_ARG;
         if (j.capacity < ec_rle_max_size(j.w, j.h)) return EC_ERR_CAPACITY;
         if (n > 0 && (reinterpret_cast<uintptr_t>(j.src) & 3u)) return EC_ERR_INVALID_ARG;
@@ -486,8 +510,15 @@ static ec_status rle_batch(ec_ctx* ctx, const ec_rle_job* jobs, int32_t njobs, b
     }
     DeviceGuard g(ctx->device);
     if (!g.ok) return EC_ERR_CUDA;
-    for (int b = 0; b < njobs; b += kRleJobsPerLaunch) {
-        const int cnt = std::min(kRleJobsPerLaunch, njobs - b);
+    // one compress launch codes one mode family: the four-plane modes first,
+    // then basic RLE (mode 0)
+    if (compress)
+        std::stable_partition(d.begin(), d.begin() + njobs, [](const RleJobDesc& x) { return x.mode != 0; });
+    for (int b = 0; b < njobs;) {
+        int cnt = std::min(kRleJobsPerLaunch, njobs - b);
+        if (compress)
+            for (int i = 1; i < cnt; ++i)
+                if ((d[b + i].mode == 0) != (d[b].mode == 0)) { cnt = i; break; }
         uint32_t units = 0;
         for (int i = 0; i < cnt; ++i) {
             d[b + i].first_unit = units;
@@ -502,6 +533,7 @@ static ec_status rle_batch(ec_ctx* ctx, const ec_rle_job* jobs, int32_t njobs, b
             e = launch_rle_decompress(&d[b], cnt, units, ctx->d_status, (cudaStream_t)s);
         }
         if (e != cudaSuccess) return EC_ERR_CUDA;
+        b += cnt;
     }
     return EC_OK;
 }

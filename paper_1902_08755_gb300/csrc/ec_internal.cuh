@@ -293,6 +293,11 @@ namespace ec {
 cudaError_t launch_fused_depth(const FusedStage* stages, const FusedUnit* units, int n_units,
                                uint32_t* status, cudaStream_t s);
 
+cudaError_t launch_yuv_encode(const uint32_t* src, int w, int h, int pitch, uint32_t* dst, int dpitch,
+                              cudaStream_t s);
+cudaError_t launch_yuv_decode(const uint32_t* src, int spitch, int w, int h, uint32_t* dst, int pitch,
+                              cudaStream_t s);
+
 // Enqueue a batch plan's persistent launch directly (no graph), for callers
 // that capture their own graph.
 cudaError_t batch_enqueue(const ec_batch* b, cudaStream_t s);

@@ -84,7 +84,7 @@ __device__ void write_header(uint8_t* d, const RleJobDesc& jb)
     put_u32(d + 16, 4u);
     put_u32(d + 20, (uint32_t)kChunk);
     put_u32(d + 24, jb.n_chunks);
-    put_u32(d + 28, 4u);
+    put_u32(d + 28, jb.mode == 0 ? 1u : 4u);       // streams per chunk
 }
 
 // Two 32-bit words holding four 16-bit lanes (planes 0,1 | planes 2,3).
@@ -751,15 +751,222 @@ k_rle_compress(const __grid_constant__ RleJobList<N> J, uint64_t* flags, uint32_
     cp_async_wait<0>();
 }
 
+// ------------------------------------------------- basic RLE, mode 0 ------
+// Thesis 5.5.1's basic RLE: 8-byte units (element pairs) in one stream per
+// chunk.  One CTA per chunk, taken in ticket order.  The chunk's elements are
+// loaded into shared memory; each thread owns 8 consecutive units.  A unit
+// equal to a neighbour belongs to a repeat run; the others form literal
+// spans.  A block max-scan gives every unit its segment's start (a run, or a
+// maximal span of single units), a block sum-scan the position of its bytes,
+// and the unit that ends a token (at most 128 units) writes the token's
+// control byte in front of it.  The chunk's offset comes from the same
+// decoupled look-back as the four-plane modes.
+constexpr int kU = kChunk / 2;                       // units per chunk
+constexpr int kUPer = kU / kT;                       // 8 per thread
+constexpr int kStage0 = 8 * kU + kU / 128 + 32;      // worst case + room for copy_out's read-ahead
+
+// Exclusive block scan (sum, or max with identity 0) of one value per thread;
+// *total receives the reduction over the block.
+template <bool MAX>
+__device__ __forceinline__ uint32_t block_excl(uint32_t v, uint32_t* wt, uint32_t* total)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t inc = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc = MAX ? max(inc, y) : inc + y;
+    }
+    if (lane == 31) wt[warp] = inc;
+    __syncthreads();
+    uint32_t pre = 0, tot = 0;
+#pragma unroll
+    for (int w = 0; w < kT / 32; ++w) {
+        const uint32_t t = wt[w];
+        if (w < warp) pre = MAX ? max(pre, t) : pre + t;
+        tot = MAX ? max(tot, t) : tot + t;
+    }
+    uint32_t ex = __shfl_up_sync(0xffffffffu, inc, 1);
+    if (lane == 0) ex = 0u;
+    *total = tot;
+    __syncthreads();                                  // wt is reused by the next scan
+    return MAX ? max(pre, ex) : pre + ex;
+}
+
+__device__ __forceinline__ void put8(uint8_t* p, uint32_t lo, uint32_t hi)
+{
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        p[k] = (uint8_t)(lo >> (8 * k));
+        p[4 + k] = (uint8_t)(hi >> (8 * k));
+    }
+}
+
+template <int N>
+__global__ void __launch_bounds__(kT)
+k_rle0_compress(const __grid_constant__ RleJobList<N> J, uint64_t* flags, uint32_t* ticket, uint32_t* status)
+{
+    __shared__ __align__(16) uint32_t e[kChunk];
+    __shared__ __align__(16) uint8_t stage[kStage0];
+    __shared__ uint32_t wt[kT / 32];
+    __shared__ uint32_t s_unit;
+    __shared__ uint64_t s_off;
+    const int tid = threadIdx.x;
+    if (tid == 0) s_unit = atomicAdd(ticket, 1u);
+    __syncthreads();
+    const uint32_t unit = s_unit;
+    const RleJobDesc& jb = J.j[find_job(J, unit)];
+    const uint32_t nc = jb.n_chunks, c = unit - jb.first_unit;
+    uint8_t* dst = reinterpret_cast<uint8_t*>(jb.dst);
+    if (c >= nc) {                                    // empty image: header only
+        if (tid == 0) {
+            write_header(dst, jb);
+            *jb.d_size = 32u;
+        }
+        return;
+    }
+    const uint32_t w = (uint32_t)jb.w, n = w * (uint32_t)jb.h, q0 = c * (uint32_t)kChunk;
+    const int len = (int)min((uint32_t)kChunk, n - q0);
+    for (int t = tid; t < len; t += kT) {
+        const uint32_t q = q0 + (uint32_t)t, y = q / w;
+        e[t] = __ldg(jb.src + (size_t)y * jb.pitch + (q - y * w));
+    }
+    __syncthreads();
+
+    const int nu = len / 2;
+    auto eq = [&](int a, int b) { return e[2 * a] == e[2 * b] && e[2 * a + 1] == e[2 * b + 1]; };
+    auto lit = [&](int k) { return !((k > 0 && eq(k, k - 1)) || (k + 1 < nu && eq(k, k + 1))); };
+    auto seg = [&](int k) {                           // unit k starts a run or a span
+        if (k == 0) return true;
+        const bool l = lit(k);
+        return l != lit(k - 1) || (!l && !eq(k, k - 1));
+    };
+    const int k0 = tid * kUPer;
+    uint32_t smax = 0, ssum = 0, tot = 0;
+    for (int j = 0; j < kUPer; ++j) {
+        const int k = k0 + j;
+        if (k < nu && seg(k)) smax = (uint32_t)k;
+    }
+    const uint32_t carry = block_excl<true>(smax, wt, &tot);
+    uint32_t S = carry;
+    for (int j = 0; j < kUPer; ++j) {
+        const int k = k0 + j;
+        if (k >= nu) break;
+        if (seg(k)) S = (uint32_t)k;
+        const bool ts = ((uint32_t)k - S) % 128u == 0u;
+        ssum += lit(k) ? 8u + (ts ? 1u : 0u) : (ts ? 9u : 0u);
+    }
+    uint32_t body = 0;
+    uint32_t P = block_excl<false>(ssum, wt, &body);
+    S = carry;
+    for (int j = 0; j < kUPer; ++j) {
+        const int k = k0 + j;
+        if (k >= nu) break;
+        if (seg(k)) S = (uint32_t)k;
+        const bool l = lit(k);
+        const uint32_t pos = (uint32_t)k - S;
+        const bool ts = pos % 128u == 0u;
+        const uint32_t sz = l ? 8u + (ts ? 1u : 0u) : (ts ? 9u : 0u);
+        const bool te = k + 1 == nu || seg(k + 1) || ((uint32_t)k + 1u - S) % 128u == 0u;
+        const uint32_t L = pos % 128u + 1u;          // units of the token so far
+        if (l) {
+            put8(stage + P + (ts ? 1u : 0u), e[2 * k], e[2 * k + 1]);
+            if (te) stage[P + sz - 1u - 8u * L] = (uint8_t)(L - 1u);
+        } else {
+            if (ts) put8(stage + P + 1u, e[2 * k], e[2 * k + 1]);
+            if (te) stage[P + sz - 9u] = (uint8_t)(128u + L - 1u);
+        }
+        P += sz;
+    }
+    const uint32_t total = body + ((len & 1) ? 4u : 0u);
+    if ((len & 1) && tid == 0) {
+        const uint32_t v = e[len - 1];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) stage[body + k] = (uint8_t)(v >> (8 * k));
+    }
+    if (tid == 0) publish(flags, unit, jb.first_unit, total);
+    __syncthreads();
+    if (tid < 32) {
+        const uint64_t acc = look_back(flags, unit, jb.first_unit, total, status);
+        if (tid == 0) s_off = acc;
+    }
+    __syncthreads();
+    const uint64_t G = s_off;
+    copy_out(dst + 32 + 4ull * nc + G, stage, total, tid, kT);
+    if (tid == 0) {
+        put_u32(dst + 32 + 4ull * c, (uint32_t)(G + total));
+        if (c == 0) write_header(dst, jb);
+        if (c == nc - 1) *jb.d_size = 32ull + 4ull * nc + G + total;
+    }
+}
+
 // ----------------------------------------------------------- decompress ----
 
 constexpr int kDT = 128;        // decoder CTA: one warp per byte plane
+
+// Element q of a job's image.
+__device__ __forceinline__ size_t elem_off(const RleJobDesc& jb, uint32_t q)
+{
+    const uint32_t y = q / (uint32_t)jb.w;
+    return (size_t)y * jb.pitch + (q - y * (uint32_t)jb.w);
+}
+
+// Mode 0 (basic 64-bit RLE): the chunk's one stream [b, e) of the payload is
+// staged in shared memory, then warp 0 walks its tokens in order, every lane
+// reading each control byte, and writes each token's units with its lanes.
+__device__ void decode_mode0(const RleJobDesc& jb, const uint8_t* pay, uint32_t b, uint32_t e, uint32_t q0,
+                             int len, uint8_t* sbuf, uint32_t* status)
+{
+    const int tid = threadIdx.x, lane = tid & 31;
+    const uint32_t w0 = b >> 2, wl = e >> 2;          // whole words [w0, wl), then bytes [4 wl, e)
+    uint32_t* st = reinterpret_cast<uint32_t*>(sbuf);
+    const uint32_t* p32 = reinterpret_cast<const uint32_t*>(pay);
+    for (uint32_t i = tid; w0 + i < wl; i += kDT) st[i] = __ldg(p32 + w0 + i);
+    if (tid < (int)(e - 4u * wl) && wl >= w0) sbuf[4u * (wl - w0) + tid] = __ldg(pay + 4u * wl + tid);
+    __syncthreads();
+    if (tid >= 32) return;
+    const uint8_t* sb = sbuf - 4u * w0;                // stream byte i at sb[i]
+    auto u32_at = [&](uint32_t i) {
+        return (uint32_t)sb[i] | ((uint32_t)sb[i + 1] << 8) | ((uint32_t)sb[i + 2] << 16) | ((uint32_t)sb[i + 3] << 24);
+    };
+    uint32_t* dst = reinterpret_cast<uint32_t*>(jb.dst);
+    const int nu = len / 2;
+    uint32_t i = b;
+    int o = 0, bad = 0;
+    while (o < nu) {
+        if (i >= e) { bad = 1; break; }
+        const uint32_t ctl = sb[i];
+        const int m = ctl < 128u ? (int)ctl + 1 : (int)ctl - 127;
+        const uint32_t need = ctl < 128u ? 1u + 8u * (uint32_t)m : 9u;
+        if (o + m > nu || i + need > e) { bad = 1; break; }
+        for (int k = lane; k < m; k += 32) {
+            const uint32_t v = ctl < 128u ? i + 1u + 8u * (uint32_t)k : i + 1u;
+            const uint32_t q = q0 + 2u * (uint32_t)(o + k);
+            dst[elem_off(jb, q)] = u32_at(v);
+            dst[elem_off(jb, q + 1u)] = u32_at(v + 4u);
+        }
+        i += need;
+        o += m;
+    }
+    if (!bad && (len & 1)) {
+        if (i + 4u > e) bad = 1;
+        else {
+            if (lane == 0) dst[elem_off(jb, q0 + (uint32_t)len - 1u)] = u32_at(i);
+            i += 4u;
+        }
+    }
+    if (!bad && i != e) bad = 1;
+    if (bad && lane == 0) set_status(status, EC_ERR_CORRUPT);
+}
 
 template <int N>
 __global__ void __launch_bounds__(kDT)
 k_rle_decompress(const __grid_constant__ RleJobList<N> J, uint32_t* status)
 {
-    __shared__ __align__(16) uint8_t planes[4][kChunk];
+    // the four decoded planes; a mode-0 chunk's stream (at most 8 * 2048 + 16
+    // bytes) is staged here instead
+    __shared__ __align__(16) uint8_t sbuf[4 * kChunk + 64];
+    uint8_t (*planes)[kChunk] = reinterpret_cast<uint8_t (*)[kChunk]>(sbuf);
     __shared__ uint32_t s_beg[5];
     __shared__ int s_fail, s_mode;
     __shared__ uint8_t s_hdr[rlec::kHdrBytes];
@@ -777,7 +984,7 @@ k_rle_decompress(const __grid_constant__ RleJobList<N> J, uint32_t* status)
     if (tid < rlec::kHdrBytes) s_hdr[tid] = rlec::header_byte(src, size, nc, c, tid);
     __syncthreads();
     if (tid == 0) {
-        const int bad = rlec::check_header(s_hdr, size, (uint32_t)jb.w, (uint32_t)jb.h, nc, c, s_beg, &s_mode);
+        const int bad = rlec::check_header(s_hdr, size, (uint32_t)jb.w, (uint32_t)jb.h, nc, c, s_beg, &s_mode, true);
         s_fail = bad;
         if (bad) set_status(status, EC_ERR_CORRUPT);
     }
@@ -787,6 +994,10 @@ k_rle_decompress(const __grid_constant__ RleJobList<N> J, uint32_t* status)
     const uint32_t n = (uint32_t)jb.w * (uint32_t)jb.h;
     const uint32_t q0 = c * (uint32_t)kChunk;
     const int len = (int)min((uint32_t)kChunk, n - q0);
+    if (s_mode == 0) {
+        decode_mode0(jb, src + 32 + 4ull * nc, s_beg[0], s_beg[1], q0, len, sbuf, status);
+        return;
+    }
     const uint8_t* payload = src + 32 + 16ull * nc;
 
     // warp p decodes byte plane p
@@ -908,6 +1119,12 @@ cudaError_t launch_rle_compress(const RleJobDesc* jobs, int n, uint32_t total_un
     uint64_t* flags = reinterpret_cast<uint64_t*>(reinterpret_cast<char*>(scratch) + 16);
     cudaError_t e = cudaMemsetAsync(scratch, 0, 16 + 8ull * total_units, s);
     if (e != cudaSuccess) return e;
+    if (jobs[0].mode == 0) {                      // basic RLE: one CTA per chunk
+        if (n <= 8) k_rle0_compress<8><<<total_units, kT, 0, s>>>(make_jobs<8>(jobs, n, total_units), flags, ticket, status);
+        else if (n <= 64) k_rle0_compress<64><<<total_units, kT, 0, s>>>(make_jobs<64>(jobs, n, total_units), flags, ticket, status);
+        else k_rle0_compress<kRleJobsPerLaunch><<<total_units, kT, 0, s>>>(make_jobs<kRleJobsPerLaunch>(jobs, n, total_units), flags, ticket, status);
+        return cudaGetLastError();
+    }
     if (n <= 8) return compress_n<8>(jobs, n, total_units, flags, ticket, status, s);
     if (n <= 64) return compress_n<64>(jobs, n, total_units, flags, ticket, status, s);
     return compress_n<kRleJobsPerLaunch>(jobs, n, total_units, flags, ticket, status, s);

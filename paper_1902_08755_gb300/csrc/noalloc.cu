@@ -54,7 +54,7 @@ extern "C" ec_status ec_rle_compress_noalloc(const void* src, int32_t w, int32_t
                                              uint32_t mode, void* dst, size_t dst_capacity,
                                              uint64_t* d_size, uint32_t* d_status, ec_stream_t s)
 {
-    if (w < 0 || h < 0 || pitch < w || (mode != 1 && mode != 2)) return EC_ERR_INVALID_ARG;
+    if (w < 0 || h < 0 || pitch < w || mode > 2) return EC_ERR_INVALID_ARG;
     const uint64_t n = (uint64_t)w * (uint64_t)h;
     if (n > EC_RLE_MAX_ELEMS) return EC_ERR_UNSUPPORTED;
     const uint64_t nchunks = (n + EC_RLE_CHUNK - 1) / EC_RLE_CHUNK;

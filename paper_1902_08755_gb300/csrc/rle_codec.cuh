@@ -11,7 +11,7 @@ namespace rlec {
 
 constexpr int kChunk = EC_RLE_CHUNK;                 // 4096 elements
 constexpr uint32_t kMagic = 0x31524345u;             // "ECR1"
-constexpr int kHdrBytes = 52;                        // header + 5 end-table entries
+constexpr int kHdrBytes = 60;                        // header + 5 four-plane and 2 one-plane entries
 
 // Bit-swizzle: byte k of the result gathers bit pair (7-2k, 6-2k) of the four
 // components, component 0 (R) in the top pair.  This is a transpose of the 4x4
@@ -41,48 +41,70 @@ __device__ __forceinline__ uint4 transpose4(uint32_t e0, uint32_t e1, uint32_t e
 
 __device__ __forceinline__ uint32_t bcast8(uint32_t w) { return 0x01010101u * (w & 0xFFu); }
 
-// Byte i (0 <= i < 52) of what the validator reads for chunk c: the 32-byte
-// header, then end-table entries 4c-1 .. 4c+3 (entry -1 reads as 0).  Bytes
-// past `size` read as 0 and fail validation.
+// Byte i (0 <= i < 60) of what the validator reads for chunk c: the 32-byte
+// header; end-table entries 4c-1 .. 4c+3 of a four-plane stream (modes 1, 2);
+// entries c-1 and c of a one-plane stream (mode 0).  Entry -1 reads as 0 and
+// bytes past `size` read as 0 (and fail validation).
 __device__ __forceinline__ uint8_t header_byte(const uint8_t* src, uint64_t size, uint32_t nc,
                                                uint32_t c, int i)
 {
     if (i < 32) return size >= 32 ? src[i] : 0;
-    const int k = i - 32;
-    const bool has_tab = nc > 0 && size >= 32ull + 16ull * nc;
-    return (has_tab && !(c == 0 && k < 4)) ? src[32 + 16ull * c - 4 + k] : 0;
+    if (i < 52) {
+        const int k = i - 32;
+        const bool has_tab = nc > 0 && size >= 32ull + 16ull * nc;
+        return (has_tab && !(c == 0 && k < 4)) ? src[32 + 16ull * c - 4 + k] : 0;
+    }
+    const int k = i - 52;
+    const bool has_tab = nc > 0 && size >= 32ull + 4ull * nc;
+    return (has_tab && !(c == 0 && k < 4)) ? src[32 + 4ull * c - 4 + k] : 0;
 }
 
+// Bytes of the end table: 16 per chunk for four-plane streams, 4 for mode 0.
+__device__ __forceinline__ uint64_t table_bytes(int mode, uint32_t nc) { return (mode == 0 ? 4ull : 16ull) * nc; }
+
 // Validate the header fields against the expected w x h and n_chunks, and
-// chunk c's four stream ends against the payload size and the all-literal
-// bound.  Writes beg[0..4] (stream offsets inside the payload) and *mode.
+// chunk c's stream ends against the payload size and the all-literal bound.
+// Four-plane streams (modes 1, 2) write beg[0..4], mode 0 (accepted only with
+// allow0) beg[0..1]: stream offsets inside the payload.  Writes *mode.
 // Returns nonzero for a malformed stream.
 __device__ __forceinline__ int check_header(const uint8_t* h, uint64_t size, uint32_t w, uint32_t hgt,
-                                            uint32_t nc, uint32_t c, uint32_t* beg, int* mode)
+                                            uint32_t nc, uint32_t c, uint32_t* beg, int* mode,
+                                            bool allow0 = false)
 {
     if (size < 32) return 1;
     int bad = 0;
     const uint32_t md = (uint32_t)h[6] | ((uint32_t)h[7] << 8);
     bad |= get_u32(h) != kMagic;
     bad |= (h[4] | (h[5] << 8)) != 1;
-    bad |= md != 1u && md != 2u;
+    bad |= md > 2u || (md == 0u && !allow0);
     bad |= get_u32(h + 8) != w || get_u32(h + 12) != hgt;
     bad |= get_u32(h + 16) != 4u || get_u32(h + 20) != (uint32_t)kChunk;
-    bad |= get_u32(h + 24) != nc || get_u32(h + 28) != 4u;
+    bad |= get_u32(h + 24) != nc || get_u32(h + 28) != (md == 0u ? 1u : 4u);
     *mode = (int)md;
-    if (!bad && nc > 0 && size < 32ull + 16ull * nc) bad = 1;
+    const uint64_t tab = table_bytes((int)md, nc);
+    if (!bad && nc > 0 && size < 32ull + tab) bad = 1;
     if (!bad && nc > 0) {
-        const uint64_t psize = size - 32ull - 16ull * nc;
+        const uint64_t psize = size - 32ull - tab;
         const uint32_t n = w * hgt;
         const uint32_t clen = min((uint32_t)kChunk, n - c * (uint32_t)kChunk);
-        const uint32_t cap = clen + (clen + 127u) / 128u;   // all-literal coding
-        beg[0] = get_u32(h + 32);                           // 0 for chunk 0
-        for (int p = 0; p < 4; ++p) {
-            beg[p + 1] = get_u32(h + 36 + 4 * p);
-            bad |= beg[p + 1] < beg[p];
-            bad |= beg[p + 1] - beg[p] > cap;               // longer than any valid stream
+        if (md == 0u) {
+            const uint32_t u = clen / 2;
+            const uint32_t cap = 8u * u + (u + 127u) / 128u + 4u * (clen & 1u);
+            beg[0] = get_u32(h + 52);                       // 0 for chunk 0
+            beg[1] = get_u32(h + 56);
+            bad |= beg[1] < beg[0];
+            bad |= beg[1] - beg[0] > cap;
+            bad |= (uint64_t)beg[1] > psize;
+        } else {
+            const uint32_t cap = clen + (clen + 127u) / 128u;   // all-literal coding
+            beg[0] = get_u32(h + 32);                           // 0 for chunk 0
+            for (int p = 0; p < 4; ++p) {
+                beg[p + 1] = get_u32(h + 36 + 4 * p);
+                bad |= beg[p + 1] < beg[p];
+                bad |= beg[p + 1] - beg[p] > cap;               // longer than any valid stream
+            }
+            bad |= (uint64_t)beg[4] > psize;
         }
-        bad |= (uint64_t)beg[4] > psize;
     }
     return bad;
 }
