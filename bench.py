@@ -11,7 +11,7 @@ its size is written, then another 2x its size is read, so that the timed step
 neither finds its inputs in L2 nor pays for writing back the flush's lines.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ec|reference]
-                    [--workload cfg2|cfg1|cfg3|cfg3h|cfg3fused|cfg3hfused|cfg4|cfg5d|cfg5a|cfg5afused|roi2|asm4k|sched2]
+                    [--workload cfg2|cfg1|cfg3|cfg3h|cfg3fused|cfg3hfused|cfg4|cfg5d|cfg5a|cfg5afused|roi2|asm4k|sched2|rle0|yuv2]
 
 Prints ONE JSON line (rank 0).  Metric: composited Gpixel-layers/s (sum over
 sources of |roi_i ∩ frame| per step, divided by the step time).  With N > 1
@@ -225,16 +225,20 @@ class DepthPipeline:
         self.out_c = torch.empty((H, W), dtype=torch.int32, device=device).view(torch.uint32)
         self.out_d = torch.empty((H, W), dtype=torch.float32, device=device)
         self.cjobs = [(t, m, None, b, sz) for (t, m), b, sz in zip(self.planes, self.bufs, self.sizes)]
+        # the batched codec calls' argument arrays are built once
+        self.comp, _ = ec.prepare_rle_compress_batch(self.cjobs, ctx=self.ctx)
+        self.decomp, _ = ec.prepare_rle_decompress_batch([(b, t.shape[1], t.shape[0], d, None)
+                                                          for b, (t, _), d in zip(self.bufs, self.planes, self.dec)],
+                                                         ctx=self.ctx)
 
     def step(self, ev=None):
         ec = self.ec
         if ev:
             ev[0].record()
-        ec.rle_compress_batch(self.cjobs, ctx=self.ctx)
+        self.comp.run()
         if ev:
             ev[1].record()
-        ec.rle_decompress_batch([(b, t.shape[1], t.shape[0], d, None)
-                                 for b, (t, _), d in zip(self.bufs, self.planes, self.dec)], ctx=self.ctx)
+        self.decomp.run()
         if ev:
             ev[2].record()
         ec.composite_depth(self.imgs, self.out_c, self.out_d, ctx=self.ctx)
@@ -280,6 +284,149 @@ class DepthPipeline:
                             zip(streams, host)))
         imgs = [oracle.Image(s.pvp, s.roi, dec[2 * i], dec[2 * i + 1].view(np.float32))
                 for i, s in enumerate(self.srcs)]
+        bands = np.linspace(0, self.H, cores + 1).astype(int)
+
+        def part(k):
+            y0, y1 = int(bands[k]), int(bands[k + 1])
+            return oracle.composite_depth(imgs, (0, y0, self.W, y1 - y0))
+        list(pool.map(part, range(cores)))
+        return time.perf_counter() - t0
+
+
+class CodecPipeline:
+    """The cfg2 sources (16 x 1920x1080 RGBA8+Z32, cropped) through the other
+    compressors of thesis 5.5, then decoded and depth-composited:
+      rle0: basic 64-bit RLE (mode 0) for colour and depth;
+      yuv2: colour through the lossy YUV compressor and RLE mode 1, depth mode 1."""
+
+    def __init__(self, kind, device):
+        import paper_1902_08755_gb300 as ec
+        import synthetic as S
+        self.ec, self.kind = ec, kind
+        self.W, self.H, self.n = 1920, 1080, 16
+        self.yuv = kind == "yuv2"
+        self.desc = (f"16 sources 1920x1080 RGBA8+Z32, ~30% coverage, ROI-cropped; "
+                     + ("colour YUV 4:2:0 (BT.601 fixed point) + RLE mode 1, depth RLE mode 1"
+                        if self.yuv else "basic 64-bit RLE (mode 0) for colour and depth")
+                     + " -> decode -> depth composite")
+        self.srcs = S.depth_sources(2, self.n, self.W, self.H, 0.3, clustered=True, cropped=True, device=device)
+        self.units = sum(max(0, min(s.roi[2], self.W)) * max(0, min(s.roi[3], self.H)) for s in self.srcs)
+        self.stored_px = sum(s.pvp[2] * s.pvp[3] for s in self.srcs)
+        self.kernels = (["yuv_encode", "rle_compress", "rle_decompress", "yuv_decode", "composite_depth"]
+                        if self.yuv else ["rle_compress", "rle_decompress", "composite_depth"])
+        if torch.device(device).type != "cuda":
+            return
+        self.ctx = ec.default_context(torch.device(device).index or 0)
+        self.packed = [torch.empty(ec.yuv_packed_shape(s.pvp[2], s.pvp[3]), dtype=torch.int32,
+                                   device=device).view(torch.uint32) for s in self.srcs] if self.yuv else []
+        self.planes = []
+        for i, s in enumerate(self.srcs):
+            self.planes.append((self.packed[i], 1) if self.yuv else (s.color, 0))
+            self.planes.append((s.depth.view(torch.uint32), 1 if self.yuv else 0))
+        self.bufs = [torch.empty(ec.rle_max_size(t.shape[1], t.shape[0]), dtype=torch.uint8, device=device)
+                     for t, _ in self.planes]
+        self.sizes = [torch.zeros(1, dtype=torch.uint64, device=device) for _ in self.planes]
+        self.dec = [torch.empty_like(t) for t, _ in self.planes]
+        self.colour = [torch.empty_like(s.color) for s in self.srcs] if self.yuv else [self.dec[2 * i] for i in range(self.n)]
+        self.imgs = [ec.Image(color=self.colour[i], depth=self.dec[2 * i + 1].view(torch.float32),
+                              pvp=s.pvp, roi=s.roi) for i, s in enumerate(self.srcs)]
+        self.out_c = torch.empty((self.H, self.W), dtype=torch.int32, device=device).view(torch.uint32)
+        self.out_d = torch.empty((self.H, self.W), dtype=torch.float32, device=device)
+        self.cjobs = [(t, m, None, b, sz) for (t, m), b, sz in zip(self.planes, self.bufs, self.sizes)]
+        if self.yuv:
+            self.enc = ec.prepare_yuv_batch([(s.color, p, s.pvp[2], s.pvp[3]) for s, p in zip(self.srcs, self.packed)],
+                                            True, ctx=self.ctx)
+            self.ydec = ec.prepare_yuv_batch([(self.dec[2 * i], self.colour[i], s.pvp[2], s.pvp[3])
+                                              for i, s in enumerate(self.srcs)], False, ctx=self.ctx)
+        self.comp, _ = ec.prepare_rle_compress_batch(self.cjobs, ctx=self.ctx)
+        self.decomp, _ = ec.prepare_rle_decompress_batch([(b, t.shape[1], t.shape[0], d, None)
+                                                          for b, (t, _), d in zip(self.bufs, self.planes, self.dec)],
+                                                         ctx=self.ctx)
+
+    def step(self, ev=None):
+        ec = self.ec
+        k = 0
+        if ev:
+            ev[0].record()
+        if self.yuv:
+            self.enc.run()
+            k += 1
+            if ev:
+                ev[k].record()
+        self.comp.run()
+        k += 1
+        if ev:
+            ev[k].record()
+        self.decomp.run()
+        k += 1
+        if ev:
+            ev[k].record()
+        if self.yuv:
+            self.ydec.run()
+            k += 1
+            if ev:
+                ev[k].record()
+        ec.composite_depth(self.imgs, self.out_c, self.out_d, ctx=self.ctx)
+        if ev:
+            ev[k + 1].record()
+
+    def launches_per_step(self):
+        return 5 if self.yuv else 3
+
+    def compressed_bytes(self):
+        return sum(int(s.item()) for s in self.sizes)
+
+    def raw_bytes(self):
+        return sum(4 * t.numel() for t, _ in self.planes)
+
+    def algorithmic_bytes(self):
+        comp = self.compressed_bytes()
+        raw = self.raw_bytes()
+        out = {"rle_compress": raw + comp, "rle_decompress": comp + raw,
+               "composite_depth": 8 * self.units + 8 * self.W * self.H}
+        if self.yuv:
+            packed = sum(4 * p.numel() for p in self.packed)
+            out["yuv_encode"] = 4 * self.stored_px + packed
+            out["yuv_decode"] = packed + 4 * self.stored_px
+        return out
+
+    def setup_e2e(self):
+        self.h_c = [s.color.view(torch.int32).cpu().pin_memory() for s in self.srcs]
+        self.h_d = [s.depth.cpu().pin_memory() for s in self.srcs]
+        self.h_out = torch.empty((self.H, self.W), dtype=torch.int32).pin_memory()
+        self.h_outd = torch.empty((self.H, self.W), dtype=torch.float32).pin_memory()
+        self.h2d = sum(t.numel() * 4 for t in self.h_c + self.h_d)
+        self.d2h = self.H * self.W * 8
+
+    def e2e_step(self):
+        for s, hc, hd in zip(self.srcs, self.h_c, self.h_d):
+            s.color.view(torch.int32).copy_(hc, non_blocking=True)
+            s.depth.copy_(hd, non_blocking=True)
+        self.step()
+        self.h_out.copy_(self.out_c.view(torch.int32), non_blocking=True)
+        self.h_outd.copy_(self.out_d, non_blocking=True)
+
+    def oracle_step(self, pool, cores):
+        import oracle
+        if not hasattr(self, "_host"):
+            self._host = [(s.color.view(torch.int32).cpu().numpy().view(np.uint32), s.depth.cpu().numpy())
+                          for s in self.srcs]
+        t0 = time.perf_counter()
+
+        def codec(a):
+            c, d = a
+            w, h = c.shape[1], c.shape[0]
+            if self.yuv:
+                p = oracle.yuv_encode(c)
+                p = oracle.rle_decompress(oracle.rle_compress(p, 1), p.shape[1], p.shape[0])
+                c2 = oracle.yuv_decode(p, w, h)
+                d2 = oracle.rle_decompress(oracle.rle_compress(d.view(np.uint32), 1), w, h)
+            else:
+                c2 = oracle.rle_decompress(oracle.rle_compress(c, 0), w, h)
+                d2 = oracle.rle_decompress(oracle.rle_compress(d.view(np.uint32), 0), w, h)
+            return c2, d2.view(np.float32)
+        dec = list(pool.map(codec, self._host))
+        imgs = [oracle.Image(s.pvp, s.roi, c, d) for s, (c, d) in zip(self.srcs, dec)]
         bands = np.linspace(0, self.H, cores + 1).astype(int)
 
         def part(k):
@@ -823,6 +970,8 @@ def make_workload(name, device):
         return Assembly(3840, 2160, device)
     if name == "sched2":
         return Schedules(device)
+    if name in ("rle0", "yuv2"):
+        return CodecPipeline(name, device)
     if name == "cfg3":
         return AlphaForward(3, 32, 2048, 2048, 0.3, torch.float32, device)
     if name == "cfg3h":
@@ -982,10 +1131,10 @@ def run_ec(args):
            "pixel_layers_per_step": wl.units, "parallelism": f"replicas x{world}"}
     if hasattr(wl, "compressed_bytes"):
         cfg["rle_compressed_bytes_per_step"] = wl.compressed_bytes()
-        cfg["rle_raw_bytes_per_step"] = 8 * wl.stored_px
+        cfg["rle_raw_bytes_per_step"] = wl.raw_bytes() if hasattr(wl, "raw_bytes") else 8 * wl.stored_px
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": max(3, args.warmup), "ms_per_step": ms, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "rgba8+f32" if isinstance(wl, (DepthPipeline, BatchedTiles, RoiDetect, Schedules)) else "u8" if isinstance(wl, Assembly) else "f32",
+            "scaling": "weak", "vs_baseline": None, "dtype": "rgba8+f32" if isinstance(wl, (DepthPipeline, BatchedTiles, RoiDetect, Schedules, CodecPipeline)) else "u8" if isinstance(wl, Assembly) else "f32",
             "data": "synthetic (seeded boxes / layers shaped like the thesis's workloads)",
             "config": cfg, "roofline": roof, "kernels": kern,
             "e2e": {"value": whole_job_value(wl.units, e2e_ms, world), "unit": UNIT,

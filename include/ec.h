@@ -492,6 +492,17 @@ ec_status ec_yuv_encode(ec_ctx* ctx, const void* src, int32_t w, int32_t h, int3
 ec_status ec_yuv_decode(ec_ctx* ctx, const void* src, int32_t src_pitch, int32_t w, int32_t h, void* dst,
                         int32_t pitch, ec_stream_t s);
 
+/* Several images in one launch. */
+typedef struct {
+    const void* src;       /* encode: RGBA8 image; decode: packed image             */
+    void* dst;             /* encode: packed image; decode: RGBA8 image             */
+    int32_t w, h;          /* frame size in pixels                                  */
+    int32_t pitch;         /* row pitch of the RGBA8 image, elements                */
+    int32_t packed_pitch;  /* row pitch of the packed image, words (>= ceil(w/2))   */
+} ec_yuv_job;
+ec_status ec_yuv_encode_batch(ec_ctx* ctx, const ec_yuv_job* jobs, int32_t njobs, ec_stream_t s);
+ec_status ec_yuv_decode_batch(ec_ctx* ctx, const ec_yuv_job* jobs, int32_t njobs, ec_stream_t s);
+
 /* ------------------------------------------------ allocation-free compressor
  * The thesis has no counterpart to this entry point; it exists for callers
  * that cannot allocate device memory.  ec_rle_compress takes its scratch

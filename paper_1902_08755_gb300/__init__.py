@@ -26,6 +26,7 @@ from .api import (  # noqa: F401
     Schedule,
     Context,
     Job,
+    Prepared,
     Image,
     assemble_pixels,
     assemble_tiles,
@@ -38,11 +39,15 @@ from .api import (  # noqa: F401
     default_context,
     detect_roi,
     pixel_layout,
+    prepare_rle_compress_batch,
+    prepare_rle_decompress_batch,
+    prepare_yuv_batch,
     rle_compress,
     rle_compress_batch,
     rle_decompress,
     rle_decompress_batch,
     rle_max_size,
+    yuv_batch,
     yuv_decode,
     yuv_encode,
     yuv_packed_shape,

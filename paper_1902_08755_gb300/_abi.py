@@ -77,6 +77,11 @@ class ec_sched_launch(C.Structure):
     _fields_ = [("level", C.c_int32), ("kind", C.c_int32), ("bytes", C.c_uint64)]
 
 
+class ec_yuv_job(C.Structure):
+    _fields_ = [("src", C.c_void_p), ("dst", C.c_void_p), ("w", C.c_int32), ("h", C.c_int32),
+                ("pitch", C.c_int32), ("packed_pitch", C.c_int32)]
+
+
 class ec_sched_message(C.Structure):
     _fields_ = [("level", C.c_int32), ("sender", C.c_int32), ("receiver", C.c_int32),
                 ("fused", C.c_int32), ("piece", ec_rect)]
@@ -114,6 +119,8 @@ SIGNATURES = {
     "ec_batch_free": (None, [_P]),
     "ec_yuv_encode": (_S, [_P, _P, _I, _I, _I, _P, _I, _P]),
     "ec_yuv_decode": (_S, [_P, _P, _I, _I, _I, _P, _I, _P]),
+    "ec_yuv_encode_batch": (_S, [_P, _P, _I, _P]),
+    "ec_yuv_decode_batch": (_S, [_P, _P, _I, _P]),
     "ec_schedule_plan": (_S, [_P, _I, _I, _P, _I, _P, _P, C.c_uint32, C.POINTER(C.c_void_p)]),
     "ec_schedule_run": (_S, [_P, _P]),
     "ec_schedule_info": (_S, [_P, _P, _P, _P, _P]),

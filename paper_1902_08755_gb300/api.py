@@ -398,6 +398,28 @@ def yuv_decode(packed: torch.Tensor, w: int, h: int, out: Optional[torch.Tensor]
     return out
 
 
+def yuv_batch(jobs, encode: bool, ctx: Optional[Context] = None, stream=None):
+    """ec_yuv_encode_batch / ec_yuv_decode_batch over [(src, dst, w, h)]: encode
+    reads RGBA8 src and writes packed dst, decode the reverse (one launch)."""
+    prepare_yuv_batch(jobs, encode, ctx).run(stream)
+
+
+def prepare_yuv_batch(jobs, encode: bool, ctx: Optional[Context] = None) -> "Prepared":
+    """Prepared ec_yuv_encode_batch / ec_yuv_decode_batch."""
+    ctx = ctx or default_context(jobs[0][0].device.index)
+    arr = (A.ec_yuv_job * max(1, len(jobs)))()
+    for i, (src, dst, w, h) in enumerate(jobs):
+        rgba, packed = (src, dst) if encode else (dst, src)
+        pitch, rw, rh = _elem_layout(rgba)
+        ppitch, pw, ph = _elem_layout(packed)
+        rows, words = yuv_packed_shape(w, h)
+        if rw < w or rh < h or pw < words or ph < rows:
+            raise ValueError("yuv job: tensors too small")
+        arr[i] = A.ec_yuv_job(src.data_ptr(), dst.data_ptr(), int(w), int(h), pitch, ppitch)
+    fn = _lib().ec_yuv_encode_batch if encode else _lib().ec_yuv_decode_batch
+    return Prepared(fn, ctx, arr, len(jobs), "ec_yuv_batch", list(jobs))
+
+
 def rle_max_size(w: int, h: int) -> int:
     return int(_lib().ec_rle_max_size(int(w), int(h)))
 
@@ -423,10 +445,45 @@ def rle_compress(src: torch.Tensor, mode: int, w: Optional[int] = None,
     return out[0]
 
 
+class Prepared:
+    """A batched call whose argument array is built once; run() only enqueues
+    it (for frame loops and for timing the kernels rather than the marshalling).
+    The tensors named by the jobs must stay alive and in place."""
+
+    def __init__(self, fn, ctx, arr, n, what, keep):
+        self.fn, self.ctx, self.arr, self.n, self.what, self._keep = fn, ctx, arr, n, what, keep
+
+    def run(self, stream=None):
+        check(self.fn(self.ctx.h, self.arr, self.n, _stream_handle(stream)), self.what)
+
+
+def prepare_rle_compress_batch(jobs, ctx: Optional[Context] = None):
+    """Prepared ec_rle_compress_batch; returns (Prepared, [(dst, d_size)])."""
+    ctx = ctx or default_context(jobs[0][0].device.index)
+    arr, outs = _rle_compress_jobs(jobs, ctx)
+    return Prepared(_lib().ec_rle_compress_batch, ctx, arr, len(jobs), "ec_rle_compress_batch",
+                    [jobs, outs]), outs
+
+
+def prepare_rle_decompress_batch(jobs, ctx: Optional[Context] = None):
+    """Prepared ec_rle_decompress_batch; returns (Prepared, [dst])."""
+    ctx = ctx or default_context(jobs[0][0].device.index)
+    arr, outs = _rle_decompress_jobs(jobs, ctx)
+    return Prepared(_lib().ec_rle_decompress_batch, ctx, arr, len(jobs), "ec_rle_decompress_batch",
+                    [jobs, outs]), outs
+
+
 def rle_compress_batch(jobs, ctx: Optional[Context] = None, stream=None):
     """ec_rle_compress_batch over [(src, mode, w|None, dst|None, d_size|None)].
     Returns [(dst, d_size)]."""
     ctx = ctx or default_context(jobs[0][0].device.index)
+    arr, outs = _rle_compress_jobs(jobs, ctx)
+    check(_lib().ec_rle_compress_batch(ctx.h, arr, len(jobs), _stream_handle(stream)),
+          "ec_rle_compress_batch")
+    return outs
+
+
+def _rle_compress_jobs(jobs, ctx):
     dev = ctx.device
     arr = (ec_rle_job * max(1, len(jobs)))()
     outs = []
@@ -443,9 +500,7 @@ def rle_compress_batch(jobs, ctx: Optional[Context] = None, stream=None):
         arr[i] = ec_rle_job(src.data_ptr(), dst.data_ptr(), dst.numel() * dst.element_size(),
                             d_size.data_ptr(), w, h, pitch, int(mode))
         outs.append((dst, d_size))
-    check(_lib().ec_rle_compress_batch(ctx.h, arr, len(jobs), _stream_handle(stream)),
-          "ec_rle_compress_batch")
-    return outs
+    return arr, outs
 
 
 def rle_decompress(src: torch.Tensor, w: int, h: int, dst: Optional[torch.Tensor] = None,
@@ -458,6 +513,13 @@ def rle_decompress(src: torch.Tensor, w: int, h: int, dst: Optional[torch.Tensor
 def rle_decompress_batch(jobs, ctx: Optional[Context] = None, stream=None):
     """ec_rle_decompress_batch over [(src, w, h, dst|None, src_size|None)]."""
     ctx = ctx or default_context(jobs[0][0].device.index)
+    arr, outs = _rle_decompress_jobs(jobs, ctx)
+    check(_lib().ec_rle_decompress_batch(ctx.h, arr, len(jobs), _stream_handle(stream)),
+          "ec_rle_decompress_batch")
+    return outs
+
+
+def _rle_decompress_jobs(jobs, ctx):
     dev = ctx.device
     arr = (ec_rle_job * max(1, len(jobs)))()
     outs = []
@@ -472,9 +534,7 @@ def rle_decompress_batch(jobs, ctx: Optional[Context] = None, stream=None):
         size = src.numel() * src.element_size() if src_size is None else int(src_size)
         arr[i] = ec_rle_job(src.data_ptr(), dst.data_ptr(), size, None, int(w), int(h), pitch, 0)
         outs.append(dst)
-    check(_lib().ec_rle_decompress_batch(ctx.h, arr, len(jobs), _stream_handle(stream)),
-          "ec_rle_decompress_batch")
-    return outs
+    return arr, outs
 
 
 # ------------------------------------------------------------------ batches

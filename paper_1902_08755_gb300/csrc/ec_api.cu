@@ -429,28 +429,59 @@ ec_status ec_detect_roi(ec_ctx* ctx, const ec_image* in, int32_t n, int32_t tile
     return EC_OK;
 }
 
+static ec_status yuv_batch(ec_ctx* ctx, const ec_yuv_job* jobs, int32_t njobs, bool encode, ec_stream_t s)
+{
+    if (!ctx || njobs < 0 || (njobs > 0 && !jobs)) return EC_ERR_INVALID_ARG;
+    std::vector<YuvJob> d;
+    for (int i = 0; i < njobs; ++i) {
+        const ec_yuv_job& j = jobs[i];
+        if (j.w < 0 || j.h < 0 || j.pitch < j.w || j.packed_pitch < (j.w + 1) / 2) return EC_ERR_INVALID_ARG;
+        if ((int64_t)j.w * j.h == 0) continue;
+        if (!j.src || !j.dst || (reinterpret_cast<uintptr_t>(j.src) & 3u) || (reinterpret_cast<uintptr_t>(j.dst) & 3u))
+            return EC_ERR_INVALID_ARG;
+        YuvJob y;
+        memset(&y, 0, sizeof(y));
+        y.src = static_cast<const uint32_t*>(j.src);
+        y.dst = static_cast<uint32_t*>(j.dst);
+        y.w = j.w;
+        y.h = j.h;
+        y.pitch = j.pitch;
+        y.dpitch = j.packed_pitch;
+        const void* rgba = encode ? j.src : j.dst;
+        y.vec = (reinterpret_cast<uintptr_t>(rgba) & 7u) == 0 && j.pitch % 2 == 0;
+        d.push_back(y);
+    }
+    DeviceGuard g(ctx->device);
+    if (!g.ok) return EC_ERR_CUDA;
+    for (size_t b = 0; b < d.size(); b += kYuvJobsPerLaunch) {
+        const int cnt = (int)std::min<size_t>(kYuvJobsPerLaunch, d.size() - b);
+        if (launch_yuv(&d[b], cnt, encode, (cudaStream_t)s) != cudaSuccess) return EC_ERR_CUDA;
+    }
+    return EC_OK;
+}
+
+ec_status ec_yuv_encode_batch(ec_ctx* ctx, const ec_yuv_job* jobs, int32_t njobs, ec_stream_t s)
+{
+    return yuv_batch(ctx, jobs, njobs, true, s);
+}
+
+ec_status ec_yuv_decode_batch(ec_ctx* ctx, const ec_yuv_job* jobs, int32_t njobs, ec_stream_t s)
+{
+    return yuv_batch(ctx, jobs, njobs, false, s);
+}
+
 ec_status ec_yuv_encode(ec_ctx* ctx, const void* src, int32_t w, int32_t h, int32_t pitch, void* dst,
                         int32_t dst_pitch, ec_stream_t s)
 {
-    if (!ctx || w < 0 || h < 0 || pitch < w || dst_pitch < (w + 1) / 2) return EC_ERR_INVALID_ARG;
-    if ((int64_t)w * h > 0 && (!src || !dst)) return EC_ERR_INVALID_ARG;
-    if ((reinterpret_cast<uintptr_t>(src) & 3u) || (reinterpret_cast<uintptr_t>(dst) & 3u)) return EC_ERR_INVALID_ARG;
-    DeviceGuard g(ctx->device);
-    if (!g.ok) return EC_ERR_CUDA;
-    return cuda_status(launch_yuv_encode(static_cast<const uint32_t*>(src), w, h, pitch, static_cast<uint32_t*>(dst),
-                                         dst_pitch, (cudaStream_t)s));
+    const ec_yuv_job j{src, dst, w, h, pitch, dst_pitch};
+    return yuv_batch(ctx, &j, 1, true, s);
 }
 
 ec_status ec_yuv_decode(ec_ctx* ctx, const void* src, int32_t src_pitch, int32_t w, int32_t h, void* dst,
                         int32_t pitch, ec_stream_t s)
 {
-    if (!ctx || w < 0 || h < 0 || pitch < w || src_pitch < (w + 1) / 2) return EC_ERR_INVALID_ARG;
-    if ((int64_t)w * h > 0 && (!src || !dst)) return EC_ERR_INVALID_ARG;
-    if ((reinterpret_cast<uintptr_t>(src) & 3u) || (reinterpret_cast<uintptr_t>(dst) & 3u)) return EC_ERR_INVALID_ARG;
-    DeviceGuard g(ctx->device);
-    if (!g.ok) return EC_ERR_CUDA;
-    return cuda_status(launch_yuv_decode(static_cast<const uint32_t*>(src), src_pitch, w, h, static_cast<uint32_t*>(dst),
-                                         pitch, (cudaStream_t)s));
+    const ec_yuv_job j{src, dst, w, h, pitch, src_pitch};
+    return yuv_batch(ctx, &j, 1, false, s);
 }
 
 size_t ec_rle_max_size(int32_t w, int32_t h)

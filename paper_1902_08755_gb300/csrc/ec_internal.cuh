@@ -293,10 +293,31 @@ namespace ec {
 cudaError_t launch_fused_depth(const FusedStage* stages, const FusedUnit* units, int n_units,
                                uint32_t* status, cudaStream_t s);
 
-cudaError_t launch_yuv_encode(const uint32_t* src, int w, int h, int pitch, uint32_t* dst, int dpitch,
-                              cudaStream_t s);
-cudaError_t launch_yuv_decode(const uint32_t* src, int spitch, int w, int h, uint32_t* dst, int pitch,
-                              cudaStream_t s);
+// One image of a YUV launch: encode reads src (RGBA8, row pitch `pitch`) and
+// writes the packed dst (row pitch dpitch); decode reads the packed src (row
+// pitch dpitch) and writes RGBA8 dst (row pitch `pitch`).
+struct YuvJob {
+    const uint32_t* src;
+    uint32_t* dst;
+    int32_t w, h, pitch, dpitch;
+    uint32_t first;      // first CTA tile of this image
+    uint32_t tiles_x;    // CTA tiles per row of blocks
+    int32_t vec;         // the RGBA8 side allows 8-byte accesses
+    int32_t pad;
+};
+static_assert(sizeof(YuvJob) == 48, "yuv job layout");
+
+constexpr int kYuvJobsPerLaunch = 128;
+
+template <int N>
+struct YuvJobList {
+    int32_t n;
+    int32_t pad[3];
+    YuvJob j[N];
+};
+
+// jobs: at most kYuvJobsPerLaunch; first/tiles_x are filled in here.
+cudaError_t launch_yuv(YuvJob* jobs, int n, bool encode, cudaStream_t s);
 
 // Enqueue a batch plan's persistent launch directly (no graph), for callers
 // that capture their own graph.

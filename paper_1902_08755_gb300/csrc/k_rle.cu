@@ -754,7 +754,8 @@ k_rle_compress(const __grid_constant__ RleJobList<N> J, uint64_t* flags, uint32_
 // ------------------------------------------------- basic RLE, mode 0 ------
 // Thesis 5.5.1's basic RLE: 8-byte units (element pairs) in one stream per
 // chunk.  One CTA per chunk, taken in ticket order.  The chunk's elements are
-// loaded into shared memory; each thread owns 8 consecutive units.  A unit
+// loaded into shared memory; each thread reads its 8 consecutive units and
+// the two on either side into registers once (16-byte reads).  A unit
 // equal to a neighbour belongs to a repeat run; the others form literal
 // spans.  A block max-scan gives every unit its segment's start (a run, or a
 // maximal span of single units), a block sum-scan the position of its bytes,
@@ -803,7 +804,7 @@ __device__ __forceinline__ void put8(uint8_t* p, uint32_t lo, uint32_t hi)
 }
 
 template <int N>
-__global__ void __launch_bounds__(kT)
+__global__ void __launch_bounds__(kT, 5)
 k_rle0_compress(const __grid_constant__ RleJobList<N> J, uint64_t* flags, uint32_t* ticket, uint32_t* status)
 {
     __shared__ __align__(16) uint32_t e[kChunk];
@@ -833,47 +834,79 @@ k_rle0_compress(const __grid_constant__ RleJobList<N> J, uint64_t* flags, uint32
     }
     __syncthreads();
 
+    // this thread's 8 units, the two before and the two after, read once
     const int nu = len / 2;
-    auto eq = [&](int a, int b) { return e[2 * a] == e[2 * b] && e[2 * a + 1] == e[2 * b + 1]; };
-    auto lit = [&](int k) { return !((k > 0 && eq(k, k - 1)) || (k + 1 < nu && eq(k, k + 1))); };
-    auto seg = [&](int k) {                           // unit k starts a run or a span
-        if (k == 0) return true;
-        const bool l = lit(k);
-        return l != lit(k - 1) || (!l && !eq(k, k - 1));
-    };
     const int k0 = tid * kUPer;
-    uint32_t smax = 0, ssum = 0, tot = 0;
-    for (int j = 0; j < kUPer; ++j) {
-        const int k = k0 + j;
-        if (k < nu && seg(k)) smax = (uint32_t)k;
+    uint32_t ul[kUPer + 4], uh[kUPer + 4];           // [0,1] = k0-2, k0-1; [2..9] = k0..k0+7; [10,11] = k0+8, k0+9
+    {
+        const uint4* e4 = reinterpret_cast<const uint4*>(e);
+        const uint4 m = tid > 0 ? e4[4 * tid - 1] : make_uint4(0u, 0u, 0u, 0u);
+        ul[0] = m.x; uh[0] = m.y; ul[1] = m.z; uh[1] = m.w;
+#pragma unroll
+        for (int g = 0; g < 4; ++g) {
+            const uint4 v = e4[4 * tid + g];
+            ul[2 + 2 * g] = v.x; uh[2 + 2 * g] = v.y; ul[3 + 2 * g] = v.z; uh[3 + 2 * g] = v.w;
+        }
+        const uint4 n = tid + 1 < kT ? e4[4 * tid + 4] : make_uint4(0u, 0u, 0u, 0u);
+        ul[10] = n.x; uh[10] = n.y; ul[11] = n.z; uh[11] = n.w;
     }
+    // eqp[i]: unit k0-2+i equals its predecessor (both exist), i = 0 .. 11
+    uint32_t eqp = 0u;
+#pragma unroll
+    for (int i = 1; i < kUPer + 4; ++i) {
+        const int k = k0 - 2 + i;
+        if (k >= 1 && k < nu && ul[i] == ul[i - 1] && uh[i] == uh[i - 1]) eqp |= 1u << i;
+    }
+    // lit[i], i = 1 .. 10: unit k0-2+i exists and equals neither neighbour
+    uint32_t lit = 0u;
+#pragma unroll
+    for (int i = 1; i < kUPer + 3; ++i) {
+        const int k = k0 - 2 + i;
+        if (k >= 0 && k < nu && !((eqp >> i) & 1u) && !((eqp >> (i + 1)) & 1u)) lit |= 1u << i;
+    }
+    // seg[i], i = 2 .. 10: unit k0-2+i starts a run or a span
+    uint32_t seg = 0u;
+#pragma unroll
+    for (int i = 2; i < kUPer + 3; ++i) {
+        const int k = k0 - 2 + i;
+        if (k >= nu) continue;
+        const bool l = (lit >> i) & 1u, lp = (lit >> (i - 1)) & 1u;
+        if (k == 0 || l != lp || (!l && !((eqp >> i) & 1u))) seg |= 1u << i;
+    }
+
+    uint32_t smax = 0, ssum = 0, tot = 0;
+#pragma unroll
+    for (int j = 0; j < kUPer; ++j)
+        if (k0 + j < nu && ((seg >> (j + 2)) & 1u)) smax = (uint32_t)(k0 + j);
     const uint32_t carry = block_excl<true>(smax, wt, &tot);
     uint32_t S = carry;
+#pragma unroll
     for (int j = 0; j < kUPer; ++j) {
         const int k = k0 + j;
         if (k >= nu) break;
-        if (seg(k)) S = (uint32_t)k;
+        if ((seg >> (j + 2)) & 1u) S = (uint32_t)k;
         const bool ts = ((uint32_t)k - S) % 128u == 0u;
-        ssum += lit(k) ? 8u + (ts ? 1u : 0u) : (ts ? 9u : 0u);
+        ssum += ((lit >> (j + 2)) & 1u) ? 8u + (ts ? 1u : 0u) : (ts ? 9u : 0u);
     }
     uint32_t body = 0;
     uint32_t P = block_excl<false>(ssum, wt, &body);
     S = carry;
+#pragma unroll
     for (int j = 0; j < kUPer; ++j) {
         const int k = k0 + j;
         if (k >= nu) break;
-        if (seg(k)) S = (uint32_t)k;
-        const bool l = lit(k);
+        if ((seg >> (j + 2)) & 1u) S = (uint32_t)k;
+        const bool l = (lit >> (j + 2)) & 1u;
         const uint32_t pos = (uint32_t)k - S;
         const bool ts = pos % 128u == 0u;
         const uint32_t sz = l ? 8u + (ts ? 1u : 0u) : (ts ? 9u : 0u);
-        const bool te = k + 1 == nu || seg(k + 1) || ((uint32_t)k + 1u - S) % 128u == 0u;
+        const bool te = k + 1 == nu || ((seg >> (j + 3)) & 1u) || ((uint32_t)k + 1u - S) % 128u == 0u;
         const uint32_t L = pos % 128u + 1u;          // units of the token so far
         if (l) {
-            put8(stage + P + (ts ? 1u : 0u), e[2 * k], e[2 * k + 1]);
+            put8(stage + P + (ts ? 1u : 0u), ul[j + 2], uh[j + 2]);
             if (te) stage[P + sz - 1u - 8u * L] = (uint8_t)(L - 1u);
         } else {
-            if (ts) put8(stage + P + 1u, e[2 * k], e[2 * k + 1]);
+            if (ts) put8(stage + P + 1u, ul[j + 2], uh[j + 2]);
             if (te) stage[P + sz - 9u] = (uint8_t)(128u + L - 1u);
         }
         P += sz;

@@ -10,8 +10,10 @@
 // rows [ceil(h/2), 2 ceil(h/2)) chroma words (bytes U, V, A, 0).
 //
 // One thread per block; a row pair of the block is one 8-byte access where
-// the buffer allows it.  Both kernels are HBM-bound: 4 bytes read and 2
-// written per pixel to encode, the reverse to decode.
+// the buffer allows it.  A launch covers many images: CTA tiles of 32 x 8
+// blocks are numbered across the images and each CTA finds its image by a
+// binary search of the images' first tiles.  Both kernels are HBM-bound: 4
+// bytes read and 2 written per pixel to encode, the reverse to decode.
 #include "ec_internal.cuh"
 
 namespace ec {
@@ -31,12 +33,34 @@ __device__ __forceinline__ void to_yuv(uint32_t p, int& Y, int& U, int& V)
     V = min(255, (128 * R - 107 * G - 21 * B + 32896) >> 8);
 }
 
-__global__ void __launch_bounds__(kYX * kYY)
-k_yuv_encode(const uint32_t* __restrict__ src, int w, int h, int pitch, bool vec, uint32_t* __restrict__ dst,
-             int dpitch)
+// CTA tile t of a job list: the job whose tiles [first, first + ntiles) hold it.
+template <int N>
+__device__ __forceinline__ const YuvJob& tile_job(const YuvJobList<N>& J, uint32_t t, int& bx, int& by)
 {
+    int lo = 0, hi = J.n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (J.j[mid].first <= t) lo = mid;
+        else hi = mid - 1;
+    }
+    const YuvJob& jb = J.j[lo];
+    const uint32_t r = t - jb.first, tx = r % jb.tiles_x;
+    bx = (int)(tx * kYX) + threadIdx.x;
+    by = (int)((r / jb.tiles_x) * kYY) + threadIdx.y;
+    return jb;
+}
+
+template <int N>
+__global__ void __launch_bounds__(kYX * kYY)
+k_yuv_encode(const __grid_constant__ YuvJobList<N> J)
+{
+    int bx, by;
+    const YuvJob& jb = tile_job(J, blockIdx.x, bx, by);
+    const uint32_t* __restrict__ src = jb.src;
+    uint32_t* __restrict__ dst = jb.dst;
+    const int w = jb.w, h = jb.h, pitch = jb.pitch, dpitch = jb.dpitch;
+    const bool vec = jb.vec;
     const int bw = (w + 1) >> 1, bh = (h + 1) >> 1;
-    const int bx = blockIdx.x * kYX + threadIdx.x, by = blockIdx.y * kYY + threadIdx.y;
     if (bx >= bw || by >= bh) return;
     const int x = 2 * bx;
     uint32_t px[4] = {0u, 0u, 0u, 0u};
@@ -80,12 +104,17 @@ k_yuv_encode(const uint32_t* __restrict__ src, int w, int h, int pitch, bool vec
                                           ((uint32_t)((sa + half) >> sh) << 16);
 }
 
+template <int N>
 __global__ void __launch_bounds__(kYX * kYY)
-k_yuv_decode(const uint32_t* __restrict__ src, int spitch, int w, int h, uint32_t* __restrict__ dst, int pitch,
-             bool vec)
+k_yuv_decode(const __grid_constant__ YuvJobList<N> J)
 {
+    int bx, by;
+    const YuvJob& jb = tile_job(J, blockIdx.x, bx, by);
+    const uint32_t* __restrict__ src = jb.src;
+    uint32_t* __restrict__ dst = jb.dst;
+    const int w = jb.w, h = jb.h, pitch = jb.pitch, spitch = jb.dpitch;
+    const bool vec = jb.vec;
     const int bw = (w + 1) >> 1, bh = (h + 1) >> 1;
-    const int bx = blockIdx.x * kYX + threadIdx.x, by = blockIdx.y * kYY + threadIdx.y;
     if (bx >= bw || by >= bh) return;
     const uint32_t luma = __ldcs(src + (size_t)by * spitch + bx);
     const uint32_t ch = __ldcs(src + (size_t)(bh + by) * spitch + bx);
@@ -114,30 +143,37 @@ k_yuv_decode(const uint32_t* __restrict__ src, int spitch, int w, int h, uint32_
     }
 }
 
-dim3 grid_of(int w, int h)
+template <int N, bool ENC>
+cudaError_t launch_n(const YuvJob* jobs, int n, uint32_t tiles, cudaStream_t s)
 {
-    const int bw = (w + 1) / 2, bh = (h + 1) / 2;
-    return dim3((unsigned)((bw + kYX - 1) / kYX), (unsigned)((bh + kYY - 1) / kYY));
+    YuvJobList<N> J;
+    J.n = n;
+    for (int i = 0; i < n; ++i) J.j[i] = jobs[i];
+    if (ENC) k_yuv_encode<N><<<tiles, dim3(kYX, kYY), 0, s>>>(J);
+    else k_yuv_decode<N><<<tiles, dim3(kYX, kYY), 0, s>>>(J);
+    return cudaGetLastError();
 }
 
 }  // namespace
 
-cudaError_t launch_yuv_encode(const uint32_t* src, int w, int h, int pitch, uint32_t* dst, int dpitch,
-                              cudaStream_t s)
+// Fills first/tiles_x of every job and launches (at most kYuvJobsPerLaunch jobs).
+cudaError_t launch_yuv(YuvJob* jobs, int n, bool encode, cudaStream_t s)
 {
-    if (w <= 0 || h <= 0) return cudaSuccess;
-    const bool vec = (reinterpret_cast<uintptr_t>(src) & 7u) == 0 && pitch % 2 == 0;
-    k_yuv_encode<<<grid_of(w, h), dim3(kYX, kYY), 0, s>>>(src, w, h, pitch, vec, dst, dpitch);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_yuv_decode(const uint32_t* src, int spitch, int w, int h, uint32_t* dst, int pitch,
-                              cudaStream_t s)
-{
-    if (w <= 0 || h <= 0) return cudaSuccess;
-    const bool vec = (reinterpret_cast<uintptr_t>(dst) & 7u) == 0 && pitch % 2 == 0;
-    k_yuv_decode<<<grid_of(w, h), dim3(kYX, kYY), 0, s>>>(src, spitch, w, h, dst, pitch, vec);
-    return cudaGetLastError();
+    uint32_t tiles = 0;
+    int m = 0;
+    for (int i = 0; i < n; ++i) {
+        const int bw = (jobs[i].w + 1) / 2, bh = (jobs[i].h + 1) / 2;
+        if (bw <= 0 || bh <= 0) continue;
+        jobs[m] = jobs[i];
+        jobs[m].tiles_x = (uint32_t)((bw + kYX - 1) / kYX);
+        jobs[m].first = tiles;
+        tiles += jobs[m].tiles_x * (uint32_t)((bh + kYY - 1) / kYY);
+        ++m;
+    }
+    if (m == 0) return cudaSuccess;
+    if (m <= 8) return encode ? launch_n<8, true>(jobs, m, tiles, s) : launch_n<8, false>(jobs, m, tiles, s);
+    return encode ? launch_n<kYuvJobsPerLaunch, true>(jobs, m, tiles, s)
+                  : launch_n<kYuvJobsPerLaunch, false>(jobs, m, tiles, s);
 }
 
 }  // namespace ec

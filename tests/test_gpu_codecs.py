@@ -185,3 +185,23 @@ def test_yuv_rle_pipeline_matches_oracle():
     out = ec.yuv_decode(dec, w, h)
     ec.default_context().check_status()
     assert np.array_equal(np_of(out), oracle.yuv_decode(ref_p, w, h))
+
+
+def test_yuv_batch_matches_single_calls():
+    """One launch over images of different sizes and pitches gives what the
+    oracle gives for each."""
+    require_gpu()
+    r = np.random.default_rng(9)
+    shapes = [(1, 1), (5, 3), (64, 129), (333, 200), (2, 8)]
+    imgs = [r.integers(0, 2**32, size=(h, w + 2), dtype=np.uint64).astype(np.uint32) for h, w in shapes]
+    srcs = [_u32(i) for i in imgs]
+    packed = [torch.zeros(ec.yuv_packed_shape(w, h), dtype=torch.int32, device="cuda").view(torch.uint32)
+              for h, w in shapes]
+    ec.yuv_batch([(s, p, w, h) for s, p, (h, w) in zip(srcs, packed, shapes)], True)
+    outs = [torch.zeros((h, w), dtype=torch.int32, device="cuda").view(torch.uint32) for h, w in shapes]
+    ec.yuv_batch([(p, o, w, h) for p, o, (h, w) in zip(packed, outs, shapes)], False)
+    ec.default_context().check_status()
+    for img, p, o, (h, w) in zip(imgs, packed, outs, shapes):
+        ref = oracle.yuv_encode(np.ascontiguousarray(img), w=w)
+        assert np.array_equal(np_of(p), ref)
+        assert np.array_equal(np_of(o), oracle.yuv_decode(ref, w, h))
