@@ -116,7 +116,10 @@ __device__ __forceinline__ int check_header(const uint8_t* h, uint64_t size, uin
 // hold tokens in order.  A warp scan places them; each lane writes the
 // unaligned head and tail bytes of its own repeat token and its aligned body
 // words when there are at most eight of them, the whole warp a longer body,
-// one token per store; literal tokens are copied by the whole warp.  Returns nonzero (the same on every lane) when a token runs
+// one token per store; literal tokens are copied by the whole warp.  Where a
+// window starts with repeat tokens no search is needed (each takes two
+// bytes): lane l reads the pair at offset 2l and the leading repeats, up to
+// 32, are placed with one scan.  Returns nonzero (the same on every lane) when a token runs
 // past its stream or the chunk, or the stream does not yield exactly len bytes.
 // plane must be 4-byte aligned.  src(i) returns stream byte i.
 struct GlobalBytes {
@@ -129,12 +132,69 @@ struct SharedBytes {     // bytes [off, ...) of the payload staged at p
     __device__ __forceinline__ uint32_t operator()(int i) const { return (uint32_t)p[i - off]; }
 };
 
+// Each lane's repeat token (rep): olen copies of byte tv at plane[o, o+olen).
+// The lane writes the unaligned head and tail bytes and a body of at most 8
+// words itself; longer bodies are written by the whole warp, one per store.
+__device__ __forceinline__ void write_repeats(uint8_t* plane, bool rep, int o, int olen, uint32_t tv, int lane)
+{
+    uint32_t* p32 = reinterpret_cast<uint32_t*>(plane);
+    int head = 0, nw = 0;
+    if (rep) {
+        head = min(olen, (4 - (o & 3)) & 3);
+        nw = (olen - head) >> 2;
+        const int tail = olen - head - 4 * nw;
+        for (int k = 0; k < head; ++k) plane[o + k] = (uint8_t)tv;
+        for (int k = 0; k < tail; ++k) plane[o + head + 4 * nw + k] = (uint8_t)tv;
+    }
+    const uint32_t pk = (uint32_t)((o + head) >> 2) | ((uint32_t)nw << 16);
+    const uint32_t wv = 0x01010101u * (tv & 0xFFu);
+    if (nw <= 8)
+        for (int k = 0; k < nw; ++k) p32[((o + head) >> 2) + k] = wv;
+    for (uint32_t m = __ballot_sync(0xffffffffu, nw > 8); m; m &= m - 1u) {
+        const int t = __ffs(m) - 1;
+        const uint32_t q = __shfl_sync(0xffffffffu, pk, t);
+        const uint32_t x = __shfl_sync(0xffffffffu, wv, t);
+        if ((uint32_t)lane < (q >> 16)) p32[(q & 0xFFFFu) + lane] = x;
+    }
+}
+
+__device__ __forceinline__ int warp_incl_sum(int v, int lane)
+{
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += y;
+    }
+    return v;
+}
+
 template <class Src>
 __device__ __forceinline__ int decode_plane(const Src& src, int beg, int end, int len, uint8_t* plane, int lane)
 {
-    uint32_t* p32 = reinterpret_cast<uint32_t*>(plane);
     int cur = beg, outp = 0;
     while (cur < end) {
+        // Fast window: if the bytes at even offsets from cur are repeat
+        // controls, each starts a token (a repeat takes exactly two bytes), so
+        // lane l holds token l without searching; take the leading run of them.
+        {
+            const int i2 = cur + 2 * lane;
+            const uint32_t c = i2 + 1 < end ? src(i2) : 0u;
+            const uint32_t v = i2 + 1 < end ? src(i2 + 1) : 0u;
+            const uint32_t lit = __ballot_sync(0xffffffffu, c < 128u);
+            const int m = lit ? __ffs(lit) - 1 : 32;
+            if (m > 0) {
+                const bool valid = lane < m;
+                const int olen = valid ? (int)c - 127 : 0;
+                const int incl = warp_incl_sum(olen, lane);
+                const int total = __shfl_sync(0xffffffffu, incl, 31);
+                const int o = outp + incl - olen;
+                if (__any_sync(0xffffffffu, valid && o + olen > len)) return 1;
+                write_repeats(plane, valid, o, olen, v, lane);
+                outp += total;
+                cur += 2 * m;
+                continue;
+            }
+        }
         const int i = cur + lane;
         const uint32_t b = i < end ? src(i) : 0u;
         const uint32_t b1 = i + 1 < end ? src(i + 1) : 0u;
@@ -160,35 +220,11 @@ __device__ __forceinline__ int decode_plane(const Src& src, int beg, int end, in
         const bool trep = tb >= 128u;
         const int olen = valid ? (trep ? (int)tb - 127 : (int)tb + 1) : 0;
         const int tnext = pos + (trep ? 2 : 2 + (int)tb);
-        int incl = olen;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int y = __shfl_up_sync(0xffffffffu, incl, o);
-            if (lane >= o) incl += y;
-        }
+        const int incl = warp_incl_sum(olen, lane);
         const int total = __shfl_sync(0xffffffffu, incl, 31);
         const int o = outp + incl - olen;
         if (__any_sync(0xffffffffu, valid && (cur + tnext > end || o + olen > len))) return 1;
-        int head = 0, nw = 0;
-        if (valid && trep) {
-            head = min(olen, (4 - (o & 3)) & 3);
-            nw = (olen - head) >> 2;
-            const int tail = olen - head - 4 * nw;
-            for (int k = 0; k < head; ++k) plane[o + k] = (uint8_t)tv;
-            for (int k = 0; k < tail; ++k) plane[o + head + 4 * nw + k] = (uint8_t)tv;
-        }
-        const uint32_t pk = (uint32_t)((o + head) >> 2) | ((uint32_t)nw << 16);
-        const uint32_t wv = 0x01010101u * (tv & 0xFFu);
-        // a body of at most 8 words is written by its own lane; longer ones by
-        // the whole warp, one token per store
-        if (nw <= 8)
-            for (int k = 0; k < nw; ++k) p32[((o + head) >> 2) + k] = wv;
-        for (uint32_t m = __ballot_sync(0xffffffffu, nw > 8); m; m &= m - 1u) {
-            const int t = __ffs(m) - 1;
-            const uint32_t q = __shfl_sync(0xffffffffu, pk, t);
-            const uint32_t x = __shfl_sync(0xffffffffu, wv, t);
-            if ((uint32_t)lane < (q >> 16)) p32[(q & 0xFFFFu) + lane] = x;
-        }
+        write_repeats(plane, valid && trep, o, olen, tv, lane);
         for (uint32_t m = __ballot_sync(0xffffffffu, valid && !trep); m; m &= m - 1u) {
             const int t = __ffs(m) - 1;
             const int oo = __shfl_sync(0xffffffffu, o, t);
