@@ -103,6 +103,14 @@ void ec_destroy(ec_ctx* ctx);
  * the last call (EC_OK if none) and clear it. */
 ec_status ec_status_sync(ec_ctx* ctx, ec_stream_t s);
 
+/* Self-test of failure detection without a fault: runs the codec's chunk
+ * look-back (the one wait in libec's kernels) for a chunk whose predecessor
+ * never publishes its size.  The wait gives up after its poll limit (2^22
+ * polls with a short sleep; about a second), records EC_ERR_TIMEOUT in the
+ * status word and the kernel returns, leaving the context usable.  Read the
+ * result with ec_status_sync.  Uses the context's codec scratch. */
+ec_status ec_selftest_wait_timeout(ec_ctx* ctx, ec_stream_t s);
+
 /* Human-readable name of a status code (static string). */
 const char* ec_status_string(ec_status st);
 

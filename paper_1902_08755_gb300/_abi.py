@@ -119,6 +119,7 @@ SIGNATURES = {
     "ec_batch_free": (None, [_P]),
     "ec_yuv_encode": (_S, [_P, _P, _I, _I, _I, _P, _I, _P]),
     "ec_yuv_decode": (_S, [_P, _P, _I, _I, _I, _P, _I, _P]),
+    "ec_selftest_wait_timeout": (_S, [_P, _P]),
     "ec_yuv_encode_batch": (_S, [_P, _P, _I, _P]),
     "ec_yuv_decode_batch": (_S, [_P, _P, _I, _P]),
     "ec_schedule_plan": (_S, [_P, _I, _I, _P, _I, _P, _P, C.c_uint32, C.POINTER(C.c_void_p)]),

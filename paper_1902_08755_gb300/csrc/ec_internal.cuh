@@ -290,6 +290,10 @@ ec_status rle_job_desc(const ec_rle_job& j, bool compress, ec::RleJobDesc* d);
 
 namespace ec {
 
+// The codec's look-back on a predecessor that never publishes (scratch: 16
+// bytes); it times out and records EC_ERR_TIMEOUT.
+cudaError_t launch_selftest_lookback(void* scratch, uint32_t* status, cudaStream_t s);
+
 cudaError_t launch_fused_depth(const FusedStage* stages, const FusedUnit* units, int n_units,
                                uint32_t* status, cudaStream_t s);
 

@@ -933,6 +933,14 @@ k_rle0_compress(const __grid_constant__ RleJobList<N> J, uint64_t* flags, uint32
     }
 }
 
+// Self-test of the bounded waits: unit 1 looks back for unit 0, which never
+// publishes its size (flags[0] stays 0); the wait gives up after its poll
+// limit, records EC_ERR_TIMEOUT and the kernel returns.
+__global__ void k_selftest_lookback(uint64_t* flags, uint32_t* status)
+{
+    if (threadIdx.x < 32) look_back(flags, 1u, 0u, 0u, status);
+}
+
 // ----------------------------------------------------------- decompress ----
 
 constexpr int kDT = 128;        // decoder CTA: one warp per byte plane
@@ -1161,6 +1169,14 @@ cudaError_t launch_rle_compress(const RleJobDesc* jobs, int n, uint32_t total_un
     if (n <= 8) return compress_n<8>(jobs, n, total_units, flags, ticket, status, s);
     if (n <= 64) return compress_n<64>(jobs, n, total_units, flags, ticket, status, s);
     return compress_n<kRleJobsPerLaunch>(jobs, n, total_units, flags, ticket, status, s);
+}
+
+cudaError_t launch_selftest_lookback(void* scratch, uint32_t* status, cudaStream_t s)
+{
+    const cudaError_t e = cudaMemsetAsync(scratch, 0, 16, s);
+    if (e != cudaSuccess) return e;
+    k_selftest_lookback<<<1, 32, 0, s>>>(reinterpret_cast<uint64_t*>(scratch), status);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_rle_decompress(const RleJobDesc* jobs, int n, uint32_t total_units,

@@ -171,3 +171,21 @@ def test_8k_frame_and_size_limit():
     with pytest.raises(ec.EcError) as e:
         ec.rle_compress(big, 1)
     assert e.value.code == 5
+
+
+def test_bounded_wait_times_out_and_context_survives():
+    """Failure detection without a fault: the codec's look-back waits on a chunk
+    that never publishes, gives up after its poll limit and records
+    EC_ERR_TIMEOUT; the kernel ends and the context keeps working."""
+    import time
+    from paper_1902_08755_gb300 import _abi as A
+    require_gpu()
+    ctx = ec.default_context()
+    ctx.status_sync()
+    t0 = time.perf_counter()
+    A.check(A.load().ec_selftest_wait_timeout(ctx.h, torch.cuda.current_stream().cuda_stream), "selftest")
+    assert ctx.status_sync() == A.EC_ERR_TIMEOUT
+    assert time.perf_counter() - t0 < 30.0
+    img = S.depth_source(200, 90, 0.4, 42, 0).color.numpy()
+    _roundtrip_check(img, 2)                 # the context still codes correctly
+    assert ctx.status_sync() == 0
