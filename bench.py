@@ -257,18 +257,48 @@ class DepthPipeline:
         return {"rle_compress": raw + comp, "rle_decompress": comp + raw,
                 "composite_depth": 8 * self.units + 8 * self.W * self.H}
 
-    # end to end: sources from pinned host memory, frame back to pinned host memory
+    # end to end: sources from pinned host memory, frame back to pinned host
+    # memory.  The sources are copied in four parts on a copy stream; each
+    # part is compressed and decoded as soon as it has landed, so the codec
+    # overlaps the copies of the later parts.
+    E2E_PARTS = 4
+
     def setup_e2e(self):
+        ec = self.ec
         self.h_planes = [t.view(torch.int32).cpu().pin_memory() for t, _ in self.planes]
         self.h_out = torch.empty((self.H, self.W), dtype=torch.int32).pin_memory()
         self.h_outd = torch.empty((self.H, self.W), dtype=torch.float32).pin_memory()
         self.h2d = sum(t.numel() * 4 for t in self.h_planes)
         self.d2h = self.H * self.W * 8
+        self.copy_stream = torch.cuda.Stream()
+        P = self.E2E_PARTS
+        bounds = [2 * ((len(self.planes) // 2) * k // P) for k in range(P + 1)]   # whole sources per part
+        self.parts = []
+        for k in range(P):
+            lo, hi = bounds[k], bounds[k + 1]
+            if hi <= lo:
+                continue
+            comp, _ = ec.prepare_rle_compress_batch(self.cjobs[lo:hi], ctx=self.ctx)
+            dec, _ = ec.prepare_rle_decompress_batch([(self.bufs[i], self.planes[i][0].shape[1],
+                                                       self.planes[i][0].shape[0], self.dec[i], None)
+                                                      for i in range(lo, hi)], ctx=self.ctx)
+            self.parts.append((lo, hi, comp, dec, torch.cuda.Event()))
+        self.ev_start = torch.cuda.Event()
 
     def e2e_step(self):
-        for (t, _), h in zip(self.planes, self.h_planes):
-            t.view(torch.int32).copy_(h, non_blocking=True)
-        self.step()
+        cur = torch.cuda.current_stream()
+        self.ev_start.record(cur)
+        self.copy_stream.wait_event(self.ev_start)
+        with torch.cuda.stream(self.copy_stream):
+            for lo, hi, _, _, ev in self.parts:
+                for i in range(lo, hi):
+                    self.planes[i][0].view(torch.int32).copy_(self.h_planes[i], non_blocking=True)
+                ev.record(self.copy_stream)
+        for lo, hi, comp, dec, ev in self.parts:
+            cur.wait_event(ev)
+            comp.run()
+            dec.run()
+        self.ec.composite_depth(self.imgs, self.out_c, self.out_d, ctx=self.ctx)
         self.h_out.copy_(self.out_c.view(torch.int32), non_blocking=True)
         self.h_outd.copy_(self.out_d, non_blocking=True)
 
