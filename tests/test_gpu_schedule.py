@@ -186,3 +186,21 @@ def test_argument_errors():
     lay = torch.zeros((32, 32, 4), dtype=torch.float32, device="cuda")
     with pytest.raises(ec.EcError):
         ec.Schedule("alpha", "stream", [ec.Image(color=lay)], lay.clone(), rle=True)
+
+
+def test_alpha_binary_swap_at_full_size():
+    """32 FP32 layers of 2048 x 2048 (the alpha workload's size) through binary
+    swap: within 2e-6 of the FP64 oracle on every pixel."""
+    require_gpu()
+    L, W, H = 32, 2048, 2048
+    lay = SY.alpha_layers(3, L, W, H, 0.3, dtype=torch.float32, device="cuda")
+    out = torch.empty((H, W, 4), dtype=torch.float32, device="cuda")
+    sch = ec.Schedule("alpha", "binary_swap", [ec.Image(color=lay[k]) for k in range(L)], out, rle=False)
+    sch.run()
+    ec.default_context().check_status()
+    host = lay.cpu().numpy()
+    ref, _, _ = oracle.composite_alpha([oracle.Image((0, 0, W, H), (0, 0, W, H), host[k]) for k in range(L)],
+                                       (0, 0, W, H))
+    assert np.abs(np_of(out).astype(np.float64) - ref).max() <= 2e-6
+    assert sch.info()["levels"] == 5
+    sch.close()
