@@ -317,6 +317,14 @@ typedef struct ec_schedule ec_schedule;
 ec_status ec_schedule_plan(ec_ctx* ctx, int32_t mode, int32_t algorithm, const ec_image* in,
                            int32_t n, const int32_t* order, const ec_target* out, uint32_t flags,
                            ec_schedule** plan);
+/* Host only, no device work: the transfers (in stage order, fused = 0) that a
+ * schedule of n resources whose data lies in rois[i] (out->pvp coordinates)
+ * makes in frame, the number of stages, and (regions, n entries, may be NULL)
+ * the region each resource owns at the end.  *n_messages receives the count
+ * even when cap is too small (EC_ERR_CAPACITY). */
+ec_status ec_schedule_geometry(int32_t algorithm, const ec_rect* rois, int32_t n, ec_rect frame,
+                               ec_sched_message* msgs, int32_t cap, int32_t* n_messages,
+                               int32_t* n_levels, ec_rect* regions);
 /* Enqueue the captured schedule on stream s. */
 ec_status ec_schedule_run(ec_schedule* plan, ec_stream_t s);
 /* Stages, transfers, kernel launches per run and arena bytes (host pointers, any may be NULL). */

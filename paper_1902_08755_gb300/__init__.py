@@ -47,6 +47,7 @@ from .api import (  # noqa: F401
     rle_decompress,
     rle_decompress_batch,
     rle_max_size,
+    schedule_geometry,
     yuv_batch,
     yuv_decode,
     yuv_encode,

@@ -124,6 +124,7 @@ SIGNATURES = {
     "ec_yuv_decode_batch": (_S, [_P, _P, _I, _P]),
     "ec_schedule_plan": (_S, [_P, _I, _I, _P, _I, _P, _P, C.c_uint32, C.POINTER(C.c_void_p)]),
     "ec_schedule_run": (_S, [_P, _P]),
+    "ec_schedule_geometry": (_S, [_I, _P, _I, ec_rect, _P, _I, _P, _P, _P]),
     "ec_schedule_info": (_S, [_P, _P, _P, _P, _P]),
     "ec_schedule_messages": (_S, [_P, _P, _I]),
     "ec_schedule_launches": (_S, [_P, _P, _I]),

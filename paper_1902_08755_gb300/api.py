@@ -618,6 +618,25 @@ SCHEDULES = {"stream": A.EC_SCHED_STREAM, "direct_send": A.EC_SCHED_DIRECT_SEND,
              "binary_swap": A.EC_SCHED_BINARY_SWAP, "two_three_swap": A.EC_SCHED_TWO_THREE_SWAP}
 
 
+def schedule_geometry(algorithm: str, rois, frame):
+    """ec_schedule_geometry (host only): ([(level, sender, receiver, (x, y, w, h))],
+    n_levels, [final region per resource]) of a schedule over resources whose
+    data lies in rois (frame coordinates)."""
+    n = len(rois)
+    arr = (ec_rect * max(1, n))(*[_rect(r) for r in rois])
+    regions = (ec_rect * max(1, n))()
+    nm, nl = C.c_int32(), C.c_int32()
+    code = _lib().ec_schedule_geometry(SCHEDULES[algorithm], arr, n, _rect(frame), None, 0, C.byref(nm),
+                                       C.byref(nl), regions)
+    if code not in (A.EC_OK, A.EC_ERR_CAPACITY):
+        check(code, "ec_schedule_geometry")
+    msgs = (A.ec_sched_message * max(1, nm.value))()
+    check(_lib().ec_schedule_geometry(SCHEDULES[algorithm], arr, n, _rect(frame), msgs, nm.value, C.byref(nm),
+                                      C.byref(nl), regions), "ec_schedule_geometry")
+    return ([(m.level, m.sender, m.receiver, (m.piece.x, m.piece.y, m.piece.w, m.piece.h)) for m in msgs[:nm.value]],
+            nl.value, [(r.x, r.y, r.w, r.h) for r in regions[:n]])
+
+
 class Schedule:
     """ec_schedule: a multi-stage compositing schedule (thesis 5.2.2, 5.2.3)
     captured in a CUDA graph.

@@ -810,6 +810,42 @@ ec_status ec_schedule_plan(ec_ctx* ctx, int32_t mode, int32_t algorithm, const e
     return EC_OK;
 }
 
+ec_status ec_schedule_geometry(int32_t algorithm, const ec_rect* rois, int32_t n, ec_rect frame,
+                               ec_sched_message* msgs, int32_t cap, int32_t* n_messages, int32_t* n_levels,
+                               ec_rect* regions)
+{
+    if (n < 1 || !rois || cap < 0 || (cap > 0 && !msgs) || frame.w < 0 || frame.h < 0) return EC_ERR_INVALID_ARG;
+    if (n > EC_MAX_SOURCES) return EC_ERR_UNSUPPORTED;
+    Planner P;
+    P.n = n;
+    P.frame = frame;
+    for (int i = 0; i < n; ++i) {
+        if (rois[i].w < 0 || rois[i].h < 0) return EC_ERR_INVALID_ARG;
+        P.roi.push_back(isect(rois[i], frame));
+    }
+    const ec_status st = P.plan(algorithm);
+    if (st != EC_OK) return st;
+    int32_t m = 0;
+    for (size_t li = 0; li < P.levels.size(); ++li)
+        for (const Stage& sg : P.levels[li])
+            for (const Piece& p : sg.pieces) {
+                if (p.sender == sg.receiver) continue;
+                if (m < cap) {
+                    msgs[m].level = (int32_t)li;
+                    msgs[m].sender = p.sender;
+                    msgs[m].receiver = sg.receiver;
+                    msgs[m].fused = 0;
+                    msgs[m].piece = p.r;
+                }
+                ++m;
+            }
+    if (n_messages) *n_messages = m;
+    if (n_levels) *n_levels = (int32_t)P.levels.size();
+    if (regions)
+        for (int i = 0; i < n; ++i) regions[i] = P.region[i];
+    return m > cap ? EC_ERR_CAPACITY : EC_OK;
+}
+
 ec_status ec_schedule_run(ec_schedule* S, ec_stream_t s)
 {
     if (!S || !S->exec) return EC_ERR_INVALID_ARG;
