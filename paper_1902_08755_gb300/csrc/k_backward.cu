@@ -163,10 +163,12 @@ k_alpha_bwd(const __grid_constant__ BwdList<N> L, const __grid_constant__ DstDes
     __shared__ int nact_s;
     BandTile* tiles = reinterpret_cast<BandTile*>(smem);                    // [cap]
     const int NS = (int)(blockDim.x / 32);
-    // per segment and pixel: [NS][PX][32], pixel (lane, q) at q * 32 + lane
-    float* Ps = reinterpret_cast<float*>(smem + (size_t)cap * sizeof(BandTile));
-    float* As = Ps + NS * TW;
-    float4* Cs = reinterpret_cast<float4*>(As + NS * TW);                   // (fused)
+    // per row parity, segment and pixel: [2][NS][PX][32], pixel (lane, q) at
+    // q * 32 + lane.  Rows alternate between the two copies, so a row's writes
+    // never meet the previous row's reads and one barrier per row suffices.
+    float* const Ps0 = reinterpret_cast<float*>(smem + (size_t)cap * sizeof(BandTile));
+    float* const As0 = Ps0 + 2 * NS * TW;
+    float4* const Cs0 = reinterpret_cast<float4*>(As0 + 2 * NS * TW);       // (fused)
 
     const int lane = threadIdx.x & 31, sg = threadIdx.x / 32;
     const int tx0 = blockIdx.x * TW, ty0 = blockIdx.y * kRows;
@@ -207,6 +209,9 @@ k_alpha_bwd(const __grid_constant__ BwdList<N> L, const __grid_constant__ DstDes
 
     auto row_pass = [&](auto full_c, int y) {
         constexpr bool FULL = decltype(full_c)::value;
+        float* const Ps = Ps0 + (y & 1) * NS * TW;
+        float* const As = As0 + (y & 1) * NS * TW;
+        float4* const Cs = Cs0 + (y & 1) * NS * TW;
         float4 gp[PX];
 #pragma unroll
         for (int q = 0; q < PX; ++q)
@@ -294,10 +299,12 @@ k_alpha_bwd(const __grid_constant__ BwdList<N> L, const __grid_constant__ DstDes
             for (int u = NS - 1; u > sg; --u) R[q] = fmaf(Ps[u * TW + q * 32 + lane], R[q], As[u * TW + q * 32 + lane]);
         }
 
-        if (FUSED && sg == 0) {
+        if (FUSED && sg < PX) {
+            // warp q (warp 0 alone in one-warp CTAs) composites the segments'
+            // partial outputs of pixel q
 #pragma unroll
             for (int q = 0; q < PX; ++q) {
-                if (!valid[q]) continue;
+                if (q % NS != sg || !valid[q]) continue;
                 float Tacc = 1.0f;
                 float4 out = make_float4(0.f, 0.f, 0.f, 0.f);
                 for (int u = 0; u < NS; ++u) {
@@ -361,7 +368,6 @@ k_alpha_bwd(const __grid_constant__ BwdList<N> L, const __grid_constant__ DstDes
                 for (int q = 0; q < PX; ++q) R[q] = fmaf(1.0f - al[j][q], R[q], gcl[j][q]);
             }
         }
-        __syncthreads();                      // Ps / As / Cs are rewritten for the next row
     };
     if (full) {
         for (int y = ty0; y < ty1; ++y) row_pass(std::true_type{}, y);
@@ -446,7 +452,7 @@ template <int N, bool F16, bool G16, bool FUSED, int PX, int MS>
 cudaError_t alpha_bwd_n(const BwdDesc* d, int n, const DstDesc& D, const float4* g, cudaStream_t s)
 {
     const int ns = alpha_bwd_warps(n, MS), cap = std::max(n, 1), tw = 32 * PX;
-    const size_t smem = (size_t)cap * sizeof(BandTile) + (size_t)ns * tw * (8 + (FUSED ? 16 : 0));
+    const size_t smem = (size_t)cap * sizeof(BandTile) + 2 * (size_t)ns * tw * (8 + (FUSED ? 16 : 0));
     auto kern = k_alpha_bwd<N, F16, G16, FUSED, PX, MS>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
