@@ -215,10 +215,13 @@ __device__ __forceinline__ float4 pixel_of(const uint4& v, int j)
 }
 
 // Front-to-back "over" of the active layers at the thread's PX pixels, U
-// layers' loads in flight per thread.
+// layers' loads in flight per thread.  full (uniform over the CTA): every
+// active layer's ROI covers the CTA's whole tile, so the per-layer and
+// per-pixel range tests are skipped (pixels past the frame's right edge are
+// computed but never stored).
 template <bool F16, class At, int U = 8>
 __device__ __forceinline__ void alpha_px(At at, const int16_t* act, int nact, int x, int y,
-                                         const DstDesc& D)
+                                         const DstDesc& D, bool full = false)
 {
     constexpr int PX = F16 ? 2 : 1;      // pixels per 16 bytes
     float4 acc[PX];
@@ -236,7 +239,7 @@ __device__ __forceinline__ void alpha_px(At at, const int16_t* act, int nact, in
             live[u] = false;
             if (idx[u] >= 0) {
                 const SrcDesc& s = at(a + u, idx[u]);
-                live[u] = y >= s.y0 && y < s.y1 && x + PX > s.x0 && x < s.x1;
+                live[u] = full || (y >= s.y0 && y < s.y1 && x + PX > s.x0 && x < s.x1);
                 if (live[u]) raw[u] = load_raw<F16>(s, x, y);
             }
         }
@@ -247,7 +250,7 @@ __device__ __forceinline__ void alpha_px(At at, const int16_t* act, int nact, in
 #pragma unroll
             for (int j = 0; j < PX; ++j) {
                 const int xj = x + j;
-                if (xj < s.x0 || xj >= s.x1) continue;   // transparent outside the ROI
+                if (!full && (xj < s.x0 || xj >= s.x1)) continue;   // transparent outside the ROI
                 const float4 c = pixel_of<F16>(raw[u], j);
                 // C += T c (premultiplied, all four channels); T *= (1 - a)
                 acc[j].x = fmaf(T[j], c.x, acc[j].x);

@@ -51,11 +51,24 @@ k_alpha_fwd(const __grid_constant__ SrcList<N> L, const __grid_constant__ DstDes
 
     const int lane = threadIdx.x & 31, row = threadIdx.x >> 5;
     const int tx0 = blockIdx.x * kTW, ty0 = blockIdx.y * kRows;
-    build_active(at, L.n, tx0, ty0, min(tx0 + kTW, D.W), min(ty0 + kRows, D.H), act, &nact_s);
+    const int tx1 = min(tx0 + kTW, D.W), ty1 = min(ty0 + kRows, D.H);
+    build_active(at, L.n, tx0, ty0, tx1, ty1, act, &nact_s);
     __syncthreads();
+    const int nact = nact_s;
+    // FP16 tiles that every active layer covers skip the range tests (FP32
+    // keeps one path: its second path would cost more registers than it saves)
+    bool full = false;
+    if constexpr (F16) {
+        bool covers = true;
+        for (int k = threadIdx.x; k < nact; k += kThreads) {
+            const SrcDesc& s = L.s[act[k]];
+            covers = covers && s.x0 <= tx0 && s.x1 >= tx1 && s.y0 <= ty0 && s.y1 >= ty1;
+        }
+        full = __syncthreads_and(covers);
+    }
     const int x = tx0 + lane * PX, y = ty0 + row;
     if (x >= D.W || y >= D.H) return;
-    alpha_px<F16>(at, act, nact_s, x, y, D);
+    alpha_px<F16>(at, act, nact, x, y, D, full);
 }
 
 template <int N>
