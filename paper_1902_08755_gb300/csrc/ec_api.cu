@@ -447,8 +447,11 @@ static ec_status yuv_batch(ec_ctx* ctx, const ec_yuv_job* jobs, int32_t njobs, b
         y.h = j.h;
         y.pitch = j.pitch;
         y.dpitch = j.packed_pitch;
-        const void* rgba = encode ? j.src : j.dst;
-        y.vec = (reinterpret_cast<uintptr_t>(rgba) & 7u) == 0 && j.pitch % 2 == 0;
+        const uintptr_t rgba = reinterpret_cast<uintptr_t>(encode ? j.src : j.dst);
+        const uintptr_t packed = reinterpret_cast<uintptr_t>(encode ? j.dst : j.src);
+        y.vec = ((rgba & 7u) == 0 && j.pitch % 2 == 0 ? 1 : 0) |          // 8-byte RGBA pairs
+                ((rgba & 15u) == 0 && j.pitch % 4 == 0 ? 2 : 0) |         // 16-byte RGBA quads
+                ((packed & 7u) == 0 && j.packed_pitch % 2 == 0 ? 4 : 0);  // 8-byte packed word pairs
         d.push_back(y);
     }
     DeviceGuard g(ctx->device);

@@ -306,7 +306,7 @@ struct YuvJob {
     int32_t w, h, pitch, dpitch;
     uint32_t first;      // first CTA tile of this image
     uint32_t tiles_x;    // CTA tiles per row of blocks
-    int32_t vec;         // the RGBA8 side allows 8-byte accesses
+    int32_t vec;         // bits: RGBA8 side 8-byte (1) / 16-byte (2) accesses, packed side 8-byte (4)
     int32_t pad;
 };
 static_assert(sizeof(YuvJob) == 48, "yuv job layout");

@@ -9,17 +9,26 @@
 // pixel (2bx + (k & 1), 2by + (k >> 1)), 0 where the image has no pixel),
 // rows [ceil(h/2), 2 ceil(h/2)) chroma words (bytes U, V, A, 0).
 //
-// One thread per block; a row pair of the block is one 8-byte access where
-// the buffer allows it.  A launch covers many images: CTA tiles of 32 x 8
-// blocks are numbered across the images and each CTA finds its image by a
-// binary search of the images' first tiles.  Both kernels are HBM-bound: 4
-// bytes read and 2 written per pixel to encode, the reverse to decode.
+// Each thread owns NP pairs of horizontally adjacent blocks, 32 pairs apart,
+// so every load instruction of a warp covers 512 contiguous bytes.  A row
+// pair of two blocks is one 16-byte access, and their two luma or chroma
+// words one 8-byte access, where the buffers allow it.  All of a thread's
+// loads are issued before any result is computed.  One block per thread left
+// HBM idle between waves of short loads; the decoder takes two pairs per
+// thread, the encoder one (a second pair's registers cost it more occupancy
+// than its loads gain).  A launch covers many images: CTA tiles of 32 NP
+// pairs x 8 block rows are numbered across the images and each CTA finds its
+// image by a binary search of the images' first tiles.  Both kernels are
+// HBM-bound: 4 bytes read and 2 written per pixel to encode, the reverse to
+// decode.
 #include "ec_internal.cuh"
 
 namespace ec {
 namespace {
 
-constexpr int kYX = 32, kYY = 8;     // blocks per CTA: 32 x 8
+constexpr int kYX = 32, kYY = 8;     // threads per CTA: 32 x 8
+constexpr int kEncNP = 1, kDecNP = 2; // block pairs per thread
+constexpr int kVec8 = 1, kVec16 = 2, kPacked8 = 4;   // YuvJob::vec bits
 
 // floor(x / 256) for x > -2^20
 __device__ __forceinline__ int floor256(int x) { return ((x + (1 << 20)) >> 8) - (1 << 12); }
@@ -33,9 +42,11 @@ __device__ __forceinline__ void to_yuv(uint32_t p, int& Y, int& U, int& V)
     V = min(255, (128 * R - 107 * G - 21 * B + 32896) >> 8);
 }
 
-// CTA tile t of a job list: the job whose tiles [first, first + ntiles) hold it.
-template <int N>
-__device__ __forceinline__ const YuvJob& tile_job(const YuvJobList<N>& J, uint32_t t, int& bx, int& by)
+// CTA tile t of a job list: the job whose tiles [first, first + ntiles) hold
+// it; bp = the thread's first block pair (its others follow 32 pairs apart),
+// by = its block row.
+template <int NP, int N>
+__device__ __forceinline__ const YuvJob& tile_job(const YuvJobList<N>& J, uint32_t t, int& bp, int& by)
 {
     int lo = 0, hi = J.n - 1;
     while (lo < hi) {
@@ -45,32 +56,24 @@ __device__ __forceinline__ const YuvJob& tile_job(const YuvJobList<N>& J, uint32
     }
     const YuvJob& jb = J.j[lo];
     const uint32_t r = t - jb.first, tx = r % jb.tiles_x;
-    bx = (int)(tx * kYX) + threadIdx.x;
+    bp = (int)(tx * kYX * NP) + threadIdx.x;
     by = (int)((r / jb.tiles_x) * kYY) + threadIdx.y;
     return jb;
 }
 
-template <int N>
-__global__ void __launch_bounds__(kYX * kYY)
-k_yuv_encode(const __grid_constant__ YuvJobList<N> J)
+// The up to four pixels of block column b (pixel k at (2b + (k & 1), 2by + (k >> 1))).
+__device__ __forceinline__ void load_block(const uint32_t* src, int pitch, int w, int h, int b, int by, bool vec8,
+                                           uint32_t (&px)[4], bool (&has)[4])
 {
-    int bx, by;
-    const YuvJob& jb = tile_job(J, blockIdx.x, bx, by);
-    const uint32_t* __restrict__ src = jb.src;
-    uint32_t* __restrict__ dst = jb.dst;
-    const int w = jb.w, h = jb.h, pitch = jb.pitch, dpitch = jb.dpitch;
-    const bool vec = jb.vec;
-    const int bw = (w + 1) >> 1, bh = (h + 1) >> 1;
-    if (bx >= bw || by >= bh) return;
-    const int x = 2 * bx;
-    uint32_t px[4] = {0u, 0u, 0u, 0u};
-    bool has[4] = {false, false, false, false};
+    const int x = 2 * b;
 #pragma unroll
     for (int r = 0; r < 2; ++r) {
         const int y = 2 * by + r;
+        has[2 * r] = has[2 * r + 1] = false;
+        px[2 * r] = px[2 * r + 1] = 0u;
         if (y >= h) continue;
         const uint32_t* row = src + (size_t)y * pitch;
-        if (vec && x + 1 < w) {
+        if (vec8 && x + 1 < w) {
             const uint2 v = __ldcs(reinterpret_cast<const uint2*>(row + x));
             px[2 * r] = v.x;
             px[2 * r + 1] = v.y;
@@ -84,7 +87,13 @@ k_yuv_encode(const __grid_constant__ YuvJobList<N> J)
             }
         }
     }
-    uint32_t luma = 0u;
+}
+
+// Luma word and chroma word (U, V, A, 0) of one block.
+__device__ __forceinline__ void encode_block(const uint32_t (&px)[4], const bool (&has)[4], uint32_t& luma,
+                                             uint32_t& chroma)
+{
+    luma = 0u;
     int su = 0, sv = 0, sa = 0, cnt = 0;
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
@@ -99,46 +108,150 @@ k_yuv_encode(const __grid_constant__ YuvJobList<N> J)
     }
     const int sh = cnt == 4 ? 2 : (cnt == 2 ? 1 : 0);          // cnt is 1, 2 or 4
     const int half = cnt >> 1;
-    dst[(size_t)by * dpitch + bx] = luma;
-    dst[(size_t)(bh + by) * dpitch + bx] = (uint32_t)((su + half) >> sh) | ((uint32_t)((sv + half) >> sh) << 8) |
-                                          ((uint32_t)((sa + half) >> sh) << 16);
+    chroma = (uint32_t)((su + half) >> sh) | ((uint32_t)((sv + half) >> sh) << 8) |
+             ((uint32_t)((sa + half) >> sh) << 16);
 }
 
 template <int N>
 __global__ void __launch_bounds__(kYX * kYY)
-k_yuv_decode(const __grid_constant__ YuvJobList<N> J)
+k_yuv_encode(const __grid_constant__ YuvJobList<N> J)
 {
-    int bx, by;
-    const YuvJob& jb = tile_job(J, blockIdx.x, bx, by);
+    constexpr int kNP = kEncNP;
+    int bp, by;
+    const YuvJob& jb = tile_job<kNP>(J, blockIdx.x, bp, by);
     const uint32_t* __restrict__ src = jb.src;
     uint32_t* __restrict__ dst = jb.dst;
-    const int w = jb.w, h = jb.h, pitch = jb.pitch, spitch = jb.dpitch;
-    const bool vec = jb.vec;
+    const int w = jb.w, h = jb.h, pitch = jb.pitch, dpitch = jb.dpitch, vec = jb.vec;
     const int bw = (w + 1) >> 1, bh = (h + 1) >> 1;
-    if (bx >= bw || by >= bh) return;
-    const uint32_t luma = __ldcs(src + (size_t)by * spitch + bx);
-    const uint32_t ch = __ldcs(src + (size_t)(bh + by) * spitch + bx);
+    if (by >= bh) return;
+    uint32_t p0[kNP][4], p1[kNP][4];
+    bool h0[kNP][4], h1[kNP][4];
+#pragma unroll
+    for (int q = 0; q < kNP; ++q) {              // every load first
+        const int b0 = 2 * (bp + 32 * q), x = 2 * b0;
+        if (b0 >= bw) continue;
+        if ((vec & kVec16) && x + 3 < w) {
+#pragma unroll
+            for (int r = 0; r < 2; ++r) {
+                const int y = 2 * by + r;
+                const bool in = y < h;
+                const uint4 v = in ? __ldcs(reinterpret_cast<const uint4*>(src + (size_t)y * pitch + x))
+                                   : make_uint4(0u, 0u, 0u, 0u);
+                p0[q][2 * r] = v.x; p0[q][2 * r + 1] = v.y; p1[q][2 * r] = v.z; p1[q][2 * r + 1] = v.w;
+                h0[q][2 * r] = h0[q][2 * r + 1] = h1[q][2 * r] = h1[q][2 * r + 1] = in;
+            }
+        } else {
+            load_block(src, pitch, w, h, b0, by, vec & kVec8, p0[q], h0[q]);
+            if (b0 + 1 < bw) load_block(src, pitch, w, h, b0 + 1, by, vec & kVec8, p1[q], h1[q]);
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < kNP; ++q) {
+        const int b0 = 2 * (bp + 32 * q);
+        if (b0 >= bw) continue;
+        const bool two = b0 + 1 < bw;
+        uint32_t l0, c0, l1 = 0u, c1 = 0u;
+        encode_block(p0[q], h0[q], l0, c0);
+        if (two) encode_block(p1[q], h1[q], l1, c1);
+        uint32_t* lrow = dst + (size_t)by * dpitch + b0;
+        uint32_t* crow = dst + (size_t)(bh + by) * dpitch + b0;
+        if (two && (vec & kPacked8)) {
+            *reinterpret_cast<uint2*>(lrow) = make_uint2(l0, l1);
+            *reinterpret_cast<uint2*>(crow) = make_uint2(c0, c1);
+        } else {
+            lrow[0] = l0;
+            crow[0] = c0;
+            if (two) {
+                lrow[1] = l1;
+                crow[1] = c1;
+            }
+        }
+    }
+}
+
+// The four RGBA8 pixels of one block from its luma and chroma words.
+__device__ __forceinline__ void decode_block(uint32_t luma, uint32_t ch, uint32_t (&px)[4])
+{
     const int U = (int)(ch & 0xFFu) - 128, V = (int)((ch >> 8) & 0xFFu) - 128;
     const uint32_t A = (ch >> 16) & 0xFFu;
     const int dR = floor256(359 * V + 128), dG = floor256(88 * U + 183 * V + 128), dB = floor256(454 * U + 128);
-    uint32_t px[4];
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
         const int Y = (int)((luma >> (8 * k)) & 0xFFu);
         px[k] = (uint32_t)clamp8(Y + dR) | ((uint32_t)clamp8(Y - dG) << 8) | ((uint32_t)clamp8(Y + dB) << 16) |
                 (A << 24);
     }
-    const int x = 2 * bx;
+}
+
+__device__ __forceinline__ void store_block(uint32_t* dst, int pitch, int w, int h, int b, int by, bool vec8,
+                                            const uint32_t (&px)[4])
+{
+    const int x = 2 * b;
 #pragma unroll
     for (int r = 0; r < 2; ++r) {
         const int y = 2 * by + r;
         if (y >= h) continue;
         uint32_t* row = dst + (size_t)y * pitch;
-        if (vec && x + 1 < w) {
+        if (vec8 && x + 1 < w) {
             __stcs(reinterpret_cast<uint2*>(row + x), make_uint2(px[2 * r], px[2 * r + 1]));
         } else {
             __stcs(row + x, px[2 * r]);
             if (x + 1 < w) __stcs(row + x + 1, px[2 * r + 1]);
+        }
+    }
+}
+
+template <int N>
+__global__ void __launch_bounds__(kYX * kYY)
+k_yuv_decode(const __grid_constant__ YuvJobList<N> J)
+{
+    constexpr int kNP = kDecNP;
+    int bp, by;
+    const YuvJob& jb = tile_job<kNP>(J, blockIdx.x, bp, by);
+    const uint32_t* __restrict__ src = jb.src;
+    uint32_t* __restrict__ dst = jb.dst;
+    const int w = jb.w, h = jb.h, pitch = jb.pitch, spitch = jb.dpitch, vec = jb.vec;
+    const int bw = (w + 1) >> 1, bh = (h + 1) >> 1;
+    if (by >= bh) return;
+    uint32_t l0[kNP], c0[kNP], l1[kNP], c1[kNP];
+#pragma unroll
+    for (int q = 0; q < kNP; ++q) {              // every load first
+        const int b0 = 2 * (bp + 32 * q);
+        l0[q] = c0[q] = l1[q] = c1[q] = 0u;
+        if (b0 >= bw) continue;
+        const uint32_t* lrow = src + (size_t)by * spitch + b0;
+        const uint32_t* crow = src + (size_t)(bh + by) * spitch + b0;
+        if (b0 + 1 < bw && (vec & kPacked8)) {
+            const uint2 l = __ldcs(reinterpret_cast<const uint2*>(lrow));
+            const uint2 c = __ldcs(reinterpret_cast<const uint2*>(crow));
+            l0[q] = l.x; l1[q] = l.y; c0[q] = c.x; c1[q] = c.y;
+        } else {
+            l0[q] = __ldcs(lrow);
+            c0[q] = __ldcs(crow);
+            if (b0 + 1 < bw) {
+                l1[q] = __ldcs(lrow + 1);
+                c1[q] = __ldcs(crow + 1);
+            }
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < kNP; ++q) {
+        const int b0 = 2 * (bp + 32 * q), x = 2 * b0;
+        if (b0 >= bw) continue;
+        uint32_t p0[4], p1[4];
+        decode_block(l0[q], c0[q], p0);
+        decode_block(l1[q], c1[q], p1);
+        if ((vec & kVec16) && x + 3 < w) {
+#pragma unroll
+            for (int r = 0; r < 2; ++r) {
+                const int y = 2 * by + r;
+                if (y < h)
+                    __stcs(reinterpret_cast<uint4*>(dst + (size_t)y * pitch + x),
+                           make_uint4(p0[2 * r], p0[2 * r + 1], p1[2 * r], p1[2 * r + 1]));
+            }
+        } else {
+            store_block(dst, pitch, w, h, b0, by, vec & kVec8, p0);
+            if (b0 + 1 < bw) store_block(dst, pitch, w, h, b0 + 1, by, vec & kVec8, p1);
         }
     }
 }
@@ -165,7 +278,8 @@ cudaError_t launch_yuv(YuvJob* jobs, int n, bool encode, cudaStream_t s)
         const int bw = (jobs[i].w + 1) / 2, bh = (jobs[i].h + 1) / 2;
         if (bw <= 0 || bh <= 0) continue;
         jobs[m] = jobs[i];
-        jobs[m].tiles_x = (uint32_t)((bw + kYX - 1) / kYX);
+        const int per = 2 * kYX * (encode ? kEncNP : kDecNP);   // block columns per CTA tile
+        jobs[m].tiles_x = (uint32_t)((bw + per - 1) / per);
         jobs[m].first = tiles;
         tiles += jobs[m].tiles_x * (uint32_t)((bh + kYY - 1) / kYY);
         ++m;

@@ -205,3 +205,36 @@ def test_yuv_batch_matches_single_calls():
         ref = oracle.yuv_encode(np.ascontiguousarray(img), w=w)
         assert np.array_equal(np_of(p), ref)
         assert np.array_equal(np_of(o), oracle.yuv_decode(ref, w, h))
+
+
+@pytest.mark.parametrize("h,w,pad,col,ppad", [
+    (9, 13, 3, 0, 1),      # pitch 16: 16-byte quads, ragged last block pair, odd height
+    (8, 12, 0, 0, 1),      # 16-byte quads, packed pitch 7 (no 8-byte word pairs)
+    (5, 7, 1, 1, 0),       # view one column in: 4-byte aligned only, scalar path
+    (6, 10, 2, 2, 2),      # view two columns in: 8-byte aligned, 8-byte pairs
+    (7, 17, 3, 4, 1),      # view four columns in: 16-byte aligned again
+    (1, 4, 0, 0, 0),       # one pixel row
+    (33, 530, 2, 0, 3),    # several CTA tiles wide, ragged
+])
+def test_yuv_access_widths(h, w, pad, col, ppad):
+    """The encoder and decoder take 16-byte, 8-byte or 4-byte accesses on the
+    RGBA side and 8- or 4-byte ones on the packed side, by alignment; every
+    combination gives the oracle's bits and writes nothing outside its image."""
+    require_gpu()
+    r = np.random.default_rng(h * 1000 + w * 10 + col)
+    big = r.integers(0, 2**32, size=(h, col + w + pad), dtype=np.uint64).astype(np.uint32)
+    src = _u32(big)[:, col:col + w]
+    rows, words = ec.yuv_packed_shape(w, h)
+    pbig = torch.full((rows, words + ppad), 0x22222222, dtype=torch.int32, device="cuda").view(torch.uint32)
+    packed = pbig[:, :words]
+    ec.yuv_encode(src, w=w, out=packed)
+    ec.default_context().check_status()
+    ref = oracle.yuv_encode(np.ascontiguousarray(big[:, col:col + w]))
+    assert np.array_equal(np_of(packed), ref)
+    assert (np_of(pbig)[:, words:].view(np.int32) == 0x22222222).all()
+    obig = torch.full((h, col + w + pad), 0x11111111, dtype=torch.int32, device="cuda").view(torch.uint32)
+    ec.yuv_decode(packed, w, h, out=obig[:, col:col + w])
+    ec.default_context().check_status()
+    o = np_of(obig)
+    assert np.array_equal(o[:, col:col + w], oracle.yuv_decode(ref, w, h))
+    assert (o[:, :col].view(np.int32) == 0x11111111).all() and (o[:, col + w:].view(np.int32) == 0x11111111).all()
