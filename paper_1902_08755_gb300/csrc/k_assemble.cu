@@ -269,39 +269,51 @@ template <int N, int BPP>
 __global__ void __launch_bounds__(kAT)
 k_assemble_pixels(const __grid_constant__ PixList<N> P, const __grid_constant__ DstDesc D)
 {
-    constexpr int PX = Grp<BPP>::PX;
+    constexpr int PX = Grp<BPP>::PX, WPP = BPP / 4;
     const int lane = threadIdx.x & 31, row = threadIdx.x >> 5;
-    const int x = blockIdx.x * (32 * PX) + lane * PX, y = blockIdx.y * kARows + row;
-    if (x >= D.W || y >= D.H) return;
-    const int ry = y % P.ny, j0 = y / P.ny;
-    int rx = x % P.nx, i0 = x / P.nx;                   // one division; then step the residue
-    uint32_t w[PX][BPP / 4];
-    uint32_t have = 0;
+    const int x = blockIdx.x * (32 * PX) + lane * PX;
+    if (x >= D.W) return;
+    const int i00 = x / P.nx, rx00 = x - i00 * P.nx;    // one division; then step the residue
+    // kAPasses rows per thread, every load issued before any store
+    uint32_t w[kAPasses][PX][WPP];
+    uint32_t have[kAPasses];
 #pragma unroll
-    for (int j = 0; j < PX; ++j) {
-        const int xj = x + j;
-        const int k = xj < D.W ? P.owner[ry * P.nx + rx] : -1;
-        if (k >= 0) {
-            const PixSrc& s = P.s[k];
-            const size_t e = (size_t)j0 * (size_t)s.pitch + (size_t)i0;
-            load_px<BPP>(reinterpret_cast<const uint8_t*>(s.color) + e * BPP, w[j]);
-            have |= 1u << j;
+    for (int pass = 0; pass < kAPasses; ++pass) {
+        const int y = blockIdx.y * (kARows * kAPasses) + pass * kARows + row;
+        have[pass] = 0u;
+        if (y >= D.H) continue;
+        const int ry = y % P.ny, j0 = y / P.ny;
+        int rx = rx00, i0 = i00;
+#pragma unroll
+        for (int j = 0; j < PX; ++j) {
+            const int xj = x + j;
+            const int k = xj < D.W ? P.owner[ry * P.nx + rx] : -1;
+            if (k >= 0) {
+                const PixSrc& s = P.s[k];
+                const size_t e = (size_t)j0 * (size_t)s.pitch + (size_t)i0;
+                load_px<BPP>(reinterpret_cast<const uint8_t*>(s.color) + e * BPP, w[pass][j]);
+                have[pass] |= 1u << j;
+            }
+            if (++rx == P.nx) { rx = 0; ++i0; }
         }
-        if (++rx == P.nx) { rx = 0; ++i0; }
     }
-    if (!have) return;
-    uint8_t* o = reinterpret_cast<uint8_t*>(D.color) + ((size_t)y * (size_t)D.pitch + (size_t)x) * BPP;
-    if (have == (1u << PX) - 1u && D.vec) {
-        uint32_t vv[4];
 #pragma unroll
-        for (int j = 0; j < PX; ++j)
+    for (int pass = 0; pass < kAPasses; ++pass) {
+        if (!have[pass]) continue;
+        const int y = blockIdx.y * (kARows * kAPasses) + pass * kARows + row;
+        uint8_t* o = reinterpret_cast<uint8_t*>(D.color) + ((size_t)y * (size_t)D.pitch + (size_t)x) * BPP;
+        if (have[pass] == (1u << PX) - 1u && D.vec) {
+            uint32_t vv[4];
 #pragma unroll
-            for (int k = 0; k < BPP / 4; ++k) vv[j * (BPP / 4) + k] = w[j][k];
-        __stcs(reinterpret_cast<uint4*>(o), make_uint4(vv[0], vv[1], vv[2], vv[3]));
-    } else {
+            for (int j = 0; j < PX; ++j)
 #pragma unroll
-        for (int j = 0; j < PX; ++j)
-            if ((have >> j) & 1u) store_px<BPP>(o + j * BPP, w[j]);
+                for (int k = 0; k < WPP; ++k) vv[j * WPP + k] = w[pass][j][k];
+            __stcs(reinterpret_cast<uint4*>(o), make_uint4(vv[0], vv[1], vv[2], vv[3]));
+        } else {
+#pragma unroll
+            for (int j = 0; j < PX; ++j)
+                if ((have[pass] >> j) & 1u) store_px<BPP>(o + j * BPP, w[pass][j]);
+        }
     }
 }
 
@@ -351,7 +363,7 @@ cudaError_t pixels_n(const PixSrc* src, const int16_t* owner, int n, int nx, int
     for (int i = 0; i < n; ++i) P.s[i] = src[i];
     for (int i = 0; i < nx * ny; ++i) P.owner[i] = owner[i];
     const int px = 16 / bpp;
-    const dim3 grid(ceil_div(D.W, 32 * px), ceil_div(D.H, kARows));
+    const dim3 grid(ceil_div(D.W, 32 * px), ceil_div(D.H, kARows * kAPasses));
     if (bpp == 4) k_assemble_pixels<N, 4><<<grid, kAT, 0, s>>>(P, D);
     else if (bpp == 8) k_assemble_pixels<N, 8><<<grid, kAT, 0, s>>>(P, D);
     else k_assemble_pixels<N, 16><<<grid, kAT, 0, s>>>(P, D);
