@@ -21,8 +21,13 @@ namespace {
 constexpr int kThreads = 256;
 constexpr int kRows = kThreads / 32;   // one warp per tile row
 
+// The depth merge runs 128-thread CTAs (tiles of 128 x 4 pixels): small
+// frames then split into enough CTAs that the last wave costs little.
+constexpr int kDThreads = 128;
+constexpr int kDRows = kDThreads / 32;
+
 template <int N, int CB>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kDThreads)
 k_depth(const __grid_constant__ SrcList<N> L, const __grid_constant__ DstDesc D)
 {
     constexpr int kTW = 128;     // 32 lanes x 4 pixels
@@ -31,8 +36,8 @@ k_depth(const __grid_constant__ SrcList<N> L, const __grid_constant__ DstDesc D)
     auto at = [&](int, int i) -> const SrcDesc& { return L.s[i]; };
 
     const int lane = threadIdx.x & 31, row = threadIdx.x >> 5;
-    const int tx0 = blockIdx.x * kTW, ty0 = blockIdx.y * kRows;
-    build_active(at, L.n, tx0, ty0, min(tx0 + kTW, D.W), min(ty0 + kRows, D.H), act, &nact_s);
+    const int tx0 = blockIdx.x * kTW, ty0 = blockIdx.y * kDRows;
+    build_active(at, L.n, tx0, ty0, min(tx0 + kTW, D.W), min(ty0 + kDRows, D.H), act, &nact_s);
     __syncthreads();
     const int x = tx0 + lane * 4, y = ty0 + row;
     if (x >= D.W || y >= D.H) return;
@@ -84,10 +89,10 @@ SrcList<N> make_list(const SrcDesc* src, int n)
 template <int N>
 cudaError_t depth_n(const SrcDesc* src, int n, int cb, const DstDesc& D, cudaStream_t s)
 {
-    const dim3 grid(ceil_div(D.W, 128), ceil_div(D.H, kRows));
+    const dim3 grid(ceil_div(D.W, 128), ceil_div(D.H, kDRows));
     const SrcList<N> L = make_list<N>(src, n);
-    if (cb == 4) k_depth<N, 4><<<grid, kThreads, 0, s>>>(L, D);
-    else k_depth<N, 16><<<grid, kThreads, 0, s>>>(L, D);
+    if (cb == 4) k_depth<N, 4><<<grid, kDThreads, 0, s>>>(L, D);
+    else k_depth<N, 16><<<grid, kDThreads, 0, s>>>(L, D);
     return cudaGetLastError();
 }
 
