@@ -2,7 +2,8 @@
 compositing): FP32 layers within 2e-6 absolute, FP16-stored layers within 2e-3
 absolute (the oracle runs on the decoded FP16 inputs), remaining transmittance
 within the same bounds.  Ragged sizes, ROIs, cropped and unaligned layers,
-arbitrary orders; the 32 x 2048^2 workload on sampled row bands."""
+arbitrary orders; the 32 x 2048^2 and 128 x 3840x2160 FP16 workloads on
+sampled row bands."""
 import numpy as np
 import pytest
 import torch
@@ -120,3 +121,26 @@ def test_cfg3_32_layers_2048_sampled_rows(dtype):
         got = np_of(out[y0:y0 + 8]).astype(np.float64)
         assert np.max(np.abs(got - ref)) <= TOL[dtype]
         assert np.max(np.abs(np_of(T[y0:y0 + 8]) - Tref)) <= 2e-6
+
+
+def test_cfg5_128_fp16_layers_4k_sampled_rows():
+    """The 128-layer FP16 workload at 3840x2160 in the launch configuration the
+    bench times (every tile covered by every layer, so the range-test-free
+    path): sampled row bands, including the last, against the oracle."""
+    require_gpu()
+    L, W, H = 128, 3840, 2160
+    lay = S.alpha_layers(5, L, W, H, 0.1, dtype=torch.float16, device="cuda")
+    gimgs = [ec.Image(color=lay[k]) for k in range(L)]
+    out = torch.empty((H, W, 4), dtype=torch.float16, device="cuda")
+    T = torch.empty((H, W), dtype=torch.float32, device="cuda")
+    ec.composite_alpha(gimgs, out, t_final=T)
+    ec.default_context().check_status()
+    for y0 in (0, 1077, 2152):
+        rows = lay[:, y0:y0 + 8].cpu().numpy()
+        oimgs = [oracle.Image((0, y0, W, 8), (0, y0, W, 8), np.ascontiguousarray(rows[k])) for k in range(L)]
+        ref, Tref, _ = oracle.composite_alpha(oimgs, (0, y0, W, 8))
+        got = np_of(out[y0:y0 + 8]).astype(np.float64)
+        assert np.max(np.abs(got - ref)) <= TOL[torch.float16]
+        assert np.max(np.abs(np_of(T[y0:y0 + 8]) - Tref)) <= 1e-5
+    del lay
+    torch.cuda.empty_cache()

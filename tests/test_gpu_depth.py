@@ -1,7 +1,7 @@
 """GPU parity of ec_composite_depth against the oracle: bit-exact colour, depth and
 winner on every pixel (thesis 5.2.1 depth-sorted compositing, 5.3 ROI).
 
-Sizes span many 128x8 tiles with ragged right/bottom edges; the full-size
+Sizes span many 128x4 tiles with ragged right/bottom edges; the full-size
 workloads (4 x 640x480, 16 x 1920x1080 cropped) are compared on every pixel,
 the 64 x 7680x4320 one on sampled row bands."""
 import numpy as np

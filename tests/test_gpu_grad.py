@@ -173,3 +173,30 @@ def test_cfg3_backward_2048_sampled_rows(dtype):
         ref = oracle.composite_alpha_backward(oimgs, (0, y0, W, 4), w[y0:y0 + 4].cpu().double().numpy())
         for k in range(L):
             _grad_close(np_of(grads[k][y0:y0 + 4]).astype(np.float64), ref[k])
+
+
+def test_cfg5_fused_128_fp16_layers_4k_sampled_rows():
+    """The 128-layer FP16 workload at 3840x2160 in the launch configuration the
+    bench times: fused forward + backward with FP16 gradients, more layers than
+    the two-pixels-per-lane path takes.  Sampled row bands of the output and of
+    every layer's gradient against the oracle."""
+    require_gpu()
+    L, W, H = 128, 3840, 2160
+    lay = S.alpha_layers(5, L, W, H, 0.1, dtype=torch.float16, device="cuda")
+    w = S.grad_weights(5, W, H, device="cuda")
+    gimgs = [ec.Image(color=lay[k]) for k in range(L)]
+    out = torch.empty((H, W, 4), dtype=torch.float16, device="cuda")
+    grads = [torch.empty_like(lay[k]) for k in range(L)]
+    ec.composite_alpha_fwd_bwd(gimgs, out, w, grads)
+    ec.default_context().check_status()
+    for y0 in (0, 1079, 2156):
+        rows = lay[:, y0:y0 + 4].cpu().numpy()
+        oimgs = [oracle.Image((0, y0, W, 4), (0, y0, W, 4), np.ascontiguousarray(rows[k])) for k in range(L)]
+        fwd, _, _ = oracle.composite_alpha(oimgs, (0, y0, W, 4))
+        assert np.max(np.abs(np_of(out[y0:y0 + 4]).astype(np.float64) - fwd)) <= 2e-3
+        ref = oracle.composite_alpha_backward(oimgs, (0, y0, W, 4), w[y0:y0 + 4].cpu().double().numpy())
+        for k in range(L):
+            got = np_of(grads[k][y0:y0 + 4]).astype(np.float64)
+            assert np.max(np.abs(got - ref[k].astype(np.float16))) <= 2e-3, k
+    del lay, grads
+    torch.cuda.empty_cache()
