@@ -167,3 +167,44 @@ def test_rgba8_average_of_many_bright_samples():
     ec.average(imgs_g, out)
     ec.default_context().check_status()
     assert np.array_equal(np_of(out), oracle.average(imgs_o, (0, 0, W, H), 0))
+
+
+def test_asm4k_workload():
+    """The 3840x2160 RGBA8 workloads the bench times: a sort-first frame from an
+    8 x 8 grid of tiles and a 2 x 2 pixel compound (every pixel, bit for bit),
+    and the average of 8 samples (sampled row bands, bit for bit)."""
+    require_gpu()
+    W, H, nt = 3840, 2160, 8
+    r = np.random.default_rng(4321)
+    tw, th = -(-W // nt), -(-H // nt)
+    base = _host(r, "rgba8", H, W)
+    imgs_o, imgs_g = [], []
+    for j in range(nt):
+        for i in range(nt):
+            rect = (i * tw, j * th, min(tw, W - i * tw), min(th, H - j * th))
+            a = _host(r, "rgba8", rect[3], rect[2])
+            imgs_o.append(oracle.Image(rect, rect, a))
+            imgs_g.append(ec.Image(color=_dev(a), pvp=rect, roi=rect))
+    out = _dev(base)
+    ec.assemble_tiles(imgs_g, out, out_pvp=(0, 0, W, H))
+    ec.default_context().check_status()
+    assert np.array_equal(np_of(out), oracle.assemble_tiles(imgs_o, base, (0, 0, W, H)))
+
+    frame = _host(r, "rgba8", H, W)
+    offs = [(kx, ky) for ky in range(2) for kx in range(2)]
+    subs = [np.ascontiguousarray(frame[ky::2, kx::2]) for kx, ky in offs]
+    out2 = _dev(base)
+    ec.assemble_pixels([_dev(s) for s in subs], offs, (2, 2), out2, out_pvp=(0, 0, W, H))
+    ec.default_context().check_status()
+    got = np_of(out2)
+    assert np.array_equal(got, oracle.assemble_pixels(subs, offs, (2, 2), base, (0, 0, W, H)))
+    assert np.array_equal(got, frame)              # the four sources rebuild the frame
+
+    samples = [_host(r, "rgba8", H, W) for _ in range(8)]
+    out3 = torch.empty((H, W), dtype=torch.int32, device="cuda").view(torch.uint32)
+    ec.average([ec.Image(color=_dev(s)) for s in samples], out3)
+    ec.default_context().check_status()
+    got = np_of(out3)
+    for y0 in (0, 1000, 2144):
+        band = [oracle.Image((0, 0, W, 16), (0, 0, W, 16), np.ascontiguousarray(s[y0:y0 + 16])) for s in samples]
+        assert np.array_equal(got[y0:y0 + 16], oracle.average(band, (0, 0, W, 16), 0))
