@@ -141,3 +141,38 @@ def test_empty_batch_and_bad_config():
     t = S.uneven_tiles(41, 2, max_side=64, lmax=4, device="cuda")
     with pytest.raises(ec.EcError):
         ec.Batch(_jobs_from_tiles(t), config=dict(depth_tile_w=100))     # not a multiple of 128
+
+
+def test_cfg4_1000_tiles_full_size():
+    """The 1000-tile workload the bench times (autotuned plan, one graph launch):
+    every output bit-identical to the per-tile calls, and the two largest depth
+    and alpha tiles equal to the oracle."""
+    require_gpu()
+    tiles = S.uneven_tiles(4, 1000, device="cuda")
+    jobs = _jobs_from_tiles(tiles)
+    ref = _single_calls(jobs)
+    for jb in jobs:
+        jb.out_color.view(torch.uint8).fill_(0xA5)
+    b = ec.Batch(jobs)
+    b.run()
+    ec.default_context().check_status()
+    _assert_same(jobs, ref)
+    b.close()
+    for mode in ("depth", "alpha"):
+        big = sorted((i for i, t in enumerate(tiles) if t.mode == mode),
+                     key=lambda i: tiles[i].w * tiles[i].h * tiles[i].L)[-2:]
+        for i in big:
+            jb, t = jobs[i], tiles[i]
+            full = (0, 0, t.w, t.h)
+            if mode == "depth":
+                oimgs = [oracle.Image(full, full, np_of(im.color), np_of(im.depth)) for im in jb.images]
+                c, d, w, _ = oracle.composite_depth(oimgs, full)
+                assert np.array_equal(np_of(jb.out_color), c) and np.array_equal(np_of(jb.winner), w)
+                assert np.array_equal(np_of(jb.out_depth).view(np.uint32), d.view(np.uint32))
+            else:
+                oimgs = [oracle.Image(full, full, np_of(im.color)) for im in jb.images]
+                o, tf, _ = oracle.composite_alpha(oimgs, full)
+                assert np.max(np.abs(np_of(jb.out_color).astype(np.float64) - o)) <= 2e-6
+                assert np.max(np.abs(np_of(jb.t_final) - tf)) <= 2e-6
+    del jobs, ref, tiles
+    torch.cuda.empty_cache()
