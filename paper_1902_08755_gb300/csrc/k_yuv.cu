@@ -34,12 +34,16 @@ constexpr int kVec8 = 1, kVec16 = 2, kPacked8 = 4;   // YuvJob::vec bits
 __device__ __forceinline__ int floor256(int x) { return ((x + (1 << 20)) >> 8) - (1 << 12); }
 __device__ __forceinline__ int clamp8(int v) { return min(255, max(0, v)); }
 
+// The three weighted sums are byte dot products of the pixel word (R, G, B,
+// A in bytes 0..3) with unsigned coefficient bytes: 77R + 150G + 29B for Y,
+// and the negative parts 43R + 85G of U and 107G + 21B of V, whose positive
+// part is 128 times one channel.  Integer arithmetic, exact.
 __device__ __forceinline__ void to_yuv(uint32_t p, int& Y, int& U, int& V)
 {
-    const int R = (int)(p & 0xFFu), G = (int)((p >> 8) & 0xFFu), B = (int)((p >> 16) & 0xFFu);
-    Y = (77 * R + 150 * G + 29 * B + 128) >> 8;
-    U = min(255, (-43 * R - 85 * G + 128 * B + 32896) >> 8);   // 128 + ... (never negative)
-    V = min(255, (128 * R - 107 * G - 21 * B + 32896) >> 8);
+    const int R = (int)(p & 0xFFu), B = (int)((p >> 16) & 0xFFu);
+    Y = (int)__dp4a(p, 0x001D964Du, 128u) >> 8;                              // (77, 150, 29, 0)
+    U = min(255, ((B << 7) - (int)__dp4a(p, 0x0000552Bu, 0u) + 32896) >> 8);   // (43, 85, 0, 0)
+    V = min(255, ((R << 7) - (int)__dp4a(p, 0x00156B00u, 0u) + 32896) >> 8);   // (0, 107, 21, 0)
 }
 
 // CTA tile t of a job list: the job whose tiles [first, first + ntiles) hold
