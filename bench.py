@@ -1036,21 +1036,31 @@ def cpu_baseline(wl, budget_s=12.0, max_reps=20):
             "sample": sample, "ms_per_step": t * 1e3}
 
 
+REF_BUDGET_S = 100.0     # wall-clock cap of the reference arm's warm-up and timed steps
+
+
 def run_reference(args):
     rank, world, local = dist_env()
     if rank != 0:
         return
     wl = make_workload(args.workload, "cpu")
     cores = os.cpu_count() or 1
+    # W warm-up and K timed steps, each a bounded sample of the workload; the run
+    # stops early (and reports the steps it ran) once it has used REF_BUDGET_S
+    t_start = time.perf_counter()
     with ThreadPoolExecutor(max_workers=cores) as pool:
-        for _ in range(min(args.warmup, 1)):
+        warm = 0
+        while warm < args.warmup and (warm == 0 or time.perf_counter() - t_start < REF_BUDGET_S / 4):
             wl.oracle_step(pool, cores)
-        times = [wl.oracle_step(pool, cores) for _ in range(max(1, min(args.steps, 10)))]
+            warm += 1
+        times = []
+        while len(times) < max(1, args.steps) and (not times or time.perf_counter() - t_start < REF_BUDGET_S):
+            times.append(wl.oracle_step(pool, cores))
     t = statistics.mean(times)
     val = wl.units / t / 1e9
     frac = getattr(wl, "sample_fraction", 1.0)
     line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
-            "steps": len(times), "warmup": min(args.warmup, 1), "ms_per_step": t * 1e3,
+            "steps": len(times), "warmup": warm, "ms_per_step": t * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "rgba8+f32",
             "data": "synthetic", "config": {"workload": f"{args.workload}: {wl.desc}"},
             "cpu_baseline": {"value": val, "unit": UNIT, "cores": cores, "kind": "oracle",

@@ -72,7 +72,7 @@ def test_reference_arm_prints_on_rank_zero_only(rank):
     env = dict(os.environ, RANK=str(rank), WORLD_SIZE="2", LOCAL_RANK=str(rank),
                MASTER_ADDR="127.0.0.1", MASTER_PORT=str(_free_port()))
     r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--gpus", "2",
-                        "--workload", "cfg1", "--steps", "1", "--warmup", "0"],
+                        "--workload", "cfg1", "--steps", "2", "--warmup", "1"],
                        cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
     assert r.returncode == 0, r.stderr[-2000:]
     lines = [l for l in r.stdout.splitlines() if l.startswith("{")]
@@ -82,5 +82,6 @@ def test_reference_arm_prints_on_rank_zero_only(rank):
     assert len(lines) == 1
     d = json.loads(lines[0])
     assert d["impl"] == "reference" and d["value"] > 0
+    assert d["steps"] == 2 and d["warmup"] == 1              # the steps asked for, well inside the time cap
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["d2h_bytes_per_step"] == 0
