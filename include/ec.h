@@ -317,11 +317,17 @@ typedef struct ec_schedule ec_schedule;
 ec_status ec_schedule_plan(ec_ctx* ctx, int32_t mode, int32_t algorithm, const ec_image* in,
                            int32_t n, const int32_t* order, const ec_target* out, uint32_t flags,
                            ec_schedule** plan);
-/* Host only, no device work: the transfers (in stage order, fused = 0) that a
- * schedule of n resources whose data lies in rois[i] (out->pvp coordinates)
- * makes in frame, the number of stages, and (regions, n entries, may be NULL)
- * the region each resource owns at the end.  *n_messages receives the count
- * even when cap is too small (EC_ERR_CAPACITY). */
+/* Host only, no device work (thesis 5.2.2, 5.2.3): the geometry of the
+ * schedule ec_schedule_plan would build for n resources whose data lies in
+ * rois[i], all rectangles in the same pixel coordinates as frame (rois are
+ * clipped to frame).  Fills msgs (host, cap entries) with the transfers in
+ * stage order (fused = 0), *n_levels with the number of stages and, when
+ * regions is not NULL, regions[0..n) with the part of frame each resource owns
+ * at the end (empty for the senders of a stream).  *n_messages receives the
+ * count even when cap is too small (EC_ERR_CAPACITY; msgs then holds the
+ * first cap).  Errors: EC_ERR_INVALID_ARG (n < 1, negative sizes, unknown
+ * algorithm, binary swap with n not a power of two), EC_ERR_UNSUPPORTED
+ * (n > EC_MAX_SOURCES). */
 ec_status ec_schedule_geometry(int32_t algorithm, const ec_rect* rois, int32_t n, ec_rect frame,
                                ec_sched_message* msgs, int32_t cap, int32_t* n_messages,
                                int32_t* n_levels, ec_rect* regions);

@@ -90,3 +90,19 @@ def test_capacity_is_reported():
     code = lib.ec_schedule_geometry(A.EC_SCHED_DIRECT_SEND, rois, 0, A.ec_rect(0, 0, 64, 64), msgs, 2,
                                     A.C.byref(nm), A.C.byref(nl), None)
     assert code == A.EC_ERR_INVALID_ARG
+
+
+def test_argument_errors():
+    lib = A.load()
+    nm, nl = A.C.c_int32(), A.C.c_int32()
+    frame = A.ec_rect(0, 0, 8, 8)
+    four = (A.ec_rect * 4)(*[A.ec_rect(0, 0, 8, 8)] * 4)
+    call = lambda alg, arr, n: lib.ec_schedule_geometry(alg, arr, n, frame, None, 0, A.C.byref(nm),
+                                                        A.C.byref(nl), None)
+    assert call(7, four, 4) == A.EC_ERR_INVALID_ARG                  # unknown algorithm
+    assert call(A.EC_SCHED_BINARY_SWAP, four, 3) == A.EC_ERR_INVALID_ARG
+    neg = (A.ec_rect * 1)(A.ec_rect(0, 0, -1, 8))
+    assert call(A.EC_SCHED_DIRECT_SEND, neg, 1) == A.EC_ERR_INVALID_ARG
+    many = (A.ec_rect * 600)(*[A.ec_rect(0, 0, 8, 8)] * 600)
+    assert call(A.EC_SCHED_DIRECT_SEND, many, 600) == 5                 # EC_ERR_UNSUPPORTED
+    assert call(A.EC_SCHED_STREAM, four, 4) == A.EC_ERR_CAPACITY and nm.value == 3 and nl.value == 3
