@@ -70,3 +70,13 @@ def test_product_does_not_import_oracle():
             if fn.endswith((".py", ".cu", ".cuh", ".h")):
                 src = open(os.path.join(dirpath, fn)).read()
                 assert "oracle" not in src.lower(), os.path.join(dirpath, fn)
+
+
+def test_missing_library_fails_loudly(monkeypatch, tmp_path):
+    """No CPU fallback: without libec.so every entry point raises."""
+    monkeypatch.setattr(A, "_lib", None)
+    monkeypatch.setattr(A, "lib_path", lambda: str(tmp_path / "libec.so"))
+    with pytest.raises(RuntimeError, match="libec.so is missing"):
+        A.load(build_if_missing=False)
+    with pytest.raises(RuntimeError, match="libec.so is missing"):
+        ec.rle_max_size(16, 16)
