@@ -1,17 +1,25 @@
 #!/usr/bin/env python
 """Benchmark of the sort-last compositing hot path on GB300.
 
-Default workload (one "step"): 16 partial images of a 1920x1080 frame,
-RGBA8 + float32 depth, ~30% coverage each, stored cropped to their ROI; every
-source's colour (swizzled, mode 2) and depth (mode 1) is RLE-compressed, the
-streams are decompressed, and the 16 decompressed sources are depth-composited
-into the frame (thesis 5.2.1, 5.3, 5.5.1).  Inputs are resident in HBM when a
-step starts; L2 is flushed between timed steps, outside the timed events: 2x
-its size is written, then another 2x its size is read, so that the timed step
-neither finds its inputs in L2 nor pays for writing back the flush's lines.
+Default workload (one "step", the thesis's large-frame sort-last case, 5.2.1 and
+5.3): 64 partial images of a 7680x4320 frame, RGBA8 + float32 depth, ~25%
+coverage each, clustered and stored cropped to their ROI; every source's colour
+(swizzled, mode 2) and depth (mode 1) is RLE-compressed (5.5.1), the 128
+streams are decompressed, and the 64 decompressed sources are depth-composited
+into the frame.  Inputs are resident in HBM when a step starts; L2 is flushed
+between timed steps, outside the timed events: 2x its size is written, then
+another 2x its size is read, so that the timed step neither finds its inputs in
+L2 nor pays for writing back the flush's lines.  Step times are medians.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ec|reference]
-                    [--workload cfg2|cfg1|cfg3|cfg3h|cfg3fused|cfg3hfused|cfg4|cfg5d|cfg5a|cfg5afused|roi2|asm4k|sched2|rle0|yuv2]
+                    [--workload cfg5d|cfg1|cfg2|cfg3|cfg3h|cfg3fused|cfg3hfused|cfg4|cfg5a|cfg5afused|roi2|asm4k|sched2|rle0|yuv2]
+                    [--sources S]
+
+The default line also carries, measured in the same run: the 16 x 1920x1080
+pipeline (secondary), the 1000 uneven tiles batched against per-tile launches,
+and the alpha forward / backward / fused forward+backward ratios at 32 x 2048^2
+(FP32 and FP16) and 128 x 3840x2160 (FP16).  --sources S keeps only the first
+S sources of a depth workload (small cases for profiling).
 
 Prints ONE JSON line (rank 0).  Metric: composited Gpixel-layers/s (sum over
 sources of |roi_i ∩ frame| per step, divided by the step time).  With N > 1
@@ -53,13 +61,16 @@ def log(*a):
 def parse():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=2000)
-    p.add_argument("--warmup", type=int, default=20)
+    p.add_argument("--steps", type=int, default=30)
+    p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", default="ec", choices=["ec", "reference"])
-    p.add_argument("--workload", default="cfg2")
+    p.add_argument("--workload", default="cfg5d")
+    p.add_argument("--sources", type=int, default=0,
+                   help="depth workloads: keep only the first S sources (0 = all)")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-extras", action="store_true",
-                   help="skip the alpha forward/backward ratio measurements")
+                   help="skip the secondary workloads measured beside the default one")
+    p.add_argument("--oracle-single-core", action="store_true", help=argparse.SUPPRESS)
     return p.parse_args()
 
 
@@ -196,16 +207,19 @@ def measured_traffic(kernel: str, workload: str):
 class DepthPipeline:
     """cfg1 / cfg2 / cfg5d: RLE compress -> decompress -> depth composite."""
 
-    def __init__(self, cfg, n, W, H, coverage, clustered, cropped, device):
+    def __init__(self, cfg, n, W, H, coverage, clustered, cropped, device, keep=0):
         import paper_1902_08755_gb300 as ec
         import synthetic as S
         self.ec = ec
-        self.W, self.H, self.n, self.cfg = W, H, n, cfg
-        self.desc = (f"{n} sources {W}x{H} RGBA8+Z32, ~{int(coverage * 100)}% coverage, "
+        self.W, self.H, self.cfg = W, H, cfg
+        self.n = min(n, keep) if keep > 0 else n
+        self.n_total = n
+        who = f"{n} sources" if self.n == n else f"the first {self.n} of {n} sources"
+        self.desc = (f"{who} {W}x{H} RGBA8+Z32, ~{int(coverage * 100)}% coverage, "
                      f"{'ROI-cropped' if cropped else 'uncropped'}; RLE compress (colour mode 2, "
                      f"depth mode 1) -> decompress -> depth composite")
-        self.srcs = S.depth_sources(cfg, n, W, H, coverage, clustered=clustered, cropped=cropped,
-                                    device=device)
+        self.srcs = [S.depth_source(W, H, coverage, cfg, i, clustered=clustered, cropped=cropped, device=device)
+                     for i in range(self.n)]
         self.planes = []
         for s in self.srcs:
             self.planes.append((s.color, 2))
@@ -303,21 +317,31 @@ class DepthPipeline:
         self.h_outd.copy_(self.out_d, non_blocking=True)
 
     # oracle (reference arm / cpu baseline): same pipeline on the host cores
-    def oracle_step(self, pool, cores):
+    def oracle_step(self, pool, cores, k=0):
+        """The same pipeline on the host cores, over the first k sources (all
+        when k is 0): each plane's codec calls on a pool thread, then the
+        composite of those sources in row bands.  Sets sample_units."""
         import oracle
-        host = [(t.view(torch.int32).cpu().numpy().view(np.uint32), m) for t, m in self.planes] \
-            if not hasattr(self, "_host") else self._host
-        self._host = host
+        k = min(k, self.n) if k > 0 else self.n
+        if getattr(self, "_host_k", None) != k:
+            self._host = [(t.view(torch.int32).cpu().numpy().view(np.uint32), m) for t, m in self.planes[:2 * k]]
+            self._host_k = k
+        host = self._host
+        self.sample_units = sum(max(0, min(s.roi[2], self.W)) * max(0, min(s.roi[3], self.H))
+                                for s in self.srcs[:k])
+        self.sample_desc = ("full steps" if k == self.n_total else
+                            f"the first {k} of the {self.n_total} sources (codec of their planes, "
+                            f"composite of those sources over the whole frame)")
         t0 = time.perf_counter()
         streams = list(pool.map(lambda a: oracle.rle_compress(a[0], a[1]), host))
         dec = list(pool.map(lambda a: oracle.rle_decompress(a[0], a[1][0].shape[1], a[1][0].shape[0]),
                             zip(streams, host)))
         imgs = [oracle.Image(s.pvp, s.roi, dec[2 * i], dec[2 * i + 1].view(np.float32))
-                for i, s in enumerate(self.srcs)]
+                for i, s in enumerate(self.srcs[:k])]
         bands = np.linspace(0, self.H, cores + 1).astype(int)
 
-        def part(k):
-            y0, y1 = int(bands[k]), int(bands[k + 1])
+        def part(b):
+            y0, y1 = int(bands[b]), int(bands[b + 1])
             return oracle.composite_depth(imgs, (0, y0, self.W, y1 - y0))
         list(pool.map(part, range(cores)))
         return time.perf_counter() - t0
@@ -936,7 +960,7 @@ class L2Flush:
 
 
 def _timed(fn, flush, reps):
-    """Mean CUDA-event time (ms) of fn over reps calls, L2 flushed before each."""
+    """Median CUDA-event time (ms) of fn over reps calls, L2 flushed before each."""
     ts = []
     for k in range(reps):
         flush(k)
@@ -946,20 +970,28 @@ def _timed(fn, flush, reps):
         b.record()
         ts.append((a, b))
     torch.cuda.synchronize()
-    return statistics.mean(a.elapsed_time(b) for a, b in ts)
+    return statistics.median(a.elapsed_time(b) for a, b in ts)
+
+
+ALPHA_RATIO_CASES = [
+    # key, cfg, layers, W, H, alpha max, storage
+    ("fp32", 3, 32, 2048, 2048, 0.3, torch.float32),
+    ("fp16", 3, 32, 2048, 2048, 0.3, torch.float16),
+    ("cfg5a_fp16", 5, 128, 3840, 2160, 0.1, torch.float16),
+]
 
 
 def alpha_fwd_bwd_ratio(device, flush, peak, reps=20):
-    """Ordered compositing of 32 layers at 2048^2 (FP32 and FP16 storage): plain
-    forward, separate backward (autograd path: forward, then backward) and the
-    fused forward+backward, with the ratios to the plain forward."""
+    """Ordered compositing, plain forward, separate backward (the autograd
+    path: forward, then backward) and the fused forward+backward, with the
+    ratios to the plain forward: 32 layers at 2048^2 (FP32 and FP16 storage)
+    and 128 FP16 layers at 3840x2160."""
     import paper_1902_08755_gb300 as ec
     import synthetic as S
     res = {}
-    L, W, H = 32, 2048, 2048
-    w = S.grad_weights(3, W, H, device=device)
-    for dtype, tag in ((torch.float32, "fp32"), (torch.float16, "fp16")):
-        lay = S.alpha_layers(3, L, W, H, 0.3, dtype=dtype, device=device)
+    for tag, cfg, L, W, H, amax, dtype in ALPHA_RATIO_CASES:
+        w = S.grad_weights(cfg, W, H, device=device)
+        lay = S.alpha_layers(cfg, L, W, H, amax, dtype=dtype, device=device)
         imgs = [ec.Image(color=lay[k]) for k in range(L)]
         out = torch.empty((H, W, 4), dtype=dtype, device=device)
         grads = [torch.empty_like(lay[k]) for k in range(L)]
@@ -976,22 +1008,24 @@ def alpha_fwd_bwd_ratio(device, flush, peak, reps=20):
         b_b = L * px * s + px * 16 + L * px * s
         b_x = L * px * s + px * 16 + px * s + L * px * s
         gb = lambda b, t: b / (t * 1e-3) / 1e9
-        res[tag] = {"fwd_ms": t_f, "bwd_ms": t_b, "fused_fwd_bwd_ms": t_x,
+        res[tag] = {"layers": L, "size": f"{W}x{H}", "storage": "FP32" if dtype == torch.float32 else "FP16",
+                    "fwd_ms": t_f, "bwd_ms": t_b, "fused_fwd_bwd_ms": t_x,
                     "fwd_plus_bwd_over_fwd": (t_f + t_b) / t_f, "fused_over_fwd": t_x / t_f,
                     "fwd_frac_of_peak": gb(b_f, t_f) / peak, "bwd_frac_of_peak": gb(b_b, t_b) / peak,
                     "fused_frac_of_peak": gb(b_x, t_x) / peak,
                     "fwd_gpixel_layers_s": L * px / (t_f * 1e-3) / 1e9}
-        del lay, imgs, out, grads
+        del lay, imgs, out, grads, w
+        torch.cuda.empty_cache()
     return res
 
 
-def make_workload(name, device):
+def make_workload(name, device, sources=0):
     if name == "cfg1":
-        return DepthPipeline(1, 4, 640, 480, 0.4, False, False, device)
+        return DepthPipeline(1, 4, 640, 480, 0.4, False, False, device, keep=sources)
     if name == "cfg2":
-        return DepthPipeline(2, 16, 1920, 1080, 0.3, True, True, device)
+        return DepthPipeline(2, 16, 1920, 1080, 0.3, True, True, device, keep=sources)
     if name == "cfg5d":
-        return DepthPipeline(5, 64, 7680, 4320, 0.25, True, True, device)
+        return DepthPipeline(5, 64, 7680, 4320, 0.25, True, True, device, keep=sources)
     if name == "cfg4":
         return BatchedTiles(device)
     if name == "roi2":
@@ -1019,21 +1053,86 @@ def make_workload(name, device):
 
 # -------------------------------------------------------------------- arms
 
+# Sources per oracle step of the depth workloads' CPU legs: (all cores, one core).
+CPU_SAMPLE = {"cfg1": (4, 4), "cfg2": (16, 2), "cfg5d": (8, 1)}
 
-def cpu_baseline(wl, budget_s=12.0, max_reps=20):
+
+def cpu_model() -> str:
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            k, _, v = line.partition(":")
+            if k.strip() == "Model name" and v.strip():
+                return v.strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                k, _, v = line.partition(":")
+                if k.strip().lower() == "model name":
+                    return v.strip()
+    except OSError:
+        pass
+    import platform
+    return platform.machine()
+
+
+def _oracle_reps(wl, pool, cores, k, budget_s, max_reps):
+    times = []
+    t_start = time.perf_counter()
+    while len(times) < max_reps and (not times or (time.perf_counter() - t_start) < budget_s):
+        times.append(wl.oracle_step(pool, cores, k) if k else wl.oracle_step(pool, cores))
+    return times
+
+
+def _sample_value(wl, t):
+    units = getattr(wl, "sample_units", None)
+    if units is None:                      # row-band samples are scaled inside oracle_step
+        units = wl.units
+    return units / t / 1e9
+
+
+def oracle_single_core(args):
+    """Child process of cpu_baseline: the oracle pinned to one core, on the
+    first sources of the workload, generated here on the host."""
+    cpus = sorted(os.sched_getaffinity(0))
+    os.sched_setaffinity(0, {cpus[-1]})
+    torch.set_num_threads(1)
+    wl = make_workload(args.workload, "cpu", sources=args.sources)
+    with ThreadPoolExecutor(max_workers=1) as pool:
+        times = _oracle_reps(wl, pool, 1, 0, 15.0, 10)
+    t = statistics.median(times)
+    print(json.dumps({"value": _sample_value(wl, t), "ms_per_step": t * 1e3, "reps": len(times),
+                      "cpu": cpus[-1], "sample": getattr(wl, "sample_desc", "full steps")}), flush=True)
+
+
+def cpu_baseline(args, wl, budget_s=12.0, max_reps=20):
+    """The oracle as it stands on the host cores: all cores over a bounded
+    sample of the workload, and (depth workloads) one pinned core."""
     cores = os.cpu_count() or 1
+    many, one = CPU_SAMPLE.get(args.workload, (0, 0))
     with ThreadPoolExecutor(max_workers=cores) as pool:
-        times = []
-        t_start = time.perf_counter()
-        while len(times) < max_reps and (time.perf_counter() - t_start) < budget_s:
-            times.append(wl.oracle_step(pool, cores))
+        times = _oracle_reps(wl, pool, cores, many, budget_s, max_reps)
     t = statistics.median(times)
     frac = getattr(wl, "sample_fraction", 1.0)
-    sample = (f"{len(times)} full steps of the workload" if frac == 1.0 else
-              f"{len(times)} x " + getattr(wl, "sample_desc", f"the first {frac:.4f} of each frame's rows") +
-              ", scaled to a full step")
-    return {"value": wl.units / t / 1e9, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": sample, "ms_per_step": t * 1e3}
+    desc = getattr(wl, "sample_desc", "full steps")
+    sample = (f"{len(times)} steps, each {desc}" if frac == 1.0 else
+              f"{len(times)} x {desc}, scaled to a full step")
+    res = {"value": _sample_value(wl, t), "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample,
+           "ms_per_step": t * 1e3, "cpu_model": cpu_model()}
+    if one:
+        cmd = [sys.executable, os.path.abspath(__file__), "--oracle-single-core", "--workload", args.workload,
+               "--sources", str(one)]
+        try:
+            r = subprocess.run(cmd, capture_output=True, text=True, timeout=300)
+            d = json.loads(r.stdout.strip().splitlines()[-1])
+            res["single_core"] = {"value": d["value"], "unit": UNIT, "cores": 1, "pinned_cpu": d["cpu"],
+                                  "ms_per_step": d["ms_per_step"],
+                                  "sample": f"{d['reps']} steps, each {d['sample']}, one thread pinned to one core"}
+        except (OSError, subprocess.SubprocessError, ValueError, IndexError, KeyError) as e:
+            res["single_core"] = {"unavailable": f"{type(e).__name__}: {e}"[:200]}
+    return res
 
 
 REF_BUDGET_S = 100.0     # wall-clock cap of the reference arm's warm-up and timed steps
@@ -1043,7 +1142,8 @@ def run_reference(args):
     rank, world, local = dist_env()
     if rank != 0:
         return
-    wl = make_workload(args.workload, "cpu")
+    many = CPU_SAMPLE.get(args.workload, (0, 0))[0]
+    wl = make_workload(args.workload, "cpu", sources=args.sources or many)
     cores = os.cpu_count() or 1
     # W warm-up and K timed steps, each a bounded sample of the workload; the run
     # stops early (and reports the steps it ran) once it has used REF_BUDGET_S
@@ -1056,18 +1156,98 @@ def run_reference(args):
         times = []
         while len(times) < max(1, args.steps) and (not times or time.perf_counter() - t_start < REF_BUDGET_S):
             times.append(wl.oracle_step(pool, cores))
-    t = statistics.mean(times)
-    val = wl.units / t / 1e9
+    t = statistics.median(times)
+    val = _sample_value(wl, t)
     frac = getattr(wl, "sample_fraction", 1.0)
+    desc = getattr(wl, "sample_desc", "full steps")
     line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
             "steps": len(times), "warmup": warm, "ms_per_step": t * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "rgba8+f32",
             "data": "synthetic", "config": {"workload": f"{args.workload}: {wl.desc}"},
             "cpu_baseline": {"value": val, "unit": UNIT, "cores": cores, "kind": "oracle",
-                             "sample": "full steps" if frac == 1.0 else
-                             getattr(wl, "sample_desc", f"first {frac:.4f} of rows") + ", scaled"},
+                             "sample": desc if frac == 1.0 else f"{desc}, scaled", "cpu_model": cpu_model()},
             "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+def step_events(wl, steps):
+    nk = len(wl.kernels)
+    return [[torch.cuda.Event(enable_timing=True) for _ in range(nk + 1)] for _ in range(steps)]
+
+
+def kernel_times(wl, evs):
+    """Per-kernel event times [kernel][step] (launches of one kernel kind in a
+    step summed), the kernel names and launches of each per step."""
+    nk, steps = len(wl.kernels), len(evs)
+    per_kernel = [[evs[k][i].elapsed_time(evs[k][i + 1]) for k in range(steps)] for i in range(nk)]
+    names = list(wl.kernels)
+    launches_of = {n: 1 for n in names}
+    if hasattr(wl, "kind_of"):              # several launches of one kernel per step: sum them
+        agg, cnt = {}, {}
+        for i, kd in enumerate(wl.kind_of):
+            a = agg.setdefault(kd, [0.0] * steps)
+            cnt[kd] = cnt.get(kd, 0) + 1
+            for k in range(steps):
+                a[k] += per_kernel[i][k]
+        names = list(agg)
+        per_kernel = [agg[n] for n in names]
+        launches_of = cnt
+    return per_kernel, names, launches_of
+
+
+def kernel_table(wl, per_kernel, names, launches_of, peak):
+    algo = wl.algorithmic_bytes()
+    steps = len(per_kernel[0])
+    step_ms = statistics.median(sum(per_kernel[i][k] for i in range(len(names))) for k in range(steps))
+    kern = {}
+    for i, name in enumerate(names):
+        kms = statistics.median(per_kernel[i])
+        gbs = algo[name] / (kms * 1e-3) / 1e9
+        kern[name] = {"ms": kms, "share": kms / step_ms, "algorithmic_bytes": algo[name],
+                      "achieved_gbs": gbs, "frac_of_peak": gbs / peak, "launches_per_step": launches_of[name]}
+    return kern
+
+
+def depth_secondary(name, device, flush, peak, steps=50, warmup=5):
+    """A depth pipeline other than the headline one, timed the same way."""
+    wl = make_workload(name, device)
+    for _ in range(warmup):
+        wl.step()
+    torch.cuda.synchronize()
+    evs = step_events(wl, steps)
+    for k in range(steps):
+        flush(k)
+        wl.step(evs[k])
+    torch.cuda.synchronize()
+    wl.ctx.check_status(what=name)
+    per_kernel, names, launches_of = kernel_times(wl, evs)
+    step_ms = statistics.median(sum(per_kernel[i][k] for i in range(len(names))) for k in range(steps))
+    res = {"workload": f"{name}: {wl.desc}", "value": wl.units / (step_ms * 1e-3) / 1e9, "unit": UNIT,
+           "ms_per_step": step_ms, "steps": steps, "pixel_layers_per_step": wl.units,
+           "rle_compressed_bytes_per_step": wl.compressed_bytes(),
+           "kernels": kernel_table(wl, per_kernel, names, launches_of, peak)}
+    del wl
+    torch.cuda.empty_cache()
+    return res
+
+
+def batched_extra(device, flush, peak, reps=20):
+    """The 1000 uneven tiles: one persistent graph-captured launch against one
+    plain launch per tile (median times)."""
+    wl = BatchedTiles(device)
+    wl.step()
+    wl.per_tile()
+    torch.cuda.synchronize()
+    b = _timed(wl.step, flush, reps)
+    pt = _timed(wl.per_tile, flush, max(5, reps // 2))
+    wl.ctx.check_status(what="batched tiles")
+    res = {"workload": f"cfg4: {wl.desc}", "batched_ms": b, "per_tile_ms": pt, "speedup": pt / b,
+           "algorithmic_bytes": wl.bytes, "batched_frac_of_peak": wl.bytes / (b * 1e-3) / 1e9 / peak,
+           "gpixel_layers_s": wl.units / (b * 1e-3) / 1e9, "plan_s": wl.plan_s, "config": wl.batch.config}
+    wl.batch.close()
+    del wl
+    torch.cuda.empty_cache()
+    return res
 
 
 def run_ec(args):
@@ -1079,17 +1259,17 @@ def run_ec(args):
     device = f"cuda:{local}"
     import paper_1902_08755_gb300 as ec
     ec.load()
-    wl = make_workload(args.workload, device)
+    wl = make_workload(args.workload, device, sources=args.sources)
     l2 = torch.cuda.get_device_properties(local).L2_cache_size
     flush = L2Flush(device, l2)
+    peak, peak_src = hbm_peak()
 
     for _ in range(max(3, args.warmup)):
         wl.step()
     wl.ctx.check_status(what="warm-up")
     torch.cuda.synchronize()
 
-    nk = len(wl.kernels)
-    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(nk + 1)] for _ in range(args.steps)]
+    evs = step_events(wl, args.steps)
     clocks = Clocks(local)
     barrier(world)
     torch.cuda.synchronize()
@@ -1105,21 +1285,9 @@ def run_ec(args):
     st = wl.ctx.status_sync()
     if st != 0:
         raise SystemExit(f"device status {st} after the timed region")
-    per_kernel = [[evs[k][i].elapsed_time(evs[k][i + 1]) for k in range(args.steps)] for i in range(nk)]
-    step_ms = [sum(per_kernel[i][k] for i in range(nk)) for k in range(args.steps)]
-    names = list(wl.kernels)
-    launches_of = {n: 1 for n in names}
-    if hasattr(wl, "kind_of"):              # several launches of one kernel per step: sum them
-        agg, cnt = {}, {}
-        for i, kd in enumerate(wl.kind_of):
-            a = agg.setdefault(kd, [0.0] * args.steps)
-            cnt[kd] = cnt.get(kd, 0) + 1
-            for k in range(args.steps):
-                a[k] += per_kernel[i][k]
-        names = list(agg)
-        per_kernel = [agg[n] for n in names]
-        launches_of = cnt
-    ms = statistics.mean(step_ms)
+    per_kernel, names, launches_of = kernel_times(wl, evs)
+    step_ms = [sum(per_kernel[i][k] for i in range(len(names))) for k in range(args.steps)]
+    ms = statistics.median(step_ms)
     per_launch_sum_ms = ms
     if hasattr(wl, "graph_step"):            # the step as users run it: one graph launch
         g_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
@@ -1131,7 +1299,7 @@ def run_ec(args):
             wl.graph_step()
             g_ev[k][1].record()
         torch.cuda.synchronize()
-        ms = statistics.mean(a.elapsed_time(b) for a, b in g_ev)
+        ms = statistics.median(a.elapsed_time(b) for a, b in g_ev)
     ms = max_over_ranks(ms, world)
     value = whole_job_value(wl.units, ms, world)
 
@@ -1141,7 +1309,7 @@ def run_ec(args):
         wl.e2e_step()
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e2e_steps = max(5, min(args.steps // 10, 200))
+    e2e_steps = max(50, min(args.steps, 200))
     barrier(world)
     torch.cuda.synchronize()
     e0.record()
@@ -1150,24 +1318,19 @@ def run_ec(args):
     e1.record()
     torch.cuda.synchronize()
     e2e_ms = max_over_ranks(e0.elapsed_time(e1) / e2e_steps, world)
+    wl.ctx.check_status(what="end to end")
 
     if rank != 0:
         return
-    peak, peak_src = hbm_peak()
-    algo = wl.algorithmic_bytes()
-    kern = {}
-    for i, name in enumerate(names):
-        kms = statistics.mean(per_kernel[i])
-        gbs = algo[name] / (kms * 1e-3) / 1e9
-        kern[name] = {"ms": kms, "share": kms / statistics.mean(step_ms), "algorithmic_bytes": algo[name],
-                      "achieved_gbs": gbs, "frac_of_peak": gbs / peak, "launches_per_step": launches_of[name]}
+    kern = kernel_table(wl, per_kernel, names, launches_of, peak)
     dom = max(kern, key=lambda k: kern[k]["ms"])
-    traffic = measured_traffic(dom, args.workload)
+    traffic = measured_traffic(dom, args.workload if not args.sources else f"{args.workload}_s{args.sources}")
     roof = {"bound": "hbm", "kernel": dom, "achieved": kern[dom]["achieved_gbs"], "peak": peak,
             "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)" if peak_src == "measured" else "fallback",
             "unit": "GB/s", "frac": kern[dom]["achieved_gbs"] / peak, "traffic": traffic}
     cfg = {"workload": f"{args.workload}: {wl.desc}",
            "l2": "flushed between timed steps (2x L2 written, then 2x L2 read; outside the events)",
+           "timing": f"median over {args.steps} steps of the per-kernel CUDA events",
            "pixel_layers_per_step": wl.units, "parallelism": f"replicas x{world}"}
     if hasattr(wl, "compressed_bytes"):
         cfg["rle_compressed_bytes_per_step"] = wl.compressed_bytes()
@@ -1178,7 +1341,8 @@ def run_ec(args):
             "data": "synthetic (seeded boxes / layers shaped like the thesis's workloads)",
             "config": cfg, "roofline": roof, "kernels": kern,
             "e2e": {"value": whole_job_value(wl.units, e2e_ms, world), "unit": UNIT,
-                    "ms_per_step": e2e_ms, "h2d_bytes_per_step": wl.h2d, "d2h_bytes_per_step": wl.d2h},
+                    "ms_per_step": e2e_ms, "steps": e2e_steps, "h2d_bytes_per_step": wl.h2d,
+                    "d2h_bytes_per_step": wl.d2h},
             "gpu_launches": wl.launches_per_step() * args.steps,
             "clocks": clk, "wall_s_timed_loop": t_wall}
     if hasattr(wl, "graph_step"):
@@ -1189,17 +1353,23 @@ def run_ec(args):
         pt = _timed(wl.per_tile, flush, 10)
         line["batched_vs_per_tile"] = {"batched_ms": ms, "per_tile_ms": pt, "speedup": pt / ms,
                                        "plan_s": wl.plan_s, "config": wl.batch.config}
-    if args.workload == "cfg2" and not args.no_extras:
-        line["alpha_fwd_bwd"] = alpha_fwd_bwd_ratio(device, flush, peak)
     if world == 1 and not args.no_cpu_baseline and hasattr(wl, "oracle_step"):
-        wl_cpu = wl
-        line["cpu_baseline"] = cpu_baseline(wl_cpu)
+        line["cpu_baseline"] = cpu_baseline(args, wl)
+    if args.workload == "cfg5d" and not args.sources and not args.no_extras:
+        # free the headline's buffers, then the other targets beside it
+        del wl
+        torch.cuda.empty_cache()
+        line["secondary"] = {"cfg2": depth_secondary("cfg2", device, flush, peak)}
+        line["batched_vs_per_tile"] = batched_extra(device, flush, peak)
+        line["alpha_fwd_bwd"] = alpha_fwd_bwd_ratio(device, flush, peak)
     print(json.dumps(line), flush=True)
 
 
 def main():
     args = parse()
-    if args.impl == "reference":
+    if args.oracle_single_core:
+        oracle_single_core(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ec(args)

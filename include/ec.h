@@ -231,7 +231,11 @@ typedef struct ec_batch ec_batch;
  * synchronises the device. */
 ec_status ec_batch_plan(ec_ctx* ctx, const ec_job* jobs, int32_t njobs,
                         const ec_batch_config* cfg, ec_batch** plan);
-/* Enqueue the captured launch on stream s. */
+/* Enqueue the captured launch on stream s.  Every replay of one plan resets
+ * and advances the same device-side queue head, so replays of one plan must
+ * not overlap on the GPU: issue them on one stream, or order them with events.
+ * Overlapping replays would skip or repeat work items and leave the
+ * destinations wrong without any error.  Distinct plans are independent. */
 ec_status ec_batch_run(ec_batch* plan, ec_stream_t s);
 /* The plan's tile shapes, work-item count and grid size (host pointers, any may be NULL). */
 ec_status ec_batch_get_config(const ec_batch* plan, ec_batch_config* cfg, int32_t* n_items,

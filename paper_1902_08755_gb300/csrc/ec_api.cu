@@ -765,6 +765,7 @@ ec_status ec_composite_depth_backward(ec_ctx* ctx, const int16_t* winner, ec_rec
 
 // -------------------------------------------------------------- batching ----
 
+#include <cctype>
 #include <cstdio>
 #include <cstdlib>
 #include <map>
@@ -899,7 +900,21 @@ std::string signature(const ec_batch& b, int device)
     }
     char buf[64];
     snprintf(buf, sizeof(buf), "%016llx", (unsigned long long)h);
-    return std::string(prop.name) + "/" + std::to_string(prop.multiProcessorCount) + "/" + buf;
+    // the key is one whitespace-free token: device names contain spaces
+    std::string name(prop.name);
+    for (char& ch : name)
+        if (!isalnum((unsigned char)ch) && ch != '-' && ch != '.') ch = '_';
+    return name + "/" + std::to_string(prop.multiProcessorCount) + "/" + buf;
+}
+
+bool shape_ok(const BatchShape& sh)
+{
+    for (int m = 0; m < 4; ++m) {
+        const int wpx = batch_warp_px(m);
+        if (sh.tw[m] <= 0 || sh.th[m] <= 0 || sh.tw[m] % wpx || sh.tw[m] > 32768 || sh.th[m] > 32768)
+            return false;
+    }
+    return true;
 }
 
 bool cache_lookup(const std::string& sig, BatchShape* sh)
@@ -911,12 +926,17 @@ bool cache_lookup(const std::string& sig, BatchShape* sh)
     if (!path) return false;
     FILE* f = fopen(path, "r");
     if (!f) return false;
-    char key[256];
-    BatchShape s{};
+    // one entry per line: key, then four tile widths and heights; lines that
+    // do not parse, or whose shape the kernel cannot run, are skipped (the
+    // batch is then autotuned and a fresh entry appended)
+    char line[512], key[256];
     bool found = false;
-    while (fscanf(f, "%255s %d %d %d %d %d %d %d %d", key, &s.tw[0], &s.th[0], &s.tw[1], &s.th[1],
-                  &s.tw[2], &s.th[2], &s.tw[3], &s.th[3]) == 9) {
-        if (sig == key) { *sh = s; found = true; }
+    while (fgets(line, sizeof(line), f)) {
+        BatchShape s{};
+        if (sscanf(line, "%255s %d %d %d %d %d %d %d %d", key, &s.tw[0], &s.th[0], &s.tw[1], &s.th[1],
+                   &s.tw[2], &s.th[2], &s.tw[3], &s.th[3]) != 9)
+            continue;
+        if (sig == key && shape_ok(s)) { *sh = s; found = true; }
     }
     fclose(f);
     if (found) g_tune_cache[sig] = *sh;
@@ -934,16 +954,6 @@ void cache_store(const std::string& sig, const BatchShape& sh)
     fprintf(f, "%s %d %d %d %d %d %d %d %d\n", sig.c_str(), sh.tw[0], sh.th[0], sh.tw[1], sh.th[1],
             sh.tw[2], sh.th[2], sh.tw[3], sh.th[3]);
     fclose(f);
-}
-
-bool shape_ok(const BatchShape& sh)
-{
-    for (int m = 0; m < 4; ++m) {
-        const int wpx = batch_warp_px(m);
-        if (sh.tw[m] <= 0 || sh.th[m] <= 0 || sh.tw[m] % wpx || sh.tw[m] > 32768 || sh.th[m] > 32768)
-            return false;
-    }
-    return true;
 }
 
 // Coordinate-descent search: depth shapes with the alpha shapes fixed, then

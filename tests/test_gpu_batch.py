@@ -176,3 +176,51 @@ def test_cfg4_1000_tiles_full_size():
                 assert np.max(np.abs(np_of(jb.t_final) - tf)) <= 2e-6
     del jobs, ref, tiles
     torch.cuda.empty_cache()
+
+
+_CACHE_CHILD = r"""
+import sys, torch
+sys.path.insert(0, sys.argv[1]); sys.path.insert(0, sys.argv[1] + "/tests")
+import paper_1902_08755_gb300 as ec, synthetic as S
+from test_gpu_batch import _jobs_from_tiles, _single_calls, _assert_same
+jobs = _jobs_from_tiles(S.uneven_tiles(42, 12, max_side=160, lmax=6, device="cuda"))
+ref = _single_calls(jobs)
+for jb in jobs:
+    jb.out_color.view(torch.uint8).fill_(0xA5)
+b = ec.Batch(jobs)
+b.run()
+ec.default_context().check_status()
+_assert_same(jobs, ref)
+c = b.config
+print("CFG", c["depth_tile_w"], c["depth_tile_h"], c["alpha32_tile_w"], c["alpha32_tile_h"])
+"""
+
+
+def _plan_in_child(tmp_path, cache):
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    env = dict(os.environ, EC_AUTOTUNE_CACHE=str(cache))
+    r = subprocess.run([sys.executable, "-c", _CACHE_CHILD, root], env=env, capture_output=True, text=True,
+                       timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    return [ln for ln in r.stdout.splitlines() if ln.startswith("CFG")][-1]
+
+
+def test_autotune_cache_file_round_trip(tmp_path):
+    """A plan autotuned in one process is stored in EC_AUTOTUNE_CACHE and a second
+    process loads it (nothing is appended); an entry whose shape the kernel
+    cannot run is ignored, and the batch is autotuned again."""
+    require_gpu()
+    cache = tmp_path / "tune.txt"
+    first = _plan_in_child(tmp_path, cache)
+    lines = cache.read_text().splitlines()
+    assert len(lines) == 1 and len(lines[0].split()) == 9          # key is one token
+    assert _plan_in_child(tmp_path, cache) == first
+    assert cache.read_text().splitlines() == lines                  # loaded, not re-tuned
+    key = lines[0].split()[0]
+    cache.write_text(f"{key} 0 0 0 0 0 0 0 0\n{key} 100 8 32 8 64 8 64 8\n")   # zero sizes; width not /128
+    again = _plan_in_child(tmp_path, cache)
+    assert again.split()[1] in ("128", "256")
+    assert len(cache.read_text().splitlines()) == 3                 # re-tuned and appended
