@@ -1,29 +1,28 @@
 // k_rle.cu -- run-length pixel codec kernels for sm_103a (thesis 5.5.1:
 // per-component RLE, bit-swizzle preconditioner, data decomposition).
 //
-// Compress: persistent CTAs (four per SM) take 4096-element chunks from an
-// atomic ticket and pipeline them: while chunk j+1 is copied in (cp.async),
-// chunk j is coded and its size published, then chunk j-1's offset is found
-// by a decoupled look-back and its bytes are copied out.
-//   1. Changes: every thread compares its 16 elements with their predecessors
-//      (one XOR per element; the swizzle is a bit permutation, so it commutes
-//      with the XOR) and records, per byte plane, which positions start a new
-//      run of equal bytes.
-//   2. Sparse path (at most 512 runs in the chunk, the common case for frames
-//      with flat regions): warp p lists plane p's run starts from the change
-//      masks with a warp scan and codes them 32 at a time: runs of three or
-//      more become repeat tokens, the first short run of a literal span codes
-//      the whole span; each plane is written to its own stage region.
-//   3. Dense path: each thread classifies its 16 positions for all four planes
-//      with byte-SIMD compares on a plane-major copy (a byte is part of a
-//      repeat iff one of the three windows of 3 around it is constant); a
-//      block max-scan of segment starts splits tokens at 128 bytes and a block
-//      sum-scan of per-position output sizes places every byte.
-//   4. The chunk's offset inside the stream comes from the look-back over the
-//      job's preceding chunks; a chunk waits only for lower tickets, which
-//      running CTAs code before any higher one, and every wait is bounded
-//      (EC_ERR_TIMEOUT).  Chunk 0 writes the header, every chunk its four
-//      end-table entries, the last chunk the stream size.
+// Compress (modes 1, 2): every warp works alone on 4096-element chunks taken
+// from an atomic ticket.  A chunk streams through two 4 KB quarter buffers in
+// shared memory (bulk asynchronous copies completing on mbarriers, each buffer
+// refilled as soon as it has been read).
+//   1. Change points: positions whose element differs from its predecessor,
+//      listed with the element.  A byte plane changes only where the element
+//      does (the swizzle permutes bits, so it commutes with the comparison).
+//   2. Sparse path (at most 128 change points): each plane's runs are the
+//      change points where that plane's byte differs from the previous one's;
+//      runs of three or more become repeat tokens, maximal spans of shorter
+//      runs literal tokens.  The streams go to a small stage in shared memory.
+//   3. Dense path: all four planes classified at once with byte-SIMD masks
+//      (a byte is part of a repeat iff one of the three windows of 3 around it
+//      is constant), with warp max- and sum-scans carried over 8 steps of 512
+//      positions; coded once for the sizes and again, from the image, when
+//      placed.
+//   4. The chunk's size is published at once; the warp places the chunk (a
+//      decoupled look-back over the job's preceding chunks for its offset, then
+//      the stage copied out) a few chunks later, when its predecessors have
+//      normally published.  Every wait is bounded (EC_ERR_TIMEOUT).  Chunk 0
+//      writes the header, every chunk its four end-table entries, the last
+//      chunk the stream size.
 //
 // Decompress: one CTA of four warps per chunk.  The header and the chunk's
 // end-table entries are fetched in one round trip and validated.  Warp p
@@ -43,16 +42,12 @@ namespace ec {
 namespace {
 
 constexpr int kChunk = EC_RLE_CHUNK;                 // 4096 elements
-constexpr int kT = 256;                              // threads per CTA
-constexpr int kPer = kChunk / kT;                    // 16 positions per thread
-constexpr int kPlaneCap = kChunk + kChunk / 128;     // worst-case stream bytes
-constexpr int kStage = 4 * kPlaneCap;                // 16512
+constexpr int kT = 256;                              // threads per mode-0 CTA
 constexpr uint32_t kMagic = 0x31524345u;             // "ECR1"
 constexpr uint64_t kAgg = 1ull << 62, kInc = 2ull << 62, kVal = (1ull << 62) - 1;
 constexpr int kSpinLimit = 1 << 22;
 
 using rlec::swizzle;
-using rlec::get_u32;
 using rlec::transpose4;
 using rlec::bcast8;
 
@@ -87,76 +82,7 @@ __device__ void write_header(uint8_t* d, const RleJobDesc& jb)
     put_u32(d + 28, jb.mode == 0 ? 1u : 4u);       // streams per chunk
 }
 
-// Two 32-bit words holding four 16-bit lanes (planes 0,1 | planes 2,3).
-struct P4 { uint32_t a, b; };
-
-template <bool MAX>
-__device__ __forceinline__ P4 combine(P4 x, P4 y)
-{
-    if (MAX) return {__vmaxu2(x.a, y.a), __vmaxu2(x.b, y.b)};
-    return {x.a + y.a, x.b + y.b};   // lanes never carry: every sum < 65536
-}
-
-// Block-wide exclusive scan of P4 values; *total receives the block total.
-template <bool MAX>
-__device__ __forceinline__ P4 block_scan(P4 v, P4* warp_tot, P4* total)
-{
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    P4 inc = v;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        P4 y;
-        y.a = __shfl_up_sync(0xffffffffu, inc.a, o);
-        y.b = __shfl_up_sync(0xffffffffu, inc.b, o);
-        if (lane >= o) inc = combine<MAX>(inc, y);
-    }
-    if (lane == 31) warp_tot[warp] = inc;
-    __syncthreads();
-    P4 pre = {0u, 0u}, tot = {0u, 0u};
-#pragma unroll
-    for (int w = 0; w < kT / 32; ++w) {
-        const P4 t = warp_tot[w];
-        if (w < warp) pre = combine<MAX>(pre, t);
-        tot = combine<MAX>(tot, t);
-    }
-    P4 ex;
-    ex.a = __shfl_up_sync(0xffffffffu, inc.a, 1);
-    ex.b = __shfl_up_sync(0xffffffffu, inc.b, 1);
-    if (lane == 0) ex = {0u, 0u};
-    *total = tot;
-    return combine<MAX>(pre, ex);
-}
-
-__device__ __forceinline__ uint32_t lane16(P4 v, int p)
-{
-    const uint32_t w = p < 2 ? v.a : v.b;
-    return (p & 1) ? (w >> 16) : (w & 0xFFFFu);
-}
-
 // ------------------------------------------------------------- compress ----
-
-// The most significant bit of each byte of w, gathered into bits 0..3.
-__device__ __forceinline__ uint32_t byte_msbs(uint32_t w)
-{
-    return ((w & 0x80808080u) * 0x00204081u) >> 28;
-}
-
-// 4-bit mask of the bytes of a and b that are equal (bit i = byte i).
-__device__ __forceinline__ uint32_t eq_bytes(uint32_t a, uint32_t b)
-{
-    const uint32_t x = a ^ b;                                   // zero byte <=> equal
-    const uint32_t t = ~(((x & 0x7F7F7F7Fu) + 0x7F7F7F7Fu) | x | 0x7F7F7F7Fu);
-    return byte_msbs(t);
-}
-
-
-// Bits [lo, hi) set (0 <= lo, hi <= 31).
-__device__ __forceinline__ uint32_t bit_range(int lo, int hi)
-{
-    lo = max(lo, 0);
-    hi = min(hi, 31);
-    return hi > lo ? ((1u << hi) - 1u) & ~((1u << lo) - 1u) : 0u;
-}
 
 __device__ __forceinline__ uint64_t warp_sum(uint64_t v)
 {
@@ -164,44 +90,6 @@ __device__ __forceinline__ uint64_t warp_sum(uint64_t v)
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     return v;
 }
-
-constexpr int kSparseMax = 512;               // most segments (all planes) the sparse path takes
-constexpr int kCPerSM = 4;                    // resident compress CTAs per SM
-// Element buffer: 4096 elements; the dense path later reuses it for the plane-
-// major copy and then as its output stage (<= kStage bytes + 16 of slack).
-constexpr int kRawBytes = kStage + 16;
-// Sparse stage: plane p's stream gets a region of sp_region(n_p) bytes (see
-// sparse_plane), at most 3 * kSparseMax + 4 * (kChunk / 64 + 3) in all, + slack.
-constexpr int kSpBytes = 3 * kSparseMax + 4 * (kChunk / 64) + 64;
-constexpr int kSegBytes = 2 * kSparseMax;     // segment starts of the sparse path
-constexpr int kChmBytes = 4 * kT * 2;         // one 16-bit change mask per thread and plane
-constexpr size_t kCompressSmem = 3ull * kRawBytes + 2ull * kSpBytes + kSegBytes + kChmBytes;
-constexpr uint32_t kNone = 0xFFFFFFFFu;
-static_assert(kRawBytes % 16 == 0 && kSpBytes % 16 == 0 && kSegBytes % 16 == 0, "16-byte aligned regions");
-static_assert(3 * kSparseMax + 4 * (kChunk / 64 + 3) + 16 <= kSpBytes, "sparse stage bound");
-
-// Element q of a chunk sits at word raw_idx(q) of its buffer.  The 16-byte
-// groups are permuted inside every 128 bytes (XOR with bits 3..5 of the group
-// index), so that a quarter warp reading 16 consecutive elements per thread
-// touches all 32 banks.
-__device__ __forceinline__ int raw_idx(int q) { return (((q >> 2) ^ ((q >> 5) & 7)) << 2) | (q & 3); }
-
-__device__ __forceinline__ void cp_async16(void* smem, const void* gmem)
-{
-    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s), "l"(gmem) : "memory");
-}
-
-__device__ __forceinline__ void cp_async4(void* smem, const void* gmem)
-{
-    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(s), "l"(gmem) : "memory");
-}
-
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-
-template <int K>
-__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(K) : "memory"); }
 
 // The chunk-size flags carry their own value, so relaxed accesses suffice.
 __device__ __forceinline__ void st_flag(uint64_t* p, uint64_t v)
@@ -214,38 +102,6 @@ __device__ __forceinline__ uint64_t ld_flag(const uint64_t* p)
     uint64_t v;
     asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
     return v;
-}
-
-// Start the copy of work unit `unit`'s elements into `raw` (positions past the
-// chunk's end are left as they are and never used).
-__device__ void load_chunk(const RleJobDesc& jb, uint32_t unit, uint32_t* raw)
-{
-    const uint32_t c = unit - jb.first_unit;
-    if (c >= jb.n_chunks) return;                     // empty image
-    const uint32_t n = (uint32_t)jb.w * (uint32_t)jb.h, q0 = c * (uint32_t)kChunk;
-    const int len = (int)min((uint32_t)kChunk, n - q0);
-    const uint32_t w = (uint32_t)jb.w;
-    const int tid = threadIdx.x;
-    if (jb.vec) {                                     // groups of 4 never straddle a row
-        const bool dense = jb.pitch == jb.w;
-#pragma unroll
-        for (int k = 0; k < kChunk / 4 / kT; ++k) {
-            const int q = 4 * (tid + k * kT);
-            if (q < len) {
-                size_t e = q0 + q;
-                if (!dense) {
-                    const uint32_t y = (q0 + q) / w;
-                    e = (size_t)y * jb.pitch + (q0 + q - y * w);
-                }
-                cp_async16(raw + raw_idx(q), jb.src + e);
-            }
-        }
-    } else {
-        for (int t = tid; t < len; t += kT) {
-            const uint32_t q = q0 + t, y = q / w;
-            cp_async4(raw + raw_idx(t), jb.src + (size_t)y * jb.pitch + (q - y * w));
-        }
-    }
 }
 
 // Exclusive prefix of work unit `unit`'s output inside its job's payload: the
@@ -283,23 +139,6 @@ __device__ uint64_t look_back(uint64_t* flags, uint32_t unit, uint32_t first_uni
     return acc;
 }
 
-// What the finishing step needs of a coded chunk.
-struct ChunkMeta {
-    uint32_t unit, job, total, dense;
-    uint32_t pend[4];        // end of plane p's stream inside the chunk's output
-    uint32_t roff[4];        // sparse path: plane p's region in the stage
-};
-
-// Shared state of one compress CTA.
-struct CState {
-    P4 wt_a[kT / 32], wt_b[kT / 32];
-    uint32_t tk[3], tj[3];   // ticket ring: work unit and its job
-    uint4 wcnt[kT / 32];     // change counts per warp and plane
-    uint32_t ptot[4];        // sparse path: stream size per plane
-    ChunkMeta meta[2];
-    uint64_t off;
-};
-
 // Publish the chunk's size: inclusive for the job's first chunk, else an
 // aggregate that the look-back of later chunks may sum.
 __device__ __forceinline__ void publish(uint64_t* flags, uint32_t unit, uint32_t first_unit, uint32_t total)
@@ -307,325 +146,6 @@ __device__ __forceinline__ void publish(uint64_t* flags, uint32_t unit, uint32_t
     st_flag(flags + unit, (unit == first_unit ? kInc : kAgg) | (uint64_t)total);
 }
 
-// Bytes reserved for a plane stream of n segments on the sparse path: a
-// repeat segment of length L codes to 2 * ceil(L / 128) <= 2 + L / 64 bytes
-// and a literal span of k short runs to at most 3k bytes, so a plane codes
-// to at most 3n + kChunk / 64 bytes.
-__device__ __forceinline__ uint32_t sp_region(uint32_t n) { return (3u * n + kChunk / 64 + 3u) & ~3u; }
-
-// Sparse path, one warp per plane: the plane's segments (maximal runs of one
-// byte value) are listed by start position from the change masks, then coded
-// 32 at a time.  Runs of three or more become repeat tokens; the first short
-// run of a literal span walks to the span's end and codes the whole span.
-// Writes the stream to `out` and returns its size.
-__device__ uint32_t sparse_plane(int p, const uint32_t* raw, const uint16_t* chm, uint16_t* seg,
-                                 uint8_t* out, uint32_t n, int len, bool sw)
-{
-    const int lane = threadIdx.x & 31;
-    // masks of threads 8l .. 8l+7 = positions 128l .. 128l+127, 32 per word
-    const uint4 mm = *reinterpret_cast<const uint4*>(chm + p * kT + 8 * lane);
-    const uint32_t c = __popc(mm.x) + __popc(mm.y) + __popc(mm.z) + __popc(mm.w);
-    uint32_t incl = c;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
-        if (lane >= o) incl += y;
-    }
-    uint32_t at = incl - c;
-    const uint32_t wd[4] = {mm.x, mm.y, mm.z, mm.w};
-#pragma unroll
-    for (int k = 0; k < 4; ++k)
-        for (uint32_t m = wd[k]; m; m &= m - 1u) seg[at++] = (uint16_t)(128 * lane + 32 * k + __ffs(m) - 1);
-    __syncwarp();
-
-    const int sh = 8 * p;
-    uint32_t carry = 0;
-    for (uint32_t r = 0; r < n; r += 32) {
-        const uint32_t i = r + lane;
-        uint32_t cost = 0, kind = 0;
-        int s = 0, L = 0;
-        if (i < n) {
-            s = seg[i];
-            const int e = i + 1 < n ? (int)seg[i + 1] : len;
-            L = e - s;
-            if (L >= 3) {
-                kind = 1;
-                cost = 2u * (uint32_t)((L + 127) >> 7);
-            } else if (i == 0 || s - (int)seg[i - 1] >= 3) {
-                int end = e;                              // first short run: find the span's end
-                for (uint32_t j = i + 1; j < n; ++j) {
-                    const int en = j + 1 < n ? (int)seg[j + 1] : len;
-                    if (en - end >= 3) break;
-                    end = en;
-                }
-                L = end - s;
-                kind = 2;
-                cost = (uint32_t)(L + ((L + 127) >> 7));
-            }
-        }
-        uint32_t inc = cost;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
-            if (lane >= o) inc += y;
-        }
-        uint32_t o = carry + inc - cost;
-        carry += __shfl_sync(0xffffffffu, inc, 31);
-        if (kind == 1u) {
-            uint32_t e = raw[raw_idx(s)];
-            if (sw) e = swizzle(e);
-            const uint8_t v = (uint8_t)(e >> sh);
-            for (int rr = L; rr > 0; rr -= 128) {
-                out[o] = (uint8_t)(127 + min(rr, 128));
-                out[o + 1] = v;
-                o += 2;
-            }
-        } else if (kind == 2u) {
-            for (int d = 0; d < L; d += 128) {
-                const int m = min(L - d, 128);
-                out[o++] = (uint8_t)(m - 1);
-                for (int t = 0; t < m; ++t) {
-                    uint32_t e = raw[raw_idx(s + d + t)];
-                    if (sw) e = swizzle(e);
-                    out[o++] = (uint8_t)(e >> sh);
-                }
-            }
-        }
-    }
-    return carry;
-}
-
-// Dense path: every position is classified with byte-SIMD bit masks on a
-// plane-major copy of the chunk (pl[b * kChunk + q] = plane b of element q),
-// which lies in the element buffer; once classified, that buffer becomes the
-// stage.
-__device__ void dense_chunk(uint8_t* pl, CState& S, ChunkMeta& M, int len,
-                            uint64_t* flags, uint32_t unit, uint32_t first_unit)
-{
-    const int tid = threadIdx.x;
-    // classify this thread's 16 positions of every plane with bit masks.
-    // Bit i of the 24-bit masks stands for position P0 - 4 + i.
-    const int P0 = tid * kPer;
-    const uint32_t VQ = bit_range(4 - P0, len - P0 + 4);          // 0 <= q < len
-    const uint32_t VEQ = bit_range(5 - P0, len - P0 + 4);         // 1 <= q < len
-    const uint32_t HIGH = bit_range(len - P0 + 4, 24);            // q >= len
-    const uint32_t Q0 = P0 == 0 ? (1u << 4) : 0u;                 // q == 0
-    uint32_t REP[4], SEG[4];
-    uint4 bytes[4];
-#pragma unroll
-    for (int b = 0; b < 4; ++b) {
-        const uint8_t* base = pl + b * kChunk + P0;
-        const uint4 v = *reinterpret_cast<const uint4*>(base);
-        // neighbours outside the chunk only feed masked-off bits
-        const uint32_t wm = P0 > 0 ? *reinterpret_cast<const uint32_t*>(base - 4) : 0u;
-        const uint32_t wp = P0 + kPer < kChunk ? *reinterpret_cast<const uint32_t*>(base + 16) : 0u;
-        bytes[b] = v;
-        // eq bit i: byte at position P0-4+i equals its predecessor
-        uint32_t EQ = eq_bytes(wm, wm << 8);
-        EQ |= eq_bytes(v.x, __funnelshift_l(wm, v.x, 8)) << 4;
-        EQ |= eq_bytes(v.y, __funnelshift_l(v.x, v.y, 8)) << 8;
-        EQ |= eq_bytes(v.z, __funnelshift_l(v.y, v.z, 8)) << 12;
-        EQ |= eq_bytes(v.w, __funnelshift_l(v.z, v.w, 8)) << 16;
-        EQ |= eq_bytes(wp, __funnelshift_l(v.w, wp, 8)) << 20;
-        EQ &= VEQ & ~1u;                                          // bit 0 has no predecessor here
-        const uint32_t T3 = EQ & (EQ << 1);                       // positions i-2, i-1, i equal
-        const uint32_t R = (T3 | (T3 >> 1) | (T3 >> 2)) & VQ;     // byte lies in a run >= 3
-        const uint32_t Sg = (((R & ~EQ) | (~R & (R << 1))) & VQ) | HIGH | Q0;
-        REP[b] = (R >> 4) & 0xFFFFu;
-        SEG[b] = (Sg >> 4) & 0x1FFFFu;                            // bit 16: position P0+16
-    }
-    const uint32_t VALID = (VQ >> 4) & 0xFFFFu;
-
-    // last segment start before each thread (max-scan of position + 1)
-    P4 mine;
-    {
-        uint32_t l[4];
-#pragma unroll
-        for (int b = 0; b < 4; ++b) {
-            const uint32_t m = SEG[b] & 0xFFFFu;
-            l[b] = m ? (uint32_t)(P0 + 31 - __clz(m) + 1) : 0u;
-        }
-        mine.a = l[0] | (l[1] << 16);
-        mine.b = l[2] | (l[3] << 16);
-    }
-    P4 tot_max;
-    const P4 before = block_scan<true>(mine, S.wt_a, &tot_max);   // (barrier inside: pl is dead after it)
-
-    // piece starts (tokens hold <= 128 bytes) and output sizes
-    uint32_t PSV[4], PE[4], LIT[4], cost[4];
-    int sbin[4];
-#pragma unroll
-    for (int b = 0; b < 4; ++b) {
-        const uint32_t seg16 = SEG[b] & 0xFFFFu;
-        const int sb_in = (int)lane16(before, b) - 1;            // -1 only for position 0
-        sbin[b] = sb_in;
-        uint32_t PS = seg16;
-        const int first = seg16 ? __ffs(seg16) - 1 : 16;
-        if (sb_in >= 0) {                                        // continuing segment
-            const int r = (P0 - sb_in) & 127;
-            const int d = r ? 128 - r : 0;
-            if (d < first) PS |= 1u << d;
-        }
-        const int sb15 = seg16 ? P0 + 31 - __clz(seg16) : sb_in;
-        const uint32_t next = ((SEG[b] >> 16) & 1u) | (((P0 + 16 - sb15) & 127) == 0 ? 1u : 0u);
-        PSV[b] = PS & VALID;
-        PE[b] = ((PS | (next << 16)) >> 1) & VALID;
-        LIT[b] = ~REP[b] & VALID;
-        cost[b] = __popc(LIT[b]) + __popc(PSV[b]) + __popc(PSV[b] & REP[b]);
-    }
-    P4 tot;
-    const P4 off0 = block_scan<false>(P4{cost[0] | (cost[1] << 16), cost[2] | (cost[3] << 16)},
-                                      S.wt_b, &tot);
-    uint32_t pbase[4], total = 0;
-#pragma unroll
-    for (int b = 0; b < 4; ++b) {
-        pbase[b] = total;
-        total += lane16(tot, b);
-    }
-    if (tid < 4) {
-        uint32_t e = 0;
-#pragma unroll
-        for (int b = 0; b < 4; ++b) e += b <= tid ? lane16(tot, b) : 0u;
-        M.pend[tid] = e;
-    }
-    if (tid == 0) {
-        publish(flags, unit, first_unit, total);
-        M.total = total;
-        M.dense = 1u;
-    }
-
-    // emit bytes and control codes into the stage
-    uint8_t* stage = pl;
-#pragma unroll
-    for (int b = 0; b < 4; ++b) {
-        uint8_t* out = stage + pbase[b];
-        const uint32_t off = lane16(off0, b);
-        const uint32_t lit = LIT[b], psv = PSV[b], psr = PSV[b] & REP[b], seg16 = SEG[b] & 0xFFFFu;
-        const uint4 v = bytes[b];
-        auto byte_at = [&](int k) -> uint8_t {
-            const uint32_t wd = k < 8 ? (k < 4 ? v.x : v.y) : (k < 12 ? v.z : v.w);
-            return (uint8_t)(wd >> (8 * (k & 3)));
-        };
-        auto inc_at = [&](int k) -> uint32_t {
-            const uint32_t le = (2u << k) - 1u;
-            return off + __popc(lit & le) + __popc(psv & le) + __popc(psr & le);
-        };
-        for (uint32_t m = lit; m; m &= m - 1u) {
-            const int k = __ffs(m) - 1;
-            out[inc_at(k) - 1] = byte_at(k);
-        }
-        for (uint32_t m = PE[b]; m; m &= m - 1u) {
-            const int k = __ffs(m) - 1;
-            const uint32_t inc = inc_at(k);
-            const uint32_t h = seg16 & ((2u << k) - 1u);
-            const int sbk = h ? P0 + 31 - __clz(h) : sbin[b];
-            const uint32_t jj = (uint32_t)(P0 + k - sbk) & 127u;
-            if ((REP[b] >> k) & 1u) {
-                out[inc - 2] = (uint8_t)(0x80u + jj);
-                out[inc - 1] = byte_at(k);
-            } else {
-                out[inc - 2 - jj] = (uint8_t)jj;
-            }
-        }
-    }
-}
-
-// Code one chunk into its stage and publish its size: find where every byte
-// plane changes value, count the segments, then take the sparse or the dense
-// path.  `raw` holds the chunk's elements (raw_idx layout).
-__device__ void code_chunk(const RleJobDesc& jb, uint32_t unit, ChunkMeta& M, uint32_t* raw, uint8_t* sp,
-                           uint16_t* seg, uint16_t* chm, CState& S, uint64_t* flags)
-{
-    const int tid = threadIdx.x;
-    const uint32_t nc = jb.n_chunks;
-    if (nc == 0) return;                             // empty image: header only, when finished
-    const uint32_t c = unit - jb.first_unit;
-    const uint32_t n = (uint32_t)jb.w * (uint32_t)jb.h;
-    const int len = (int)min((uint32_t)kChunk, n - c * (uint32_t)kChunk);
-    const bool sw = jb.mode == 2;
-
-    // 1. value changes: bit i of CH[p] is set when plane p of element P0+i
-    // differs from element P0+i-1 (the swizzle permutes bits, so it commutes
-    // with the XOR); position 0 starts a segment in every plane
-    const int P0 = tid * kPer;
-    uint32_t e[kPer];
-#pragma unroll
-    for (int k = 0; k < kPer / 4; ++k) {
-        const uint4 v = *reinterpret_cast<const uint4*>(raw + raw_idx(P0 + 4 * k));
-        e[4 * k] = v.x; e[4 * k + 1] = v.y; e[4 * k + 2] = v.z; e[4 * k + 3] = v.w;
-    }
-    const uint32_t prev = P0 > 0 ? raw[raw_idx(P0 - 1)] : e[0];
-    const int nv = min(max(len - P0, 0), kPer);
-    uint32_t nzm = 0u;
-#pragma unroll
-    for (int i = 0; i < kPer; ++i) nzm |= (e[i] != (i ? e[i - 1] : prev) ? 1u : 0u) << i;
-    nzm &= (1u << nv) - 1u;
-    uint32_t CH[4] = {0u, 0u, 0u, 0u};
-    for (uint32_t m = nzm; m; m &= m - 1u) {
-        const int i = __ffs(m) - 1;
-        uint32_t x = raw[raw_idx(P0 + i)] ^ raw[raw_idx(P0 + i - 1)];
-        if (sw) x = swizzle(x);
-#pragma unroll
-        for (int p = 0; p < 4; ++p) CH[p] |= ((x >> (8 * p)) & 0xFFu ? 1u : 0u) << i;
-    }
-    if (P0 == 0) {
-#pragma unroll
-        for (int p = 0; p < 4; ++p) CH[p] |= 1u;
-    }
-
-    // 2. segment counts per plane; masks to shared memory for the sparse path
-    const int lane = tid & 31, warp = tid >> 5;
-    uint32_t wc[4];
-#pragma unroll
-    for (int p = 0; p < 4; ++p) {
-        chm[p * kT + tid] = (uint16_t)CH[p];
-        wc[p] = __reduce_add_sync(0xffffffffu, (uint32_t)__popc(CH[p]));
-    }
-    if (lane == 0) S.wcnt[warp] = make_uint4(wc[0], wc[1], wc[2], wc[3]);
-    __syncthreads();                                 // (also: every thread has read its elements)
-    uint32_t n0 = 0, n1 = 0, n2 = 0, n3 = 0;
-#pragma unroll
-    for (int w = 0; w < kT / 32; ++w) {
-        const uint4 v = S.wcnt[w];
-        n0 += v.x; n1 += v.y; n2 += v.z; n3 += v.w;
-    }
-
-    if (n0 + n1 + n2 + n3 <= (uint32_t)kSparseMax) {
-        // plane p: segments at seg[lb_p ..), stream at sp + ro_p
-        const uint32_t r0 = 0, r1 = sp_region(n0), r2 = r1 + sp_region(n1), r3 = r2 + sp_region(n2);
-        if (warp < 4) {
-            const uint32_t np = warp == 0 ? n0 : warp == 1 ? n1 : warp == 2 ? n2 : n3;
-            const uint32_t lb = warp == 0 ? 0u : warp == 1 ? n0 : warp == 2 ? n0 + n1 : n0 + n1 + n2;
-            const uint32_t ro = warp == 0 ? r0 : warp == 1 ? r1 : warp == 2 ? r2 : r3;
-            const uint32_t t = sparse_plane(warp, raw, chm, seg + lb, sp + ro, np, len, sw);
-            if (lane == 0) S.ptot[warp] = t;
-        }
-        __syncthreads();
-        if (tid == 0) {
-            const uint32_t e0 = S.ptot[0], e1 = e0 + S.ptot[1], e2 = e1 + S.ptot[2], e3 = e2 + S.ptot[3];
-            publish(flags, unit, jb.first_unit, e3);
-            M.total = e3;
-            M.dense = 0u;
-            M.pend[0] = e0; M.pend[1] = e1; M.pend[2] = e2; M.pend[3] = e3;
-            M.roff[0] = r0; M.roff[1] = r1; M.roff[2] = r2; M.roff[3] = r3;
-        }
-    } else {
-        // plane-major copy, written over the element buffer
-        uint8_t* pl = reinterpret_cast<uint8_t*>(raw);
-#pragma unroll
-        for (int k = 0; k < kPer / 4; ++k) {
-            uint32_t a = e[4 * k], b = e[4 * k + 1], cc = e[4 * k + 2], d = e[4 * k + 3];
-            if (sw) { a = swizzle(a); b = swizzle(b); cc = swizzle(cc); d = swizzle(d); }
-            const uint4 t = transpose4(a, b, cc, d);
-            *reinterpret_cast<uint32_t*>(pl + 0 * kChunk + P0 + 4 * k) = t.x;
-            *reinterpret_cast<uint32_t*>(pl + 1 * kChunk + P0 + 4 * k) = t.y;
-            *reinterpret_cast<uint32_t*>(pl + 2 * kChunk + P0 + 4 * k) = t.z;
-            *reinterpret_cast<uint32_t*>(pl + 3 * kChunk + P0 + 4 * k) = t.w;
-        }
-        __syncthreads();
-        dense_chunk(pl, S, M, len, flags, unit, jb.first_unit);
-    }
-}
 
 // Copy n stage bytes (src 4-byte aligned) to o, threads t, t+nt, ...: byte
 // stores up to o's first word boundary and after its last, word stores of
@@ -651,104 +171,764 @@ __device__ __forceinline__ void copy_out(uint8_t* o, const uint8_t* src, uint32_
     }
 }
 
-// Place a coded chunk in its stream and copy it out: look back for its
-// offset (warp 0), then write the payload bytes, the chunk's four end-table
-// entries, the header (chunk 0) and the stream size (last chunk).
-__device__ void finish_chunk(const RleJobDesc& jb, const ChunkMeta& M, const uint8_t* stage, CState& S,
-                             uint64_t* flags, uint32_t* status)
+// ---- compressor (modes 1 and 2): one warp per chunk ------------------------
+// Every warp works alone, chunk after chunk.  It streams each chunk through a
+// ring of four 4 KB quarter buffers in shared memory, filled by bulk
+// asynchronous copies (one per row segment) that complete on the quarter's
+// mbarrier; a quarter is refilled with the same quarter of the warp's next
+// chunk as soon as it has been read, so about three quarters are always in
+// flight.  Reading a chunk, the warp lists its change points: the positions
+// where the element differs from its predecessor, with the element there.  A
+// byte plane can change only where the element does, so each plane's runs are
+// the change points where that plane's byte differs from the previous change
+// point's, and every run's value is the byte at its start: the sparse path
+// sizes and later writes the chunk's streams from the change list alone.
+// Chunks with more change points than the list holds take the dense path,
+// which codes all four planes at once from registers (the chunk re-read from
+// global memory, mostly from L2).  A chunk's size is published as soon as it
+// is known; the warp places the chunk (look-back, then the tokens written
+// straight to their place in the stream) two chunks later, by which time the
+// chunks before it have normally published theirs.
+constexpr int kWPB = 2;                       // warps per CTA
+constexpr int kCap = 128;                     // change points the sparse path takes
+constexpr int kQ = 1024;                      // elements per quarter buffer
+constexpr int kSlots = 2;                     // quarter buffers per warp
+constexpr int kDefer = 3;                     // chunks coded but not yet placed, per warp
+
+// Stage bytes kept per plane of a sparse chunk.  A plane that codes to more
+// (possible from about 60 runs on) is not kept: the chunk is coded again from
+// the image when it is placed, like a dense one.
+constexpr int kStagePlane = 192;
+
+// A coded chunk waiting to be placed: sparse chunks keep their four plane
+// streams (plane p at stage + p * kStagePlane), dense ones (and sparse ones
+// whose streams did not fit) only their sizes.
+struct Coded {
+    uint32_t unit, job, dense;
+    uint32_t T[4];            // plane stream sizes
+    uint32_t pad;
+    uint8_t stage[4 * kStagePlane];
+};
+
+// One warp's shared memory.  Quarter s of the warp's sequence of quarters
+// (4 per chunk) goes to buf[s % kSlots].
+struct WarpRing {
+    uint32_t buf[kSlots][kQ + 4];   // + 16 guard bytes before each quarter
+    uint64_t full[kSlots];
+    uint64_t pad[4 - kSlots];       // (keeps what follows 16-byte aligned)
+    Coded def[kDefer];
+    uint32_t ce[kCap];              // the chunk being read: element at each change point
+    uint16_t cq[kCap];              // (swizzled in mode 2) and its position
+    uint8_t rl[4][kCap];            // the planes' runs: index of the change point starting each
+};
+static_assert(sizeof(Coded) % 16 == 0 && (kQ + 4) * 4 % 16 == 0 && sizeof(WarpRing) % 16 == 0,
+              "16-byte aligned buffers");
+constexpr size_t kCompressSmem = kWPB * sizeof(WarpRing);
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* b, uint32_t count)
 {
-    const int tid = threadIdx.x;
-    uint8_t* dst = reinterpret_cast<uint8_t*>(jb.dst);
-    const uint32_t nc = jb.n_chunks;
-    if (nc == 0) {                                   // empty image: header only
-        if (tid == 0) {
-            write_header(dst, jb);
-            *jb.d_size = 32u;
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(b)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* b)
+{
+    asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.shared::cta.b64 st, [%0];\n\t}" ::"r"(smem_u32(b)) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_tx(uint64_t* b, uint32_t bytes)
+{
+    asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n\t}"
+                 ::"r"(smem_u32(b)), "r"(bytes) : "memory");
+}
+
+// One try of a wait for the phase of the given parity; the thread may sleep
+// in it (up to about a microsecond) until the phase completes.
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* b, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+                 : "=r"(ok) : "r"(smem_u32(b)), "r"(parity), "r"(1000u) : "memory");
+    return ok != 0u;
+}
+
+// Wait for the phase of the given parity to complete; gives up after
+// kSpinLimit tries (recording EC_ERR_TIMEOUT) instead of spinning forever.
+__device__ __forceinline__ void mbar_wait(uint64_t* b, uint32_t parity, uint32_t* status)
+{
+    for (int i = 0; i < kSpinLimit; ++i)
+        if (mbar_try_wait(b, parity)) return;
+    set_status(status, EC_ERR_TIMEOUT);
+}
+
+// Bulk copy of `bytes` (a multiple of 16, both addresses 16-byte aligned) from
+// global to shared memory, completing on mbarrier b.
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* b)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 ::"r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(smem_u32(b)) : "memory");
+}
+
+// Elements [q, q + 4) of a chunk that starts at element q0 (q a multiple of
+// 4; zeros past len).  16-byte loads where the image allows them (the four
+// elements then lie in one row), else one load per element.
+__device__ __forceinline__ uint4 load_elems(const RleJobDesc& jb, uint32_t q0, int len, int q)
+{
+    if (q >= len) return make_uint4(0u, 0u, 0u, 0u);
+    const uint32_t w = (uint32_t)jb.w;
+    if (jb.vec) {
+        size_t e = q0 + (uint32_t)q;
+        if (jb.pitch != jb.w) {
+            const uint32_t y = (q0 + (uint32_t)q) / w;
+            e = (size_t)y * jb.pitch + (q0 + (uint32_t)q - y * w);
         }
+        return __ldg(reinterpret_cast<const uint4*>(jb.src + e));
+    }
+    uint32_t v[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        v[k] = 0u;
+        if (q + k < len) {
+            const uint32_t qq = q0 + (uint32_t)(q + k), y = qq / w;
+            v[k] = __ldg(jb.src + (size_t)y * jb.pitch + (qq - y * w));
+        }
+    }
+    return make_uint4(v[0], v[1], v[2], v[3]);
+}
+
+// Start the copy of quarter qi of chunk `unit` into W.buf[slot]: lane 0 sets the
+// expected bytes, every lane copies row segments.  Quarters with nothing to
+// copy (past the image's end, an empty image, or an image whose rows are not
+// 16-byte aligned, which is read from global memory instead) just arrive.
+__device__ void issue_quarter(const RleJobDesc& jb, uint32_t unit, int qi, int slot, WarpRing& W)
+{
+    const int lane = threadIdx.x & 31;
+    int qlen = 0;
+    uint32_t qs = 0u;
+    if (jb.n_chunks > 0 && jb.vec) {
+        const uint32_t q0 = (unit - jb.first_unit) * (uint32_t)kChunk;
+        const int len = (int)min((uint32_t)kChunk, (uint32_t)jb.w * (uint32_t)jb.h - q0);
+        qlen = min(max(len - kQ * qi, 0), kQ);
+        qs = q0 + (uint32_t)(kQ * qi);
+    }
+    if (qlen == 0) {
+        if (lane == 0) mbar_arrive(&W.full[slot]);
         return;
     }
-    const uint32_t c = M.unit - jb.first_unit;
-    const uint32_t total = M.total;
-    if (tid < 32) {
-        const uint64_t acc = look_back(flags, M.unit, jb.first_unit, total, status);
-        if (tid == 0) S.off = acc;
+    if (lane == 0) mbar_arrive_tx(&W.full[slot], 4u * (uint32_t)qlen);
+    __syncwarp();
+    uint32_t* dst = W.buf[slot] + 4;
+    const uint32_t w = (uint32_t)jb.w;
+    if (jb.pitch == jb.w) {
+        if (lane == 0) bulk_load(dst, jb.src + qs, 4u * (uint32_t)qlen, &W.full[slot]);
+        return;
     }
-    __syncthreads();
-    const uint64_t G = S.off;
+    const uint32_t y0 = qs / w, y1 = (qs + (uint32_t)qlen - 1u) / w;
+    for (uint32_t y = y0 + (uint32_t)lane; y <= y1; y += 32) {
+        const uint32_t a = y == y0 ? qs - y0 * w : 0u;                   // first column of the segment
+        const uint32_t b = min(w, qs + (uint32_t)qlen - y * w);          // its end column
+        bulk_load(dst + (y * w + a - qs), jb.src + (size_t)y * jb.pitch + a, 4u * (b - a), &W.full[slot]);
+    }
+}
+
+// Append the change points among positions [kQ qi, kQ qi + kQ) of the chunk
+// to W.ce / W.cq (the quarter's elements in shared memory at `data`, or read
+// from global memory when data is null).  carry: the element before the
+// quarter (updated to the quarter's last).  Every lane first compares its
+// four elements of all eight groups of 128 positions, one OR-reduction over
+// the warp tells which groups changed, and only those are listed.  Returns
+// false once the chunk has more than kCap change points.
+__device__ bool detect_quarter(const uint32_t* data, const RleJobDesc& jb, uint32_t q0, int len, int qi,
+                               WarpRing& W, int& m, uint32_t& carry)
+{
+    const int lane = threadIdx.x & 31;
+    const uint32_t lt = (1u << lane) - 1u;
+    constexpr int G = kQ / 128;
+    uint4 vv[G];
+    uint32_t pv[G];
+    if (data) {
+#pragma unroll
+        for (int g = 0; g < G; ++g) {
+            vv[g] = *reinterpret_cast<const uint4*>(data + 128 * g + 4 * lane);
+            pv[g] = data[128 * g + 4 * lane - 1];         // g = lane = 0 reads the guard word
+        }
+    } else {
+#pragma unroll
+        for (int g = 0; g < G; ++g) vv[g] = load_elems(jb, q0, len, kQ * qi + 128 * g + 4 * lane);
+        uint32_t cy = carry;
+#pragma unroll
+        for (int g = 0; g < G; ++g) {
+            pv[g] = __shfl_up_sync(0xffffffffu, vv[g].w, 1);
+            const uint32_t last = __shfl_sync(0xffffffffu, vv[g].w, 31);
+            if (lane == 0) pv[g] = cy;
+            cy = last;
+        }
+    }
+    if (lane == 0) pv[0] = qi == 0 ? ~vv[0].x : carry;    // position 0 is always listed
+    carry = __shfl_sync(0xffffffffu, vv[G - 1].w, 31);   // (used only when the quarter is full)
+    const int qend = min(len - kQ * qi, kQ);              // positions of this quarter
+    uint32_t mine = 0u;
+#pragma unroll
+    for (int g = 0; g < G; ++g) {
+        const uint4 v = vv[g];
+        const uint32_t x = (v.x ^ pv[g]) | (v.y ^ v.x) | (v.z ^ v.y) | (v.w ^ v.z);
+        mine |= (x != 0u ? 1u : 0u) << g;
+    }
+    if (qend < kQ) {                                      // the chunk's last quarter: positions past len
+#pragma unroll
+        for (int g = 0; g < G; ++g)
+            if (128 * g + 4 * lane >= qend) mine &= ~(1u << g);
+    }
+    const uint32_t groups = __reduce_or_sync(0xffffffffu, mine);
+#pragma unroll
+    for (int g = 0; g < G; ++g) {
+        if (!((groups >> g) & 1u)) continue;
+        const uint4 v = vv[g];
+        const int q = 128 * g + 4 * lane;                 // within the quarter
+        uint32_t f = (v.x != pv[g] ? 1u : 0u) | (v.y != v.x ? 2u : 0u) | (v.z != v.y ? 4u : 0u) |
+                     (v.w != v.z ? 8u : 0u);
+        if (q + 4 > qend) f &= q >= qend ? 0u : (1u << (qend - q)) - 1u;
+        const uint32_t b0 = __ballot_sync(0xffffffffu, f & 1u), b1 = __ballot_sync(0xffffffffu, f & 2u);
+        const uint32_t b2 = __ballot_sync(0xffffffffu, f & 4u), b3 = __ballot_sync(0xffffffffu, f & 8u);
+        const int cnt = __popc(b0) + __popc(b1) + __popc(b2) + __popc(b3);
+        if (m + cnt > kCap) return false;
+        int o = m + __popc(b0 & lt) + __popc(b1 & lt) + __popc(b2 & lt) + __popc(b3 & lt);
+        const int qq = kQ * qi + q;
+        if (f & 1u) { W.cq[o] = (uint16_t)qq; W.ce[o] = v.x; ++o; }
+        if (f & 2u) { W.cq[o] = (uint16_t)(qq + 1); W.ce[o] = v.y; ++o; }
+        if (f & 4u) { W.cq[o] = (uint16_t)(qq + 2); W.ce[o] = v.z; ++o; }
+        if (f & 8u) { W.cq[o] = (uint16_t)(qq + 3); W.ce[o] = v.w; }
+        m += cnt;
+    }
+    return true;
+}
+
+// Sparse path, fast case: at most 32 change points and every run of every
+// plane at least 3 bytes long (so every run is repeat tokens).  Lane i holds
+// change point i; for each plane the lanes that start a run are found with
+// one ballot, each run's end is the next such lane's position (a shuffle) or
+// the chunk's end, and one scan over the four planes (16-bit halves) places
+// the tokens.  Returns false, writing nothing, when the case does not apply.
+__device__ bool code_sparse_fast(const WarpRing& W, int m, int len, uint32_t* T, uint8_t* stage)
+{
+    const int lane = threadIdx.x & 31;
+    if (m > 32) return false;
+    __syncwarp();                                     // the change list is complete
+    const bool valid = lane < m;
+    const uint32_t e = valid ? W.ce[lane] : 0u;
+    const int q = valid ? (int)W.cq[lane] : 0;
+    uint32_t diff = e ^ __shfl_up_sync(0xffffffffu, e, 1);
+    if (lane == 0) diff = 0xFFFFFFFFu;                // change point 0 starts a run in every plane
+    const uint32_t above = lane == 31 ? 0u : ~((2u << lane) - 1u);
+    uint32_t cost[4], K[4];
+    int L[4];
+    bool bad = false;
+#pragma unroll
+    for (int p = 0; p < 4; ++p) {
+        const bool keep = valid && ((diff >> (8 * p)) & 0xFFu) != 0u;
+        K[p] = __ballot_sync(0xffffffffu, keep);
+        const uint32_t nm = K[p] & above;
+        const int qn = __shfl_sync(0xffffffffu, q, nm ? __ffs(nm) - 1 : 0);
+        L[p] = keep ? (nm ? qn : len) - q : 0;
+        bad |= keep && L[p] < 3;
+        cost[p] = keep ? 2u * (uint32_t)((L[p] + 127) >> 7) : 0u;
+    }
+    if (__any_sync(0xffffffffu, bad)) return false;
+    const uint32_t a = cost[0] | (cost[1] << 16), b = cost[2] | (cost[3] << 16);
+    uint32_t ia = a, ib = b;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t ya = __shfl_up_sync(0xffffffffu, ia, o), yb = __shfl_up_sync(0xffffffffu, ib, o);
+        if (lane >= o) { ia += ya; ib += yb; }
+    }
+    const uint32_t ta = __shfl_sync(0xffffffffu, ia, 31), tb = __shfl_sync(0xffffffffu, ib, 31);
+    const uint32_t ea = ia - a, eb = ib - b;
+    const uint32_t ex[4] = {ea & 0xFFFFu, ea >> 16, eb & 0xFFFFu, eb >> 16};
+    T[0] = ta & 0xFFFFu; T[1] = ta >> 16; T[2] = tb & 0xFFFFu; T[3] = tb >> 16;
+#pragma unroll
+    for (int p = 0; p < 4; ++p) {
+        if (!((K[p] >> lane) & 1u) || ex[p] + cost[p] > (uint32_t)kStagePlane) continue;
+        uint8_t* ob = stage + p * kStagePlane + ex[p];
+        const uint8_t v = (uint8_t)(e >> (8 * p));
+        for (int rr = L[p]; rr > 0; rr -= 128) {
+            ob[0] = (uint8_t)(127 + min(rr, 128));
+            ob[1] = v;
+            ob += 2;
+        }
+    }
+    return true;
+}
+
+// Sparse path, the four planes together (their chains of shuffles and shared
+// memory accesses overlap).  Runs of plane p: change point i starts one iff
+// its plane-p byte differs from change point i-1's (point 0 always does);
+// rl[p][0, n_p) lists those change points.  Then the runs are coded 32 at a
+// time: a run of three or more bytes becomes repeat tokens; the first short
+// run of a literal span walks to the span's end and codes the whole span.
+// Plane p's stream goes to stage + p * kStagePlane (as far as it fits); its
+// size to T[p].
+__device__ void code_sparse(WarpRing& W, int m, int len, uint32_t* T, uint8_t* stage)
+{
+    const int lane = threadIdx.x & 31;
+    const uint32_t lt = (1u << lane) - 1u;
+    __syncwarp();                                     // the change list is complete
+    int n[4] = {0, 0, 0, 0};
+    uint32_t preve = 0u;
+    for (int r = 0; r < m; r += 32) {
+        const int i = r + lane;
+        const bool valid = i < m;
+        const uint32_t e = valid ? W.ce[i] : 0u;
+        uint32_t ep = __shfl_up_sync(0xffffffffu, e, 1);
+        if (lane == 0) ep = preve;
+        const uint32_t diff = e ^ ep;
+#pragma unroll
+        for (int p = 0; p < 4; ++p) {
+            const bool keep = valid && (i == 0 || ((diff >> (8 * p)) & 0xFFu) != 0u);
+            const uint32_t K = __ballot_sync(0xffffffffu, keep);
+            if (keep) W.rl[p][n[p] + __popc(K & lt)] = (uint8_t)i;
+            n[p] += __popc(K);
+        }
+        preve = __shfl_sync(0xffffffffu, e, 31);
+    }
+    __syncwarp();
+    uint32_t carry[4] = {0u, 0u, 0u, 0u};
+    const int nmax = max(max(n[0], n[1]), max(n[2], n[3]));
+    for (int r = 0; r < nmax; r += 32) {
+        const int i = r + lane;
+        uint32_t cost[4], kind[4];
+        int L[4];
+#pragma unroll
+        for (int p = 0; p < 4; ++p) {
+            const uint8_t* R = W.rl[p];
+            const int np = n[p];
+            auto start = [&](int k) { return (int)W.cq[R[k]]; };
+            cost[p] = 0u;
+            kind[p] = 0u;
+            L[p] = 0;
+            if (i < np) {
+                const int s = start(i);
+                const int e = i + 1 < np ? start(i + 1) : len;
+                L[p] = e - s;
+                if (L[p] >= 3) {
+                    kind[p] = 1u;
+                    cost[p] = 2u * (uint32_t)((L[p] + 127) >> 7);
+                } else if (i == 0 || s - start(i - 1) >= 3) {
+                    int end = e;                          // first short run: find the span's end
+                    for (int j = i + 1; j < np; ++j) {
+                        const int en = j + 1 < np ? start(j + 1) : len;
+                        if (en - end >= 3) break;
+                        end = en;
+                    }
+                    L[p] = end - s;
+                    kind[p] = 2u;
+                    cost[p] = (uint32_t)(L[p] + ((L[p] + 127) >> 7));
+                }
+            }
+        }
+        // four scans at once: planes 0,1 and 2,3 in 16-bit halves
+        const uint32_t a = cost[0] | (cost[1] << 16), b = cost[2] | (cost[3] << 16);
+        uint32_t ia = a, ib = b;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t ya = __shfl_up_sync(0xffffffffu, ia, o), yb = __shfl_up_sync(0xffffffffu, ib, o);
+            if (lane >= o) { ia += ya; ib += yb; }
+        }
+        const uint32_t ta = __shfl_sync(0xffffffffu, ia, 31), tb = __shfl_sync(0xffffffffu, ib, 31);
+        const uint32_t ea = ia - a, eb = ib - b;
+        const uint32_t ex[4] = {ea & 0xFFFFu, ea >> 16, eb & 0xFFFFu, eb >> 16};
+        const uint32_t tot[4] = {ta & 0xFFFFu, ta >> 16, tb & 0xFFFFu, tb >> 16};
+#pragma unroll
+        for (int p = 0; p < 4; ++p) {
+            uint32_t o = carry[p] + ex[p];
+            carry[p] += tot[p];
+            if (kind[p] == 0u) continue;
+            const uint8_t* R = W.rl[p];
+            const int np = n[p];
+            const int sh = 8 * p;
+            auto start = [&](int k) { return (int)W.cq[R[k]]; };
+            auto value = [&](int k) { return (uint8_t)(W.ce[R[k]] >> sh); };
+            uint8_t* ob = stage + p * kStagePlane;
+            if (o + cost[p] > (uint32_t)kStagePlane) continue;   // not kept (see kStagePlane)
+            if (kind[p] == 1u) {
+                const uint8_t v = value(i);
+                for (int rr = L[p]; rr > 0; rr -= 128) {
+                    ob[o] = (uint8_t)(127 + min(rr, 128));
+                    ob[o + 1] = v;
+                    o += 2;
+                }
+            } else {
+                // the span's bytes: run j contributes (start of j+1 - start of j) copies of its byte
+                int j = i;
+                uint8_t v = value(j);
+                int rem = (j + 1 < np ? start(j + 1) : len) - start(j);
+                for (int d = 0; d < L[p]; d += 128) {
+                    const int ml = min(L[p] - d, 128);
+                    ob[o++] = (uint8_t)(ml - 1);
+                    for (int t = 0; t < ml; ++t) {
+                        ob[o++] = v;
+                        if (--rem == 0 && d + t + 1 < L[p]) {
+                            ++j;
+                            v = value(j);
+                            rem = (j + 1 < np ? start(j + 1) : len) - start(j);
+                        }
+                    }
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int p = 0; p < 4; ++p) T[p] = carry[p];
+}
+
+// Four 16-bit lanes in two words (planes 0,1 | planes 2,3).
+struct P4 { uint32_t a, b; };
+
+template <bool MAX>
+__device__ __forceinline__ P4 combine(P4 x, P4 y)
+{
+    if (MAX) return {__vmaxu2(x.a, y.a), __vmaxu2(x.b, y.b)};
+    return {x.a + y.a, x.b + y.b};   // lanes never carry: every sum < 65536
+}
+
+__device__ __forceinline__ uint32_t lane16(P4 v, int p)
+{
+    const uint32_t w = p < 2 ? v.a : v.b;
+    return (p & 1) ? (w >> 16) : (w & 0xFFFFu);
+}
+
+// Warp-wide exclusive scan of P4 values; *total receives the warp's total.
+template <bool MAX>
+__device__ __forceinline__ P4 warp_scan4(P4 v, int lane, P4* total)
+{
+    P4 inc = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        P4 y;
+        y.a = __shfl_up_sync(0xffffffffu, inc.a, o);
+        y.b = __shfl_up_sync(0xffffffffu, inc.b, o);
+        if (lane >= o) inc = combine<MAX>(inc, y);
+    }
+    total->a = __shfl_sync(0xffffffffu, inc.a, 31);
+    total->b = __shfl_sync(0xffffffffu, inc.b, 31);
+    P4 ex;
+    ex.a = __shfl_up_sync(0xffffffffu, inc.a, 1);
+    ex.b = __shfl_up_sync(0xffffffffu, inc.b, 1);
+    if (lane == 0) ex = {0u, 0u};
+    return ex;
+}
+
+// The most significant bit of each byte of w, gathered into bits 0..3.
+__device__ __forceinline__ uint32_t byte_msbs(uint32_t w)
+{
+    return ((w & 0x80808080u) * 0x00204081u) >> 28;
+}
+
+// 4-bit mask of the bytes of a and b that are equal (bit i = byte i).
+__device__ __forceinline__ uint32_t eq_bytes(uint32_t a, uint32_t b)
+{
+    const uint32_t x = a ^ b;                                   // zero byte <=> equal
+    const uint32_t t = ~(((x & 0x7F7F7F7Fu) + 0x7F7F7F7Fu) | x | 0x7F7F7F7Fu);
+    return byte_msbs(t);
+}
+
+// Bits [lo, hi) set (0 <= lo, hi <= 31).
+__device__ __forceinline__ uint32_t bit_range(int lo, int hi)
+{
+    lo = max(lo, 0);
+    hi = min(hi, 31);
+    return hi > lo ? ((1u << hi) - 1u) & ~((1u << lo) - 1u) : 0u;
+}
+
+// Elements [q, q + 4) of the chunk (q a multiple of 4), swizzled in mode 2.
+__device__ __forceinline__ uint4 load4(const RleJobDesc& jb, uint32_t q0, int len, int q, bool sw)
+{
+    uint4 v = load_elems(jb, q0, len, q);
+    if (sw) { v.x = swizzle(v.x); v.y = swizzle(v.y); v.z = swizzle(v.z); v.w = swizzle(v.w); }
+    return v;
+}
+
+// Dense path: every position is classified with byte-SIMD bit masks, all four
+// planes at once.  The chunk is taken in 8 steps of 512 positions; in step k
+// lane l holds positions [P0, P0 + 16), P0 = 16 (32 k + l), in registers, and
+// the bytes just before and after them come from its neighbours (shuffles)
+// and the previous / next step.  A byte lies in a repeat iff one of the three
+// windows of 3 around it is constant; a warp max-scan of segment starts
+// (carried across steps) cuts tokens every 128 bytes of a segment, and a warp
+// sum-scan of output bytes (carried likewise) places them.  Without EMIT the
+// plane stream sizes are returned in T; with EMIT (T holding them) the streams
+// are written to out.
+template <bool EMIT>
+__device__ __noinline__ void dense_chunk(const RleJobDesc& jb, uint32_t q0, int len, bool sw, uint32_t* T, uint8_t* out)
+{
+    const int lane = threadIdx.x & 31;
+    P4 cmax = {0u, 0u}, csum = {0u, 0u};
+    uint32_t prevw[4] = {0u, 0u, 0u, 0u};
+    uint32_t pbase[4] = {0u, 0u, 0u, 0u};
+    if (EMIT) {
+        pbase[1] = T[0];
+        pbase[2] = T[0] + T[1];
+        pbase[3] = T[0] + T[1] + T[2];
+    }
+#pragma unroll 1
+    for (int k = 0; k < kChunk / 512 && 512 * k < len; ++k) {
+        const int P0 = 16 * (32 * k + lane);
+        uint4 t[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const uint4 g = load4(jb, q0, len, P0 + 4 * i, sw);
+            t[i] = transpose4(g.x, g.y, g.z, g.w);              // t[i] word b = plane b of 4 positions
+        }
+        uint4 tn = make_uint4(0u, 0u, 0u, 0u);
+        if (lane == 31) {
+            const uint4 g = load4(jb, q0, len, P0 + 16, sw);
+            tn = transpose4(g.x, g.y, g.z, g.w);
+        }
+        const uint32_t VQ = bit_range(4 - P0, len - P0 + 4);          // 0 <= q < len
+        const uint32_t VEQ = bit_range(5 - P0, len - P0 + 4);         // 1 <= q < len
+        const uint32_t HIGH = bit_range(len - P0 + 4, 24);            // q >= len
+        const uint32_t Q0 = P0 == 0 ? (1u << 4) : 0u;                 // q == 0
+        const uint32_t VALID = (VQ >> 4) & 0xFFFFu;
+        uint32_t REP[4], SEG[4];
+        uint4 bytes[4];
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+            auto pw = [&](const uint4& x) { return b == 0 ? x.x : b == 1 ? x.y : b == 2 ? x.z : x.w; };
+            const uint4 v = make_uint4(pw(t[0]), pw(t[1]), pw(t[2]), pw(t[3]));
+            uint32_t wm = __shfl_up_sync(0xffffffffu, v.w, 1);
+            if (lane == 0) wm = prevw[b];
+            uint32_t wp = __shfl_down_sync(0xffffffffu, v.x, 1);
+            if (lane == 31) wp = pw(tn);
+            prevw[b] = __shfl_sync(0xffffffffu, v.w, 31);
+            bytes[b] = v;
+            // eq bit i: byte at position P0-4+i equals its predecessor
+            uint32_t EQ = eq_bytes(wm, wm << 8);
+            EQ |= eq_bytes(v.x, __funnelshift_l(wm, v.x, 8)) << 4;
+            EQ |= eq_bytes(v.y, __funnelshift_l(v.x, v.y, 8)) << 8;
+            EQ |= eq_bytes(v.z, __funnelshift_l(v.y, v.z, 8)) << 12;
+            EQ |= eq_bytes(v.w, __funnelshift_l(v.z, v.w, 8)) << 16;
+            EQ |= eq_bytes(wp, __funnelshift_l(v.w, wp, 8)) << 20;
+            EQ &= VEQ & ~1u;                                          // bit 0 has no predecessor here
+            const uint32_t T3 = EQ & (EQ << 1);                       // positions i-2, i-1, i equal
+            const uint32_t R = (T3 | (T3 >> 1) | (T3 >> 2)) & VQ;     // byte lies in a run >= 3
+            const uint32_t Sg = (((R & ~EQ) | (~R & (R << 1))) & VQ) | HIGH | Q0;
+            REP[b] = (R >> 4) & 0xFFFFu;
+            SEG[b] = (Sg >> 4) & 0x1FFFFu;                            // bit 16: position P0+16
+        }
+        // last segment start before each position range (max-scan of position + 1)
+        P4 mine;
+        {
+            uint32_t l[4];
+#pragma unroll
+            for (int b = 0; b < 4; ++b) {
+                const uint32_t m = SEG[b] & 0xFFFFu;
+                l[b] = m ? (uint32_t)(P0 + 31 - __clz(m) + 1) : 0u;
+            }
+            mine.a = l[0] | (l[1] << 16);
+            mine.b = l[2] | (l[3] << 16);
+        }
+        P4 tmax;
+        const P4 before = combine<true>(cmax, warp_scan4<true>(mine, lane, &tmax));
+        cmax = combine<true>(cmax, tmax);
+        // piece starts (tokens hold <= 128 bytes) and output sizes
+        uint32_t PSV[4], PE[4], LIT[4], cost[4];
+        int sbin[4];
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+            const uint32_t seg16 = SEG[b] & 0xFFFFu;
+            const int sb_in = (int)lane16(before, b) - 1;            // -1 only for position 0
+            sbin[b] = sb_in;
+            uint32_t PS = seg16;
+            const int first = seg16 ? __ffs(seg16) - 1 : 16;
+            if (sb_in >= 0) {                                        // continuing segment
+                const int r = (P0 - sb_in) & 127;
+                const int d = r ? 128 - r : 0;
+                if (d < first) PS |= 1u << d;
+            }
+            const int sb15 = seg16 ? P0 + 31 - __clz(seg16) : sb_in;
+            const uint32_t next = ((SEG[b] >> 16) & 1u) | (((P0 + 16 - sb15) & 127) == 0 ? 1u : 0u);
+            PSV[b] = PS & VALID;
+            PE[b] = ((PS | (next << 16)) >> 1) & VALID;
+            LIT[b] = ~REP[b] & VALID;
+            cost[b] = __popc(LIT[b]) + __popc(PSV[b]) + __popc(PSV[b] & REP[b]);
+        }
+        P4 tsum;
+        const P4 off0 = combine<false>(csum, warp_scan4<false>(P4{cost[0] | (cost[1] << 16), cost[2] | (cost[3] << 16)},
+                                                               lane, &tsum));
+        csum = combine<false>(csum, tsum);
+#pragma unroll
+        for (int b = 0; b < (EMIT ? 4 : 0); ++b) {
+            uint8_t* o = out + pbase[b];
+            const uint32_t off = lane16(off0, b);
+            const uint32_t lit = LIT[b], psv = PSV[b], psr = PSV[b] & REP[b], seg16 = SEG[b] & 0xFFFFu;
+            const uint4 v = bytes[b];
+            auto byte_at = [&](int i) -> uint8_t {
+                const uint32_t wd = i < 8 ? (i < 4 ? v.x : v.y) : (i < 12 ? v.z : v.w);
+                return (uint8_t)(wd >> (8 * (i & 3)));
+            };
+            auto inc_at = [&](int i) -> uint32_t {
+                const uint32_t le = (2u << i) - 1u;
+                return off + __popc(lit & le) + __popc(psv & le) + __popc(psr & le);
+            };
+            for (uint32_t m = lit; m; m &= m - 1u) {
+                const int i = __ffs(m) - 1;
+                o[inc_at(i) - 1] = byte_at(i);
+            }
+            for (uint32_t m = PE[b]; m; m &= m - 1u) {
+                const int i = __ffs(m) - 1;
+                const uint32_t inc = inc_at(i);
+                const uint32_t h = seg16 & ((2u << i) - 1u);
+                const int sbk = h ? P0 + 31 - __clz(h) : sbin[b];
+                const uint32_t jj = (uint32_t)(P0 + i - sbk) & 127u;
+                if ((REP[b] >> i) & 1u) {
+                    o[inc - 2] = (uint8_t)(0x80u + jj);
+                    o[inc - 1] = byte_at(i);
+                } else {
+                    o[inc - 2 - jj] = (uint8_t)jj;
+                }
+            }
+        }
+    }
+    if (!EMIT)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) T[b] = lane16(csum, b);
+}
+
+// Place a coded chunk: look back for its offset, then write its four plane
+// streams (sparse: copied from its stage; dense: coded again from the image),
+// its four end-table entries, the header (chunk 0) and the stream size (last
+// chunk).
+__device__ void place_chunk(const RleJobDesc& jb, const Coded& C, uint64_t* flags, uint32_t* status)
+{
+    const int lane = threadIdx.x & 31;
+    uint8_t* dst = reinterpret_cast<uint8_t*>(jb.dst);
+    const uint32_t nc = jb.n_chunks, c = C.unit - jb.first_unit;
+    const uint32_t T0 = C.T[0], T1 = C.T[1], T2 = C.T[2], T3 = C.T[3];
+    const uint32_t total = T0 + T1 + T2 + T3;
+    const uint64_t G = look_back(flags, C.unit, jb.first_unit, total, status);
     uint8_t* o = dst + 32 + 16ull * nc + G;
-    if (M.dense) {
-        copy_out(o, stage, total, tid, kT);
-    } else if (tid < 128) {                           // one warp per plane
-        const int p = tid >> 5;
-        const uint32_t b = p ? M.pend[p - 1] : 0u;
-        copy_out(o + b, stage + M.roff[p], M.pend[p] - b, tid & 31, 32);
+    if (!C.dense) {
+        const uint32_t e1 = T0, e2 = e1 + T1, e3 = e2 + T2;
+        for (uint32_t i = lane; i < total; i += 32) {
+            const int p = (i >= e1) + (i >= e2) + (i >= e3);
+            const uint32_t b = p == 0 ? 0u : p == 1 ? e1 : p == 2 ? e2 : e3;
+            o[i] = C.stage[p * kStagePlane + (i - b)];
+        }
+    } else {
+        const uint32_t q0 = c * (uint32_t)kChunk;
+        const int len = (int)min((uint32_t)kChunk, (uint32_t)jb.w * (uint32_t)jb.h - q0);
+        uint32_t T[4] = {T0, T1, T2, T3};
+        dense_chunk<true>(jb, q0, len, jb.mode == 2, T, o);
     }
-    if (tid < 4) put_u32(dst + 32 + 16ull * c + 4u * tid, (uint32_t)(G + M.pend[tid]));
-    if (tid == 0) {
+    const uint32_t mine = lane == 0 ? T0 : lane == 1 ? T0 + T1 : lane == 2 ? T0 + T1 + T2 : total;
+    if (lane < 4) put_u32(dst + 32 + 16ull * c + 4u * lane, (uint32_t)(G + mine));
+    if (lane == 0) {
         if (c == 0) write_header(dst, jb);
         if (c == nc - 1) *jb.d_size = 32ull + 16ull * nc + G + total;
     }
 }
 
-// Persistent compressor.  Each CTA takes work units (chunks) from an atomic
-// ticket and runs a three-stage pipeline over them: while the copy of chunk
-// j+1 is in flight, it codes chunk j and publishes its size, then looks back
-// for chunk j-1's offset and copies that chunk out.  A chunk's size is thus
-// published before its CTA waits on anything, and a look-back waits only for
-// chunks with lower tickets, whose CTAs code them before any higher one.
+// Persistent compressor.  Per chunk a warp: takes its next ticket (the atomic
+// overlaps the wait for the first quarter); places the chunk it coded kDefer
+// chunks ago, if any; reads the four quarters, refilling each slot as soon as
+// it has been read (with the next quarter of this chunk or of the next one);
+// sizes the plane streams and publishes the chunk's size.  The look-back of a
+// placement waits only for chunks with lower tickets.  The lowest chunk not
+// yet published belongs to a warp that has read or is reading it (its earlier
+// chunks are published), and that warp's only wait before publishing it is a
+// placement of an earlier chunk of its own, whose lower chunks are all
+// published; so the lowest chunk is always published in the end.  Every wait
+// is bounded.
 template <int N>
-__global__ void __launch_bounds__(kT, kCPerSM)
-k_rle_compress(const __grid_constant__ RleJobList<N> J, uint64_t* flags, uint32_t* ticket,
-               uint32_t* status)
+__global__ void __launch_bounds__(32 * kWPB, 9)
+k_rle_compress(const __grid_constant__ RleJobList<N> J, uint64_t* flags, uint32_t* ticket, uint32_t* status)
 {
     extern __shared__ __align__(16) uint8_t smem[];
-    __shared__ CState S;
-    const int tid = threadIdx.x;
+    WarpRing& W = reinterpret_cast<WarpRing*>(smem)[threadIdx.x >> 5];
+    const int lane = threadIdx.x & 31;
     const uint32_t T = J.total_units;
-    // dynamic shared memory: three element buffers, two sparse stages, the
-    // sparse segment list and the change masks
-    auto rawb = [&](int j) { return reinterpret_cast<uint32_t*>(smem + (j % 3) * kRawBytes); };
-    auto spb = [&](int j) { return smem + 3 * kRawBytes + (j & 1) * kSpBytes; };
-    uint16_t* seg = reinterpret_cast<uint16_t*>(smem + 3 * kRawBytes + 2 * kSpBytes);
-    uint16_t* chm = reinterpret_cast<uint16_t*>(smem + 3 * kRawBytes + 2 * kSpBytes + kSegBytes);
-    auto take = [&](int slot) {                       // thread 0
-        const uint32_t u = atomicAdd(ticket, 1u);
-        S.tk[slot] = u;
-        S.tj[slot] = u < T ? (uint32_t)find_job(J, u) : 0u;
-    };
-
-    if (tid == 0) { take(0); take(1); }
-    __syncthreads();
-    uint32_t cur = S.tk[0], nxt = S.tk[1], prev = kNone;
-    if (cur < T) load_chunk(J.j[S.tj[0]], cur, rawb(0));
-    cp_async_commit();
-    if (nxt < T) load_chunk(J.j[S.tj[1]], nxt, rawb(1));
-    cp_async_commit();
-    for (int j = 0; cur < T || prev != kNone; ++j) {
-        cp_async_wait<1>();                           // this thread's copies of chunk j landed
-        __syncthreads();
-        if (cur < T) {
-            ChunkMeta& M = S.meta[j & 1];
-            const RleJobDesc& jb = J.j[S.tj[j % 3]];
-            if (tid == 0) { M.unit = cur; M.job = S.tj[j % 3]; }
-            code_chunk(jb, cur, M, rawb(j), spb(j), seg, chm, S, flags);
-            __syncthreads();
-        }
-        if (prev != kNone) {
-            const ChunkMeta& M = S.meta[(j + 1) & 1];
-            const uint8_t* stage = M.dense ? reinterpret_cast<const uint8_t*>(rawb(j + 2)) : spb(j + 1);
-            finish_chunk(J.j[M.job], M, stage, S, flags, status);
-        }
-        if (tid == 0) take((j + 2) % 3);
-        __syncthreads();                              // chunk j-1's buffers are free
-        const uint32_t nn = S.tk[(j + 2) % 3];
-        if (nn < T) load_chunk(J.j[S.tj[(j + 2) % 3]], nn, rawb(j + 2));
-        cp_async_commit();
-        prev = cur < T ? cur : kNone;
-        cur = nxt;
-        nxt = nn;
+    if (lane == 0) {
+        for (int q = 0; q < kSlots; ++q) mbar_init(&W.full[q], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    cp_async_wait<0>();
+    __syncwarp();
+    uint32_t cur = 0u;
+    if (lane == 0) cur = atomicAdd(ticket, 1u);
+    cur = __shfl_sync(0xffffffffu, cur, 0);
+    int ji = cur < T ? find_job(J, cur) : 0;            // job of the current chunk
+    if (cur < T)
+        for (int q = 0; q < kSlots; ++q) issue_quarter(J.j[ji], cur, q, q, W);
+    int nd = 0, dh = 0;                               // coded chunks waiting: count, oldest
+    for (uint32_t seq = 0; cur < T; ++seq) {
+        uint32_t nxt = 0u;
+        if (lane == 0) nxt = atomicAdd(ticket, 1u);
+        if (nd == kDefer) {                           // place the chunk coded kDefer chunks ago
+            const Coded& O = W.def[dh];
+            place_chunk(J.j[O.job], O, flags, status);
+            dh = (dh + 1) % kDefer;
+            --nd;
+        }
+        nxt = __shfl_sync(0xffffffffu, nxt, 0);
+        const RleJobDesc& jb = J.j[ji];
+        const int jn = nxt < T ? find_job(J, nxt) : 0;
+        Coded& C = W.def[(dh + nd) % kDefer];
+        const uint32_t nc = jb.n_chunks;
+        const uint32_t q0 = nc ? (cur - jb.first_unit) * (uint32_t)kChunk : 0u;
+        const int len = nc ? (int)min((uint32_t)kChunk, (uint32_t)jb.w * (uint32_t)jb.h - q0) : 0;
+        int m = 0;
+        uint32_t carry = 0u;
+        bool fits = true;
+        for (int q = 0; q < 4; ++q) {
+            const uint32_t qs = 4u * seq + (uint32_t)q;   // the warp's quarter sequence number
+            const int slot = (int)(qs % kSlots);
+            mbar_wait(&W.full[slot], (qs / kSlots) & 1u, status);
+            if (fits && kQ * q < len)
+                fits = detect_quarter(jb.vec ? W.buf[slot] + 4 : nullptr, jb, q0, len, q, W, m, carry);
+            // the quarter's values have all been consumed (compared, voted on) by
+            // now, so its reads are complete before the refill below starts
+            __syncwarp();
+            // refill the slot with quarter qs + kSlots: of this chunk or of the next
+            const int qn = q + kSlots;
+            if (qn < 4) issue_quarter(jb, cur, qn, slot, W);
+            else if (nxt < T) issue_quarter(J.j[jn], nxt, qn - 4, slot, W);
+        }
+        if (nc == 0) {                                // empty image: header only
+            if (lane == 0) {
+                write_header(reinterpret_cast<uint8_t*>(jb.dst), jb);
+                *jb.d_size = 32u;
+            }
+        } else {
+            const bool sw = jb.mode == 2;
+            uint32_t Ts[4];
+            if (fits) {
+                __syncwarp();
+                if (sw)
+                    for (int i = lane; i < m; i += 32) W.ce[i] = swizzle(W.ce[i]);
+                if (!code_sparse_fast(W, m, len, Ts, C.stage)) code_sparse(W, m, len, Ts, C.stage);
+            } else {
+                dense_chunk<false>(jb, q0, len, sw, Ts, nullptr);
+            }
+            if (lane == 0) {
+                C.unit = cur;
+                C.job = (uint32_t)ji;
+                const bool kept = Ts[0] <= (uint32_t)kStagePlane && Ts[1] <= (uint32_t)kStagePlane &&
+                                  Ts[2] <= (uint32_t)kStagePlane && Ts[3] <= (uint32_t)kStagePlane;
+                C.dense = fits && kept ? 0u : 1u;
+                C.T[0] = Ts[0]; C.T[1] = Ts[1]; C.T[2] = Ts[2]; C.T[3] = Ts[3];
+                publish(flags, cur, jb.first_unit, Ts[0] + Ts[1] + Ts[2] + Ts[3]);
+            }
+            __syncwarp();
+            ++nd;
+        }
+        cur = nxt;
+        ji = jn;
+    }
+    while (nd > 0) {                                  // the warp's last coded chunks
+        const Coded& O = W.def[dh];
+        place_chunk(J.j[O.job], O, flags, status);
+        dh = (dh + 1) % kDefer;
+        --nd;
+    }
 }
 
 // ------------------------------------------------- basic RLE, mode 0 ------
@@ -1115,8 +1295,7 @@ RleJobList<N> make_jobs(const RleJobDesc* jobs, int n, uint32_t total)
 
 namespace {
 
-// Persistent grid: as many compress CTAs as fit on the device at once (the
-// kernel's dynamic shared memory attribute is set on first use per device).
+// Persistent grid: as many compress CTAs as fit on the device at once.
 template <int N>
 cudaError_t compress_grid(int* grid)
 {
@@ -1129,7 +1308,7 @@ cudaError_t compress_grid(int* grid)
     e = cudaFuncSetAttribute(k_rle_compress<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kCompressSmem);
     if (e != cudaSuccess) return e;
     int per_sm = 0, sms = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_rle_compress<N>, kT, kCompressSmem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_rle_compress<N>, 32 * kWPB, kCompressSmem);
     if (e != cudaSuccess) return e;
     e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return e;
@@ -1145,8 +1324,8 @@ cudaError_t compress_n(const RleJobDesc* jobs, int n, uint32_t total_units, uint
     int grid = 0;
     const cudaError_t e = compress_grid<N>(&grid);
     if (e != cudaSuccess) return e;
-    grid = (int)std::min<uint32_t>((uint32_t)grid, total_units);
-    k_rle_compress<N><<<grid, kT, kCompressSmem, s>>>(make_jobs<N>(jobs, n, total_units), flags, ticket, status);
+    grid = (int)std::min<uint32_t>((uint32_t)grid, (total_units + kWPB - 1) / kWPB);
+    k_rle_compress<N><<<grid, 32 * kWPB, kCompressSmem, s>>>(make_jobs<N>(jobs, n, total_units), flags, ticket, status);
     return cudaGetLastError();
 }
 
