@@ -1180,6 +1180,82 @@ __device__ void decode_mode0(const RleJobDesc& jb, const uint8_t* pay, uint32_t 
     if (bad && lane == 0) set_status(status, EC_ERR_CORRUPT);
 }
 
+// Run path of the decoder (few runs): the chunk's elements are constant
+// between the union of the four planes' run starts, so each such segment's
+// element is assembled once (one byte per plane, found by the rank of the
+// segment's start among that plane's run starts) and written with 16-byte
+// stores of constant groups.  bm: the planes' run-start bitmaps [4][128];
+// val: their run bytes [4][256]; work: shared scratch of kRunArea bytes
+// (bitmaps included).
+constexpr int kRunCap = 255;                        // runs per plane the run path takes
+constexpr int kRunArea = 2048 + 3 * 512;            // bitmaps, union, two prefix arrays
+
+__device__ void fill_segments(const RleJobDesc& jb, uint32_t q0, int len, bool sw, const uint32_t* bm,
+                              const uint8_t* val, uint8_t* work, uint32_t* dstp)
+{
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    uint32_t* U = reinterpret_cast<uint32_t*>(work + 2048);      // [128] union of run starts
+    uint32_t* PU = U + 128;                                       // [128] segments before word i
+    uint32_t* wt = PU + 128;                                      // per-warp totals (scan)
+    uint32_t* SV = reinterpret_cast<uint32_t*>(work + kRunArea + 1024);   // segment elements
+    // word tid of every bitmap; exclusive prefixes of their bit counts
+    const uint32_t b0 = bm[tid], b1 = bm[128 + tid], b2 = bm[256 + tid], b3 = bm[384 + tid];
+    const uint32_t u = b0 | b1 | b2 | b3;
+    const uint32_t cu = __popc(u);
+    const uint32_t cb = __popc(b0) | (__popc(b1) << 8) | (__popc(b2) << 16) | ((uint32_t)__popc(b3) << 24);
+    uint32_t iu = cu, ib = cb;                   // (each plane has <= 255 runs: its byte never carries)
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t yu = __shfl_up_sync(0xffffffffu, iu, o), yb = __shfl_up_sync(0xffffffffu, ib, o);
+        if (lane >= o) { iu += yu; ib += yb; }
+    }
+    if (lane == 31) { wt[2 * warp] = iu; wt[2 * warp + 1] = ib; }
+    __syncthreads();
+    uint32_t eu = iu - cu, eb = ib - cb;
+    for (int k = 0; k < warp; ++k) { eu += wt[2 * k]; eb += wt[2 * k + 1]; }
+    U[tid] = u;
+    PU[tid] = eu;
+    // the element of every segment starting in word tid
+    for (uint32_t m = u; m; m &= m - 1u) {
+        const int b = __ffs(m) - 1;
+        const uint32_t le = (2u << b) - 1u;      // bits 0..b
+        const uint32_t r0 = ((eb >> 0) & 0xFFu) + __popc(b0 & le) - 1u;
+        const uint32_t r1 = ((eb >> 8) & 0xFFu) + __popc(b1 & le) - 1u;
+        const uint32_t r2 = ((eb >> 16) & 0xFFu) + __popc(b2 & le) - 1u;
+        const uint32_t r3 = (eb >> 24) + __popc(b3 & le) - 1u;
+        uint32_t e = (uint32_t)val[r0] | ((uint32_t)val[256 + r1] << 8) | ((uint32_t)val[512 + r2] << 16) |
+                     ((uint32_t)val[768 + r3] << 24);
+        if (sw) e = swizzle(e);
+        SV[eu + __popc(u & (le >> 1))] = e;
+    }
+    __syncthreads();
+    const uint32_t w = (uint32_t)jb.w;
+    const bool dense = jb.pitch == jb.w;
+    for (int g = tid; 4 * g < len; g += kDT) {
+        const uint32_t uw = U[g >> 3];
+        const int bb = (g & 7) << 2;
+        const uint32_t k0 = PU[g >> 3] + __popc(uw & ((2u << bb) - 1u)) - 1u;
+        const uint32_t in = (uw >> (bb + 1)) & 7u;                // segments starting inside the group
+        const uint32_t k1 = k0 + (in & 1u), k2 = k1 + ((in >> 1) & 1u), k3 = k2 + (in >> 2);
+        const uint32_t v0 = SV[k0];
+        const uint4 v = in ? make_uint4(v0, SV[k1], SV[k2], SV[k3]) : make_uint4(v0, v0, v0, v0);
+        const uint32_t q = q0 + 4u * (uint32_t)g;
+        if (jb.vec) {
+            size_t e = q;
+            if (!dense) {
+                const uint32_t y = q / w;
+                e = (size_t)y * jb.pitch + (q - y * w);
+            }
+            st_stream(reinterpret_cast<uint4*>(dstp + e), v);
+        } else {
+            const uint32_t vv[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+                if (4 * g + j < len) dstp[elem_off(jb, q + (uint32_t)j)] = vv[j];
+        }
+    }
+}
+
 template <int N>
 __global__ void __launch_bounds__(kDT)
 k_rle_decompress(const __grid_constant__ RleJobList<N> J, uint32_t* status)
@@ -1189,11 +1265,15 @@ k_rle_decompress(const __grid_constant__ RleJobList<N> J, uint32_t* status)
     __shared__ __align__(16) uint8_t sbuf[4 * kChunk + 64];
     uint8_t (*planes)[kChunk] = reinterpret_cast<uint8_t (*)[kChunk]>(sbuf);
     __shared__ uint32_t s_beg[5];
-    __shared__ int s_fail, s_mode;
+    __shared__ int s_fail, s_over, s_mode;
     __shared__ uint8_t s_hdr[rlec::kHdrBytes];
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const uint32_t unit = blockIdx.x;
+    // the run bitmaps start empty; nothing else uses sbuf before they are filled
+#pragma unroll
+    for (int i = 0; i < 4; ++i) reinterpret_cast<uint32_t*>(sbuf)[tid + kDT * i] = 0u;
+    if (tid == 0) s_over = 0;
     const RleJobDesc& jb = J.j[find_job(J, unit)];
     const uint8_t* src = reinterpret_cast<const uint8_t*>(jb.src);
     const uint64_t size = jb.capacity;
@@ -1220,8 +1300,32 @@ k_rle_decompress(const __grid_constant__ RleJobList<N> J, uint32_t* status)
         return;
     }
     const uint8_t* payload = src + 32 + 16ull * nc;
+    uint32_t* dstp = reinterpret_cast<uint32_t*>(jb.dst);
+    const uint32_t w = (uint32_t)jb.w;
+    const bool sw = s_mode == 2;
 
-    // warp p decodes byte plane p
+    // Runs first: warp p walks plane p's tokens, marking where each run starts
+    // (every repeat token, every literal byte) and keeping its byte.
+    {
+        uint32_t* bm = reinterpret_cast<uint32_t*>(sbuf);          // [4][128] run starts per plane
+        uint8_t* val = sbuf + kRunArea;                             // [4][256] run bytes per plane
+        int nr = 0;
+        const int r = rlec::decode_plane_runs(rlec::GlobalBytes{payload}, (int)s_beg[warp], (int)s_beg[warp + 1],
+                                              len, bm + 128 * warp, val + 256 * warp, kRunCap, &nr, lane);
+        if (lane == 0 && r == 1) s_fail = 1;
+        if (lane == 0 && r == 2) s_over = 1;
+        __syncthreads();
+        if (s_fail) {
+            if (tid == 0) set_status(status, EC_ERR_CORRUPT);
+            return;
+        }
+        if (!s_over) {
+            fill_segments(jb, q0, len, sw, bm, val, sbuf, dstp);
+            return;
+        }
+    }
+
+    // many runs: warp p decodes byte plane p into shared memory
     if (rlec::decode_plane(rlec::GlobalBytes{payload}, (int)s_beg[warp], (int)s_beg[warp + 1], len, planes[warp],
                            lane) &&
         lane == 0)
@@ -1234,9 +1338,6 @@ k_rle_decompress(const __grid_constant__ RleJobList<N> J, uint32_t* status)
 
     // transpose planes back into elements, 16 per thread; groups of four
     // equal elements (each plane word one repeated byte) are un-swizzled once
-    uint32_t* dstp = reinterpret_cast<uint32_t*>(jb.dst);
-    const uint32_t w = (uint32_t)jb.w;
-    const bool sw = s_mode == 2;
     if (jb.vec) {
         const bool dense = jb.pitch == jb.w;
         for (int g16 = tid; 16 * g16 < len; g16 += kDT) {

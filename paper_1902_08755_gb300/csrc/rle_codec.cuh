@@ -238,5 +238,96 @@ __device__ __forceinline__ int decode_plane(const Src& src, int beg, int end, in
     return outp != len;
 }
 
+// decode_plane's token walk (and validation), recording runs instead of bytes:
+// every repeat token and every literal byte starts a run, in position order.
+// Run r starting at position o sets bit o of the plane's bitmap bm (zero on
+// entry; 128 words) and stores its byte in val[r].  Returns 0 with *nruns set,
+// 1 for a malformed stream (as decode_plane), 2 once there would be more than
+// cap runs (nothing about the stream's validity is then known).
+template <class Src>
+__device__ __forceinline__ int decode_plane_runs(const Src& src, int beg, int end, int len, uint32_t* bm,
+                                                 uint8_t* val, int cap, int* nruns, int lane)
+{
+    int cur = beg, outp = 0, runs = 0;
+    while (cur < end) {
+        {
+            const int i2 = cur + 2 * lane;
+            const uint32_t c = i2 + 1 < end ? src(i2) : 0u;
+            const uint32_t v = i2 + 1 < end ? src(i2 + 1) : 0u;
+            const uint32_t lit = __ballot_sync(0xffffffffu, c < 128u);
+            const int m = lit ? __ffs(lit) - 1 : 32;
+            if (m > 0) {
+                const bool valid = lane < m;
+                const int olen = valid ? (int)c - 127 : 0;
+                const int incl = warp_incl_sum(olen, lane);
+                const int total = __shfl_sync(0xffffffffu, incl, 31);
+                const int o = outp + incl - olen;
+                if (__any_sync(0xffffffffu, valid && o + olen > len)) return 1;
+                if (runs + m > cap) return 2;
+                if (valid) {
+                    atomicOr(bm + (o >> 5), 1u << (o & 31));
+                    val[runs + lane] = (uint8_t)v;
+                }
+                runs += m;
+                outp += total;
+                cur += 2 * m;
+                continue;
+            }
+        }
+        const int i = cur + lane;
+        const uint32_t b = i < end ? src(i) : 0u;
+        const uint32_t b1 = i + 1 < end ? src(i + 1) : 0u;
+        int J = lane + (b >= 128u ? 2 : 2 + (int)b);   // next^(2^k), relative to cur
+        int pos = 0;                                   // start of token #lane
+#pragma unroll
+        for (int k = 0; k < 5; ++k) {
+            const int y = __shfl_sync(0xffffffffu, J, min(pos, 31));
+            if (((lane >> k) & 1) && pos < 32) pos = y;
+            if (k < 4) {
+                const int z = __shfl_sync(0xffffffffu, J, min(J, 31));
+                if (J < 32) J = z;
+            }
+        }
+        const bool valid = pos < min(32, end - cur);
+        const int ntok = __popc(__ballot_sync(0xffffffffu, valid));
+        const int sl = __shfl_sync(0xffffffffu, pos, ntok);
+        const int ps = min(pos, 31);
+        const uint32_t tb = __shfl_sync(0xffffffffu, b, ps);
+        const uint32_t tv = __shfl_sync(0xffffffffu, b1, ps);
+        const bool trep = tb >= 128u;
+        const int olen = valid ? (trep ? (int)tb - 127 : (int)tb + 1) : 0;
+        const int tnext = pos + (trep ? 2 : 2 + (int)tb);
+        const int incl = warp_incl_sum(olen, lane);
+        const int total = __shfl_sync(0xffffffffu, incl, 31);
+        const int o = outp + incl - olen;
+        if (__any_sync(0xffffffffu, valid && (cur + tnext > end || o + olen > len))) return 1;
+        const int nr = valid ? (trep ? 1 : olen) : 0;      // runs this token starts
+        const int rinc = warp_incl_sum(nr, lane);
+        const int rtot = __shfl_sync(0xffffffffu, rinc, 31);
+        if (runs + rtot > cap) return 2;
+        const int rb = runs + rinc - nr;
+        if (valid && trep) {
+            atomicOr(bm + (o >> 5), 1u << (o & 31));
+            val[rb] = (uint8_t)tv;
+        }
+        for (uint32_t m = __ballot_sync(0xffffffffu, valid && !trep); m; m &= m - 1u) {
+            const int t = __ffs(m) - 1;
+            const int oo = __shfl_sync(0xffffffffu, o, t);
+            const int ml = __shfl_sync(0xffffffffu, olen, t);
+            const int r0 = __shfl_sync(0xffffffffu, rb, t);
+            const int s0 = cur + __shfl_sync(0xffffffffu, pos, t) + 1;   // after the control
+            for (int k = lane; k < ml; k += 32) {
+                atomicOr(bm + ((oo + k) >> 5), 1u << ((oo + k) & 31));
+                val[r0 + k] = (uint8_t)src(s0 + k);
+            }
+        }
+        runs += rtot;
+        outp += total;
+        cur += sl;
+    }
+    *nruns = runs;
+    return outp != len;
+}
+
 }  // namespace rlec
 }  // namespace ec
