@@ -177,10 +177,23 @@ class Clocks:
                 "samples": len(sm)}
 
 
-def kernel_hash() -> str:
+# Source files each measured kernel is built from (its traffic record stays
+# valid while they are unchanged); kernels not listed hash every source.
+KERNEL_SOURCES = {
+    "rle_compress": ["k_rle.cu", "rle_codec.cuh", "ec_internal.cuh"],
+    "rle_decompress": ["k_rle.cu", "rle_codec.cuh", "ec_internal.cuh"],
+    "composite_depth": ["k_composite.cu", "composite_body.cuh", "ec_internal.cuh"],
+    "composite_alpha": ["k_composite.cu", "composite_body.cuh", "ec_internal.cuh"],
+    "composite_alpha_fwd_bwd": ["k_backward.cu", "ec_internal.cuh"],
+    "batch": ["k_batch.cu", "composite_body.cuh", "ec_internal.cuh"],
+}
+
+
+def kernel_hash(kernel: str = "") -> str:
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1902_08755_gb300", "csrc")
-    for fn in sorted(os.listdir(csrc)):
+    files = KERNEL_SOURCES.get(kernel) or sorted(os.listdir(csrc))
+    for fn in files:
         with open(os.path.join(csrc, fn), "rb") as f:
             h.update(fn.encode() + f.read())
     return h.hexdigest()[:16]
@@ -188,13 +201,13 @@ def kernel_hash() -> str:
 
 def measured_traffic(kernel: str, workload: str):
     """dram bytes per launch from the committed ncu summary, if it was taken on
-    the current kernel sources."""
+    the kernel's current sources."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(path) as f:
             d = json.load(f)
         e = d[workload][kernel]
-        if e.get("source_hash") == kernel_hash():
+        if e.get("source_hash") == kernel_hash(kernel):
             return float(e["dram_bytes_per_launch"])
     except (OSError, KeyError, ValueError):
         pass
