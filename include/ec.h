@@ -532,8 +532,8 @@ ec_status ec_yuv_decode_batch(ec_ctx* ctx, const ec_yuv_job* jobs, int32_t njobs
 /* ------------------------------------------------ allocation-free compressor
  * The thesis has no counterpart to this entry point; it exists for callers
  * that cannot allocate device memory.  ec_rle_compress takes its scratch
- * memory (look-back words and a ticket) from an ec_ctx, which allocates it
- * with cudaMalloc.  Code that must not allocate once it runs -- a frame loop
+ * memory (a record per chunk, a pool for the coded chunks, counters) from an
+ * ec_ctx, which allocates it with cudaMalloc.  Code that must not allocate once it runs -- a frame loop
  * that reserved all of its memory at start-up, code whose device memory is
  * owned by another framework's pool, or code that cannot absorb the implicit
  * device synchronisation cudaMalloc/cudaFree may cause -- can call this
@@ -556,7 +556,7 @@ ec_status ec_yuv_decode_batch(ec_ctx* ctx, const ec_yuv_job* jobs, int32_t njobs
  * up), since there is no context status word.  The stream written is byte for
  * byte the one ec_rle_compress writes. */
 #define EC_RLE_NOALLOC_MAX_CHUNKS 8192
-#define EC_RLE_NOALLOC_SCRATCH_BYTES (16 + 8 * EC_RLE_NOALLOC_MAX_CHUNKS)
+#define EC_RLE_NOALLOC_SCRATCH_BYTES (16 + 532 * EC_RLE_NOALLOC_MAX_CHUNKS)
 ec_status ec_rle_compress_noalloc(const void* src, int32_t w, int32_t h, int32_t pitch,
                                   uint32_t mode, void* dst, size_t dst_capacity,
                                   uint64_t* d_size, uint32_t* d_status, ec_stream_t s);

@@ -165,7 +165,7 @@ ec_status ec_create(ec_ctx** out, int device)
     cudaDeviceGetAttribute(&ctx->sm_count, cudaDevAttrMultiProcessorCount, device);
     if (cudaMalloc(&ctx->d_status, sizeof(uint32_t)) != cudaSuccess ||
         cudaMemset(ctx->d_status, 0, sizeof(uint32_t)) != cudaSuccess ||
-        ensure_scratch(ctx, 16 + 8 * 65536) != EC_OK) {
+        ensure_scratch(ctx, rle_compress_scratch_bytes(1024, kRlePoolPerUnit)) != EC_OK) {
         ec_destroy(ctx);
         return EC_ERR_CUDA;
     }
@@ -568,9 +568,10 @@ static ec_status rle_batch(ec_ctx* ctx, const ec_rle_job* jobs, int32_t njobs, b
         }
         cudaError_t e;
         if (compress) {
-            const ec_status st = ensure_scratch(ctx, 16 + 8ull * units);
+            const ec_status st = ensure_scratch(ctx, rle_compress_scratch_bytes(units, kRlePoolPerUnit));
             if (st != EC_OK) return st;
-            e = launch_rle_compress(&d[b], cnt, units, ctx->scratch, ctx->d_status, (cudaStream_t)s);
+            e = launch_rle_compress(&d[b], cnt, units, ctx->scratch, ctx->scratch_bytes, ctx->d_status,
+                                    (cudaStream_t)s);
         } else {
             e = launch_rle_decompress(&d[b], cnt, units, ctx->d_status, (cudaStream_t)s);
         }

@@ -181,8 +181,17 @@ struct RleJobList {
 };
 static_assert(sizeof(RleJobList<kRleJobsPerLaunch>) < 32764 - 256, "kernel parameter limit");
 
+// Scratch of a compress launch of `units` work units: a ticket, a counter and a
+// pool cursor, a 16-byte record and a 4-byte list entry per unit (modes 1, 2;
+// mode 0 uses 8 bytes per unit of them), then a pool for the coded chunks,
+// pool_per_unit bytes per unit.  A
+// chunk that finds the pool full is coded a second time when placed, so any
+// pool size gives the same stream.
+size_t rle_compress_scratch_bytes(uint32_t units, size_t pool_per_unit);
+constexpr size_t kRlePoolPerUnit = 512;
+
 cudaError_t launch_rle_compress(const RleJobDesc* jobs, int n, uint32_t total_units,
-                                void* scratch, uint32_t* status, cudaStream_t s);
+                                void* scratch, size_t scratch_bytes, uint32_t* status, cudaStream_t s);
 cudaError_t launch_rle_decompress(const RleJobDesc* jobs, int n, uint32_t total_units,
                                   uint32_t* status, cudaStream_t s);
 

@@ -375,7 +375,8 @@ struct SchedLaunch {
 struct ec_schedule {
     ec_ctx* ctx = nullptr;
     std::vector<SchedLaunch> launches;
-    void* scratch = nullptr;             // the compressor's look-back words, inside the arena
+    void* scratch = nullptr;             // the compressor's scratch, inside the arena
+    size_t scratch_bytes = 0;
     int mode = 0, algo = 0, n = 0, fmt = 0;
     uint32_t flags = 0;
     char* arena = nullptr;
@@ -395,7 +396,8 @@ cudaError_t enqueue(ec_schedule* S, const SchedLaunch& r, cudaStream_t s)
 {
     switch (r.kind) {
     case EC_SCHED_LAUNCH_COMPRESS:
-        return ec::launch_rle_compress(r.jobs.data(), (int)r.jobs.size(), r.units, S->scratch, S->ctx->d_status, s);
+        return ec::launch_rle_compress(r.jobs.data(), (int)r.jobs.size(), r.units, S->scratch, S->scratch_bytes,
+                                       S->ctx->d_status, s);
     case EC_SCHED_LAUNCH_DECOMPRESS:
         return ec::launch_rle_decompress(r.jobs.data(), (int)r.jobs.size(), r.units, S->ctx->d_status, s);
     case EC_SCHED_LAUNCH_FUSED:
@@ -572,7 +574,9 @@ ec_status ec_schedule_plan(ec_ctx* ctx, int32_t mode, int32_t algorithm, const e
         lr.fst_off = A.take(std::max<size_t>(ns, 1) * sizeof(FusedStage));
         lr.fun_off = A.take(std::max<size_t>(nu, 1) * sizeof(FusedUnit));
     }
-    const size_t scratch_off = A.take(16 + 8 * std::max<uint64_t>(max_units, 1));
+    const size_t scratch_bytes = ec::rle_compress_scratch_bytes((uint32_t)std::max<uint64_t>(max_units, 1),
+                                                                ec::kRlePoolPerUnit);
+    const size_t scratch_off = A.take(scratch_bytes);
 
     DeviceGuard g(ctx->device);
     if (!g.ok) return fail(EC_ERR_CUDA);
@@ -743,6 +747,7 @@ ec_status ec_schedule_plan(ec_ctx* ctx, int32_t mode, int32_t algorithm, const e
 
     // ---- phase 3: launch records, then the graph
     S->scratch = base + scratch_off;
+    S->scratch_bytes = scratch_bytes;
     const uint64_t pxb = (uint64_t)bpp + (depth ? 4u : 0u);    // bytes per pixel with depth
     for (size_t li = 0; li < L.size(); ++li) {
         for (int kind = EC_SCHED_LAUNCH_COMPRESS; kind <= EC_SCHED_LAUNCH_DECOMPRESS; ++kind) {

@@ -191,24 +191,15 @@ __device__ __forceinline__ void copy_out(uint8_t* o, const uint8_t* src, uint32_
 // chunks before it have normally published theirs.
 constexpr int kWPB = 2;                       // warps per CTA
 constexpr int kCap = 128;                     // change points the sparse path takes
-constexpr int kQ = 1024;                      // elements per quarter buffer
+constexpr int kQ = 512;                       // elements per quarter buffer
+constexpr int kQPC = kChunk / kQ;             // quarters per chunk
 constexpr int kSlots = 2;                     // quarter buffers per warp
-constexpr int kDefer = 3;                     // chunks coded but not yet placed, per warp
 
-// Stage bytes kept per plane of a sparse chunk.  A plane that codes to more
-// (possible from about 60 runs on) is not kept: the chunk is coded again from
-// the image when it is placed, like a dense one.
-constexpr int kStagePlane = 192;
-
-// A coded chunk waiting to be placed: sparse chunks keep their four plane
-// streams (plane p at stage + p * kStagePlane), dense ones (and sparse ones
-// whose streams did not fit) only their sizes.
-struct Coded {
-    uint32_t unit, job, dense;
-    uint32_t T[4];            // plane stream sizes
-    uint32_t pad;
-    uint8_t stage[4 * kStagePlane];
-};
+// Each plane of a sparse chunk has at most kCap runs and codes to at most
+// 3 kCap + kChunk / 64 bytes (a repeat run of length L to 2 ceil(L / 128) <=
+// 2 + L / 64 bytes, a literal span of k short runs to at most 3k bytes).
+constexpr int kStagePlane = 3 * kCap + kChunk / 64;
+constexpr uint32_t kRecode = 0xFFFFFFFFu;      // record: coded again when placed
 
 // One warp's shared memory.  Quarter s of the warp's sequence of quarters
 // (4 per chunk) goes to buf[s % kSlots].
@@ -216,13 +207,23 @@ struct WarpRing {
     uint32_t buf[kSlots][kQ + 4];   // + 16 guard bytes before each quarter
     uint64_t full[kSlots];
     uint64_t pad[4 - kSlots];       // (keeps what follows 16-byte aligned)
-    Coded def[kDefer];
+    uint8_t stage[4 * kStagePlane]; // the chunk's plane streams (plane p at p * kStagePlane)
     uint32_t ce[kCap];              // the chunk being read: element at each change point
     uint16_t cq[kCap];              // (swizzled in mode 2) and its position
     uint8_t rl[4][kCap];            // the planes' runs: index of the change point starting each
 };
-static_assert(sizeof(Coded) % 16 == 0 && (kQ + 4) * 4 % 16 == 0 && sizeof(WarpRing) % 16 == 0,
-              "16-byte aligned buffers");
+static_assert((kQ + 4) * 4 % 16 == 0 && sizeof(WarpRing) % 16 == 0, "16-byte aligned buffers");
+
+// A coded chunk, as the coding kernel leaves it for the placing kernels: its
+// four plane stream sizes, where its streams wait in the pool (kRecode: not
+// kept, coded again from the image when placed), and its offset inside the
+// stream's payload (written by the scan).
+struct ChunkRec {
+    uint16_t T[4];
+    uint32_t pool;
+    uint32_t off;
+};
+static_assert(sizeof(ChunkRec) == 16, "chunk record");
 constexpr size_t kCompressSmem = kWPB * sizeof(WarpRing);
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -404,13 +405,21 @@ __device__ bool detect_quarter(const uint32_t* data, const RleJobDesc& jb, uint3
     return true;
 }
 
+// The change lists a sparse coder reads: element (swizzled in mode 2) and
+// position of each change point, in order; rl is its scratch.
+struct Lists {
+    uint32_t* ce;
+    uint16_t* cq;
+    uint8_t (*rl)[kCap];
+};
+
 // Sparse path, fast case: at most 32 change points and every run of every
 // plane at least 3 bytes long (so every run is repeat tokens).  Lane i holds
 // change point i; for each plane the lanes that start a run are found with
 // one ballot, each run's end is the next such lane's position (a shuffle) or
 // the chunk's end, and one scan over the four planes (16-bit halves) places
 // the tokens.  Returns false, writing nothing, when the case does not apply.
-__device__ bool code_sparse_fast(const WarpRing& W, int m, int len, uint32_t* T, uint8_t* stage)
+__device__ bool code_sparse_fast(const Lists& W, int m, int len, uint32_t* T, uint8_t* stage)
 {
     const int lane = threadIdx.x & 31;
     if (m > 32) return false;
@@ -468,7 +477,7 @@ __device__ bool code_sparse_fast(const WarpRing& W, int m, int len, uint32_t* T,
 // run of a literal span walks to the span's end and codes the whole span.
 // Plane p's stream goes to stage + p * kStagePlane (as far as it fits); its
 // size to T[p].
-__device__ void code_sparse(WarpRing& W, int m, int len, uint32_t* T, uint8_t* stage)
+__device__ void code_sparse(const Lists& W, int m, int len, uint32_t* T, uint8_t* stage)
 {
     const int lane = threadIdx.x & 31;
     const uint32_t lt = (1u << lane) - 1u;
@@ -794,59 +803,24 @@ __device__ __noinline__ void dense_chunk(const RleJobDesc& jb, uint32_t q0, int 
         for (int b = 0; b < 4; ++b) T[b] = lane16(csum, b);
 }
 
-// Place a coded chunk: look back for its offset, then write its four plane
-// streams (sparse: copied from its stage; dense: coded again from the image),
-// its four end-table entries, the header (chunk 0) and the stream size (last
-// chunk).
-__device__ void place_chunk(const RleJobDesc& jb, const Coded& C, uint64_t* flags, uint32_t* status)
-{
-    const int lane = threadIdx.x & 31;
-    uint8_t* dst = reinterpret_cast<uint8_t*>(jb.dst);
-    const uint32_t nc = jb.n_chunks, c = C.unit - jb.first_unit;
-    const uint32_t T0 = C.T[0], T1 = C.T[1], T2 = C.T[2], T3 = C.T[3];
-    const uint32_t total = T0 + T1 + T2 + T3;
-    const uint64_t G = look_back(flags, C.unit, jb.first_unit, total, status);
-    uint8_t* o = dst + 32 + 16ull * nc + G;
-    if (!C.dense) {
-        const uint32_t e1 = T0, e2 = e1 + T1, e3 = e2 + T2;
-        for (uint32_t i = lane; i < total; i += 32) {
-            const int p = (i >= e1) + (i >= e2) + (i >= e3);
-            const uint32_t b = p == 0 ? 0u : p == 1 ? e1 : p == 2 ? e2 : e3;
-            o[i] = C.stage[p * kStagePlane + (i - b)];
-        }
-    } else {
-        const uint32_t q0 = c * (uint32_t)kChunk;
-        const int len = (int)min((uint32_t)kChunk, (uint32_t)jb.w * (uint32_t)jb.h - q0);
-        uint32_t T[4] = {T0, T1, T2, T3};
-        dense_chunk<true>(jb, q0, len, jb.mode == 2, T, o);
-    }
-    const uint32_t mine = lane == 0 ? T0 : lane == 1 ? T0 + T1 : lane == 2 ? T0 + T1 + T2 : total;
-    if (lane < 4) put_u32(dst + 32 + 16ull * c + 4u * lane, (uint32_t)(G + mine));
-    if (lane == 0) {
-        if (c == 0) write_header(dst, jb);
-        if (c == nc - 1) *jb.d_size = 32ull + 16ull * nc + G + total;
-    }
-}
-
-// Persistent compressor.  Per chunk a warp: takes its next ticket (the atomic
-// overlaps the wait for the first quarter); places the chunk it coded kDefer
-// chunks ago, if any; reads the four quarters, refilling each slot as soon as
-// it has been read (with the next quarter of this chunk or of the next one);
-// sizes the plane streams and publishes the chunk's size.  The look-back of a
-// placement waits only for chunks with lower tickets.  The lowest chunk not
-// yet published belongs to a warp that has read or is reading it (its earlier
-// chunks are published), and that warp's only wait before publishing it is a
-// placement of an earlier chunk of its own, whose lower chunks are all
-// published; so the lowest chunk is always published in the end.  Every wait
-// is bounded.
+// Coding kernel.  Per chunk a warp: takes its next ticket (the atomic overlaps
+// the wait for the first quarter); reads the four quarters, refilling each
+// slot as soon as it has been read (with the next quarter of this chunk or of
+// the next one); sizes the plane streams; and leaves the chunk's record and,
+// for a sparse chunk, its streams in the pool (space taken with an atomic
+// cursor; a chunk that finds the pool full is coded again when placed, like a
+// dense one; such chunks are listed for the recoding kernel).  No warp waits
+// for another.
 template <int N>
-__global__ void __launch_bounds__(32 * kWPB, 9)
-k_rle_compress(const __grid_constant__ RleJobList<N> J, uint64_t* flags, uint32_t* ticket, uint32_t* status)
+__global__ void __launch_bounds__(32 * kWPB, 11)
+k_rle_compress(const __grid_constant__ RleJobList<N> J, ChunkRec* rec, uint32_t* recode, uint8_t* pool,
+               uint32_t pool_bytes, uint32_t* ticket, uint32_t* status)
 {
     extern __shared__ __align__(16) uint8_t smem[];
     WarpRing& W = reinterpret_cast<WarpRing*>(smem)[threadIdx.x >> 5];
     const int lane = threadIdx.x & 31;
     const uint32_t T = J.total_units;
+    unsigned long long* cursor = reinterpret_cast<unsigned long long*>(ticket + 2);   // pool bytes taken
     if (lane == 0) {
         for (int q = 0; q < kSlots; ++q) mbar_init(&W.full[q], 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -858,28 +832,20 @@ k_rle_compress(const __grid_constant__ RleJobList<N> J, uint64_t* flags, uint32_
     int ji = cur < T ? find_job(J, cur) : 0;            // job of the current chunk
     if (cur < T)
         for (int q = 0; q < kSlots; ++q) issue_quarter(J.j[ji], cur, q, q, W);
-    int nd = 0, dh = 0;                               // coded chunks waiting: count, oldest
     for (uint32_t seq = 0; cur < T; ++seq) {
         uint32_t nxt = 0u;
         if (lane == 0) nxt = atomicAdd(ticket, 1u);
-        if (nd == kDefer) {                           // place the chunk coded kDefer chunks ago
-            const Coded& O = W.def[dh];
-            place_chunk(J.j[O.job], O, flags, status);
-            dh = (dh + 1) % kDefer;
-            --nd;
-        }
         nxt = __shfl_sync(0xffffffffu, nxt, 0);
         const RleJobDesc& jb = J.j[ji];
         const int jn = nxt < T ? find_job(J, nxt) : 0;
-        Coded& C = W.def[(dh + nd) % kDefer];
         const uint32_t nc = jb.n_chunks;
         const uint32_t q0 = nc ? (cur - jb.first_unit) * (uint32_t)kChunk : 0u;
         const int len = nc ? (int)min((uint32_t)kChunk, (uint32_t)jb.w * (uint32_t)jb.h - q0) : 0;
         int m = 0;
         uint32_t carry = 0u;
         bool fits = true;
-        for (int q = 0; q < 4; ++q) {
-            const uint32_t qs = 4u * seq + (uint32_t)q;   // the warp's quarter sequence number
+        for (int q = 0; q < kQPC; ++q) {
+            const uint32_t qs = (uint32_t)kQPC * seq + (uint32_t)q;   // the warp's quarter sequence number
             const int slot = (int)(qs % kSlots);
             mbar_wait(&W.full[slot], (qs / kSlots) & 1u, status);
             if (fits && kQ * q < len)
@@ -889,45 +855,151 @@ k_rle_compress(const __grid_constant__ RleJobList<N> J, uint64_t* flags, uint32_
             __syncwarp();
             // refill the slot with quarter qs + kSlots: of this chunk or of the next
             const int qn = q + kSlots;
-            if (qn < 4) issue_quarter(jb, cur, qn, slot, W);
-            else if (nxt < T) issue_quarter(J.j[jn], nxt, qn - 4, slot, W);
+            if (qn < kQPC) issue_quarter(jb, cur, qn, slot, W);
+            else if (nxt < T) issue_quarter(J.j[jn], nxt, qn - kQPC, slot, W);
         }
-        if (nc == 0) {                                // empty image: header only
-            if (lane == 0) {
-                write_header(reinterpret_cast<uint8_t*>(jb.dst), jb);
-                *jb.d_size = 32u;
-            }
-        } else {
+        if (nc > 0) {
             const bool sw = jb.mode == 2;
-            uint32_t Ts[4];
+            uint32_t Ts[4] = {0u, 0u, 0u, 0u};          // (a dense chunk is sized by the recoding kernels)
             if (fits) {
                 __syncwarp();
                 if (sw)
                     for (int i = lane; i < m; i += 32) W.ce[i] = swizzle(W.ce[i]);
-                if (!code_sparse_fast(W, m, len, Ts, C.stage)) code_sparse(W, m, len, Ts, C.stage);
-            } else {
-                dense_chunk<false>(jb, q0, len, sw, Ts, nullptr);
+                const Lists L{W.ce, W.cq, W.rl};
+                if (!code_sparse_fast(L, m, len, Ts, W.stage)) code_sparse(L, m, len, Ts, W.stage);
+            }
+            const uint32_t total = Ts[0] + Ts[1] + Ts[2] + Ts[3];
+            uint32_t po = kRecode;
+            if (fits && lane == 0) {
+                // (+ 4: the copy-out reads up to one word past a chunk's bytes)
+                const unsigned long long a = atomicAdd(cursor, (unsigned long long)((total + 3u) & ~3u));
+                if (a + total + 4u <= pool_bytes) po = (uint32_t)a;
+            }
+            po = __shfl_sync(0xffffffffu, po, 0);
+            __syncwarp();
+            if (po != kRecode) {                      // the four streams, back to back
+                const uint32_t e1 = Ts[0], e2 = e1 + Ts[1], e3 = e2 + Ts[2];
+                for (uint32_t i = lane; i < total; i += 32) {
+                    const int p = (i >= e1) + (i >= e2) + (i >= e3);
+                    const uint32_t b = p == 0 ? 0u : p == 1 ? e1 : p == 2 ? e2 : e3;
+                    pool[po + i] = W.stage[p * kStagePlane + (i - b)];
+                }
             }
             if (lane == 0) {
-                C.unit = cur;
-                C.job = (uint32_t)ji;
-                const bool kept = Ts[0] <= (uint32_t)kStagePlane && Ts[1] <= (uint32_t)kStagePlane &&
-                                  Ts[2] <= (uint32_t)kStagePlane && Ts[3] <= (uint32_t)kStagePlane;
-                C.dense = fits && kept ? 0u : 1u;
-                C.T[0] = Ts[0]; C.T[1] = Ts[1]; C.T[2] = Ts[2]; C.T[3] = Ts[3];
-                publish(flags, cur, jb.first_unit, Ts[0] + Ts[1] + Ts[2] + Ts[3]);
+                ChunkRec r;
+                r.T[0] = (uint16_t)Ts[0]; r.T[1] = (uint16_t)Ts[1]; r.T[2] = (uint16_t)Ts[2]; r.T[3] = (uint16_t)Ts[3];
+                r.pool = po;
+                r.off = 0u;
+                rec[cur] = r;
+                if (po == kRecode) recode[atomicAdd(ticket + 1, 1u)] = cur;   // coded again when placed
             }
             __syncwarp();
-            ++nd;
         }
         cur = nxt;
         ji = jn;
     }
-    while (nd > 0) {                                  // the warp's last coded chunks
-        const Coded& O = W.def[dh];
-        place_chunk(J.j[O.job], O, flags, status);
-        dh = (dh + 1) % kDefer;
-        --nd;
+}
+
+// Scan kernel: one CTA per job.  The exclusive prefix of the job's chunk sizes
+// gives every chunk its offset in the payload (written to its record); the
+// job's header and stream size are written here too.
+template <int N>
+__global__ void __launch_bounds__(1024)
+k_rle_scan(const __grid_constant__ RleJobList<N> J, ChunkRec* rec)
+{
+    __shared__ uint32_t wsum[32];
+    const RleJobDesc& jb = J.j[blockIdx.x];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    uint8_t* dst = reinterpret_cast<uint8_t*>(jb.dst);
+    const uint32_t nc = jb.n_chunks;
+    if (nc == 0) {                                    // empty image: header only
+        if (tid == 0) {
+            write_header(dst, jb);
+            *jb.d_size = 32u;
+        }
+        return;
+    }
+    ChunkRec* R = rec + jb.first_unit;
+    const uint32_t per = (nc + blockDim.x - 1) / blockDim.x;   // contiguous chunks per thread
+    const uint32_t c0 = min(nc, tid * per), c1 = min(nc, c0 + per);
+    uint32_t mine = 0u;
+    for (uint32_t c = c0; c < c1; ++c) mine += (uint32_t)R[c].T[0] + R[c].T[1] + R[c].T[2] + R[c].T[3];
+    uint32_t inc = mine;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += y;
+    }
+    if (lane == 31) wsum[warp] = inc;
+    __syncthreads();
+    uint32_t base = inc - mine;
+    for (int k = 0; k < warp; ++k) base += wsum[k];
+    for (uint32_t c = c0; c < c1; ++c) {
+        R[c].off = base;
+        base += (uint32_t)R[c].T[0] + R[c].T[1] + R[c].T[2] + R[c].T[3];
+    }
+    if (tid == (int)blockDim.x - 1) {                 // its base is now the job's total
+        write_header(dst, jb);
+        *jb.d_size = 32ull + 16ull * nc + base;
+    }
+}
+
+// Placing kernel: one warp per chunk copies its streams from the pool to their
+// place and writes its four end-table entries (chunks to be coded again are
+// left to the recoding kernel).
+template <int N>
+__global__ void __launch_bounds__(128)
+k_rle_place(const __grid_constant__ RleJobList<N> J, const ChunkRec* rec, const uint8_t* pool)
+{
+    const int lane = threadIdx.x & 31;
+    const uint32_t unit = blockIdx.x * 4u + (threadIdx.x >> 5);
+    if (unit >= J.total_units) return;
+    const RleJobDesc& jb = J.j[find_job(J, unit)];
+    const uint32_t nc = jb.n_chunks;
+    if (nc == 0) return;                              // header written by the scan
+    const ChunkRec r = rec[unit];
+    if (r.pool == kRecode) return;
+    const uint32_t c = unit - jb.first_unit;
+    const uint32_t T0 = r.T[0], T1 = r.T[1], T2 = r.T[2], T3 = r.T[3];
+    const uint32_t total = T0 + T1 + T2 + T3;
+    uint8_t* dst = reinterpret_cast<uint8_t*>(jb.dst);
+    copy_out(dst + 32 + 16ull * nc + r.off, pool + r.pool, total, lane, 32);
+    const uint32_t mine = lane == 0 ? T0 : lane == 1 ? T0 + T1 : lane == 2 ? T0 + T1 + T2 : total;
+    if (lane < 4) put_u32(dst + 32 + 16ull * c + 4u * lane, r.off + mine);
+}
+
+// Recoding kernels: the listed chunks (dense, or sparse ones that found the
+// pool full) are coded from the image, a warp per listed chunk over a
+// persistent grid.  Before the scan (EMIT false) the dense ones are sized,
+// their sizes written to their records; after it (EMIT true) every listed
+// chunk is written straight to its place with its four end-table entries.
+template <int N, bool EMIT>
+__global__ void __launch_bounds__(128)
+k_rle_recode(const __grid_constant__ RleJobList<N> J, ChunkRec* rec, const uint32_t* recode, const uint32_t* count)
+{
+    const int lane = threadIdx.x & 31;
+    const uint32_t n = *count;
+    for (uint32_t i = blockIdx.x * 4u + (threadIdx.x >> 5); i < n; i += gridDim.x * 4u) {
+        const uint32_t unit = recode[i];
+        const RleJobDesc& jb = J.j[find_job(J, unit)];
+        const uint32_t nc = jb.n_chunks, c = unit - jb.first_unit;
+        const ChunkRec r = rec[unit];
+        uint32_t T[4] = {r.T[0], r.T[1], r.T[2], r.T[3]};
+        const uint32_t total = T[0] + T[1] + T[2] + T[3];
+        uint8_t* dst = reinterpret_cast<uint8_t*>(jb.dst);
+        const uint32_t q0 = c * (uint32_t)kChunk;
+        const int len = (int)min((uint32_t)kChunk, (uint32_t)jb.w * (uint32_t)jb.h - q0);
+        if (!EMIT) {
+            if (total != 0u) continue;                    // sized already (a sparse chunk)
+            dense_chunk<false>(jb, q0, len, jb.mode == 2, T, nullptr);
+            if (lane == 0)
+#pragma unroll
+                for (int p = 0; p < 4; ++p) rec[unit].T[p] = (uint16_t)T[p];
+            continue;
+        }
+        dense_chunk<true>(jb, q0, len, jb.mode == 2, T, dst + 32 + 16ull * nc + r.off);
+        const uint32_t mine = lane == 0 ? T[0] : lane == 1 ? T[0] + T[1] : lane == 2 ? T[0] + T[1] + T[2] : total;
+        if (lane < 4) put_u32(dst + 32 + 16ull * c + 4u * lane, r.off + mine);
     }
 }
 
@@ -1396,7 +1468,7 @@ RleJobList<N> make_jobs(const RleJobDesc* jobs, int n, uint32_t total)
 
 namespace {
 
-// Persistent grid: as many compress CTAs as fit on the device at once.
+// Persistent grid: as many coding CTAs as fit on the device at once.
 template <int N>
 cudaError_t compress_grid(int* grid)
 {
@@ -1418,37 +1490,68 @@ cudaError_t compress_grid(int* grid)
     return cudaSuccess;
 }
 
+// Modes 1 and 2: code (persistent warps), scan the sizes (a CTA per job),
+// place (a warp per chunk).
 template <int N>
-cudaError_t compress_n(const RleJobDesc* jobs, int n, uint32_t total_units, uint64_t* flags,
-                       uint32_t* ticket, uint32_t* status, cudaStream_t s)
+cudaError_t compress_n(const RleJobDesc* jobs, int n, uint32_t total_units, void* scratch, size_t scratch_bytes,
+                       uint32_t* status, cudaStream_t s)
 {
     int grid = 0;
-    const cudaError_t e = compress_grid<N>(&grid);
+    cudaError_t e = compress_grid<N>(&grid);
     if (e != cudaSuccess) return e;
     grid = (int)std::min<uint32_t>((uint32_t)grid, (total_units + kWPB - 1) / kWPB);
-    k_rle_compress<N><<<grid, 32 * kWPB, kCompressSmem, s>>>(make_jobs<N>(jobs, n, total_units), flags, ticket, status);
+    uint32_t* ticket = reinterpret_cast<uint32_t*>(scratch);     // [0] ticket, [1] chunks to recode
+    ChunkRec* rec = reinterpret_cast<ChunkRec*>(reinterpret_cast<char*>(scratch) + 16);
+    uint32_t* recode = reinterpret_cast<uint32_t*>(rec + total_units);
+    uint8_t* pool = reinterpret_cast<uint8_t*>(recode + ((total_units + 3u) & ~3u));
+    const size_t used = rle_compress_scratch_bytes(total_units, 0);
+    const uint32_t pool_bytes = (uint32_t)std::min<size_t>(scratch_bytes - used, 0xFFFFFFF0u);
+    const RleJobList<N> J = make_jobs<N>(jobs, n, total_units);
+    int sms = 0;
+    int dev = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+    const int rgrid = std::max(1, sms) * 4;
+    k_rle_compress<N><<<grid, 32 * kWPB, kCompressSmem, s>>>(J, rec, recode, pool, pool_bytes, ticket, status);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    k_rle_recode<N, false><<<rgrid, 128, 0, s>>>(J, rec, recode, ticket + 1);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    k_rle_scan<N><<<n, 1024, 0, s>>>(J, rec);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    k_rle_place<N><<<(total_units + 3) / 4, 128, 0, s>>>(J, rec, pool);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    k_rle_recode<N, true><<<rgrid, 128, 0, s>>>(J, rec, recode, ticket + 1);
     return cudaGetLastError();
 }
 
 }  // namespace
 
+size_t rle_compress_scratch_bytes(uint32_t units, size_t pool_per_unit)
+{
+    const size_t u = std::max<uint32_t>(units, 1);
+    return 16 + sizeof(ChunkRec) * u + 4 * ((u + 3) & ~(size_t)3) + pool_per_unit * u;
+}
+
 cudaError_t launch_rle_compress(const RleJobDesc* jobs, int n, uint32_t total_units,
-                                void* scratch, uint32_t* status, cudaStream_t s)
+                                void* scratch, size_t scratch_bytes, uint32_t* status, cudaStream_t s)
 {
     if (n <= 0 || total_units == 0) return cudaSuccess;
+    if (scratch_bytes < rle_compress_scratch_bytes(total_units, 0)) return cudaErrorInvalidValue;
     uint32_t* ticket = reinterpret_cast<uint32_t*>(scratch);
-    uint64_t* flags = reinterpret_cast<uint64_t*>(reinterpret_cast<char*>(scratch) + 16);
-    cudaError_t e = cudaMemsetAsync(scratch, 0, 16 + 8ull * total_units, s);
-    if (e != cudaSuccess) return e;
-    if (jobs[0].mode == 0) {                      // basic RLE: one CTA per chunk
+    if (jobs[0].mode == 0) {                      // basic RLE: one CTA per chunk, look-back flags
+        uint64_t* flags = reinterpret_cast<uint64_t*>(reinterpret_cast<char*>(scratch) + 16);
+        cudaError_t e = cudaMemsetAsync(scratch, 0, 16 + 8ull * total_units, s);
+        if (e != cudaSuccess) return e;
         if (n <= 8) k_rle0_compress<8><<<total_units, kT, 0, s>>>(make_jobs<8>(jobs, n, total_units), flags, ticket, status);
         else if (n <= 64) k_rle0_compress<64><<<total_units, kT, 0, s>>>(make_jobs<64>(jobs, n, total_units), flags, ticket, status);
         else k_rle0_compress<kRleJobsPerLaunch><<<total_units, kT, 0, s>>>(make_jobs<kRleJobsPerLaunch>(jobs, n, total_units), flags, ticket, status);
         return cudaGetLastError();
     }
-    if (n <= 8) return compress_n<8>(jobs, n, total_units, flags, ticket, status, s);
-    if (n <= 64) return compress_n<64>(jobs, n, total_units, flags, ticket, status, s);
-    return compress_n<kRleJobsPerLaunch>(jobs, n, total_units, flags, ticket, status, s);
+    const cudaError_t e = cudaMemsetAsync(scratch, 0, 16, s);   // ticket and pool cursor (bytes 8..15)
+    if (e != cudaSuccess) return e;
+    if (n <= 8) return compress_n<8>(jobs, n, total_units, scratch, scratch_bytes, status, s);
+    if (n <= 64) return compress_n<64>(jobs, n, total_units, scratch, scratch_bytes, status, s);
+    return compress_n<kRleJobsPerLaunch>(jobs, n, total_units, scratch, scratch_bytes, status, s);
 }
 
 cudaError_t launch_selftest_lookback(void* scratch, uint32_t* status, cudaStream_t s)

@@ -1,8 +1,9 @@
 // noalloc.cu -- ec_rle_compress_noalloc: the run-length compressor for callers
 // that cannot allocate device memory.
 //
-// ec_rle_compress needs scratch memory (one look-back word per 4096-element
-// chunk plus a ticket counter) that an ec_ctx allocates with cudaMalloc.  Some
+// ec_rle_compress needs scratch memory (a record per 4096-element chunk, a pool
+// that holds the coded chunks until they are placed, and two counters) that an
+// ec_ctx allocates with cudaMalloc.  Some
 // callers cannot do that: code that must not allocate once it is running (a
 // render loop that reserved all of its memory at start-up, or code whose
 // device memory belongs to another framework's pool), and code that cannot
@@ -24,10 +25,10 @@
 
 namespace {
 
-constexpr size_t kScratchBytes = 16 + 8ull * EC_RLE_NOALLOC_MAX_CHUNKS;
+constexpr size_t kScratchBytes = 16 + (16 + 4 + ec::kRlePoolPerUnit) * EC_RLE_NOALLOC_MAX_CHUNKS;
 static_assert(kScratchBytes == EC_RLE_NOALLOC_SCRATCH_BYTES, "documented scratch size");
 
-// Look-back flags and ticket shared by every call of the entry point.
+// Counters, chunk records and pool shared by every call of the entry point.
 static __device__ __align__(256) unsigned char g_rle_scratch[kScratchBytes];
 
 constexpr int kMaxDevices = 64;
@@ -84,8 +85,8 @@ extern "C" ec_status ec_rle_compress_noalloc(const void* src, int32_t w, int32_t
     d.first_unit = 0;
     d.vec = (reinterpret_cast<uintptr_t>(src) & 15u) == 0 && w % 4 == 0 && pitch % 4 == 0;
     const uint32_t units = nchunks > 0 ? (uint32_t)nchunks : 1u;
-    // the launcher clears the ticket and the flags this call uses (a memset,
-    // no allocation) before the kernel runs
-    return ec::launch_rle_compress(&d, 1, units, scratch, d_status, (cudaStream_t)s) == cudaSuccess
+    // the launcher clears the counters this call uses (a memset, no
+    // allocation) before the kernels run
+    return ec::launch_rle_compress(&d, 1, units, scratch, kScratchBytes, d_status, (cudaStream_t)s) == cudaSuccess
                ? EC_OK : EC_ERR_CUDA;
 }
