@@ -5,12 +5,16 @@
 // (thesis 5.2.1) without writing the decoded pieces to memory first.
 //
 // One CTA of eight warps per work unit.  A decode unit is one 4096-element
-// chunk of a received piece: warps 0-3 decode the colour stream's four byte
-// planes and warps 4-7 the depth stream's into shared memory (the decoder of
-// the RLE kernels, including its validation); then the threads take the
-// chunk's pixels four at a time (quads aligned to the output's 16-byte
-// boundaries), transpose them back from the planes with funnel shifts, read
-// the local input at the same frame pixels and write the merge.  A fill unit,
+// chunk of a received piece: warps 0-3 walk the colour stream's four byte
+// planes and warps 4-7 the depth stream's (the decoder of the RLE kernels,
+// including its validation).  When every plane has at most 255 runs they
+// record the runs only: between the union of the eight planes' run starts
+// colour and depth are constant, so each segment's pair is assembled once and
+// a pixel's pair is found by its rank among the run starts.  Otherwise they
+// decode the planes into shared memory, and pixels are transposed back from
+// them with funnel shifts.  The threads take the chunk's pixels four at a
+// time (quads aligned to the output's 16-byte boundaries), read the local
+// input at the same frame pixels and write the merge.  A fill unit,
 // a band of rows that no piece reaches, writes the local input (or the
 // background) there.
 //
@@ -100,12 +104,37 @@ __device__ __forceinline__ void load_local(const FusedStage& S, Quad& Q)
     }
 }
 
+// Run path of a decode unit: the chunk's elements are constant between the
+// union of its eight planes' run starts.  U: that union (128 words), PU: the
+// segments starting before each word, SC / SD: each segment's colour and depth.
+struct Segs {
+    const uint32_t* U;
+    const uint32_t* PU;
+    const uint32_t* SC;
+    const uint32_t* SD;
+};
+
 template <bool CODED>
 __device__ __forceinline__ void finish(const FusedStage& S, const Quad& Q, int q0, const uint8_t (*planes)[kChunk],
-                                       bool csw, bool dsw)
+                                       bool csw, bool dsw, const Segs* G = nullptr)
 {
     uint32_t oc[4], od[4];
-    if (CODED) {
+    if (CODED && G) {
+        const int i0 = Q.qa - q0;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            uint32_t ic = 0u, id = kBgDepth;
+            if (k >= Q.lo && k < Q.hi) {
+                const int i = i0 + k;
+                const uint32_t u = G->U[i >> 5];
+                const uint32_t s = G->PU[i >> 5] + __popc(u & ((2u << (i & 31)) - 1u)) - 1u;
+                ic = G->SC[s];
+                id = G->SD[s];
+            }
+            if (S.front) merge(ic, id, Q.lc[k], Q.ld[k], oc[k], od[k]);
+            else merge(Q.lc[k], Q.ld[k], ic, id, oc[k], od[k]);
+        }
+    } else if (CODED) {
         // bytes of elements qa - q0 .. +3 of every plane: two words and a funnel shift
         const int i0 = Q.qa - q0;
         const int wi = i0 >> 2, sh = 8 * (i0 & 3);
@@ -161,7 +190,8 @@ __device__ __forceinline__ Grid grid_of(const FusedStage& S, const FusedUnit& u,
 // Two quads per thread at a time: both local loads are in flight together.
 template <bool CODED>
 __device__ __forceinline__ void compose(const FusedStage& S, const FusedUnit& u, int ra, int nrows,
-                                        int q0, int len, const uint8_t (*planes)[kChunk], bool csw, bool dsw)
+                                        int q0, int len, const uint8_t (*planes)[kChunk], bool csw, bool dsw,
+                                        const Segs* G = nullptr)
 {
     const Grid g = grid_of(S, u, nrows);
     for (int s = threadIdx.x; s < g.slots; s += 2 * kFT) {
@@ -170,8 +200,8 @@ __device__ __forceinline__ void compose(const FusedStage& S, const FusedUnit& u,
         const bool b = s + kFT < g.slots && quad_at<CODED>(u, g, s + kFT, ra, q0, len, B);
         if (a) load_local(S, A);
         if (b) load_local(S, B);
-        if (a) finish<CODED>(S, A, q0, planes, csw, dsw);
-        if (b) finish<CODED>(S, B, q0, planes, csw, dsw);
+        if (a) finish<CODED>(S, A, q0, planes, csw, dsw, G);
+        if (b) finish<CODED>(S, B, q0, planes, csw, dsw, G);
     }
 }
 
@@ -183,7 +213,7 @@ k_fused_depth(const FusedStage* __restrict__ stages, const FusedUnit* __restrict
     __shared__ uint8_t s_hdr[2][rlec::kHdrBytes];
     __shared__ uint32_t s_beg[2][5];
     __shared__ int s_mode[2];
-    __shared__ int s_fail;
+    __shared__ int s_fail, s_over;
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const FusedUnit u = units[blockIdx.x];
@@ -204,7 +234,10 @@ k_fused_depth(const FusedStage* __restrict__ stages, const FusedUnit* __restrict
     if (tid < rlec::kHdrBytes) s_hdr[0][tid] = rlec::header_byte(u.cs, (uint64_t)u.cap, nc, u.chunk, tid);
     else if (tid >= 64 && tid < 64 + rlec::kHdrBytes)
         s_hdr[1][tid - 64] = rlec::header_byte(u.ds, (uint64_t)u.cap, nc, u.chunk, tid - 64);
-    if (tid == 0) s_fail = 0;
+    if (tid == 0) { s_fail = 0; s_over = 0; }
+    // the run bitmaps (aliased with the planes) start empty
+    uint32_t* bm = reinterpret_cast<uint32_t*>(&planes[0][0]);       // [8][128] run starts per plane
+    for (int i = tid; i < 8 * 128; i += kFT) bm[i] = 0u;
     __syncthreads();
     if (tid == 0 || tid == 32) {
         const int k = tid >> 5;
@@ -229,6 +262,79 @@ k_fused_depth(const FusedStage* __restrict__ stages, const FusedUnit* __restrict
     if (dnw <= kStageWords)
         for (int i = tid; i < dnw; i += kFT) staged[1][i] = __ldg(reinterpret_cast<const uint32_t*>(dpay) + dw0 + i);
     __syncthreads();
+    // run path: warp k*4+p walks stream k's plane p, recording its runs
+    uint8_t* const base8 = &planes[0][0];
+    {
+        const int k = warp >> 2, p = warp & 3;
+        const int b = (int)s_beg[k][p], e = (int)s_beg[k][p + 1];
+        const int w0 = k ? dw0 : cw0, nw = k ? dnw : cnw;
+        uint8_t* val = base8 + 4096 + 256 * warp;                   // [8][256] run bytes
+        int nr = 0;
+        const int r = nw <= kStageWords
+            ? rlec::decode_plane_runs(rlec::SharedBytes{reinterpret_cast<const uint8_t*>(staged[k]), 4 * w0},
+                                      b, e, len, bm + 128 * warp, val, 255, &nr, lane)
+            : rlec::decode_plane_runs(rlec::GlobalBytes{k ? dpay : cpay}, b, e, len, bm + 128 * warp, val, 255,
+                                      &nr, lane);
+        if (r == 1 && lane == 0) s_fail = 1;
+        if (r == 2 && lane == 0) s_over = 1;
+    }
+    __syncthreads();
+    if (s_fail) {
+        if (tid == 0) set_status(status, EC_ERR_CORRUPT);
+        return;
+    }
+    if (!s_over) {
+        uint32_t* U = reinterpret_cast<uint32_t*>(base8 + 6144);
+        uint32_t* PU = U + 128;
+        uint32_t* wt = PU + 128;                                     // scan scratch
+        uint32_t* SC = reinterpret_cast<uint32_t*>(base8 + 7296);    // <= 8 * 255 segments
+        uint32_t* SD = SC + 2040;
+        const uint8_t* val = base8 + 4096;
+        const bool csw = s_mode[0] == 2, dsw = s_mode[1] == 2;
+        uint32_t un = 0u, eu = 0u, ec = 0u, ed = 0u, wb[8];
+        if (tid < 128) {
+#pragma unroll
+            for (int q = 0; q < 8; ++q) { wb[q] = bm[128 * q + tid]; un |= wb[q]; }
+            const uint32_t cu = __popc(un);
+            const uint32_t cc = __popc(wb[0]) | (__popc(wb[1]) << 8) | (__popc(wb[2]) << 16) | ((uint32_t)__popc(wb[3]) << 24);
+            const uint32_t cd = __popc(wb[4]) | (__popc(wb[5]) << 8) | (__popc(wb[6]) << 16) | ((uint32_t)__popc(wb[7]) << 24);
+            uint32_t iu = cu, ic = cc, id = cd;      // (a plane has <= 255 runs: its byte never carries)
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t yu = __shfl_up_sync(0xffffffffu, iu, o), yc = __shfl_up_sync(0xffffffffu, ic, o);
+                const uint32_t yd = __shfl_up_sync(0xffffffffu, id, o);
+                if (lane >= o) { iu += yu; ic += yc; id += yd; }
+            }
+            if (lane == 31) { wt[3 * warp] = iu; wt[3 * warp + 1] = ic; wt[3 * warp + 2] = id; }
+            eu = iu - cu; ec = ic - cc; ed = id - cd;
+        }
+        __syncthreads();
+        if (tid < 128) {
+            for (int w = 0; w < warp; ++w) { eu += wt[3 * w]; ec += wt[3 * w + 1]; ed += wt[3 * w + 2]; }
+            U[tid] = un;
+            PU[tid] = eu;
+            for (uint32_t m = un; m; m &= m - 1u) {
+                const int bb = __ffs(m) - 1;
+                const uint32_t le = (2u << bb) - 1u;
+                uint32_t c = 0u, d = 0u;
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const uint32_t rc = ((ec >> (8 * q)) & 0xFFu) + __popc(wb[q] & le) - 1u;
+                    const uint32_t rd = ((ed >> (8 * q)) & 0xFFu) + __popc(wb[4 + q] & le) - 1u;
+                    c |= (uint32_t)val[256 * q + rc] << (8 * q);
+                    d |= (uint32_t)val[256 * (4 + q) + rd] << (8 * q);
+                }
+                const uint32_t sidx = eu + __popc(un & (le >> 1));
+                SC[sidx] = csw ? rlec::swizzle(c) : c;
+                SD[sidx] = dsw ? rlec::swizzle(d) : d;
+            }
+        }
+        __syncthreads();
+        const Segs G{U, PU, SC, SD};
+        compose<true>(S, u, ra, rb - ra + 1, (int)q0, len, planes, false, false, &G);
+        return;
+    }
+    // many runs: decode the planes into shared memory
     {
         const int k = warp >> 2, p = warp & 3;
         const int b = (int)s_beg[k][p], e = (int)s_beg[k][p + 1];
