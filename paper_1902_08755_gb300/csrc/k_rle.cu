@@ -287,27 +287,40 @@ __device__ __forceinline__ uint4 load_elems(const RleJobDesc& jb, uint32_t q0, i
         return __ldg(reinterpret_cast<const uint4*>(jb.src + e));
     }
     uint32_t v[4];
+    uint32_t y = (q0 + (uint32_t)q) / w, x = q0 + (uint32_t)q - y * w;
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
-        v[k] = 0u;
-        if (q + k < len) {
-            const uint32_t qq = q0 + (uint32_t)(q + k), y = qq / w;
-            v[k] = __ldg(jb.src + (size_t)y * jb.pitch + (qq - y * w));
-        }
+        v[k] = q + k < len ? __ldg(jb.src + (size_t)y * jb.pitch + x) : 0u;
+        if (++x == w) { x = 0u; ++y; }
     }
     return make_uint4(v[0], v[1], v[2], v[3]);
 }
 
-// Start the copy of quarter qi of chunk `unit` into W.buf[slot]: lane 0 sets the
-// expected bytes, every lane copies row segments.  Quarters with nothing to
-// copy (past the image's end, an empty image, or an image whose rows are not
-// 16-byte aligned, which is read from global memory instead) just arrive.
+// Asynchronous 4-byte copy from global to shared memory, and the arrival on
+// mbarrier b once all of this thread's earlier such copies have landed (the
+// barrier's pending count is raised by one now and lowered by the arrival).
+__device__ __forceinline__ void cp_async4(void* dst, const void* src)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+
+__device__ __forceinline__ void cp_async_arrive(uint64_t* b)
+{
+    asm volatile("cp.async.mbarrier.arrive.shared::cta.b64 [%0];" ::"r"(smem_u32(b)) : "memory");
+}
+
+// Start the copy of quarter qi of chunk `unit` into W.buf[slot].  Images whose
+// rows are 16-byte aligned: lane 0 sets the expected bytes, every lane copies
+// row segments with bulk copies.  Other images: every lane copies elements
+// lane, lane + 32, ... with 4-byte asynchronous copies, and the barrier
+// completes once all of them have landed.  Quarters with nothing to copy (past
+// the image's end, an empty image) just arrive.
 __device__ void issue_quarter(const RleJobDesc& jb, uint32_t unit, int qi, int slot, WarpRing& W)
 {
     const int lane = threadIdx.x & 31;
     int qlen = 0;
     uint32_t qs = 0u;
-    if (jb.n_chunks > 0 && jb.vec) {
+    if (jb.n_chunks > 0) {
         const uint32_t q0 = (unit - jb.first_unit) * (uint32_t)kChunk;
         const int len = (int)min((uint32_t)kChunk, (uint32_t)jb.w * (uint32_t)jb.h - q0);
         qlen = min(max(len - kQ * qi, 0), kQ);
@@ -317,10 +330,22 @@ __device__ void issue_quarter(const RleJobDesc& jb, uint32_t unit, int qi, int s
         if (lane == 0) mbar_arrive(&W.full[slot]);
         return;
     }
-    if (lane == 0) mbar_arrive_tx(&W.full[slot], 4u * (uint32_t)qlen);
-    __syncwarp();
     uint32_t* dst = W.buf[slot] + 4;
     const uint32_t w = (uint32_t)jb.w;
+    if (!jb.vec) {
+        uint32_t y = (qs + (uint32_t)lane) / w, x = qs + (uint32_t)lane - y * w;
+        for (int i = lane; i < qlen; i += 32) {
+            cp_async4(dst + i, jb.src + (size_t)y * jb.pitch + x);
+            x += 32u;
+            while (x >= w) { x -= w; ++y; }
+        }
+        cp_async_arrive(&W.full[slot]);
+        __syncwarp();                                  // every lane's pending count is in
+        if (lane == 0) mbar_arrive(&W.full[slot]);
+        return;
+    }
+    if (lane == 0) mbar_arrive_tx(&W.full[slot], 4u * (uint32_t)qlen);
+    __syncwarp();
     if (jb.pitch == jb.w) {
         if (lane == 0) bulk_load(dst, jb.src + qs, 4u * (uint32_t)qlen, &W.full[slot]);
         return;
@@ -334,37 +359,22 @@ __device__ void issue_quarter(const RleJobDesc& jb, uint32_t unit, int qi, int s
 }
 
 // Append the change points among positions [kQ qi, kQ qi + kQ) of the chunk
-// to W.ce / W.cq (the quarter's elements in shared memory at `data`, or read
-// from global memory when data is null).  carry: the element before the
-// quarter (updated to the quarter's last).  Every lane first compares its
-// four elements of all eight groups of 128 positions, one OR-reduction over
-// the warp tells which groups changed, and only those are listed.  Returns
-// false once the chunk has more than kCap change points.
-__device__ bool detect_quarter(const uint32_t* data, const RleJobDesc& jb, uint32_t q0, int len, int qi,
-                               WarpRing& W, int& m, uint32_t& carry)
+// to W.ce / W.cq (the quarter's elements in shared memory at `data`).  carry:
+// the element before the quarter (updated to the quarter's last).  Every lane
+// first compares its four elements of all G groups of 128 positions, one
+// OR-reduction over the warp tells which groups changed, and only those are
+// listed.  Returns false once the chunk has more than kCap change points.
+__device__ bool detect_quarter(const uint32_t* data, int len, int qi, WarpRing& W, int& m, uint32_t& carry)
 {
     const int lane = threadIdx.x & 31;
     const uint32_t lt = (1u << lane) - 1u;
     constexpr int G = kQ / 128;
     uint4 vv[G];
     uint32_t pv[G];
-    if (data) {
 #pragma unroll
-        for (int g = 0; g < G; ++g) {
-            vv[g] = *reinterpret_cast<const uint4*>(data + 128 * g + 4 * lane);
-            pv[g] = data[128 * g + 4 * lane - 1];         // g = lane = 0 reads the guard word
-        }
-    } else {
-#pragma unroll
-        for (int g = 0; g < G; ++g) vv[g] = load_elems(jb, q0, len, kQ * qi + 128 * g + 4 * lane);
-        uint32_t cy = carry;
-#pragma unroll
-        for (int g = 0; g < G; ++g) {
-            pv[g] = __shfl_up_sync(0xffffffffu, vv[g].w, 1);
-            const uint32_t last = __shfl_sync(0xffffffffu, vv[g].w, 31);
-            if (lane == 0) pv[g] = cy;
-            cy = last;
-        }
+    for (int g = 0; g < G; ++g) {
+        vv[g] = *reinterpret_cast<const uint4*>(data + 128 * g + 4 * lane);
+        pv[g] = data[128 * g + 4 * lane - 1];             // g = lane = 0 reads the guard word
     }
     if (lane == 0) pv[0] = qi == 0 ? ~vv[0].x : carry;    // position 0 is always listed
     carry = __shfl_sync(0xffffffffu, vv[G - 1].w, 31);   // (used only when the quarter is full)
@@ -849,7 +859,7 @@ k_rle_compress(const __grid_constant__ RleJobList<N> J, ChunkRec* rec, uint32_t*
             const int slot = (int)(qs % kSlots);
             mbar_wait(&W.full[slot], (qs / kSlots) & 1u, status);
             if (fits && kQ * q < len)
-                fits = detect_quarter(jb.vec ? W.buf[slot] + 4 : nullptr, jb, q0, len, q, W, m, carry);
+                fits = detect_quarter(W.buf[slot] + 4, len, q, W, m, carry);
             // the quarter's values have all been consumed (compared, voted on) by
             // now, so its reads are complete before the refill below starts
             __syncwarp();
