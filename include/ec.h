@@ -103,12 +103,12 @@ void ec_destroy(ec_ctx* ctx);
  * the last call (EC_OK if none) and clear it. */
 ec_status ec_status_sync(ec_ctx* ctx, ec_stream_t s);
 
-/* Self-test of failure detection without a fault: runs the codec's chunk
- * look-back (the one wait in libec's kernels) for a chunk whose predecessor
- * never publishes its size.  The wait gives up after its poll limit (2^22
- * polls with a short sleep; about a second), records EC_ERR_TIMEOUT in the
- * status word and the kernel returns, leaving the context usable.  Read the
- * result with ec_status_sync.  Uses the context's codec scratch. */
+/* Self-test of failure detection without a fault: one warp runs the
+ * compressor's bounded mbarrier wait (the one kind of wait in libec's kernels)
+ * on a barrier that nothing arrives on.  The wait gives up after its try limit
+ * (2^20 tries of at most about a microsecond each), records EC_ERR_TIMEOUT in
+ * the status word and the kernel returns, leaving the context usable.  Read
+ * the result with ec_status_sync. */
 ec_status ec_selftest_wait_timeout(ec_ctx* ctx, ec_stream_t s);
 
 /* Human-readable name of a status code (static string). */

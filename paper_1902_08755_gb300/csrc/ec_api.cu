@@ -492,7 +492,7 @@ ec_status ec_selftest_wait_timeout(ec_ctx* ctx, ec_stream_t s)
     if (!ctx) return EC_ERR_INVALID_ARG;
     DeviceGuard g(ctx->device);
     if (!g.ok) return EC_ERR_CUDA;
-    return cuda_status(launch_selftest_lookback(ctx->scratch, ctx->d_status, (cudaStream_t)s));
+    return cuda_status(launch_selftest_wait(ctx->d_status, (cudaStream_t)s));
 }
 
 size_t ec_rle_max_size(int32_t w, int32_t h)

@@ -33,7 +33,7 @@ inline bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 
 struct ec_ctx {
     int device = 0;
     uint32_t* d_status = nullptr;   // first device-side error (0 = none)
-    void* scratch = nullptr;        // codec look-back flags + ticket counter
+    void* scratch = nullptr;        // codec scratch: counters, chunk records, pool
     size_t scratch_bytes = 0;
     void* roi_scratch = nullptr;    // ROI detection: per-image box accumulators + done counter
     size_t roi_scratch_bytes = 0;
@@ -299,9 +299,9 @@ ec_status rle_job_desc(const ec_rle_job& j, bool compress, ec::RleJobDesc* d);
 
 namespace ec {
 
-// The codec's look-back on a predecessor that never publishes (scratch: 16
-// bytes); it times out and records EC_ERR_TIMEOUT.
-cudaError_t launch_selftest_lookback(void* scratch, uint32_t* status, cudaStream_t s);
+// A bounded mbarrier wait (the compressor's) on a barrier that nothing
+// arrives on; it gives up and records EC_ERR_TIMEOUT.
+cudaError_t launch_selftest_wait(uint32_t* status, cudaStream_t s);
 
 cudaError_t launch_fused_depth(const FusedStage* stages, const FusedUnit* units, int n_units,
                                uint32_t* status, cudaStream_t s);

@@ -1,28 +1,25 @@
 // k_rle.cu -- run-length pixel codec kernels for sm_103a (thesis 5.5.1:
 // per-component RLE, bit-swizzle preconditioner, data decomposition).
 //
-// Compress (modes 1, 2): every warp works alone on 4096-element chunks taken
-// from an atomic ticket.  A chunk streams through two 4 KB quarter buffers in
-// shared memory (bulk asynchronous copies completing on mbarriers, each buffer
-// refilled as soon as it has been read).
-//   1. Change points: positions whose element differs from its predecessor,
-//      listed with the element.  A byte plane changes only where the element
-//      does (the swizzle permutes bits, so it commutes with the comparison).
-//   2. Sparse path (at most 128 change points): each plane's runs are the
-//      change points where that plane's byte differs from the previous one's;
-//      runs of three or more become repeat tokens, maximal spans of shorter
-//      runs literal tokens.  The streams go to a small stage in shared memory.
-//   3. Dense path: all four planes classified at once with byte-SIMD masks
-//      (a byte is part of a repeat iff one of the three windows of 3 around it
-//      is constant), with warp max- and sum-scans carried over 8 steps of 512
-//      positions; coded once for the sizes and again, from the image, when
-//      placed.
-//   4. The chunk's size is published at once; the warp places the chunk (a
-//      decoupled look-back over the job's preceding chunks for its offset, then
-//      the stage copied out) a few chunks later, when its predecessors have
-//      normally published.  Every wait is bounded (EC_ERR_TIMEOUT).  Chunk 0
-//      writes the header, every chunk its four end-table entries, the last
-//      chunk the stream size.
+// Compress: a pipeline of kernels with no waits between warps.
+//   1. Coding (persistent warps, a chunk of 4096 elements at a time from an
+//      atomic ticket): the chunk streams through shared memory and its change
+//      points are listed; a chunk with few of them (sparse) is coded at once
+//      from the list into a scratch pool, the others (dense) are listed.
+//      Modes 1, 2: element change points, four byte planes (mode 2 swizzled;
+//      the swizzle permutes bits, so it commutes with the comparison); runs of
+//      three or more bytes become repeat tokens, maximal spans of shorter runs
+//      literal tokens.  Mode 0 (basic RLE): change points of 8-byte units,
+//      one stream; runs of two or more units repeat, single units literal.
+//   2. Sizing of the dense chunks from the image: all four planes classified
+//      at once with byte-SIMD masks (a byte is part of a repeat iff one of the
+//      three windows of 3 around it is constant), warp max- and sum-scans over
+//      8 steps of 512 positions; in mode 0 a CTA per chunk with block scans.
+//   3. A scan of each job's chunk sizes: the chunks' offsets, the header and
+//      the stream size.
+//   4. Placing: the pooled chunks copied to their place with their end-table
+//      entries; the dense chunks coded again, straight to their place.
+// Every wait (the copies into shared memory) is bounded (EC_ERR_TIMEOUT).
 //
 // Decompress: one CTA of four warps per chunk.  The header and the chunk's
 // end-table entries are fetched in one round trip and validated.  Warp p
@@ -44,8 +41,7 @@ namespace {
 constexpr int kChunk = EC_RLE_CHUNK;                 // 4096 elements
 constexpr int kT = 256;                              // threads per mode-0 CTA
 constexpr uint32_t kMagic = 0x31524345u;             // "ECR1"
-constexpr uint64_t kAgg = 1ull << 62, kInc = 2ull << 62, kVal = (1ull << 62) - 1;
-constexpr int kSpinLimit = 1 << 22;
+constexpr int kSpinLimit = 1 << 20;            // tries of a bounded mbarrier wait
 
 using rlec::swizzle;
 using rlec::transpose4;
@@ -69,6 +65,13 @@ __device__ __forceinline__ void put_u32(uint8_t* p, uint32_t v)
 }
 
 
+// Element q of a job's image.
+__device__ __forceinline__ size_t elem_off(const RleJobDesc& jb, uint32_t q)
+{
+    const uint32_t y = q / (uint32_t)jb.w;
+    return (size_t)y * jb.pitch + (q - y * (uint32_t)jb.w);
+}
+
 __device__ void write_header(uint8_t* d, const RleJobDesc& jb)
 {
     put_u32(d + 0, kMagic);
@@ -83,69 +86,6 @@ __device__ void write_header(uint8_t* d, const RleJobDesc& jb)
 }
 
 // ------------------------------------------------------------- compress ----
-
-__device__ __forceinline__ uint64_t warp_sum(uint64_t v)
-{
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
-}
-
-// The chunk-size flags carry their own value, so relaxed accesses suffice.
-__device__ __forceinline__ void st_flag(uint64_t* p, uint64_t v)
-{
-    asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
-}
-
-__device__ __forceinline__ uint64_t ld_flag(const uint64_t* p)
-{
-    uint64_t v;
-    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
-    return v;
-}
-
-// Exclusive prefix of work unit `unit`'s output inside its job's payload: the
-// sizes of the preceding chunks of the job, summed 32 flags at a time back to
-// one that holds its inclusive prefix; then this chunk's inclusive prefix is
-// published.  Run by one warp; every wait is bounded.
-__device__ uint64_t look_back(uint64_t* flags, uint32_t unit, uint32_t first_unit, uint64_t total,
-                              uint32_t* status)
-{
-    const int lane = threadIdx.x & 31;
-    if (unit == first_unit) return 0;                 // published inclusive when coded
-    uint64_t acc = 0;
-    int64_t hi = (int64_t)unit - 1;
-    int spins = 0;
-    for (;;) {
-        const int64_t k = hi - lane;
-        const uint64_t v = k >= (int64_t)first_unit ? ld_flag(flags + k) : kInc;
-        const uint32_t st = (uint32_t)(v >> 62);
-        const uint32_t incm = __ballot_sync(0xffffffffu, st == 2u);
-        const uint32_t zerom = __ballot_sync(0xffffffffu, st == 0u);
-        const uint32_t upto = incm ? ((incm & (0u - incm)) << 1) - 1u : 0xffffffffu;
-        if (zerom & upto) {
-            if (++spins > kSpinLimit) {
-                if (lane == 0) set_status(status, EC_ERR_TIMEOUT);
-                break;
-            }
-            __nanosleep(64);
-            continue;
-        }
-        acc += warp_sum(((upto >> lane) & 1u) ? (v & kVal) : 0ull);
-        if (incm) break;
-        hi -= 32;
-    }
-    if (lane == 0) st_flag(flags + unit, kInc | (acc + total));
-    return acc;
-}
-
-// Publish the chunk's size: inclusive for the job's first chunk, else an
-// aggregate that the look-back of later chunks may sum.
-__device__ __forceinline__ void publish(uint64_t* flags, uint32_t unit, uint32_t first_unit, uint32_t total)
-{
-    st_flag(flags + unit, (unit == first_unit ? kInc : kAgg) | (uint64_t)total);
-}
-
 
 // Copy n stage bytes (src 4-byte aligned) to o, threads t, t+nt, ...: byte
 // stores up to o's first word boundary and after its last, word stores of
@@ -171,24 +111,24 @@ __device__ __forceinline__ void copy_out(uint8_t* o, const uint8_t* src, uint32_
     }
 }
 
-// ---- compressor (modes 1 and 2): one warp per chunk ------------------------
-// Every warp works alone, chunk after chunk.  It streams each chunk through a
-// ring of four 4 KB quarter buffers in shared memory, filled by bulk
-// asynchronous copies (one per row segment) that complete on the quarter's
-// mbarrier; a quarter is refilled with the same quarter of the warp's next
-// chunk as soon as it has been read, so about three quarters are always in
-// flight.  Reading a chunk, the warp lists its change points: the positions
-// where the element differs from its predecessor, with the element there.  A
-// byte plane can change only where the element does, so each plane's runs are
-// the change points where that plane's byte differs from the previous change
-// point's, and every run's value is the byte at its start: the sparse path
-// sizes and later writes the chunk's streams from the change list alone.
-// Chunks with more change points than the list holds take the dense path,
-// which codes all four planes at once from registers (the chunk re-read from
-// global memory, mostly from L2).  A chunk's size is published as soon as it
-// is known; the warp places the chunk (look-back, then the tokens written
-// straight to their place in the stream) two chunks later, by which time the
-// chunks before it have normally published theirs.
+// ---- compressor: one warp per chunk ---------------------------------------
+// Every warp of the coding kernel works alone, chunk after chunk.  It streams
+// each chunk through a ring of two 2 KB quarter buffers in shared memory,
+// filled by asynchronous copies (bulk copies of row segments, or 4-byte copies
+// where rows are not 16-byte aligned) that complete on the buffer's mbarrier;
+// a buffer is refilled with the next quarter (of this chunk or the next) as
+// soon as it has been read.  Reading a chunk, the warp lists its change
+// points: the positions where the element differs from its predecessor, with
+// the element there.  A byte plane can change only where the element does, so
+// each plane's runs are the change points where that plane's byte differs
+// from the previous change point's, and every run's value is the byte at its
+// start: the sparse path codes the chunk's streams from the change list alone,
+// into the warp's stage, and leaves them in a scratch pool.  Chunks with more
+// change points than the list holds are dense: a recoding kernel sizes them
+// from the image.  A scan over each job's chunk sizes gives every chunk its
+// offset; a placing kernel copies the pooled chunks to their place and the
+// recoding kernel writes the dense ones there (coded again from the image,
+// partly from L2).  No kernel waits for another's warps.
 constexpr int kWPB = 2;                       // warps per CTA
 constexpr int kCap = 128;                     // change points the sparse path takes
 constexpr int kQ = 512;                       // elements per quarter buffer
@@ -813,6 +753,278 @@ __device__ __noinline__ void dense_chunk(const RleJobDesc& jb, uint32_t q0, int 
         for (int b = 0; b < 4; ++b) T[b] = lane16(csum, b);
 }
 
+// ---- basic RLE (mode 0) on the same pipeline --------------------------------
+// Thesis 5.5.1's basic RLE codes 8-byte units (element pairs) in one stream
+// per chunk.  The coding kernel lists the chunk's unit change points (units
+// that differ from their predecessor) as it lists element change points for
+// the four-plane modes; a run of one unit is literal, maximal spans of literal
+// units become literal tokens and longer runs repeat tokens, both at most 128
+// units per token, full tokens first.  Chunks with more change points than the
+// list holds are coded by a CTA per chunk from the image (code0_block).
+constexpr int kU = kChunk / 2;                       // units per chunk
+constexpr int kUPer = kU / kT;                       // 8 per thread of a CTA
+constexpr int kStage0 = 8 * kU + kU / 128 + 32;      // worst case + room for copy_out's read-ahead
+
+__device__ __forceinline__ void put8(uint8_t* p, uint32_t lo, uint32_t hi)
+{
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        p[k] = (uint8_t)(lo >> (8 * k));
+        p[4 + k] = (uint8_t)(hi >> (8 * k));
+    }
+}
+
+// Append the unit change points among units [kQ/2 qi, kQ/2 qi + kQ/2) of the
+// chunk (unit k = elements 2k, 2k + 1) to W.cq (the unit's index) and W.ce /
+// the second list `ch` (its two elements), as detect_quarter does for
+// elements: a lane's 16-byte group holds two units.  carry: the unit before
+// the quarter (updated to the quarter's last).  Returns false once the chunk
+// has more than kCap change points.
+__device__ bool detect_quarter0(const uint32_t* data, int len, int qi, WarpRing& W, uint32_t* ch, int& m,
+                                uint2& carry)
+{
+    const int lane = threadIdx.x & 31;
+    const uint32_t lt = (1u << lane) - 1u;
+    constexpr int G = kQ / 128;
+    uint4 vv[G];
+    uint2 pv[G];
+#pragma unroll
+    for (int g = 0; g < G; ++g) {
+        vv[g] = *reinterpret_cast<const uint4*>(data + 128 * g + 4 * lane);
+        pv[g] = *reinterpret_cast<const uint2*>(data + 128 * g + 4 * lane - 2);   // g = lane = 0: guard words
+    }
+    if (lane == 0) pv[0] = qi == 0 ? make_uint2(~vv[0].x, vv[0].y) : carry;     // unit 0 is always listed
+    carry = make_uint2(__shfl_sync(0xffffffffu, vv[G - 1].z, 31), __shfl_sync(0xffffffffu, vv[G - 1].w, 31));
+    const int uend = min(len / 2 - kQ / 2 * qi, kQ / 2);                         // units of this quarter
+    uint32_t mine = 0u;
+#pragma unroll
+    for (int g = 0; g < G; ++g) {
+        const uint4 v = vv[g];
+        const uint32_t x = (v.x ^ pv[g].x) | (v.y ^ pv[g].y) | (v.z ^ v.x) | (v.w ^ v.y);
+        mine |= (x != 0u && 64 * g + 2 * lane < uend ? 1u : 0u) << g;
+    }
+    const uint32_t groups = __reduce_or_sync(0xffffffffu, mine);
+#pragma unroll
+    for (int g = 0; g < G; ++g) {
+        if (!((groups >> g) & 1u)) continue;
+        const uint4 v = vv[g];
+        const int u = 64 * g + 2 * lane;                  // within the quarter
+        uint32_t f = (v.x != pv[g].x || v.y != pv[g].y ? 1u : 0u) | (v.z != v.x || v.w != v.y ? 2u : 0u);
+        if (u + 2 > uend) f &= u >= uend ? 0u : 1u;
+        const uint32_t b0 = __ballot_sync(0xffffffffu, f & 1u), b1 = __ballot_sync(0xffffffffu, f & 2u);
+        const int cnt = __popc(b0) + __popc(b1);
+        if (m + cnt > kCap) return false;
+        int o = m + __popc(b0 & lt) + __popc(b1 & lt);
+        const int uu = kQ / 2 * qi + u;
+        if (f & 1u) { W.cq[o] = (uint16_t)uu; W.ce[o] = v.x; ch[o] = v.y; ++o; }
+        if (f & 2u) { W.cq[o] = (uint16_t)(uu + 1); W.ce[o] = v.z; ch[o] = v.w; }
+        m += cnt;
+    }
+    return true;
+}
+
+// Mode 0, sparse path: the tokens of a chunk of nu units from its m <= 128
+// unit change points (run i starts at unit cq[i], its unit is (ce[i], ch[i]),
+// and it ends where run i + 1 starts, or at nu).  Lane l takes runs 4l .. 4l+3.
+// A warp max-scan gives every literal run the start of its span, a sum-scan
+// the place of its bytes; a repeat run writes its tokens, a literal unit its
+// 8 bytes, and the unit that ends a literal token the token's control byte.
+// Returns the bytes written.
+__device__ uint32_t code_sparse0(const uint32_t* ce, const uint32_t* ch, const uint16_t* cq, int m, int nu,
+                                 uint8_t* out)
+{
+    const int lane = threadIdx.x & 31;
+    const int i0 = 4 * lane;
+    int s[5];
+#pragma unroll
+    for (int k = 0; k < 5; ++k) s[k] = i0 + k < m ? (int)cq[i0 + k] : nu;
+    uint32_t lit = 0u;                                    // bit k: run i0 + k is one unit
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+        if (i0 + k < m && s[k + 1] - s[k] == 1) lit |= 1u << k;
+    const uint32_t litn = __shfl_down_sync(0xffffffffu, lit, 1);
+    const uint32_t litp = __shfl_up_sync(0xffffffffu, lit, 1);
+    const uint32_t lx = lit | ((lane < 31 ? (litn & 1u) : 0u) << 4);   // bit 4: the next lane's first run
+    const uint32_t pre = (lit << 1) | (lane > 0 ? ((litp >> 3) & 1u) : 0u);   // bit k: run i0 + k - 1 literal
+    const uint32_t starts = lit & ~pre;                   // literal runs that start a span
+    // the last span start up to each lane (index + 1; 0: none)
+    uint32_t last = starts ? (uint32_t)(i0 + 32 - __clz(starts)) : 0u;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, last, o);
+        if (lane >= o) last = max(last, y);
+    }
+    uint32_t S0 = __shfl_up_sync(0xffffffffu, last, 1);
+    if (lane == 0) S0 = 0u;
+    uint32_t sz = 0u, S = S0;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        if (i0 + k >= m) break;
+        if ((starts >> k) & 1u) S = (uint32_t)(i0 + k + 1);
+        if ((lit >> k) & 1u) sz += ((uint32_t)(i0 + k) - (S - 1u)) % 128u == 0u ? 9u : 8u;
+        else sz += 9u * (((uint32_t)(s[k + 1] - s[k]) + 127u) / 128u);
+    }
+    uint32_t inc = sz;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += y;
+    }
+    const uint32_t total = __shfl_sync(0xffffffffu, inc, 31);
+    uint32_t P = inc - sz;
+    S = S0;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const int i = i0 + k;
+        if (i >= m) break;
+        const uint32_t lo = ce[i], hi = ch[i];
+        if ((starts >> k) & 1u) S = (uint32_t)(i + 1);
+        if ((lit >> k) & 1u) {
+            const uint32_t p = ((uint32_t)i - (S - 1u)) % 128u;   // place in its token
+            const uint32_t ts = p == 0u ? 1u : 0u;
+            put8(out + P + ts, lo, hi);
+            P += 8u + ts;
+            if (p == 127u || !((lx >> (k + 1)) & 1u)) out[P - 8u * (p + 1u) - 1u] = (uint8_t)p;
+        } else {
+            for (uint32_t L = (uint32_t)(s[k + 1] - s[k]); L > 0u;) {
+                const uint32_t piece = min(L, 128u);
+                out[P] = (uint8_t)(127u + piece);
+                put8(out + P + 1u, lo, hi);
+                P += 9u;
+                L -= piece;
+            }
+        }
+    }
+    return total;
+}
+
+// Exclusive block scan (sum, or max with identity 0) of one value per thread;
+// *total receives the reduction over the block.
+template <bool MAX>
+__device__ __forceinline__ uint32_t block_excl(uint32_t v, uint32_t* wt, uint32_t* total)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t inc = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc = MAX ? max(inc, y) : inc + y;
+    }
+    if (lane == 31) wt[warp] = inc;
+    __syncthreads();
+    uint32_t pre = 0, tot = 0;
+#pragma unroll
+    for (int w = 0; w < kT / 32; ++w) {
+        const uint32_t t = wt[w];
+        if (w < warp) pre = MAX ? max(pre, t) : pre + t;
+        tot = MAX ? max(tot, t) : tot + t;
+    }
+    uint32_t ex = __shfl_up_sync(0xffffffffu, inc, 1);
+    if (lane == 0) ex = 0u;
+    *total = tot;
+    __syncthreads();                                  // wt is reused by the next scan
+    return MAX ? max(pre, ex) : pre + ex;
+}
+
+// Mode 0, dense path: one CTA of kT threads codes chunk [q0, q0 + len) of the
+// job into stage and returns its size (the odd tail element included).  The
+// chunk's elements go to e in shared memory; each thread reads its 8
+// consecutive units and the two on either side into registers once (16-byte
+// reads).  A unit equal to a neighbour belongs to a repeat run, the others form
+// literal spans; a block max-scan gives every unit its segment's start (a run,
+// or a maximal span of single units), a block sum-scan the place of its bytes,
+// and the unit that ends a token writes the token's control byte.
+__device__ uint32_t code0_block(const RleJobDesc& jb, uint32_t q0, int len, uint32_t* e, uint8_t* stage,
+                                uint32_t* wt)
+{
+    const int tid = threadIdx.x;
+    for (int t = tid; 4 * t < len; t += kT)
+        *reinterpret_cast<uint4*>(e + 4 * t) = load_elems(jb, q0, len, 4 * t);
+    __syncthreads();
+    const int nu = len / 2;
+    const int k0 = tid * kUPer;
+    uint32_t ul[kUPer + 4], uh[kUPer + 4];           // [0,1] = k0-2, k0-1; [2..9] = k0..k0+7; [10,11] = k0+8, k0+9
+    {
+        const uint4* e4 = reinterpret_cast<const uint4*>(e);
+        const uint4 m = tid > 0 ? e4[4 * tid - 1] : make_uint4(0u, 0u, 0u, 0u);
+        ul[0] = m.x; uh[0] = m.y; ul[1] = m.z; uh[1] = m.w;
+#pragma unroll
+        for (int g = 0; g < 4; ++g) {
+            const uint4 v = e4[4 * tid + g];
+            ul[2 + 2 * g] = v.x; uh[2 + 2 * g] = v.y; ul[3 + 2 * g] = v.z; uh[3 + 2 * g] = v.w;
+        }
+        const uint4 n = tid + 1 < kT ? e4[4 * tid + 4] : make_uint4(0u, 0u, 0u, 0u);
+        ul[10] = n.x; uh[10] = n.y; ul[11] = n.z; uh[11] = n.w;
+    }
+    // eqp bit i: unit k0-2+i equals its predecessor (both exist), i = 0 .. 11
+    uint32_t eqp = 0u;
+#pragma unroll
+    for (int i = 1; i < kUPer + 4; ++i) {
+        const int k = k0 - 2 + i;
+        if (k >= 1 && k < nu && ul[i] == ul[i - 1] && uh[i] == uh[i - 1]) eqp |= 1u << i;
+    }
+    // lit bit i, i = 1 .. 10: unit k0-2+i exists and equals neither neighbour
+    uint32_t lit = 0u;
+#pragma unroll
+    for (int i = 1; i < kUPer + 3; ++i) {
+        const int k = k0 - 2 + i;
+        if (k >= 0 && k < nu && !((eqp >> i) & 1u) && !((eqp >> (i + 1)) & 1u)) lit |= 1u << i;
+    }
+    // seg bit i, i = 2 .. 10: unit k0-2+i starts a run or a span
+    uint32_t seg = 0u;
+#pragma unroll
+    for (int i = 2; i < kUPer + 3; ++i) {
+        const int k = k0 - 2 + i;
+        if (k >= nu) continue;
+        const bool l = (lit >> i) & 1u, lp = (lit >> (i - 1)) & 1u;
+        if (k == 0 || l != lp || (!l && !((eqp >> i) & 1u))) seg |= 1u << i;
+    }
+    uint32_t smax = 0, ssum = 0, tot = 0;
+#pragma unroll
+    for (int j = 0; j < kUPer; ++j)
+        if (k0 + j < nu && ((seg >> (j + 2)) & 1u)) smax = (uint32_t)(k0 + j);
+    const uint32_t carry = block_excl<true>(smax, wt, &tot);
+    uint32_t S = carry;
+#pragma unroll
+    for (int j = 0; j < kUPer; ++j) {
+        const int k = k0 + j;
+        if (k >= nu) break;
+        if ((seg >> (j + 2)) & 1u) S = (uint32_t)k;
+        const bool ts = ((uint32_t)k - S) % 128u == 0u;
+        ssum += ((lit >> (j + 2)) & 1u) ? 8u + (ts ? 1u : 0u) : (ts ? 9u : 0u);
+    }
+    uint32_t body = 0;
+    uint32_t P = block_excl<false>(ssum, wt, &body);
+    S = carry;
+#pragma unroll
+    for (int j = 0; j < kUPer; ++j) {
+        const int k = k0 + j;
+        if (k >= nu) break;
+        if ((seg >> (j + 2)) & 1u) S = (uint32_t)k;
+        const bool l = (lit >> (j + 2)) & 1u;
+        const uint32_t pos = (uint32_t)k - S;
+        const bool ts = pos % 128u == 0u;
+        const uint32_t sz = l ? 8u + (ts ? 1u : 0u) : (ts ? 9u : 0u);
+        const bool te = k + 1 == nu || ((seg >> (j + 3)) & 1u) || ((uint32_t)k + 1u - S) % 128u == 0u;
+        const uint32_t L = pos % 128u + 1u;          // units of the token so far
+        if (l) {
+            put8(stage + P + (ts ? 1u : 0u), ul[j + 2], uh[j + 2]);
+            if (te) stage[P + sz - 1u - 8u * L] = (uint8_t)(L - 1u);
+        } else {
+            if (ts) put8(stage + P + 1u, ul[j + 2], uh[j + 2]);
+            if (te) stage[P + sz - 9u] = (uint8_t)(128u + L - 1u);
+        }
+        P += sz;
+    }
+    if ((len & 1) && tid == 0) {
+        const uint32_t v = e[len - 1];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) stage[body + k] = (uint8_t)(v >> (8 * k));
+    }
+    __syncthreads();                                  // the stage is complete
+    return body + ((len & 1) ? 4u : 0u);
+}
+
 // Coding kernel.  Per chunk a warp: takes its next ticket (the atomic overlaps
 // the wait for the first quarter); reads the four quarters, refilling each
 // slot as soon as it has been read (with the next quarter of this chunk or of
@@ -820,8 +1032,8 @@ __device__ __noinline__ void dense_chunk(const RleJobDesc& jb, uint32_t q0, int 
 // for a sparse chunk, its streams in the pool (space taken with an atomic
 // cursor; a chunk that finds the pool full is coded again when placed, like a
 // dense one; such chunks are listed for the recoding kernel).  No warp waits
-// for another.
-template <int N>
+// for another.  M0: basic RLE (mode 0), from unit change points.
+template <int N, bool M0>
 __global__ void __launch_bounds__(32 * kWPB, 11)
 k_rle_compress(const __grid_constant__ RleJobList<N> J, ChunkRec* rec, uint32_t* recode, uint8_t* pool,
                uint32_t pool_bytes, uint32_t* ticket, uint32_t* status)
@@ -853,13 +1065,16 @@ k_rle_compress(const __grid_constant__ RleJobList<N> J, ChunkRec* rec, uint32_t*
         const int len = nc ? (int)min((uint32_t)kChunk, (uint32_t)jb.w * (uint32_t)jb.h - q0) : 0;
         int m = 0;
         uint32_t carry = 0u;
+        uint2 carry2 = make_uint2(0u, 0u);
+        uint32_t* ch = reinterpret_cast<uint32_t*>(W.rl);    // mode 0: second element of each listed unit
         bool fits = true;
         for (int q = 0; q < kQPC; ++q) {
             const uint32_t qs = (uint32_t)kQPC * seq + (uint32_t)q;   // the warp's quarter sequence number
             const int slot = (int)(qs % kSlots);
             mbar_wait(&W.full[slot], (qs / kSlots) & 1u, status);
             if (fits && kQ * q < len)
-                fits = detect_quarter(W.buf[slot] + 4, len, q, W, m, carry);
+                fits = M0 ? detect_quarter0(W.buf[slot] + 4, len, q, W, ch, m, carry2)
+                          : detect_quarter(W.buf[slot] + 4, len, q, W, m, carry);
             // the quarter's values have all been consumed (compared, voted on) by
             // now, so its reads are complete before the refill below starts
             __syncwarp();
@@ -871,7 +1086,14 @@ k_rle_compress(const __grid_constant__ RleJobList<N> J, ChunkRec* rec, uint32_t*
         if (nc > 0) {
             const bool sw = jb.mode == 2;
             uint32_t Ts[4] = {0u, 0u, 0u, 0u};          // (a dense chunk is sized by the recoding kernels)
-            if (fits) {
+            if (fits && M0) {
+                __syncwarp();
+                Ts[0] = code_sparse0(W.ce, ch, W.cq, m, len / 2, W.stage);
+                if (len & 1) {                            // the odd last element follows the tokens
+                    if (lane == 0) put_u32(W.stage + Ts[0], __ldg(jb.src + elem_off(jb, q0 + (uint32_t)len - 1u)));
+                    Ts[0] += 4u;
+                }
+            } else if (fits) {
                 __syncwarp();
                 if (sw)
                     for (int i = lane; i < m; i += 32) W.ce[i] = swizzle(W.ce[i]);
@@ -950,13 +1172,13 @@ k_rle_scan(const __grid_constant__ RleJobList<N> J, ChunkRec* rec)
     }
     if (tid == (int)blockDim.x - 1) {                 // its base is now the job's total
         write_header(dst, jb);
-        *jb.d_size = 32ull + 16ull * nc + base;
+        *jb.d_size = 32ull + (jb.mode == 0 ? 4ull : 16ull) * nc + base;
     }
 }
 
 // Placing kernel: one warp per chunk copies its streams from the pool to their
-// place and writes its four end-table entries (chunks to be coded again are
-// left to the recoding kernel).
+// place and writes its end-table entries (four; one in mode 0).  Chunks to be
+// coded again are left to the recoding kernel.
 template <int N>
 __global__ void __launch_bounds__(128)
 k_rle_place(const __grid_constant__ RleJobList<N> J, const ChunkRec* rec, const uint8_t* pool)
@@ -973,6 +1195,11 @@ k_rle_place(const __grid_constant__ RleJobList<N> J, const ChunkRec* rec, const 
     const uint32_t T0 = r.T[0], T1 = r.T[1], T2 = r.T[2], T3 = r.T[3];
     const uint32_t total = T0 + T1 + T2 + T3;
     uint8_t* dst = reinterpret_cast<uint8_t*>(jb.dst);
+    if (jb.mode == 0) {                               // one stream, one end-table entry
+        copy_out(dst + 32 + 4ull * nc + r.off, pool + r.pool, total, lane, 32);
+        if (lane == 0) put_u32(dst + 32 + 4ull * c, r.off + total);
+        return;
+    }
     copy_out(dst + 32 + 16ull * nc + r.off, pool + r.pool, total, lane, 32);
     const uint32_t mine = lane == 0 ? T0 : lane == 1 ? T0 + T1 : lane == 2 ? T0 + T1 + T2 : total;
     if (lane < 4) put_u32(dst + 32 + 16ull * c + 4u * lane, r.off + mine);
@@ -1013,253 +1240,143 @@ k_rle_recode(const __grid_constant__ RleJobList<N> J, ChunkRec* rec, const uint3
     }
 }
 
-// ------------------------------------------------- basic RLE, mode 0 ------
-// Thesis 5.5.1's basic RLE: 8-byte units (element pairs) in one stream per
-// chunk.  One CTA per chunk, taken in ticket order.  The chunk's elements are
-// loaded into shared memory; each thread reads its 8 consecutive units and
-// the two on either side into registers once (16-byte reads).  A unit
-// equal to a neighbour belongs to a repeat run; the others form literal
-// spans.  A block max-scan gives every unit its segment's start (a run, or a
-// maximal span of single units), a block sum-scan the position of its bytes,
-// and the unit that ends a token (at most 128 units) writes the token's
-// control byte in front of it.  The chunk's offset comes from the same
-// decoupled look-back as the four-plane modes.
-constexpr int kU = kChunk / 2;                       // units per chunk
-constexpr int kUPer = kU / kT;                       // 8 per thread
-constexpr int kStage0 = 8 * kU + kU / 128 + 32;      // worst case + room for copy_out's read-ahead
-
-// Exclusive block scan (sum, or max with identity 0) of one value per thread;
-// *total receives the reduction over the block.
-template <bool MAX>
-__device__ __forceinline__ uint32_t block_excl(uint32_t v, uint32_t* wt, uint32_t* total)
-{
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    uint32_t inc = v;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
-        if (lane >= o) inc = MAX ? max(inc, y) : inc + y;
-    }
-    if (lane == 31) wt[warp] = inc;
-    __syncthreads();
-    uint32_t pre = 0, tot = 0;
-#pragma unroll
-    for (int w = 0; w < kT / 32; ++w) {
-        const uint32_t t = wt[w];
-        if (w < warp) pre = MAX ? max(pre, t) : pre + t;
-        tot = MAX ? max(tot, t) : tot + t;
-    }
-    uint32_t ex = __shfl_up_sync(0xffffffffu, inc, 1);
-    if (lane == 0) ex = 0u;
-    *total = tot;
-    __syncthreads();                                  // wt is reused by the next scan
-    return MAX ? max(pre, ex) : pre + ex;
-}
-
-__device__ __forceinline__ void put8(uint8_t* p, uint32_t lo, uint32_t hi)
-{
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-        p[k] = (uint8_t)(lo >> (8 * k));
-        p[4 + k] = (uint8_t)(hi >> (8 * k));
-    }
-}
-
-template <int N>
-__global__ void __launch_bounds__(kT, 5)
-k_rle0_compress(const __grid_constant__ RleJobList<N> J, uint64_t* flags, uint32_t* ticket, uint32_t* status)
+// Mode-0 recoding kernels: as k_rle_recode, with one CTA per listed chunk
+// (code0_block).  Before the scan (EMIT false) the dense chunks are sized;
+// after it (EMIT true) every listed chunk is written to its place with its
+// end-table entry.
+template <int N, bool EMIT>
+__global__ void __launch_bounds__(kT)
+k_rle0_recode(const __grid_constant__ RleJobList<N> J, ChunkRec* rec, const uint32_t* recode, const uint32_t* count)
 {
     __shared__ __align__(16) uint32_t e[kChunk];
     __shared__ __align__(16) uint8_t stage[kStage0];
     __shared__ uint32_t wt[kT / 32];
-    __shared__ uint32_t s_unit;
-    __shared__ uint64_t s_off;
     const int tid = threadIdx.x;
-    if (tid == 0) s_unit = atomicAdd(ticket, 1u);
-    __syncthreads();
-    const uint32_t unit = s_unit;
-    const RleJobDesc& jb = J.j[find_job(J, unit)];
-    const uint32_t nc = jb.n_chunks, c = unit - jb.first_unit;
-    uint8_t* dst = reinterpret_cast<uint8_t*>(jb.dst);
-    if (c >= nc) {                                    // empty image: header only
-        if (tid == 0) {
-            write_header(dst, jb);
-            *jb.d_size = 32u;
-        }
-        return;
-    }
-    const uint32_t w = (uint32_t)jb.w, n = w * (uint32_t)jb.h, q0 = c * (uint32_t)kChunk;
-    const int len = (int)min((uint32_t)kChunk, n - q0);
-    for (int t = tid; t < len; t += kT) {
-        const uint32_t q = q0 + (uint32_t)t, y = q / w;
-        e[t] = __ldg(jb.src + (size_t)y * jb.pitch + (q - y * w));
-    }
-    __syncthreads();
-
-    // this thread's 8 units, the two before and the two after, read once
-    const int nu = len / 2;
-    const int k0 = tid * kUPer;
-    uint32_t ul[kUPer + 4], uh[kUPer + 4];           // [0,1] = k0-2, k0-1; [2..9] = k0..k0+7; [10,11] = k0+8, k0+9
-    {
-        const uint4* e4 = reinterpret_cast<const uint4*>(e);
-        const uint4 m = tid > 0 ? e4[4 * tid - 1] : make_uint4(0u, 0u, 0u, 0u);
-        ul[0] = m.x; uh[0] = m.y; ul[1] = m.z; uh[1] = m.w;
-#pragma unroll
-        for (int g = 0; g < 4; ++g) {
-            const uint4 v = e4[4 * tid + g];
-            ul[2 + 2 * g] = v.x; uh[2 + 2 * g] = v.y; ul[3 + 2 * g] = v.z; uh[3 + 2 * g] = v.w;
-        }
-        const uint4 n = tid + 1 < kT ? e4[4 * tid + 4] : make_uint4(0u, 0u, 0u, 0u);
-        ul[10] = n.x; uh[10] = n.y; ul[11] = n.z; uh[11] = n.w;
-    }
-    // eqp[i]: unit k0-2+i equals its predecessor (both exist), i = 0 .. 11
-    uint32_t eqp = 0u;
-#pragma unroll
-    for (int i = 1; i < kUPer + 4; ++i) {
-        const int k = k0 - 2 + i;
-        if (k >= 1 && k < nu && ul[i] == ul[i - 1] && uh[i] == uh[i - 1]) eqp |= 1u << i;
-    }
-    // lit[i], i = 1 .. 10: unit k0-2+i exists and equals neither neighbour
-    uint32_t lit = 0u;
-#pragma unroll
-    for (int i = 1; i < kUPer + 3; ++i) {
-        const int k = k0 - 2 + i;
-        if (k >= 0 && k < nu && !((eqp >> i) & 1u) && !((eqp >> (i + 1)) & 1u)) lit |= 1u << i;
-    }
-    // seg[i], i = 2 .. 10: unit k0-2+i starts a run or a span
-    uint32_t seg = 0u;
-#pragma unroll
-    for (int i = 2; i < kUPer + 3; ++i) {
-        const int k = k0 - 2 + i;
-        if (k >= nu) continue;
-        const bool l = (lit >> i) & 1u, lp = (lit >> (i - 1)) & 1u;
-        if (k == 0 || l != lp || (!l && !((eqp >> i) & 1u))) seg |= 1u << i;
-    }
-
-    uint32_t smax = 0, ssum = 0, tot = 0;
-#pragma unroll
-    for (int j = 0; j < kUPer; ++j)
-        if (k0 + j < nu && ((seg >> (j + 2)) & 1u)) smax = (uint32_t)(k0 + j);
-    const uint32_t carry = block_excl<true>(smax, wt, &tot);
-    uint32_t S = carry;
-#pragma unroll
-    for (int j = 0; j < kUPer; ++j) {
-        const int k = k0 + j;
-        if (k >= nu) break;
-        if ((seg >> (j + 2)) & 1u) S = (uint32_t)k;
-        const bool ts = ((uint32_t)k - S) % 128u == 0u;
-        ssum += ((lit >> (j + 2)) & 1u) ? 8u + (ts ? 1u : 0u) : (ts ? 9u : 0u);
-    }
-    uint32_t body = 0;
-    uint32_t P = block_excl<false>(ssum, wt, &body);
-    S = carry;
-#pragma unroll
-    for (int j = 0; j < kUPer; ++j) {
-        const int k = k0 + j;
-        if (k >= nu) break;
-        if ((seg >> (j + 2)) & 1u) S = (uint32_t)k;
-        const bool l = (lit >> (j + 2)) & 1u;
-        const uint32_t pos = (uint32_t)k - S;
-        const bool ts = pos % 128u == 0u;
-        const uint32_t sz = l ? 8u + (ts ? 1u : 0u) : (ts ? 9u : 0u);
-        const bool te = k + 1 == nu || ((seg >> (j + 3)) & 1u) || ((uint32_t)k + 1u - S) % 128u == 0u;
-        const uint32_t L = pos % 128u + 1u;          // units of the token so far
-        if (l) {
-            put8(stage + P + (ts ? 1u : 0u), ul[j + 2], uh[j + 2]);
-            if (te) stage[P + sz - 1u - 8u * L] = (uint8_t)(L - 1u);
+    const uint32_t n = *count;
+    for (uint32_t i = blockIdx.x; i < n; i += gridDim.x) {
+        const uint32_t unit = recode[i];
+        const RleJobDesc& jb = J.j[find_job(J, unit)];
+        const uint32_t nc = jb.n_chunks, c = unit - jb.first_unit;
+        const ChunkRec r = rec[unit];
+        if (!EMIT && r.T[0] != 0u) continue;              // sized already (a sparse chunk)
+        const uint32_t q0 = c * (uint32_t)kChunk;
+        const int len = (int)min((uint32_t)kChunk, (uint32_t)jb.w * (uint32_t)jb.h - q0);
+        const uint32_t total = code0_block(jb, q0, len, e, stage, wt);
+        if (!EMIT) {
+            if (tid == 0) rec[unit].T[0] = (uint16_t)total;
         } else {
-            if (ts) put8(stage + P + 1u, ul[j + 2], uh[j + 2]);
-            if (te) stage[P + sz - 9u] = (uint8_t)(128u + L - 1u);
+            uint8_t* dst = reinterpret_cast<uint8_t*>(jb.dst);
+            copy_out(dst + 32 + 4ull * nc + r.off, stage, total, tid, kT);
+            if (tid == 0) put_u32(dst + 32 + 4ull * c, r.off + total);
         }
-        P += sz;
-    }
-    const uint32_t total = body + ((len & 1) ? 4u : 0u);
-    if ((len & 1) && tid == 0) {
-        const uint32_t v = e[len - 1];
-#pragma unroll
-        for (int k = 0; k < 4; ++k) stage[body + k] = (uint8_t)(v >> (8 * k));
-    }
-    if (tid == 0) publish(flags, unit, jb.first_unit, total);
-    __syncthreads();
-    if (tid < 32) {
-        const uint64_t acc = look_back(flags, unit, jb.first_unit, total, status);
-        if (tid == 0) s_off = acc;
-    }
-    __syncthreads();
-    const uint64_t G = s_off;
-    copy_out(dst + 32 + 4ull * nc + G, stage, total, tid, kT);
-    if (tid == 0) {
-        put_u32(dst + 32 + 4ull * c, (uint32_t)(G + total));
-        if (c == 0) write_header(dst, jb);
-        if (c == nc - 1) *jb.d_size = 32ull + 4ull * nc + G + total;
+        __syncthreads();                                  // e and stage are reused
     }
 }
 
-// Self-test of the bounded waits: unit 1 looks back for unit 0, which never
-// publishes its size (flags[0] stays 0); the wait gives up after its poll
-// limit, records EC_ERR_TIMEOUT and the kernel returns.
-__global__ void k_selftest_lookback(uint64_t* flags, uint32_t* status)
+// Self-test of the bounded waits: a warp waits on an mbarrier that nothing
+// arrives on; the wait gives up after its try limit, records EC_ERR_TIMEOUT
+// and the kernel returns.
+__global__ void k_selftest_wait(uint32_t* status)
 {
-    if (threadIdx.x < 32) look_back(flags, 1u, 0u, 0u, status);
+    __shared__ uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncwarp();
+    mbar_wait(&bar, 0u, status);
 }
 
 // ----------------------------------------------------------- decompress ----
 
 constexpr int kDT = 128;        // decoder CTA: one warp per byte plane
 
-// Element q of a job's image.
-__device__ __forceinline__ size_t elem_off(const RleJobDesc& jb, uint32_t q)
-{
-    const uint32_t y = q / (uint32_t)jb.w;
-    return (size_t)y * jb.pitch + (q - y * (uint32_t)jb.w);
-}
 
 // Mode 0 (basic 64-bit RLE): the chunk's one stream [b, e) of the payload is
-// staged in shared memory, then warp 0 walks its tokens in order, every lane
-// reading each control byte, and writes each token's units with its lanes.
+// staged in shared memory.  Then, up to kTok0 tokens at a time, one thread
+// walks the tokens (control byte, size, bounds) and lists each token's first
+// unit and stream offset in tok, and the four warps write the listed tokens,
+// one token per warp and a unit per lane (8-byte stores of the unit's two
+// elements where the image allows).  A unit's 8 stream bytes are funnel-
+// shifted out of three aligned shared-memory words.
+constexpr int kTok0 = 256;
+
 __device__ void decode_mode0(const RleJobDesc& jb, const uint8_t* pay, uint32_t b, uint32_t e, uint32_t q0,
-                             int len, uint8_t* sbuf, uint32_t* status)
+                             int len, uint8_t* sbuf, uint32_t* tok, uint32_t* status)
 {
-    const int tid = threadIdx.x, lane = tid & 31;
+    __shared__ uint32_t s_ntok, s_i, s_o, s_bad;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const uint32_t w0 = b >> 2, wl = e >> 2;          // whole words [w0, wl), then bytes [4 wl, e)
     uint32_t* st = reinterpret_cast<uint32_t*>(sbuf);
     const uint32_t* p32 = reinterpret_cast<const uint32_t*>(pay);
     for (uint32_t i = tid; w0 + i < wl; i += kDT) st[i] = __ldg(p32 + w0 + i);
     if (tid < (int)(e - 4u * wl) && wl >= w0) sbuf[4u * (wl - w0) + tid] = __ldg(pay + 4u * wl + tid);
+    if (tid == 0) { s_i = b; s_o = 0u; s_bad = 0u; }
     __syncthreads();
-    if (tid >= 32) return;
     const uint8_t* sb = sbuf - 4u * w0;                // stream byte i at sb[i]
-    auto u32_at = [&](uint32_t i) {
-        return (uint32_t)sb[i] | ((uint32_t)sb[i + 1] << 8) | ((uint32_t)sb[i + 2] << 16) | ((uint32_t)sb[i + 3] << 24);
-    };
+    const uint32_t* sw = st - w0;                      // stream word j (bytes 4j .. 4j+3) at sw[j]
     uint32_t* dst = reinterpret_cast<uint32_t*>(jb.dst);
-    const int nu = len / 2;
-    uint32_t i = b;
-    int o = 0, bad = 0;
-    while (o < nu) {
-        if (i >= e) { bad = 1; break; }
-        const uint32_t ctl = sb[i];
-        const int m = ctl < 128u ? (int)ctl + 1 : (int)ctl - 127;
-        const uint32_t need = ctl < 128u ? 1u + 8u * (uint32_t)m : 9u;
-        if (o + m > nu || i + need > e) { bad = 1; break; }
-        for (int k = lane; k < m; k += 32) {
-            const uint32_t v = ctl < 128u ? i + 1u + 8u * (uint32_t)k : i + 1u;
-            const uint32_t q = q0 + 2u * (uint32_t)(o + k);
-            dst[elem_off(jb, q)] = u32_at(v);
-            dst[elem_off(jb, q + 1u)] = u32_at(v + 4u);
+    const bool pairs = jb.vec != 0u;                   // rows 16-byte aligned: a unit never straddles rows
+    const bool dense = jb.pitch == jb.w;
+    const uint32_t nu = (uint32_t)len / 2u;
+    for (;;) {
+        if (tid == 0) {
+            uint32_t i = s_i, o = s_o, k = 0u, bad = 0u;
+            while (o < nu && k < (uint32_t)kTok0) {
+                if (i >= e) { bad = 1u; break; }
+                const uint32_t ctl = sb[i];
+                const uint32_t m = ctl < 128u ? ctl + 1u : ctl - 127u;
+                const uint32_t need = ctl < 128u ? 1u + 8u * m : 9u;
+                if (o + m > nu || i + need > e) { bad = 1u; break; }
+                tok[k++] = o | ((i - b) << 12);
+                i += need;
+                o += m;
+            }
+            s_ntok = k; s_i = i; s_o = o; s_bad = bad;
         }
-        i += need;
-        o += m;
+        __syncthreads();
+        const uint32_t ntok = s_ntok;
+        for (uint32_t t = (uint32_t)warp; t < ntok; t += kDT / 32) {
+            const uint32_t r = tok[t], o = r & 0xFFFu, i = b + (r >> 12);
+            const uint32_t ctl = sb[i];
+            const bool lit = ctl < 128u;
+            const uint32_t m = lit ? ctl + 1u : ctl - 127u;
+            for (uint32_t k = (uint32_t)lane; k < m; k += 32u) {
+                const uint32_t x = i + 1u + (lit ? 8u * k : 0u);   // the unit's first stream byte
+                const uint32_t sh = 8u * (x & 3u), j = x >> 2;
+                const uint32_t a0 = sw[j], a1 = sw[j + 1], a2 = sw[j + 2];
+                const uint32_t lo = __funnelshift_r(a0, a1, sh), hi = __funnelshift_r(a1, a2, sh);
+                const uint32_t q = q0 + 2u * (o + k);
+                if (pairs) {
+                    size_t eo = q;
+                    if (!dense) {
+                        const uint32_t y = q / (uint32_t)jb.w;
+                        eo = (size_t)y * jb.pitch + (q - y * (uint32_t)jb.w);
+                    }
+                    __stcs(reinterpret_cast<uint2*>(dst + eo), make_uint2(lo, hi));
+                } else {
+                    dst[elem_off(jb, q)] = lo;
+                    dst[elem_off(jb, q + 1u)] = hi;
+                }
+            }
+        }
+        const bool done = s_bad != 0u || s_o >= nu;
+        __syncthreads();                              // tok and the shared words are reused
+        if (done) break;
     }
+    if (tid != 0) return;
+    uint32_t i = s_i;
+    bool bad = s_bad != 0u;
     if (!bad && (len & 1)) {
-        if (i + 4u > e) bad = 1;
+        if (i + 4u > e) bad = true;
         else {
-            if (lane == 0) dst[elem_off(jb, q0 + (uint32_t)len - 1u)] = u32_at(i);
+            dst[elem_off(jb, q0 + (uint32_t)len - 1u)] =
+                (uint32_t)sb[i] | ((uint32_t)sb[i + 1] << 8) | ((uint32_t)sb[i + 2] << 16) | ((uint32_t)sb[i + 3] << 24);
             i += 4u;
         }
     }
-    if (!bad && i != e) bad = 1;
-    if (bad && lane == 0) set_status(status, EC_ERR_CORRUPT);
+    if (!bad && i != e) bad = true;
+    if (bad) set_status(status, EC_ERR_CORRUPT);
 }
 
 // Run path of the decoder (few runs): the chunk's elements are constant
@@ -1349,6 +1466,7 @@ k_rle_decompress(const __grid_constant__ RleJobList<N> J, uint32_t* status)
     __shared__ uint32_t s_beg[5];
     __shared__ int s_fail, s_over, s_mode;
     __shared__ uint8_t s_hdr[rlec::kHdrBytes];
+    __shared__ uint32_t s_tok[kTok0];                 // mode 0: listed tokens
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const uint32_t unit = blockIdx.x;
@@ -1378,7 +1496,7 @@ k_rle_decompress(const __grid_constant__ RleJobList<N> J, uint32_t* status)
     const uint32_t q0 = c * (uint32_t)kChunk;
     const int len = (int)min((uint32_t)kChunk, n - q0);
     if (s_mode == 0) {
-        decode_mode0(jb, src + 32 + 4ull * nc, s_beg[0], s_beg[1], q0, len, sbuf, status);
+        decode_mode0(jb, src + 32 + 4ull * nc, s_beg[0], s_beg[1], q0, len, sbuf, s_tok, status);
         return;
     }
     const uint8_t* payload = src + 32 + 16ull * nc;
@@ -1479,7 +1597,7 @@ RleJobList<N> make_jobs(const RleJobDesc* jobs, int n, uint32_t total)
 namespace {
 
 // Persistent grid: as many coding CTAs as fit on the device at once.
-template <int N>
+template <int N, bool M0>
 cudaError_t compress_grid(int* grid)
 {
     constexpr int kMaxDev = 64;
@@ -1488,10 +1606,10 @@ cudaError_t compress_grid(int* grid)
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (dev < kMaxDev && (*grid = cache[dev].load(std::memory_order_relaxed)) > 0) return cudaSuccess;
-    e = cudaFuncSetAttribute(k_rle_compress<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kCompressSmem);
+    e = cudaFuncSetAttribute(k_rle_compress<N, M0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kCompressSmem);
     if (e != cudaSuccess) return e;
     int per_sm = 0, sms = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_rle_compress<N>, 32 * kWPB, kCompressSmem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_rle_compress<N, M0>, 32 * kWPB, kCompressSmem);
     if (e != cudaSuccess) return e;
     e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return e;
@@ -1500,14 +1618,14 @@ cudaError_t compress_grid(int* grid)
     return cudaSuccess;
 }
 
-// Modes 1 and 2: code (persistent warps), scan the sizes (a CTA per job),
-// place (a warp per chunk).
-template <int N>
+// Code (persistent warps), size the dense chunks, scan the sizes (a CTA per
+// job), place (a warp per chunk), write the dense chunks.  M0: basic RLE.
+template <int N, bool M0>
 cudaError_t compress_n(const RleJobDesc* jobs, int n, uint32_t total_units, void* scratch, size_t scratch_bytes,
                        uint32_t* status, cudaStream_t s)
 {
     int grid = 0;
-    cudaError_t e = compress_grid<N>(&grid);
+    cudaError_t e = compress_grid<N, M0>(&grid);
     if (e != cudaSuccess) return e;
     grid = (int)std::min<uint32_t>((uint32_t)grid, (total_units + kWPB - 1) / kWPB);
     uint32_t* ticket = reinterpret_cast<uint32_t*>(scratch);     // [0] ticket, [1] chunks to recode
@@ -1522,15 +1640,17 @@ cudaError_t compress_n(const RleJobDesc* jobs, int n, uint32_t total_units, void
     if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
     if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
     const int rgrid = std::max(1, sms) * 4;
-    k_rle_compress<N><<<grid, 32 * kWPB, kCompressSmem, s>>>(J, rec, recode, pool, pool_bytes, ticket, status);
+    k_rle_compress<N, M0><<<grid, 32 * kWPB, kCompressSmem, s>>>(J, rec, recode, pool, pool_bytes, ticket, status);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    k_rle_recode<N, false><<<rgrid, 128, 0, s>>>(J, rec, recode, ticket + 1);
+    if (M0) k_rle0_recode<N, false><<<rgrid, kT, 0, s>>>(J, rec, recode, ticket + 1);
+    else k_rle_recode<N, false><<<rgrid, 128, 0, s>>>(J, rec, recode, ticket + 1);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     k_rle_scan<N><<<n, 1024, 0, s>>>(J, rec);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     k_rle_place<N><<<(total_units + 3) / 4, 128, 0, s>>>(J, rec, pool);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    k_rle_recode<N, true><<<rgrid, 128, 0, s>>>(J, rec, recode, ticket + 1);
+    if (M0) k_rle0_recode<N, true><<<rgrid, kT, 0, s>>>(J, rec, recode, ticket + 1);
+    else k_rle_recode<N, true><<<rgrid, 128, 0, s>>>(J, rec, recode, ticket + 1);
     return cudaGetLastError();
 }
 
@@ -1547,28 +1667,21 @@ cudaError_t launch_rle_compress(const RleJobDesc* jobs, int n, uint32_t total_un
 {
     if (n <= 0 || total_units == 0) return cudaSuccess;
     if (scratch_bytes < rle_compress_scratch_bytes(total_units, 0)) return cudaErrorInvalidValue;
-    uint32_t* ticket = reinterpret_cast<uint32_t*>(scratch);
-    if (jobs[0].mode == 0) {                      // basic RLE: one CTA per chunk, look-back flags
-        uint64_t* flags = reinterpret_cast<uint64_t*>(reinterpret_cast<char*>(scratch) + 16);
-        cudaError_t e = cudaMemsetAsync(scratch, 0, 16 + 8ull * total_units, s);
-        if (e != cudaSuccess) return e;
-        if (n <= 8) k_rle0_compress<8><<<total_units, kT, 0, s>>>(make_jobs<8>(jobs, n, total_units), flags, ticket, status);
-        else if (n <= 64) k_rle0_compress<64><<<total_units, kT, 0, s>>>(make_jobs<64>(jobs, n, total_units), flags, ticket, status);
-        else k_rle0_compress<kRleJobsPerLaunch><<<total_units, kT, 0, s>>>(make_jobs<kRleJobsPerLaunch>(jobs, n, total_units), flags, ticket, status);
-        return cudaGetLastError();
-    }
-    const cudaError_t e = cudaMemsetAsync(scratch, 0, 16, s);   // ticket and pool cursor (bytes 8..15)
+    const cudaError_t e = cudaMemsetAsync(scratch, 0, 16, s);   // ticket, recode count, pool cursor
     if (e != cudaSuccess) return e;
-    if (n <= 8) return compress_n<8>(jobs, n, total_units, scratch, scratch_bytes, status, s);
-    if (n <= 64) return compress_n<64>(jobs, n, total_units, scratch, scratch_bytes, status, s);
-    return compress_n<kRleJobsPerLaunch>(jobs, n, total_units, scratch, scratch_bytes, status, s);
+    if (jobs[0].mode == 0) {                      // (one launch codes one mode family)
+        if (n <= 8) return compress_n<8, true>(jobs, n, total_units, scratch, scratch_bytes, status, s);
+        if (n <= 64) return compress_n<64, true>(jobs, n, total_units, scratch, scratch_bytes, status, s);
+        return compress_n<kRleJobsPerLaunch, true>(jobs, n, total_units, scratch, scratch_bytes, status, s);
+    }
+    if (n <= 8) return compress_n<8, false>(jobs, n, total_units, scratch, scratch_bytes, status, s);
+    if (n <= 64) return compress_n<64, false>(jobs, n, total_units, scratch, scratch_bytes, status, s);
+    return compress_n<kRleJobsPerLaunch, false>(jobs, n, total_units, scratch, scratch_bytes, status, s);
 }
 
-cudaError_t launch_selftest_lookback(void* scratch, uint32_t* status, cudaStream_t s)
+cudaError_t launch_selftest_wait(uint32_t* status, cudaStream_t s)
 {
-    const cudaError_t e = cudaMemsetAsync(scratch, 0, 16, s);
-    if (e != cudaSuccess) return e;
-    k_selftest_lookback<<<1, 32, 0, s>>>(reinterpret_cast<uint64_t*>(scratch), status);
+    k_selftest_wait<<<1, 32, 0, s>>>(status);
     return cudaGetLastError();
 }
 

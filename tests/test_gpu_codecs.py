@@ -98,6 +98,26 @@ def test_mode0_full_size_source():
         assert _bytes(buf, size) == oracle.rle_compress(np.ascontiguousarray(arr), 0)
 
 
+@pytest.mark.parametrize("mode", [0, 1, 2])
+def test_sparse_chunks_that_overflow_the_pool(mode):
+    """Every chunk is sparse (126 noisy elements, then one value) but codes to
+    more bytes than the compressor's scratch pool holds per chunk on average
+    (512), so part of them find the pool full and are coded again from the
+    image when placed.  A fresh context sizes its scratch for exactly this
+    job (2048 chunks), so the overflow is certain."""
+    require_gpu()
+    r = np.random.default_rng(90 + mode)
+    img = np.repeat(r.integers(0, 2**32, size=(2048, 1), dtype=np.uint64).astype(np.uint32), 4096, axis=1)
+    img[:, :126] = r.integers(0, 2**32, size=(2048, 126), dtype=np.uint64).astype(np.uint32)
+    ctx = ec.Context()
+    try:
+        buf, size = ec.rle_compress(_u32(img), mode, ctx=ctx)
+        ctx.check_status()
+        assert _bytes(buf, size) == oracle.rle_compress(img, mode)
+    finally:
+        ctx.close()
+
+
 def test_mode0_without_allocation():
     require_gpu()
     img = _images()["boxes"]
