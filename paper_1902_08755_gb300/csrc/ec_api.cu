@@ -528,7 +528,9 @@ ec_status rle_job_desc(const ec_rle_job& j, bool compress, RleJobDesc* d)
         if (n > 0 && (reinterpret_cast<uintptr_t>(j.src) & 3u)) return EC_ERR_INVALID_ARG;
         d->mode = j.mode;
         d->d_size = j.d_size;
-        d->vec = aligned16(j.src) && j.w % 4 == 0 && j.pitch % 4 == 0;
+        // 16-byte reads: rows of whole 16-byte groups, or one contiguous run
+        // of a multiple of 4 elements
+        d->vec = aligned16(j.src) && ((j.w % 4 == 0 && j.pitch % 4 == 0) || (j.pitch == j.w && n % 4 == 0));
     } else {
         if (!j.src || (reinterpret_cast<uintptr_t>(j.src) & 3u)) return EC_ERR_INVALID_ARG;
         if (n > 0 && (reinterpret_cast<uintptr_t>(j.dst) & 3u)) return EC_ERR_INVALID_ARG;

@@ -9,6 +9,8 @@
 // loads where the layout allows) and writes the group once.  HBM-bound.
 #include "composite_body.cuh"
 
+#include <algorithm>
+
 namespace ec {
 namespace {
 
@@ -57,18 +59,37 @@ __device__ __forceinline__ uint32_t covered(const SrcDesc& s, int x, int y, int 
 
 // ---- sort-first / tile assembly -----------------------------------------
 
-template <int N, int BPP>
+// Up to 64 sources: which sources meet each column and each row of CTA tiles,
+// as bit masks (bit i: source i), computed on the host.  A tile's sources are
+// its column's mask and its row's, so a CTA finds them with two uniform
+// parameter reads instead of testing every source.
+constexpr int kMaskCols = 128, kMaskRows = 512;
+struct TileMasks {
+    uint64_t col[kMaskCols];
+    uint64_t row[kMaskRows];
+};
+
+// MASK: the sources come from the tile masks (n <= 64), else each CTA lists
+// them (build_active).  Every pixel walks them from last to first and stops
+// once its 16-byte group is complete.
+template <int N, int BPP, bool MASK>
 __global__ void __launch_bounds__(kAT)
-k_assemble_tiles(const __grid_constant__ SrcList<N> L, const __grid_constant__ DstDesc D)
+k_assemble_tiles(const __grid_constant__ SrcList<N> L, const __grid_constant__ DstDesc D,
+                 const __grid_constant__ TileMasks M)
 {
     constexpr int PX = Grp<BPP>::PX, TW = 32 * PX, WPP = BPP / 4;
-    __shared__ int16_t act[N > 0 ? N : 1];
+    __shared__ int16_t act[MASK ? 1 : (N > 0 ? N : 1)];
     __shared__ int nact_s;
-    auto at = [&](int, int i) -> const SrcDesc& { return L.s[i]; };
     const int lane = threadIdx.x & 31, row = threadIdx.x >> 5;
     const int tx0 = blockIdx.x * TW, ty0 = blockIdx.y * (kARows * kAPasses);
-    build_active(at, L.n, tx0, ty0, min(tx0 + TW, D.W), min(ty0 + kARows * kAPasses, D.H), act, &nact_s);
-    __syncthreads();
+    uint64_t amask = 0;
+    if (MASK) {
+        amask = M.col[blockIdx.x] & M.row[blockIdx.y];
+    } else {
+        auto at = [&](int, int i) -> const SrcDesc& { return L.s[i]; };
+        build_active(at, L.n, tx0, ty0, min(tx0 + TW, D.W), min(ty0 + kARows * kAPasses, D.H), act, &nact_s);
+        __syncthreads();
+    }
     const int x = tx0 + lane * PX;
     if (x >= D.W) return;
     const uint32_t full = x + PX <= D.W ? (1u << PX) - 1u : (1u << (D.W - x)) - 1u;
@@ -78,8 +99,18 @@ k_assemble_tiles(const __grid_constant__ SrcList<N> L, const __grid_constant__ D
     uint32_t w[PX][WPP];
     uint32_t have = 0;
     // the last source covering a pixel wins: walk back until every pixel is set
-    for (int a = nact_s - 1; a >= 0 && have != full; --a) {
-        const SrcDesc& s = L.s[act[a]];
+    uint64_t mm = amask;
+    for (int a = MASK ? 0 : nact_s - 1; have != full; --a) {
+        int i;
+        if (MASK) {
+            if (!mm) break;
+            i = 63 - __clzll((long long)mm);
+            mm ^= 1ull << i;
+        } else {
+            if (a < 0) break;
+            i = act[a];
+        }
+        const SrcDesc& s = L.s[i];
         const uint32_t m = covered<PX>(s, x, y, D.W) & ~have;
         if (!m) continue;
         const size_t e = (size_t)(y - s.oy) * (size_t)s.pitch + (size_t)(x - s.ox);
@@ -327,15 +358,42 @@ SrcList<N> make_src_list(const SrcDesc* src, int n)
     return L;
 }
 
+template <int N, int BPP, bool MASK>
+void tiles_launch(const SrcList<N>& L, const DstDesc& D, const TileMasks& M, dim3 grid, cudaStream_t s)
+{
+    k_assemble_tiles<N, BPP, MASK><<<grid, kAT, 0, s>>>(L, D, M);
+}
+
+template <int N, bool MASK>
+void tiles_bpp(const SrcList<N>& L, int bpp, const DstDesc& D, const TileMasks& M, dim3 grid, cudaStream_t s)
+{
+    if (bpp == 4) tiles_launch<N, 4, MASK>(L, D, M, grid, s);
+    else if (bpp == 8) tiles_launch<N, 8, MASK>(L, D, M, grid, s);
+    else tiles_launch<N, 16, MASK>(L, D, M, grid, s);
+}
+
 template <int N>
 cudaError_t tiles_n(const SrcDesc* src, int n, int bpp, const DstDesc& D, cudaStream_t s)
 {
     const SrcList<N> L = make_src_list<N>(src, n);
-    const int px = 16 / bpp;
-    const dim3 grid(ceil_div(D.W, 32 * px), ceil_div(D.H, kARows * kAPasses));
-    if (bpp == 4) k_assemble_tiles<N, 4><<<grid, kAT, 0, s>>>(L, D);
-    else if (bpp == 8) k_assemble_tiles<N, 8><<<grid, kAT, 0, s>>>(L, D);
-    else k_assemble_tiles<N, 16><<<grid, kAT, 0, s>>>(L, D);
+    const int tw = 32 * (16 / bpp), th = kARows * kAPasses;
+    const dim3 grid(ceil_div(D.W, tw), ceil_div(D.H, th));
+    static thread_local TileMasks M;
+    if (N <= 64 && grid.x <= (unsigned)kMaskCols && grid.y <= (unsigned)kMaskRows) {
+        for (unsigned c = 0; c < grid.x; ++c) M.col[c] = 0;
+        for (unsigned r = 0; r < grid.y; ++r) M.row[r] = 0;
+        for (int i = 0; i < n; ++i) {
+            const SrcDesc& d = src[i];
+            const int x0 = std::max(d.x0, 0), x1 = std::min(d.x1, D.W);
+            const int y0 = std::max(d.y0, 0), y1 = std::min(d.y1, D.H);
+            if (x0 >= x1 || y0 >= y1) continue;
+            for (int c = x0 / tw; c < ceil_div(x1, tw); ++c) M.col[c] |= 1ull << i;
+            for (int r = y0 / th; r < ceil_div(y1, th); ++r) M.row[r] |= 1ull << i;
+        }
+        tiles_bpp<N, true>(L, bpp, D, M, grid, s);
+    } else {
+        tiles_bpp<N, false>(L, bpp, D, M, grid, s);
+    }
     return cudaGetLastError();
 }
 

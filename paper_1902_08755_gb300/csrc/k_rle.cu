@@ -423,10 +423,14 @@ __device__ bool code_sparse_fast(const Lists& W, int m, int len, uint32_t* T, ui
 // memory accesses overlap).  Runs of plane p: change point i starts one iff
 // its plane-p byte differs from change point i-1's (point 0 always does);
 // rl[p][0, n_p) lists those change points.  Then the runs are coded 32 at a
-// time: a run of three or more bytes becomes repeat tokens; the first short
-// run of a literal span walks to the span's end and codes the whole span.
-// Plane p's stream goes to stage + p * kStagePlane (as far as it fits); its
-// size to T[p].
+// time, a run per lane: a run of three or more bytes becomes repeat tokens; a
+// shorter one belongs to a literal span (a maximal sequence of short runs),
+// whose start a warp max-scan finds (four planes in the bytes of one word).
+// A short run at byte offset b of its span writes its bytes, the control
+// byte of a token that starts among them, and, if it holds a token's last
+// byte, that token's control byte (127 for a full token; the span's last run
+// knows the span's length).  Plane p's stream goes to stage + p * kStagePlane
+// (as far as it fits); its size to T[p].
 __device__ void code_sparse(const Lists& W, int m, int len, uint32_t* T, uint8_t* stage)
 {
     const int lane = threadIdx.x & 31;
@@ -452,86 +456,103 @@ __device__ void code_sparse(const Lists& W, int m, int len, uint32_t* T, uint8_t
     }
     __syncwarp();
     uint32_t carry[4] = {0u, 0u, 0u, 0u};
+    uint32_t sscarry = 0u;                            // byte p: 1 + the last span start of plane p so far
+    uint32_t prevshort = 0u;                          // bit p: the previous block's last run was short
     const int nmax = max(max(n[0], n[1]), max(n[2], n[3]));
     for (int r = 0; r < nmax; r += 32) {
         const int i = r + lane;
-        uint32_t cost[4], kind[4];
-        int L[4];
+        int s[4], L[4];
+        uint32_t shm = 0u, nshm = 0u, stv = 0u;
 #pragma unroll
         for (int p = 0; p < 4; ++p) {
             const uint8_t* R = W.rl[p];
             const int np = n[p];
-            auto start = [&](int k) { return (int)W.cq[R[k]]; };
-            cost[p] = 0u;
-            kind[p] = 0u;
+            s[p] = 0;
             L[p] = 0;
             if (i < np) {
-                const int s = start(i);
-                const int e = i + 1 < np ? start(i + 1) : len;
-                L[p] = e - s;
-                if (L[p] >= 3) {
-                    kind[p] = 1u;
-                    cost[p] = 2u * (uint32_t)((L[p] + 127) >> 7);
-                } else if (i == 0 || s - start(i - 1) >= 3) {
-                    int end = e;                          // first short run: find the span's end
-                    for (int j = i + 1; j < np; ++j) {
-                        const int en = j + 1 < np ? start(j + 1) : len;
-                        if (en - end >= 3) break;
-                        end = en;
-                    }
-                    L[p] = end - s;
-                    kind[p] = 2u;
-                    cost[p] = (uint32_t)(L[p] + ((L[p] + 127) >> 7));
+                s[p] = (int)W.cq[R[i]];
+                L[p] = (i + 1 < np ? (int)W.cq[R[i + 1]] : len) - s[p];
+                if (L[p] < 3) shm |= 1u << p;
+            }
+        }
+        uint32_t prevm = __shfl_up_sync(0xffffffffu, shm, 1);
+        if (lane == 0) prevm = prevshort;
+        nshm = __shfl_down_sync(0xffffffffu, shm, 1);
+        if (lane == 31) {                             // the next block's first runs
+            nshm = 0u;
+#pragma unroll
+            for (int p = 0; p < 4; ++p) {
+                const uint8_t* R = W.rl[p];
+                const int np = n[p];
+                if (i + 1 < np) {
+                    const int ln = (i + 2 < np ? (int)W.cq[R[i + 2]] : len) - (int)W.cq[R[i + 1]];
+                    if (ln < 3) nshm |= 1u << p;
                 }
             }
         }
+#pragma unroll
+        for (int p = 0; p < 4; ++p)
+            if (((shm & ~prevm) >> p) & 1u) stv |= (uint32_t)(i + 1) << (8 * p);
+        uint32_t ss = stv;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, ss, o);
+            if (lane >= o) ss = __vmaxu4(ss, y);
+        }
+        ss = __vmaxu4(ss, sscarry);
+        sscarry = __shfl_sync(0xffffffffu, ss, 31);
+        prevshort = __shfl_sync(0xffffffffu, shm, 31);
+        uint32_t cost[4], B[4];
+#pragma unroll
+        for (int p = 0; p < 4; ++p) {
+            cost[p] = 0u;
+            B[p] = 0u;
+            if (i >= n[p]) continue;
+            if (!((shm >> p) & 1u)) {
+                cost[p] = 2u * (uint32_t)((L[p] + 127) >> 7);
+            } else {
+                const int ssi = (int)((ss >> (8 * p)) & 0xFFu) - 1;
+                const uint32_t b = (uint32_t)(s[p] - (int)W.cq[W.rl[p][ssi]]);   // offset in the span
+                B[p] = b;
+                cost[p] = (uint32_t)L[p] + (((b + (uint32_t)L[p] + 127u) >> 7) - ((b + 127u) >> 7));
+            }
+        }
         // four scans at once: planes 0,1 and 2,3 in 16-bit halves
-        const uint32_t a = cost[0] | (cost[1] << 16), b = cost[2] | (cost[3] << 16);
-        uint32_t ia = a, ib = b;
+        const uint32_t a = cost[0] | (cost[1] << 16), bb = cost[2] | (cost[3] << 16);
+        uint32_t ia = a, ib = bb;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
             const uint32_t ya = __shfl_up_sync(0xffffffffu, ia, o), yb = __shfl_up_sync(0xffffffffu, ib, o);
             if (lane >= o) { ia += ya; ib += yb; }
         }
         const uint32_t ta = __shfl_sync(0xffffffffu, ia, 31), tb = __shfl_sync(0xffffffffu, ib, 31);
-        const uint32_t ea = ia - a, eb = ib - b;
+        const uint32_t ea = ia - a, eb = ib - bb;
         const uint32_t ex[4] = {ea & 0xFFFFu, ea >> 16, eb & 0xFFFFu, eb >> 16};
         const uint32_t tot[4] = {ta & 0xFFFFu, ta >> 16, tb & 0xFFFFu, tb >> 16};
 #pragma unroll
         for (int p = 0; p < 4; ++p) {
-            uint32_t o = carry[p] + ex[p];
+            const uint32_t o = carry[p] + ex[p];
             carry[p] += tot[p];
-            if (kind[p] == 0u) continue;
-            const uint8_t* R = W.rl[p];
-            const int np = n[p];
-            const int sh = 8 * p;
-            auto start = [&](int k) { return (int)W.cq[R[k]]; };
-            auto value = [&](int k) { return (uint8_t)(W.ce[R[k]] >> sh); };
+            if (i >= n[p] || o + cost[p] > (uint32_t)kStagePlane) continue;   // (never exceeds: kStagePlane)
             uint8_t* ob = stage + p * kStagePlane;
-            if (o + cost[p] > (uint32_t)kStagePlane) continue;   // not kept (see kStagePlane)
-            if (kind[p] == 1u) {
-                const uint8_t v = value(i);
+            const uint8_t v = (uint8_t)(W.ce[W.rl[p][i]] >> (8 * p));
+            if (!((shm >> p) & 1u)) {
+                uint32_t q = o;
                 for (int rr = L[p]; rr > 0; rr -= 128) {
-                    ob[o] = (uint8_t)(127 + min(rr, 128));
-                    ob[o + 1] = v;
-                    o += 2;
+                    ob[q] = (uint8_t)(127 + min(rr, 128));
+                    ob[q + 1] = v;
+                    q += 2;
                 }
             } else {
-                // the span's bytes: run j contributes (start of j+1 - start of j) copies of its byte
-                int j = i;
-                uint8_t v = value(j);
-                int rem = (j + 1 < np ? start(j + 1) : len) - start(j);
-                for (int d = 0; d < L[p]; d += 128) {
-                    const int ml = min(L[p] - d, 128);
-                    ob[o++] = (uint8_t)(ml - 1);
-                    for (int t = 0; t < ml; ++t) {
-                        ob[o++] = v;
-                        if (--rem == 0 && d + t + 1 < L[p]) {
-                            ++j;
-                            v = value(j);
-                            rem = (j + 1 < np ? start(j + 1) : len) - start(j);
-                        }
-                    }
+                const uint32_t b = B[p];
+                const uint32_t so = o - b - ((b + 127u) >> 7);   // the span's first control byte
+                for (uint32_t x = b; x < b + (uint32_t)L[p]; ++x) {
+                    ob[so + x + (x >> 7) + 1u] = v;
+                    if ((x & 127u) == 127u) ob[so + 129u * (x >> 7)] = 127u;
+                }
+                if (!((nshm >> p) & 1u)) {            // the span's last run: its last token
+                    const uint32_t last = b + (uint32_t)L[p] - 1u;
+                    ob[so + 129u * (last >> 7)] = (uint8_t)(last & 127u);
                 }
             }
         }
@@ -607,58 +628,62 @@ __device__ __forceinline__ uint4 load4(const RleJobDesc& jb, uint32_t q0, int le
     return v;
 }
 
-// Dense path: every position is classified with byte-SIMD bit masks, all four
-// planes at once.  The chunk is taken in 8 steps of 512 positions; in step k
-// lane l holds positions [P0, P0 + 16), P0 = 16 (32 k + l), in registers, and
-// the bytes just before and after them come from its neighbours (shuffles)
-// and the previous / next step.  A byte lies in a repeat iff one of the three
-// windows of 3 around it is constant; a warp max-scan of segment starts
-// (carried across steps) cuts tokens every 128 bytes of a segment, and a warp
-// sum-scan of output bytes (carried likewise) places them.  Without EMIT the
-// plane stream sizes are returned in T; with EMIT (T holding them) the streams
-// are written to out.
+// Dense path, a CTA of 8 warps per chunk: every position is classified with
+// byte-SIMD bit masks, all four planes at once.  Warp k takes positions
+// [512 k, 512 k + 512): lane l holds positions [P0, P0 + 16), P0 = 16 (32 k +
+// l), in registers, and the bytes just before and after them come from its
+// neighbours (shuffles; lane 0 and lane 31 load the neighbouring words).  A
+// byte lies in a repeat iff one of the three windows of 3 around it is
+// constant.  A max-scan of segment starts (warp scans, then the warps' totals
+// through shared memory) cuts tokens every 128 bytes of a segment, and a
+// sum-scan of output bytes (likewise) places them.  Without EMIT the plane
+// stream sizes are returned in T; with EMIT (T holding them) the streams are
+// written to out.  xw: 16 P4 of shared memory.
 template <bool EMIT>
-__device__ __noinline__ void dense_chunk(const RleJobDesc& jb, uint32_t q0, int len, bool sw, uint32_t* T, uint8_t* out)
+__device__ void dense_chunk(const RleJobDesc& jb, uint32_t q0, int len, bool sw, uint32_t* T, uint8_t* out, P4* xw)
 {
-    const int lane = threadIdx.x & 31;
-    P4 cmax = {0u, 0u}, csum = {0u, 0u};
-    uint32_t prevw[4] = {0u, 0u, 0u, 0u};
+    const int lane = threadIdx.x & 31, k = threadIdx.x >> 5;
+    const bool act = 512 * k < len;                          // (uniform in the warp)
     uint32_t pbase[4] = {0u, 0u, 0u, 0u};
     if (EMIT) {
         pbase[1] = T[0];
         pbase[2] = T[0] + T[1];
         pbase[3] = T[0] + T[1] + T[2];
     }
-#pragma unroll 1
-    for (int k = 0; k < kChunk / 512 && 512 * k < len; ++k) {
-        const int P0 = 16 * (32 * k + lane);
+    const int P0 = 16 * (32 * k + lane);
+    uint32_t REP[4] = {0u, 0u, 0u, 0u}, SEG[4] = {0u, 0u, 0u, 0u};
+    uint4 bytes[4];
+    uint32_t VALID = 0u;
+    P4 mine = {0u, 0u};
+    if (act) {
         uint4 t[4];
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
             const uint4 g = load4(jb, q0, len, P0 + 4 * i, sw);
             t[i] = transpose4(g.x, g.y, g.z, g.w);              // t[i] word b = plane b of 4 positions
         }
-        uint4 tn = make_uint4(0u, 0u, 0u, 0u);
+        uint4 tn = make_uint4(0u, 0u, 0u, 0u), tp = make_uint4(0u, 0u, 0u, 0u);
         if (lane == 31) {
             const uint4 g = load4(jb, q0, len, P0 + 16, sw);
             tn = transpose4(g.x, g.y, g.z, g.w);
+        }
+        if (lane == 0 && P0 > 0) {
+            const uint4 g = load4(jb, q0, len, P0 - 4, sw);
+            tp = transpose4(g.x, g.y, g.z, g.w);
         }
         const uint32_t VQ = bit_range(4 - P0, len - P0 + 4);          // 0 <= q < len
         const uint32_t VEQ = bit_range(5 - P0, len - P0 + 4);         // 1 <= q < len
         const uint32_t HIGH = bit_range(len - P0 + 4, 24);            // q >= len
         const uint32_t Q0 = P0 == 0 ? (1u << 4) : 0u;                 // q == 0
-        const uint32_t VALID = (VQ >> 4) & 0xFFFFu;
-        uint32_t REP[4], SEG[4];
-        uint4 bytes[4];
+        VALID = (VQ >> 4) & 0xFFFFu;
 #pragma unroll
         for (int b = 0; b < 4; ++b) {
             auto pw = [&](const uint4& x) { return b == 0 ? x.x : b == 1 ? x.y : b == 2 ? x.z : x.w; };
             const uint4 v = make_uint4(pw(t[0]), pw(t[1]), pw(t[2]), pw(t[3]));
             uint32_t wm = __shfl_up_sync(0xffffffffu, v.w, 1);
-            if (lane == 0) wm = prevw[b];
+            if (lane == 0) wm = pw(tp);
             uint32_t wp = __shfl_down_sync(0xffffffffu, v.x, 1);
             if (lane == 31) wp = pw(tn);
-            prevw[b] = __shfl_sync(0xffffffffu, v.w, 31);
             bytes[b] = v;
             // eq bit i: byte at position P0-4+i equals its predecessor
             uint32_t EQ = eq_bytes(wm, wm << 8);
@@ -674,83 +699,92 @@ __device__ __noinline__ void dense_chunk(const RleJobDesc& jb, uint32_t q0, int 
             REP[b] = (R >> 4) & 0xFFFFu;
             SEG[b] = (Sg >> 4) & 0x1FFFFu;                            // bit 16: position P0+16
         }
-        // last segment start before each position range (max-scan of position + 1)
-        P4 mine;
-        {
-            uint32_t l[4];
-#pragma unroll
-            for (int b = 0; b < 4; ++b) {
-                const uint32_t m = SEG[b] & 0xFFFFu;
-                l[b] = m ? (uint32_t)(P0 + 31 - __clz(m) + 1) : 0u;
-            }
-            mine.a = l[0] | (l[1] << 16);
-            mine.b = l[2] | (l[3] << 16);
-        }
-        P4 tmax;
-        const P4 before = combine<true>(cmax, warp_scan4<true>(mine, lane, &tmax));
-        cmax = combine<true>(cmax, tmax);
-        // piece starts (tokens hold <= 128 bytes) and output sizes
-        uint32_t PSV[4], PE[4], LIT[4], cost[4];
-        int sbin[4];
+        // last segment start in each lane's range (position + 1)
+        uint32_t l[4];
 #pragma unroll
         for (int b = 0; b < 4; ++b) {
-            const uint32_t seg16 = SEG[b] & 0xFFFFu;
-            const int sb_in = (int)lane16(before, b) - 1;            // -1 only for position 0
-            sbin[b] = sb_in;
-            uint32_t PS = seg16;
-            const int first = seg16 ? __ffs(seg16) - 1 : 16;
-            if (sb_in >= 0) {                                        // continuing segment
-                const int r = (P0 - sb_in) & 127;
-                const int d = r ? 128 - r : 0;
-                if (d < first) PS |= 1u << d;
-            }
-            const int sb15 = seg16 ? P0 + 31 - __clz(seg16) : sb_in;
-            const uint32_t next = ((SEG[b] >> 16) & 1u) | (((P0 + 16 - sb15) & 127) == 0 ? 1u : 0u);
-            PSV[b] = PS & VALID;
-            PE[b] = ((PS | (next << 16)) >> 1) & VALID;
-            LIT[b] = ~REP[b] & VALID;
-            cost[b] = __popc(LIT[b]) + __popc(PSV[b]) + __popc(PSV[b] & REP[b]);
+            const uint32_t m = SEG[b] & 0xFFFFu;
+            l[b] = m ? (uint32_t)(P0 + 31 - __clz(m) + 1) : 0u;
         }
-        P4 tsum;
-        const P4 off0 = combine<false>(csum, warp_scan4<false>(P4{cost[0] | (cost[1] << 16), cost[2] | (cost[3] << 16)},
-                                                               lane, &tsum));
-        csum = combine<false>(csum, tsum);
+        mine.a = l[0] | (l[1] << 16);
+        mine.b = l[2] | (l[3] << 16);
+    }
+    // max-scan over the chunk: in the warp, then over the warps before
+    P4 tmax = {0u, 0u}, smax = {0u, 0u};
+    if (act) smax = warp_scan4<true>(mine, lane, &tmax);
+    if (lane == 0) xw[k] = tmax;
+    __syncthreads();
+    P4 before = smax;
+    for (int j = 0; j < k; ++j) before = combine<true>(before, xw[j]);
+    // piece starts (tokens hold <= 128 bytes) and output sizes
+    uint32_t PSV[4], PE[4], LIT[4], cost[4];
+    int sbin[4];
 #pragma unroll
-        for (int b = 0; b < (EMIT ? 4 : 0); ++b) {
-            uint8_t* o = out + pbase[b];
-            const uint32_t off = lane16(off0, b);
-            const uint32_t lit = LIT[b], psv = PSV[b], psr = PSV[b] & REP[b], seg16 = SEG[b] & 0xFFFFu;
-            const uint4 v = bytes[b];
-            auto byte_at = [&](int i) -> uint8_t {
-                const uint32_t wd = i < 8 ? (i < 4 ? v.x : v.y) : (i < 12 ? v.z : v.w);
-                return (uint8_t)(wd >> (8 * (i & 3)));
-            };
-            auto inc_at = [&](int i) -> uint32_t {
-                const uint32_t le = (2u << i) - 1u;
-                return off + __popc(lit & le) + __popc(psv & le) + __popc(psr & le);
-            };
-            for (uint32_t m = lit; m; m &= m - 1u) {
-                const int i = __ffs(m) - 1;
-                o[inc_at(i) - 1] = byte_at(i);
-            }
-            for (uint32_t m = PE[b]; m; m &= m - 1u) {
-                const int i = __ffs(m) - 1;
-                const uint32_t inc = inc_at(i);
-                const uint32_t h = seg16 & ((2u << i) - 1u);
-                const int sbk = h ? P0 + 31 - __clz(h) : sbin[b];
-                const uint32_t jj = (uint32_t)(P0 + i - sbk) & 127u;
-                if ((REP[b] >> i) & 1u) {
-                    o[inc - 2] = (uint8_t)(0x80u + jj);
-                    o[inc - 1] = byte_at(i);
-                } else {
-                    o[inc - 2 - jj] = (uint8_t)jj;
-                }
+    for (int b = 0; b < 4; ++b) {
+        const uint32_t seg16 = SEG[b] & 0xFFFFu;
+        const int sb_in = (int)lane16(before, b) - 1;            // -1 only for position 0
+        sbin[b] = sb_in;
+        uint32_t PS = seg16;
+        const int first = seg16 ? __ffs(seg16) - 1 : 16;
+        if (sb_in >= 0) {                                        // continuing segment
+            const int r = (P0 - sb_in) & 127;
+            const int d = r ? 128 - r : 0;
+            if (d < first) PS |= 1u << d;
+        }
+        const int sb15 = seg16 ? P0 + 31 - __clz(seg16) : sb_in;
+        const uint32_t next = ((SEG[b] >> 16) & 1u) | (((P0 + 16 - sb15) & 127) == 0 ? 1u : 0u);
+        PSV[b] = PS & VALID;
+        PE[b] = ((PS | (next << 16)) >> 1) & VALID;
+        LIT[b] = ~REP[b] & VALID;
+        cost[b] = __popc(LIT[b]) + __popc(PSV[b]) + __popc(PSV[b] & REP[b]);
+    }
+    P4 tsum = {0u, 0u}, ssum = {0u, 0u};
+    if (act) ssum = warp_scan4<false>(P4{cost[0] | (cost[1] << 16), cost[2] | (cost[3] << 16)}, lane, &tsum);
+    if (lane == 0) xw[8 + k] = tsum;
+    __syncthreads();
+    P4 off0 = ssum, total = {0u, 0u};
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        const P4 x = xw[8 + j];
+        if (j < k) off0 = combine<false>(off0, x);
+        total = combine<false>(total, x);
+    }
+    __syncthreads();                                         // xw is reused by the next chunk
+#pragma unroll
+    for (int b = 0; b < ((EMIT && act) ? 4 : 0); ++b) {
+        uint8_t* o = out + pbase[b];
+        const uint32_t off = lane16(off0, b);
+        const uint32_t lit = LIT[b], psv = PSV[b], psr = PSV[b] & REP[b], seg16 = SEG[b] & 0xFFFFu;
+        const uint4 v = bytes[b];
+        auto byte_at = [&](int i) -> uint8_t {
+            const uint32_t wd = i < 8 ? (i < 4 ? v.x : v.y) : (i < 12 ? v.z : v.w);
+            return (uint8_t)(wd >> (8 * (i & 3)));
+        };
+        auto inc_at = [&](int i) -> uint32_t {
+            const uint32_t le = (2u << i) - 1u;
+            return off + __popc(lit & le) + __popc(psv & le) + __popc(psr & le);
+        };
+        for (uint32_t m = lit; m; m &= m - 1u) {
+            const int i = __ffs(m) - 1;
+            o[inc_at(i) - 1] = byte_at(i);
+        }
+        for (uint32_t m = PE[b]; m; m &= m - 1u) {
+            const int i = __ffs(m) - 1;
+            const uint32_t inc = inc_at(i);
+            const uint32_t h = seg16 & ((2u << i) - 1u);
+            const int sbk = h ? P0 + 31 - __clz(h) : sbin[b];
+            const uint32_t jj = (uint32_t)(P0 + i - sbk) & 127u;
+            if ((REP[b] >> i) & 1u) {
+                o[inc - 2] = (uint8_t)(0x80u + jj);
+                o[inc - 1] = byte_at(i);
+            } else {
+                o[inc - 2 - jj] = (uint8_t)jj;
             }
         }
     }
     if (!EMIT)
 #pragma unroll
-        for (int b = 0; b < 4; ++b) T[b] = lane16(csum, b);
+        for (int b = 0; b < 4; ++b) T[b] = lane16(total, b);
 }
 
 // ---- basic RLE (mode 0) on the same pipeline --------------------------------
@@ -1206,17 +1240,17 @@ k_rle_place(const __grid_constant__ RleJobList<N> J, const ChunkRec* rec, const 
 }
 
 // Recoding kernels: the listed chunks (dense, or sparse ones that found the
-// pool full) are coded from the image, a warp per listed chunk over a
-// persistent grid.  Before the scan (EMIT false) the dense ones are sized,
+// pool full) are coded from the image, a CTA of 8 warps per listed chunk over
+// a persistent grid.  Before the scan (EMIT false) the dense ones are sized,
 // their sizes written to their records; after it (EMIT true) every listed
 // chunk is written straight to its place with its four end-table entries.
 template <int N, bool EMIT>
-__global__ void __launch_bounds__(128)
+__global__ void __launch_bounds__(256)
 k_rle_recode(const __grid_constant__ RleJobList<N> J, ChunkRec* rec, const uint32_t* recode, const uint32_t* count)
 {
-    const int lane = threadIdx.x & 31;
+    __shared__ P4 xw[16];
     const uint32_t n = *count;
-    for (uint32_t i = blockIdx.x * 4u + (threadIdx.x >> 5); i < n; i += gridDim.x * 4u) {
+    for (uint32_t i = blockIdx.x; i < n; i += gridDim.x) {
         const uint32_t unit = recode[i];
         const RleJobDesc& jb = J.j[find_job(J, unit)];
         const uint32_t nc = jb.n_chunks, c = unit - jb.first_unit;
@@ -1228,15 +1262,16 @@ k_rle_recode(const __grid_constant__ RleJobList<N> J, ChunkRec* rec, const uint3
         const int len = (int)min((uint32_t)kChunk, (uint32_t)jb.w * (uint32_t)jb.h - q0);
         if (!EMIT) {
             if (total != 0u) continue;                    // sized already (a sparse chunk)
-            dense_chunk<false>(jb, q0, len, jb.mode == 2, T, nullptr);
-            if (lane == 0)
+            dense_chunk<false>(jb, q0, len, jb.mode == 2, T, nullptr, xw);
+            if (threadIdx.x == 0)
 #pragma unroll
                 for (int p = 0; p < 4; ++p) rec[unit].T[p] = (uint16_t)T[p];
             continue;
         }
-        dense_chunk<true>(jb, q0, len, jb.mode == 2, T, dst + 32 + 16ull * nc + r.off);
-        const uint32_t mine = lane == 0 ? T[0] : lane == 1 ? T[0] + T[1] : lane == 2 ? T[0] + T[1] + T[2] : total;
-        if (lane < 4) put_u32(dst + 32 + 16ull * c + 4u * lane, r.off + mine);
+        dense_chunk<true>(jb, q0, len, jb.mode == 2, T, dst + 32 + 16ull * nc + r.off, xw);
+        const uint32_t t = threadIdx.x;
+        const uint32_t mine = t == 0 ? T[0] : t == 1 ? T[0] + T[1] : t == 2 ? T[0] + T[1] + T[2] : total;
+        if (t < 4) put_u32(dst + 32 + 16ull * c + 4u * t, r.off + mine);
     }
 }
 
@@ -1643,14 +1678,14 @@ cudaError_t compress_n(const RleJobDesc* jobs, int n, uint32_t total_units, void
     k_rle_compress<N, M0><<<grid, 32 * kWPB, kCompressSmem, s>>>(J, rec, recode, pool, pool_bytes, ticket, status);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if (M0) k_rle0_recode<N, false><<<rgrid, kT, 0, s>>>(J, rec, recode, ticket + 1);
-    else k_rle_recode<N, false><<<rgrid, 128, 0, s>>>(J, rec, recode, ticket + 1);
+    else k_rle_recode<N, false><<<rgrid, 256, 0, s>>>(J, rec, recode, ticket + 1);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     k_rle_scan<N><<<n, 1024, 0, s>>>(J, rec);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     k_rle_place<N><<<(total_units + 3) / 4, 128, 0, s>>>(J, rec, pool);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if (M0) k_rle0_recode<N, true><<<rgrid, kT, 0, s>>>(J, rec, recode, ticket + 1);
-    else k_rle_recode<N, true><<<rgrid, 128, 0, s>>>(J, rec, recode, ticket + 1);
+    else k_rle_recode<N, true><<<rgrid, 256, 0, s>>>(J, rec, recode, ticket + 1);
     return cudaGetLastError();
 }
 

@@ -116,6 +116,32 @@ __device__ __forceinline__ void encode_block(const uint32_t (&px)[4], const bool
              ((uint32_t)((sa + half) >> sh) << 16);
 }
 
+// Whole 2x2 blocks (the interior of an image): the same sums with no
+// per-pixel presence tests.  Y is byte 1 of its dot product (which is below
+// 2^16), so four of them pack into the luma word with three byte permutes;
+// the alpha sum is one more byte dot product per pixel.
+__device__ __forceinline__ uint32_t u_of(uint32_t p)
+{
+    return min(255u, (((p >> 9) & 0x7F80u) - __dp4a(p, 0x0000552Bu, 0u) + 32896u) >> 8);
+}
+
+__device__ __forceinline__ uint32_t v_of(uint32_t p)
+{
+    return min(255u, (((p << 7) & 0x7F80u) - __dp4a(p, 0x00156B00u, 0u) + 32896u) >> 8);
+}
+
+__device__ __forceinline__ void encode_full(uint32_t a, uint32_t b, uint32_t c, uint32_t d, uint32_t& luma,
+                                            uint32_t& chroma)
+{
+    const uint32_t ab = __byte_perm(__dp4a(a, 0x001D964Du, 128u), __dp4a(b, 0x001D964Du, 128u), 0x0051);
+    const uint32_t cd = __byte_perm(__dp4a(c, 0x001D964Du, 128u), __dp4a(d, 0x001D964Du, 128u), 0x0051);
+    luma = __byte_perm(ab, cd, 0x5410);
+    const uint32_t su = u_of(a) + u_of(b) + u_of(c) + u_of(d);
+    const uint32_t sv = v_of(a) + v_of(b) + v_of(c) + v_of(d);
+    const uint32_t sa = __dp4a(a, 0x01000000u, __dp4a(b, 0x01000000u, __dp4a(c, 0x01000000u, __dp4a(d, 0x01000000u, 0u))));
+    chroma = ((su + 2u) >> 2) | (((sv + 2u) >> 2) << 8) | (((sa + 2u) >> 2) << 16);
+}
+
 template <int N>
 __global__ void __launch_bounds__(kYX * kYY)
 k_yuv_encode(const __grid_constant__ YuvJobList<N> J)
@@ -128,6 +154,17 @@ k_yuv_encode(const __grid_constant__ YuvJobList<N> J)
     const int w = jb.w, h = jb.h, pitch = jb.pitch, dpitch = jb.dpitch, vec = jb.vec;
     const int bw = (w + 1) >> 1, bh = (h + 1) >> 1;
     if (by >= bh) return;
+    if (kNP == 1 && (vec & kVec16) && (vec & kPacked8) && 4 * bp + 3 < w && 2 * by + 1 < h) {
+        // a pair of whole blocks: two 16-byte loads, two 8-byte stores
+        const uint4 r0 = __ldcs(reinterpret_cast<const uint4*>(src + (size_t)(2 * by) * pitch + 4 * bp));
+        const uint4 r1 = __ldcs(reinterpret_cast<const uint4*>(src + (size_t)(2 * by + 1) * pitch + 4 * bp));
+        uint32_t l0, c0, l1, c1;
+        encode_full(r0.x, r0.y, r1.x, r1.y, l0, c0);
+        encode_full(r0.z, r0.w, r1.z, r1.w, l1, c1);
+        *reinterpret_cast<uint2*>(dst + (size_t)by * dpitch + 2 * bp) = make_uint2(l0, l1);
+        *reinterpret_cast<uint2*>(dst + (size_t)(bh + by) * dpitch + 2 * bp) = make_uint2(c0, c1);
+        return;
+    }
     uint32_t p0[kNP][4], p1[kNP][4];
     bool h0[kNP][4], h1[kNP][4];
 #pragma unroll

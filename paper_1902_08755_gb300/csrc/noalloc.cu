@@ -83,7 +83,8 @@ extern "C" ec_status ec_rle_compress_noalloc(const void* src, int32_t w, int32_t
     d.mode = mode;
     d.n_chunks = (uint32_t)nchunks;
     d.first_unit = 0;
-    d.vec = (reinterpret_cast<uintptr_t>(src) & 15u) == 0 && w % 4 == 0 && pitch % 4 == 0;
+    d.vec = (reinterpret_cast<uintptr_t>(src) & 15u) == 0 &&
+            ((w % 4 == 0 && pitch % 4 == 0) || (pitch == w && ((uint64_t)w * (uint64_t)h) % 4 == 0));
     const uint32_t units = nchunks > 0 ? (uint32_t)nchunks : 1u;
     // the launcher clears the counters this call uses (a memset, no
     // allocation) before the kernels run

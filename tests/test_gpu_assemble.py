@@ -72,6 +72,30 @@ def test_tiles_match_oracle(kind, seed):
     assert np.array_equal(_bits(out), np.ascontiguousarray(want).view(np.uint8))
 
 
+@pytest.mark.parametrize("case", ["many_sources", "wide_frame"])
+def test_tiles_without_tile_masks(case):
+    """More than 64 sources, or a frame wider than 128 CTA tiles: the CTAs list
+    their sources themselves instead of reading the host's tile masks."""
+    require_gpu()
+    r = np.random.default_rng(1300 + len(case))
+    W, H = (300, 120) if case == "many_sources" else (16500, 9)
+    n = 80 if case == "many_sources" else 6
+    base = _host(r, "rgba8", H, W)
+    imgs_o, imgs_g = [], []
+    for i in range(n):
+        w, h = int(r.integers(1, min(W, 4000))), int(r.integers(1, H + 5))
+        pvp = (int(r.integers(-10, W)), int(r.integers(-5, H)), w, h)
+        roi = (pvp[0], pvp[1], w, h)
+        a = _host(r, "rgba8", h, w)
+        imgs_o.append(oracle.Image(pvp, roi, a))
+        imgs_g.append(ec.Image(color=_dev(a), pvp=pvp, roi=roi))
+    out = _dev(base)
+    ec.assemble_tiles(imgs_g, out, out_pvp=(0, 0, W, H))
+    ec.default_context().check_status()
+    want = oracle.assemble_tiles(imgs_o, base, (0, 0, W, H))
+    assert np.array_equal(_bits(out), np.ascontiguousarray(want).view(np.uint8))
+
+
 @pytest.mark.parametrize("kind", list(KINDS))
 @pytest.mark.parametrize("kernel", [(2, 2), (3, 1), (4, 3), (16, 16)])
 def test_pixels_match_oracle(kind, kernel):

@@ -50,7 +50,9 @@ def test_adversarial_patterns_bit_exact(name, mode):
 
 
 @pytest.mark.parametrize("shape", [(1, 1), (1, 4095), (1, 4096), (1, 4097), (2, 3), (65, 127),
-                                   (3, 5000), (40, 4096), (1080, 1920)])
+                                   (3, 5000), (40, 4096), (1080, 1920),
+                                   # contiguous rows that are not 16-byte groups, 4k elements in all
+                                   (12, 999), (4, 4099), (1050, 498)])
 @pytest.mark.parametrize("mode", [1, 2])
 def test_shapes_and_pitches(shape, mode):
     require_gpu()
