@@ -73,7 +73,7 @@ struct TileMasks {
 // them (build_active).  Every pixel walks them from last to first and stops
 // once its 16-byte group is complete.
 template <int N, int BPP, bool MASK>
-__global__ void __launch_bounds__(kAT)
+__global__ void __launch_bounds__(kAT, 8)
 k_assemble_tiles(const __grid_constant__ SrcList<N> L, const __grid_constant__ DstDesc D,
                  const __grid_constant__ TileMasks M)
 {
@@ -93,9 +93,46 @@ k_assemble_tiles(const __grid_constant__ SrcList<N> L, const __grid_constant__ D
     const int x = tx0 + lane * PX;
     if (x >= D.W) return;
     const uint32_t full = x + PX <= D.W ? (1u << PX) - 1u : (1u << (D.W - x)) - 1u;
+    uint32_t fast = 0;                                   // passes already written
+    if (MASK && PX * BPP == 16 && D.vec && full == (1u << PX) - 1u) {
+        // groups that one source covers whole (the usual case): every such
+        // pass's 16-byte load is issued before any store
+        const uint4* fp[kAPasses];
+#pragma unroll
+        for (int pass = 0; pass < kAPasses; ++pass) {
+            fp[pass] = nullptr;
+            const int y = ty0 + pass * kARows + row;
+            if (y >= D.H) continue;
+            for (uint64_t mm = amask; mm;) {
+                const int i = 63 - __clzll((long long)mm);
+                mm ^= 1ull << i;
+                const SrcDesc& s = L.s[i];
+                const uint32_t m = covered<PX>(s, x, y, D.W);
+                if (!m) continue;
+                if (m == full && s.vec) {
+                    const size_t e = (size_t)(y - s.oy) * (size_t)s.pitch + (size_t)(x - s.ox);
+                    fp[pass] = reinterpret_cast<const uint4*>(reinterpret_cast<const uint8_t*>(s.color) + e * BPP);
+                    fast |= 1u << pass;
+                }
+                break;
+            }
+        }
+        uint4 v[kAPasses];
+#pragma unroll
+        for (int pass = 0; pass < kAPasses; ++pass)
+            if ((fast >> pass) & 1u) v[pass] = __ldcs(fp[pass]);
+#pragma unroll
+        for (int pass = 0; pass < kAPasses; ++pass) {
+            if (!((fast >> pass) & 1u)) continue;
+            const int y = ty0 + pass * kARows + row;
+            __stcs(reinterpret_cast<uint4*>(reinterpret_cast<uint8_t*>(D.color) + ((size_t)y * (size_t)D.pitch + (size_t)x) * BPP),
+                   v[pass]);
+        }
+    }
     for (int pass = 0; pass < kAPasses; ++pass) {
     const int y = ty0 + pass * kARows + row;
     if (y >= D.H) break;
+    if ((fast >> pass) & 1u) continue;
     uint32_t w[PX][WPP];
     uint32_t have = 0;
     // the last source covering a pixel wins: walk back until every pixel is set

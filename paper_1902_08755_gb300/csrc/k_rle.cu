@@ -1068,7 +1068,7 @@ __device__ uint32_t code0_block(const RleJobDesc& jb, uint32_t q0, int len, uint
 // dense one; such chunks are listed for the recoding kernel).  No warp waits
 // for another.  M0: basic RLE (mode 0), from unit change points.
 template <int N, bool M0>
-__global__ void __launch_bounds__(32 * kWPB, 11)
+__global__ void __launch_bounds__(32 * kWPB, 16)
 k_rle_compress(const __grid_constant__ RleJobList<N> J, ChunkRec* rec, uint32_t* recode, uint8_t* pool,
                uint32_t pool_bytes, uint32_t* ticket, uint32_t* status)
 {
