@@ -16,7 +16,8 @@ namespace {
 
 constexpr int kAT = 256;
 constexpr int kARows = kAT / 32;          // rows a CTA covers at once
-constexpr int kAPasses = 4;                 // row passes per CTA (tile and average kernels)
+constexpr int kAPasses = 4;                 // row passes per CTA (average and pixel kernels)
+constexpr int kTPasses = 4;                 // row passes per CTA (tile kernel)
 
 template <int BPP> struct Grp;                 // one 16-byte group of pixels
 template <> struct Grp<4> { static constexpr int PX = 4; };
@@ -81,13 +82,13 @@ k_assemble_tiles(const __grid_constant__ SrcList<N> L, const __grid_constant__ D
     __shared__ int16_t act[MASK ? 1 : (N > 0 ? N : 1)];
     __shared__ int nact_s;
     const int lane = threadIdx.x & 31, row = threadIdx.x >> 5;
-    const int tx0 = blockIdx.x * TW, ty0 = blockIdx.y * (kARows * kAPasses);
+    const int tx0 = blockIdx.x * TW, ty0 = blockIdx.y * (kARows * kTPasses);
     uint64_t amask = 0;
     if (MASK) {
         amask = M.col[blockIdx.x] & M.row[blockIdx.y];
     } else {
         auto at = [&](int, int i) -> const SrcDesc& { return L.s[i]; };
-        build_active(at, L.n, tx0, ty0, min(tx0 + TW, D.W), min(ty0 + kARows * kAPasses, D.H), act, &nact_s);
+        build_active(at, L.n, tx0, ty0, min(tx0 + TW, D.W), min(ty0 + kARows * kTPasses, D.H), act, &nact_s);
         __syncthreads();
     }
     const int x = tx0 + lane * PX;
@@ -97,9 +98,9 @@ k_assemble_tiles(const __grid_constant__ SrcList<N> L, const __grid_constant__ D
     if (MASK && PX * BPP == 16 && D.vec && full == (1u << PX) - 1u) {
         // groups that one source covers whole (the usual case): every such
         // pass's 16-byte load is issued before any store
-        const uint4* fp[kAPasses];
+        const uint4* fp[kTPasses];
 #pragma unroll
-        for (int pass = 0; pass < kAPasses; ++pass) {
+        for (int pass = 0; pass < kTPasses; ++pass) {
             fp[pass] = nullptr;
             const int y = ty0 + pass * kARows + row;
             if (y >= D.H) continue;
@@ -117,19 +118,19 @@ k_assemble_tiles(const __grid_constant__ SrcList<N> L, const __grid_constant__ D
                 break;
             }
         }
-        uint4 v[kAPasses];
+        uint4 v[kTPasses];
 #pragma unroll
-        for (int pass = 0; pass < kAPasses; ++pass)
+        for (int pass = 0; pass < kTPasses; ++pass)
             if ((fast >> pass) & 1u) v[pass] = __ldcs(fp[pass]);
 #pragma unroll
-        for (int pass = 0; pass < kAPasses; ++pass) {
+        for (int pass = 0; pass < kTPasses; ++pass) {
             if (!((fast >> pass) & 1u)) continue;
             const int y = ty0 + pass * kARows + row;
             __stcs(reinterpret_cast<uint4*>(reinterpret_cast<uint8_t*>(D.color) + ((size_t)y * (size_t)D.pitch + (size_t)x) * BPP),
                    v[pass]);
         }
     }
-    for (int pass = 0; pass < kAPasses; ++pass) {
+    for (int pass = 0; pass < kTPasses; ++pass) {
     const int y = ty0 + pass * kARows + row;
     if (y >= D.H) break;
     if ((fast >> pass) & 1u) continue;
@@ -413,7 +414,7 @@ template <int N>
 cudaError_t tiles_n(const SrcDesc* src, int n, int bpp, const DstDesc& D, cudaStream_t s)
 {
     const SrcList<N> L = make_src_list<N>(src, n);
-    const int tw = 32 * (16 / bpp), th = kARows * kAPasses;
+    const int tw = 32 * (16 / bpp), th = kARows * kTPasses;
     const dim3 grid(ceil_div(D.W, tw), ceil_div(D.H, th));
     static thread_local TileMasks M;
     if (N <= 64 && grid.x <= (unsigned)kMaskCols && grid.y <= (unsigned)kMaskRows) {
