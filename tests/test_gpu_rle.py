@@ -176,9 +176,9 @@ def test_8k_frame_and_size_limit():
 
 
 def test_bounded_wait_times_out_and_context_survives():
-    """Failure detection without a fault: the codec's look-back waits on a chunk
-    that never publishes, gives up after its poll limit and records
-    EC_ERR_TIMEOUT; the kernel ends and the context keeps working."""
+    """Failure detection without a fault: the compressor's bounded mbarrier wait
+    runs on a barrier that nothing arrives on, gives up after its try limit and
+    records EC_ERR_TIMEOUT; the kernel ends and the context keeps working."""
     import time
     from paper_1902_08755_gb300 import _abi as A
     require_gpu()
