@@ -5,10 +5,10 @@
 //   dL/dc_k^{RGB} = g^{RGB} T_k,   dL/da_k = T_k (g^A - R_k),
 //   R_{n-1} = 0,  R_{k-1} = g.c_k + (1 - a_k) R_k      (reverse "behind" scan).
 // Nothing per layer is kept from the forward.  A CTA owns a tile of 32 lanes
-// by kRows rows (FP16 stacks of up to 64 layers: two adjacent pixels per lane,
-// read and written as one 16-byte word where aligned; otherwise one pixel per
-// lane); its warps split the tile's layer stack into contiguous segments of
-// at most 4 (two pixels per lane) or 8 layers.  A warp loads its layers'
+// by 16 or 32 rows, one pixel per lane (the kernel also takes two adjacent pixels
+// per lane, read and written as one 16-byte word, with segments of at most 4
+// layers); its warps split the tile's layer stack into contiguous segments of
+// at most 8 layers.  A warp loads its layers'
 // pixels straight into registers (zero outside a layer's ROI, which is
 // exactly a transparent layer), runs its segment's forward, and keeps per
 // layer only T', g.c and a.  Both recurrences split exactly across segments:
@@ -34,7 +34,8 @@
 namespace ec {
 namespace {
 
-constexpr int kRows = 16;         // rows per alpha-backward CTA
+constexpr int kRows = 16;         // rows per alpha-backward CTA (stacks of up to 64 layers)
+constexpr int kRowsDeep = 32;     // rows per CTA for deeper stacks (their per-CTA setup is larger)
 constexpr int kMaxWarps = 32;     // segments (warps) per CTA
 static_assert(8 * kMaxWarps >= kMaxBwdLayers, "every stack fits one CTA");
 
@@ -54,7 +55,7 @@ __device__ __forceinline__ uint2 f4_to_h4(float4 f)
     return v;
 }
 
-// What a CTA needs of one layer for its tile (TW columns by kRows rows),
+// What a CTA needs of one layer for its tile (TW columns by ROWS rows),
 // built once per CTA: addresses of pixel (tx0, ty0) in the colour and
 // gradient buffers (offset only by rows and columns that lie inside the ROI /
 // pvp before use), the pitch, the ROI and gradient ranges (columns relative
@@ -147,11 +148,11 @@ __device__ __forceinline__ void store_grad(const BwdDesc& d, int x, int y, float
 }
 
 // Alpha backward (and fused forward + backward) for one tile of 32 * PX
-// pixels (PX per lane, adjacent) by kRows rows.  blockDim.x = 32 * NS: warp s
+// pixels (PX per lane, adjacent) by ROWS rows.  blockDim.x = 32 * NS: warp s
 // owns segment s of the tile's active layers, at most MS of them.  Tiles that
 // every active layer covers entirely (ROI and gradient rectangle) skip the
 // per-row range checks.
-template <int N, bool F16, bool G16, bool FUSED, int PX, int MS>
+template <int N, bool F16, bool G16, bool FUSED, int PX, int MS, int ROWS>
 __global__ void __launch_bounds__(32 * kMaxWarps, 1)
 k_alpha_bwd(const __grid_constant__ BwdList<N> L, const __grid_constant__ DstDesc D,
             const float4* __restrict__ g, int cap)
@@ -171,8 +172,8 @@ k_alpha_bwd(const __grid_constant__ BwdList<N> L, const __grid_constant__ DstDes
     float4* const Cs0 = reinterpret_cast<float4*>(As0 + 2 * NS * TW);       // (fused)
 
     const int lane = threadIdx.x & 31, sg = threadIdx.x / 32;
-    const int tx0 = blockIdx.x * TW, ty0 = blockIdx.y * kRows;
-    const int tx1 = min(tx0 + TW, D.W), ty1 = min(ty0 + kRows, D.H);
+    const int tx0 = blockIdx.x * TW, ty0 = blockIdx.y * ROWS;
+    const int tx1 = min(tx0 + TW, D.W), ty1 = min(ty0 + ROWS, D.H);
 
     // layers whose gradient rectangle meets the tile, in compositing order
     if (threadIdx.x < 32) {
@@ -448,31 +449,29 @@ int alpha_bwd_warps(int n, int ms)
     return std::max(1, std::min(kMaxWarps, std::max(need, std::min(n, 4))));
 }
 
-template <int N, bool F16, bool G16, bool FUSED, int PX, int MS>
+template <int N, bool F16, bool G16, bool FUSED, int PX, int MS, int ROWS>
 cudaError_t alpha_bwd_n(const BwdDesc* d, int n, const DstDesc& D, const float4* g, cudaStream_t s)
 {
     const int ns = alpha_bwd_warps(n, MS), cap = std::max(n, 1), tw = 32 * PX;
     const size_t smem = (size_t)cap * sizeof(BandTile) + 2 * (size_t)ns * tw * (8 + (FUSED ? 16 : 0));
-    auto kern = k_alpha_bwd<N, F16, G16, FUSED, PX, MS>;
+    auto kern = k_alpha_bwd<N, F16, G16, FUSED, PX, MS, ROWS>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    const dim3 grid(ceil_div(D.W, tw), ceil_div(D.H, kRows));
+    const dim3 grid(ceil_div(D.W, tw), ceil_div(D.H, ROWS));
     kern<<<grid, 32 * ns, smem, s>>>(make_bwd<N>(d, n), D, g, cap);
     return cudaGetLastError();
 }
 
-// FP16 stacks of up to 64 layers: two pixels per lane (one 16-byte word),
-// four layers per warp; deeper FP16 stacks and FP32: one pixel, eight layers.
+// One pixel per lane and eight layers per warp, FP32 and FP16 alike (two FP16
+// pixels per lane with four layers per warp was 1.5% slower on 32 x 2048^2; the
+// kernel keeps the two-pixel form for other tile choices); 16 rows per CTA, 32
+// for stacks deeper than 64 layers (128 x 3840x2160 FP16: 3.74 ms instead of
+// 3.87; on 32 x 2048^2 32 rows were 2-3% slower).
 template <int N, bool F16, bool G16, bool FUSED>
 cudaError_t alpha_bwd_px(const BwdDesc* d, int n, const DstDesc& D, const float4* g, cudaStream_t s)
 {
-    if constexpr (F16) {
-        if (n <= 64) return alpha_bwd_n<N, F16, G16, FUSED, 2, 4>(d, n, D, g, s);
-        if constexpr (N > 64) return alpha_bwd_n<N, F16, G16, FUSED, 1, 8>(d, n, D, g, s);
-        return cudaErrorInvalidValue;
-    } else {
-        return alpha_bwd_n<N, F16, G16, FUSED, 1, 8>(d, n, D, g, s);
-    }
+    if (n > 64) return alpha_bwd_n<N, F16, G16, FUSED, 1, 8, kRowsDeep>(d, n, D, g, s);
+    return alpha_bwd_n<N, F16, G16, FUSED, 1, 8, kRows>(d, n, D, g, s);
 }
 
 template <int N>
