@@ -12,7 +12,7 @@ another 2x its size is read, so that the timed step neither finds its inputs in
 L2 nor pays for writing back the flush's lines.  Step times are medians.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ec|reference]
-                    [--workload cfg5d|cfg1|cfg2|cfg3|cfg3h|cfg3fused|cfg3hfused|cfg4|cfg5a|cfg5afused|roi2|asm4k|sched2|rle0|yuv2]
+                    [--workload cfg5d|cfg1|cfg2|cfg3|cfg3h|cfg3fused|cfg3hfused|cfg4|cfg5a|cfg5afused|cfg5afusedq|roi2|asm4k|sched2|rle0|yuv2]
                     [--sources S]
 
 The default line also carries, measured in the same run: the 16 x 1920x1080
@@ -273,7 +273,7 @@ class DepthPipeline:
             ev[3].record()
 
     def launches_per_step(self):
-        return 3
+        return 7                             # compress: five kernels; decompress; merge
 
     def compressed_bytes(self):
         return sum(int(s.item()) for s in self.sizes)
@@ -438,7 +438,7 @@ class CodecPipeline:
             ev[k + 1].record()
 
     def launches_per_step(self):
-        return 5 if self.yuv else 3
+        return 9 if self.yuv else 7          # compress: five kernels
 
     def compressed_bytes(self):
         return sum(int(s.item()) for s in self.sizes)
@@ -642,7 +642,7 @@ class RoiDetect:
             ev[1].record()
 
     def launches_per_step(self):
-        return 1
+        return 2                             # the depth kind's scan, then the finalize kernel
 
     def algorithmic_bytes(self):
         return {"detect_roi": 4 * self.units + self.n * (self.gw * self.gh + 16)}
@@ -1061,6 +1061,8 @@ def make_workload(name, device, sources=0):
         return AlphaFused(5, 128, 3840, 2160, 0.1, torch.float16, device)
     if name == "cfg5a":
         return AlphaForward(5, 128, 3840, 2160, 0.1, torch.float16, device)
+    if name == "cfg5afusedq":               # a quarter of the frame's rows: sized for ncu captures
+        return AlphaFused(5, 128, 3840, 540, 0.1, torch.float16, device)
     raise SystemExit(f"unknown workload {name}")
 
 

@@ -193,20 +193,114 @@ k_alpha_bwd(const __grid_constant__ BwdList<N> L, const __grid_constant__ DstDes
     }
     __syncthreads();
     const int nact = nact_s;
-    bool covers = true;
+    const int pitch0 = nact > 0 ? L.d[act[0]].pitch : 0;
+    bool covers = true, lean = true;
     for (int k = threadIdx.x; k < nact; k += blockDim.x) {
-        const BandTile t = make_band_tile<F16, G16, TW>(L.d[act[k]], tx0, ty0);
+        const BwdDesc& dk = L.d[act[k]];
+        const BandTile t = make_band_tile<F16, G16, TW>(dk, tx0, ty0);
         tiles[k] = t;
         covers = covers && t.rx0 == 0 && t.rx1 >= tx1 - tx0 && t.ry0 <= ty0 && t.ry1 >= ty1 &&
                  t.gx0 == 0 && t.gx1 >= tx1 - tx0 && t.gy0 <= ty0 && t.gy1 >= ty1;
+        lean = lean && dk.pitch == pitch0 && dk.cls >= S && dk.gvec;
     }
     const bool full = __syncthreads_and(covers);
+    // lean tiles: every active layer covers the whole tile, which lies inside
+    // the frame, with whole-pixel vector loads and stores and one pitch, so a
+    // row's addresses are one offset from the tile records
+    const bool lean_all = __syncthreads_and(covers && lean);
+    const bool fast = PX == 1 && tx0 + TW <= D.W && lean_all;
 
     const int k0 = (sg * nact) / NS, cnt = ((sg + 1) * nact) / NS - k0;   // cnt <= MS
     const int c0 = PX * lane;                                              // first column of this lane
     bool valid[PX];
 #pragma unroll
     for (int q = 0; q < PX; ++q) valid[q] = tx0 + c0 + q < D.W;
+
+    // Fused output of row y: out = sum over segments u of Tstart(u) C_u,
+    // evaluated front to back.  Lane (pixel, channel) of the first warps takes
+    // one channel of one pixel (TW * 4 of them), so no single warp carries the
+    // whole composite; T_final is the running product after the last segment.
+    auto composite_row = [&](int y, const float* Ps, const float4* Cs) {
+        for (int i = threadIdx.x; i < 4 * TW; i += blockDim.x) {
+            const int idx = i >> 2, ch = i & 3;
+            const int x = tx0 + PX * (idx & 31) + (idx >> 5);
+            if (x >= D.W) continue;
+            float Tacc = 1.0f, o = 0.0f;
+#pragma unroll 4
+            for (int u = 0; u < NS; ++u) {
+                o = fmaf(Tacc, reinterpret_cast<const float*>(Cs + u * TW + idx)[ch], o);
+                Tacc *= Ps[u * TW + idx];
+            }
+            const size_t e = ((size_t)y * (size_t)D.pitch + (size_t)x) * 4 + ch;
+            if constexpr (F16) reinterpret_cast<__half*>(D.color)[e] = __float2half_rn(o);
+            else reinterpret_cast<float*>(D.color)[e] = o;
+            if (ch == 0 && D.tfinal) D.tfinal[(size_t)y * D.W + x] = Tacc;
+        }
+    };
+
+    // Row pass of a lean tile (one pixel per lane): no range or alignment
+    // tests, one row offset for every layer's load and gradient store.
+    auto row_fast = [&](int y) {
+        float* const Ps = Ps0 + (y & 1) * NS * TW;
+        float* const As = As0 + (y & 1) * NS * TW;
+        float4* const Cs = Cs0 + (y & 1) * NS * TW;
+        const float4 gp = __ldcs(g + (size_t)y * D.W + tx0 + lane);
+        const int64_t r = (int64_t)(y - ty0) * pitch0 + lane;
+        RawPx raw[MS];
+#pragma unroll
+        for (int j = 0; j < MS; ++j) {
+            if constexpr (F16) raw[j] = make_uint2(0u, 0u);
+            else raw[j] = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (j < cnt) {
+                const uintptr_t a = tiles[k0 + j].src + (uintptr_t)(r * S);
+                if constexpr (F16) raw[j] = __ldcs(reinterpret_cast<const uint2*>(a));
+                else raw[j] = __ldcs(reinterpret_cast<const float4*>(a));
+            }
+        }
+        float Tl[MS], gcl[MS], al[MS];
+        float Tp = 1.0f, A = 0.0f;
+        float4 Cl = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+        for (int j = 0; j < MS; ++j) {
+            float4 c;
+            if constexpr (F16) c = h4_to_f4(raw[j]);
+            else c = raw[j];
+            const float gc = fmaf(gp.x, c.x, fmaf(gp.y, c.y, fmaf(gp.z, c.z, gp.w * c.w)));
+            Tl[j] = Tp;
+            gcl[j] = gc;
+            al[j] = c.w;
+            if (j < cnt) {
+                if (FUSED) {
+                    Cl.x = fmaf(Tp, c.x, Cl.x);
+                    Cl.y = fmaf(Tp, c.y, Cl.y);
+                    Cl.z = fmaf(Tp, c.z, Cl.z);
+                    Cl.w = fmaf(Tp, c.w, Cl.w);
+                }
+                A = fmaf(Tp, gc, A);
+                Tp = fmaf(-Tp, c.w, Tp);
+            }
+        }
+        Ps[sg * TW + lane] = Tp;
+        As[sg * TW + lane] = A;
+        if (FUSED) Cs[sg * TW + lane] = Cl;
+        __syncthreads();
+
+        float Tstart = 1.0f, R = 0.0f;
+        for (int u = 0; u < sg; ++u) Tstart *= Ps[u * TW + lane];
+        for (int u = NS - 1; u > sg; --u) R = fmaf(Ps[u * TW + lane], R, As[u * TW + lane]);
+        if (FUSED) composite_row(y, Ps, Cs);
+
+#pragma unroll
+        for (int j = MS - 1; j >= 0; --j) {
+            if (j < cnt) {
+                const float Tk = Tstart * Tl[j];
+                const float4 gr = make_float4(gp.x * Tk, gp.y * Tk, gp.z * Tk, Tk * (gp.w - R));
+                const uintptr_t ga = tiles[k0 + j].grad + (uintptr_t)(r * GS);
+                store_grad_at<G16>(ga, true, gr);
+                R = fmaf(1.0f - al[j], R, gcl[j]);
+            }
+        }
+    };
 
     auto row_pass = [&](auto full_c, int y) {
         constexpr bool FULL = decltype(full_c)::value;
@@ -300,37 +394,7 @@ k_alpha_bwd(const __grid_constant__ BwdList<N> L, const __grid_constant__ DstDes
             for (int u = NS - 1; u > sg; --u) R[q] = fmaf(Ps[u * TW + q * 32 + lane], R[q], As[u * TW + q * 32 + lane]);
         }
 
-        if (FUSED && sg < PX) {
-            // warp q (warp 0 alone in one-warp CTAs) composites the segments'
-            // partial outputs of pixel q
-#pragma unroll
-            for (int q = 0; q < PX; ++q) {
-                if (q % NS != sg || !valid[q]) continue;
-                float Tacc = 1.0f;
-                float4 out = make_float4(0.f, 0.f, 0.f, 0.f);
-                for (int u = 0; u < NS; ++u) {
-                    const float4 c = Cs[u * TW + q * 32 + lane];
-                    out.x = fmaf(Tacc, c.x, out.x);
-                    out.y = fmaf(Tacc, c.y, out.y);
-                    out.z = fmaf(Tacc, c.z, out.z);
-                    out.w = fmaf(Tacc, c.w, out.w);
-                    Tacc *= Ps[u * TW + q * 32 + lane];
-                }
-                const int x = tx0 + c0 + q;
-                const size_t o = (size_t)y * (size_t)D.pitch + (size_t)x;
-                if constexpr (F16) {
-                    const uint2 h = f4_to_h4(out);
-                    unsigned short* hp = reinterpret_cast<unsigned short*>(reinterpret_cast<uint2*>(D.color) + o);
-                    if (D.vec) __stcs(reinterpret_cast<uint2*>(hp), h);
-                    else { hp[0] = (unsigned short)h.x; hp[1] = (unsigned short)(h.x >> 16); hp[2] = (unsigned short)h.y; hp[3] = (unsigned short)(h.y >> 16); }
-                } else {
-                    float4* op = reinterpret_cast<float4*>(D.color) + o;
-                    if (D.vec) __stcs(op, out);
-                    else { float* f = reinterpret_cast<float*>(op); f[0] = out.x; f[1] = out.y; f[2] = out.z; f[3] = out.w; }
-                }
-                if (D.tfinal) D.tfinal[(size_t)y * D.W + x] = Tacc;
-            }
-        }
+        if (FUSED) composite_row(y, Ps, Cs);
 
         // reverse over this segment, entering with the R of the layers behind it
 #pragma unroll
@@ -370,7 +434,9 @@ k_alpha_bwd(const __grid_constant__ BwdList<N> L, const __grid_constant__ DstDes
             }
         }
     };
-    if (full) {
+    if (fast) {
+        for (int y = ty0; y < ty1; ++y) row_fast(y);
+    } else if (full) {
         for (int y = ty0; y < ty1; ++y) row_pass(std::true_type{}, y);
     } else {
         for (int y = ty0; y < ty1; ++y) row_pass(std::false_type{}, y);
