@@ -170,6 +170,12 @@ k_alpha_bwd(const __grid_constant__ BwdList<N> L, const __grid_constant__ DstDes
     float* const Ps0 = reinterpret_cast<float*>(smem + (size_t)cap * sizeof(BandTile));
     float* const As0 = Ps0 + 2 * NS * TW;
     float4* const Cs0 = reinterpret_cast<float4*>(As0 + 2 * NS * TW);       // (fused)
+    // FP16 lean tiles: each warp's per-layer state of its row, [MS][32] per
+    // warp -- (T', g.c) as floats and a as the half it was read as (exact) --
+    // so that the registers can hold the next row's loads
+    float2* const St0 = reinterpret_cast<float2*>(Cs0 + (FUSED ? 2 * NS * TW : 0));
+    float2* const St = St0 + (threadIdx.x / 32) * MS * 32;
+    unsigned short* const Sa = reinterpret_cast<unsigned short*>(St0 + NS * MS * 32) + (threadIdx.x / 32) * MS * 32;
 
     const int lane = threadIdx.x & 31, sg = threadIdx.x / 32;
     const int tx0 = blockIdx.x * TW, ty0 = blockIdx.y * ROWS;
@@ -298,6 +304,80 @@ k_alpha_bwd(const __grid_constant__ BwdList<N> L, const __grid_constant__ DstDes
                 const uintptr_t ga = tiles[k0 + j].grad + (uintptr_t)(r * GS);
                 store_grad_at<G16>(ga, true, gr);
                 R = fmaf(1.0f - al[j], R, gcl[j]);
+            }
+        }
+    };
+
+    // FP16 lean tiles, software-pipelined: the next row's layers and upstream
+    // gradient are loaded while this row's exchange and reverse scan run.
+    // The per-layer state lives in shared memory (St) meanwhile.
+    auto rows_fast16 = [&]() {
+        RawPx raw[MS];
+        float4 gn;
+        auto load_row = [&](int y) {
+            const int64_t r = (int64_t)(y - ty0) * pitch0 + lane;
+            gn = __ldcs(g + (size_t)y * D.W + tx0 + lane);
+#pragma unroll
+            for (int j = 0; j < MS; ++j) {
+                if constexpr (F16) raw[j] = make_uint2(0u, 0u);
+                else raw[j] = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (j < cnt) {
+                    const uintptr_t a = tiles[k0 + j].src + (uintptr_t)(r * S);
+                    if constexpr (F16) raw[j] = __ldcs(reinterpret_cast<const uint2*>(a));
+                    else raw[j] = __ldcs(reinterpret_cast<const float4*>(a));
+                }
+            }
+        };
+        load_row(ty0);
+        for (int y = ty0; y < ty1; ++y) {
+            float* const Ps = Ps0 + (y & 1) * NS * TW;
+            float* const As = As0 + (y & 1) * NS * TW;
+            float4* const Cs = Cs0 + (y & 1) * NS * TW;
+            const float4 gp = gn;
+            float Tp = 1.0f, A = 0.0f;
+            float4 Cl = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+            for (int j = 0; j < MS; ++j) {
+                float4 c;
+                if constexpr (F16) c = h4_to_f4(raw[j]);
+                else c = raw[j];
+                const float gc = fmaf(gp.x, c.x, fmaf(gp.y, c.y, fmaf(gp.z, c.z, gp.w * c.w)));
+                St[j * 32 + lane] = make_float2(Tp, gc);
+                if constexpr (F16) Sa[j * 32 + lane] = (unsigned short)(raw[j].y >> 16);
+                if (j < cnt) {
+                    if (FUSED) {
+                        Cl.x = fmaf(Tp, c.x, Cl.x);
+                        Cl.y = fmaf(Tp, c.y, Cl.y);
+                        Cl.z = fmaf(Tp, c.z, Cl.z);
+                        Cl.w = fmaf(Tp, c.w, Cl.w);
+                    }
+                    A = fmaf(Tp, gc, A);
+                    Tp = fmaf(-Tp, c.w, Tp);
+                }
+            }
+            Ps[sg * TW + lane] = Tp;
+            As[sg * TW + lane] = A;
+            if (FUSED) Cs[sg * TW + lane] = Cl;
+            __syncthreads();
+            if (y + 1 < ty1) load_row(y + 1);
+
+            float Tstart = 1.0f, R = 0.0f;
+            for (int u = 0; u < sg; ++u) Tstart *= Ps[u * TW + lane];
+            for (int u = NS - 1; u > sg; --u) R = fmaf(Ps[u * TW + lane], R, As[u * TW + lane]);
+            if (FUSED) composite_row(y, Ps, Cs);
+
+            const int64_t r = (int64_t)(y - ty0) * pitch0 + lane;
+#pragma unroll
+            for (int j = MS - 1; j >= 0; --j) {
+                if (j < cnt) {
+                    const float2 st = St[j * 32 + lane];
+                    const float a = __half2float(__ushort_as_half(Sa[j * 32 + lane]));
+                    const float Tk = Tstart * st.x;
+                    const float4 gr = make_float4(gp.x * Tk, gp.y * Tk, gp.z * Tk, Tk * (gp.w - R));
+                    const uintptr_t ga = tiles[k0 + j].grad + (uintptr_t)(r * GS);
+                    store_grad_at<G16>(ga, true, gr);
+                    R = fmaf(1.0f - a, R, st.y);
+                }
             }
         }
     };
@@ -435,7 +515,8 @@ k_alpha_bwd(const __grid_constant__ BwdList<N> L, const __grid_constant__ DstDes
         }
     };
     if (fast) {
-        for (int y = ty0; y < ty1; ++y) row_fast(y);
+        if constexpr (F16) rows_fast16();
+        else for (int y = ty0; y < ty1; ++y) row_fast(y);
     } else if (full) {
         for (int y = ty0; y < ty1; ++y) row_pass(std::true_type{}, y);
     } else {
@@ -519,7 +600,8 @@ template <int N, bool F16, bool G16, bool FUSED, int PX, int MS, int ROWS>
 cudaError_t alpha_bwd_n(const BwdDesc* d, int n, const DstDesc& D, const float4* g, cudaStream_t s)
 {
     const int ns = alpha_bwd_warps(n, MS), cap = std::max(n, 1), tw = 32 * PX;
-    const size_t smem = (size_t)cap * sizeof(BandTile) + 2 * (size_t)ns * tw * (8 + (FUSED ? 16 : 0));
+    const size_t smem = (size_t)cap * sizeof(BandTile) + 2 * (size_t)ns * tw * (8 + (FUSED ? 16 : 0)) +
+                        (F16 ? (size_t)ns * MS * 32 * (sizeof(float2) + sizeof(unsigned short)) : 0);
     auto kern = k_alpha_bwd<N, F16, G16, FUSED, PX, MS, ROWS>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;

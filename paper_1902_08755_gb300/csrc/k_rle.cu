@@ -1070,7 +1070,7 @@ __device__ uint32_t code0_block(const RleJobDesc& jb, uint32_t q0, int len, uint
 template <int N, bool M0>
 __global__ void __launch_bounds__(32 * kWPB, 16)
 k_rle_compress(const __grid_constant__ RleJobList<N> J, ChunkRec* rec, uint32_t* recode, uint8_t* pool,
-               uint32_t pool_bytes, uint32_t* ticket, uint32_t* status)
+               uint32_t pool_bytes, uint32_t slab, uint32_t* ticket, uint32_t* status)
 {
     extern __shared__ __align__(16) uint8_t smem[];
     WarpRing& W = reinterpret_cast<WarpRing*>(smem)[threadIdx.x >> 5];
@@ -1082,6 +1082,7 @@ k_rle_compress(const __grid_constant__ RleJobList<N> J, ChunkRec* rec, uint32_t*
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncwarp();
+    uint32_t sb = 0u, sl = 0u;                          // lane 0: the warp's pool slab (base, bytes left)
     uint32_t cur = 0u;
     if (lane == 0) cur = atomicAdd(ticket, 1u);
     cur = __shfl_sync(0xffffffffu, cur, 0);
@@ -1138,8 +1139,20 @@ k_rle_compress(const __grid_constant__ RleJobList<N> J, ChunkRec* rec, uint32_t*
             uint32_t po = kRecode;
             if (fits && lane == 0) {
                 // (+ 4: the copy-out reads up to one word past a chunk's bytes)
-                const unsigned long long a = atomicAdd(cursor, (unsigned long long)((total + 3u) & ~3u));
-                if (a + total + 4u <= pool_bytes) po = (uint32_t)a;
+                const uint32_t need = (total + 3u) & ~3u;
+                if (slab == 0u) {                         // small pools: space per chunk
+                    const unsigned long long a = atomicAdd(cursor, (unsigned long long)need);
+                    if (a + total + 4u <= pool_bytes) po = (uint32_t)a;
+                } else {
+                    // space from the warp's own slab, one atomic per slab (a
+                    // sparse chunk codes to at most 4 kStagePlane <= slab bytes)
+                    if (need > sl) {
+                        const unsigned long long a = atomicAdd(cursor, (unsigned long long)slab);
+                        sl = a + slab + 4u <= pool_bytes ? slab : 0u;
+                        sb = (uint32_t)a;
+                    }
+                    if (need <= sl) { po = sb; sb += need; sl -= need; }
+                }
             }
             po = __shfl_sync(0xffffffffu, po, 0);
             __syncwarp();
@@ -1643,6 +1656,11 @@ cudaError_t compress_grid(int* grid)
     if (dev < kMaxDev && (*grid = cache[dev].load(std::memory_order_relaxed)) > 0) return cudaSuccess;
     e = cudaFuncSetAttribute(k_rle_compress<N, M0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kCompressSmem);
     if (e != cudaSuccess) return e;
+    // the persistent grid is sized for the largest shared-memory carveout:
+    // ask for it, so that every CTA of the grid is resident at once
+    e = cudaFuncSetAttribute(k_rle_compress<N, M0>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             (int)cudaSharedmemCarveoutMaxShared);
+    if (e != cudaSuccess) return e;
     int per_sm = 0, sms = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_rle_compress<N, M0>, 32 * kWPB, kCompressSmem);
     if (e != cudaSuccess) return e;
@@ -1669,13 +1687,19 @@ cudaError_t compress_n(const RleJobDesc* jobs, int n, uint32_t total_units, void
     uint8_t* pool = reinterpret_cast<uint8_t*>(recode + ((total_units + 3u) & ~3u));
     const size_t used = rle_compress_scratch_bytes(total_units, 0);
     const uint32_t pool_bytes = (uint32_t)std::min<size_t>(scratch_bytes - used, 0xFFFFFFF0u);
+    // pool space is taken in slabs of up to 16 KB per warp where the pool
+    // has room for four slabs per warp of the grid (their unused tails are
+    // then at most a quarter of it), else chunk by chunk
+    uint32_t slab = std::min<uint32_t>(pool_bytes / (4u * (uint32_t)grid * kWPB), 16384u) & ~255u;
+    if (slab < 4u * kStagePlane) slab = 0u;
     const RleJobList<N> J = make_jobs<N>(jobs, n, total_units);
     int sms = 0;
     int dev = 0;
     if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
     if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
     const int rgrid = std::max(1, sms) * 4;
-    k_rle_compress<N, M0><<<grid, 32 * kWPB, kCompressSmem, s>>>(J, rec, recode, pool, pool_bytes, ticket, status);
+    k_rle_compress<N, M0><<<grid, 32 * kWPB, kCompressSmem, s>>>(J, rec, recode, pool, pool_bytes, slab, ticket,
+                                                                 status);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if (M0) k_rle0_recode<N, false><<<rgrid, kT, 0, s>>>(J, rec, recode, ticket + 1);
     else k_rle_recode<N, false><<<rgrid, 256, 0, s>>>(J, rec, recode, ticket + 1);
