@@ -301,14 +301,16 @@ __device__ void issue_quarter(const RleJobDesc& jb, uint32_t unit, int qi, int s
 // Append the change points among positions [kQ qi, kQ qi + kQ) of the chunk
 // to W.ce / W.cq (the quarter's elements in shared memory at `data`).  carry:
 // the element before the quarter (updated to the quarter's last).  Every lane
-// first compares its four elements of all G groups of 128 positions, one
-// OR-reduction over the warp tells which groups changed, and only those are
-// listed.  Returns false once the chunk has more than kCap change points.
+// flags the changes among its four elements of each of the G groups of 128
+// positions; one warp scan of the four groups' per-lane counts, packed in the
+// bytes of a word (a group has at most 128 changes, so no byte carries into
+// the next), places every change point in position order at once.  Returns
+// false once the chunk has more than kCap change points.
 __device__ bool detect_quarter(const uint32_t* data, int len, int qi, WarpRing& W, int& m, uint32_t& carry)
 {
     const int lane = threadIdx.x & 31;
-    const uint32_t lt = (1u << lane) - 1u;
     constexpr int G = kQ / 128;
+    static_assert(G == 4, "four groups' counts in the bytes of one word");
     uint4 vv[G];
     uint32_t pv[G];
 #pragma unroll
@@ -319,39 +321,46 @@ __device__ bool detect_quarter(const uint32_t* data, int len, int qi, WarpRing& 
     if (lane == 0) pv[0] = qi == 0 ? ~vv[0].x : carry;    // position 0 is always listed
     carry = __shfl_sync(0xffffffffu, vv[G - 1].w, 31);   // (used only when the quarter is full)
     const int qend = min(len - kQ * qi, kQ);              // positions of this quarter
-    uint32_t mine = 0u;
+    uint32_t f[G], packed = 0u;
 #pragma unroll
     for (int g = 0; g < G; ++g) {
         const uint4 v = vv[g];
-        const uint32_t x = (v.x ^ pv[g]) | (v.y ^ v.x) | (v.z ^ v.y) | (v.w ^ v.z);
-        mine |= (x != 0u ? 1u : 0u) << g;
+        f[g] = (uint32_t)(v.x != pv[g]) | ((uint32_t)(v.y != v.x) << 1) | ((uint32_t)(v.z != v.y) << 2) |
+               ((uint32_t)(v.w != v.z) << 3);
     }
     if (qend < kQ) {                                      // the chunk's last quarter: positions past len
 #pragma unroll
-        for (int g = 0; g < G; ++g)
-            if (128 * g + 4 * lane >= qend) mine &= ~(1u << g);
+        for (int g = 0; g < G; ++g) {
+            const int q = 128 * g + 4 * lane;
+            if (q + 4 > qend) f[g] &= q >= qend ? 0u : (1u << (qend - q)) - 1u;
+        }
     }
-    const uint32_t groups = __reduce_or_sync(0xffffffffu, mine);
+#pragma unroll
+    for (int g = 0; g < G; ++g) packed |= (uint32_t)__popc(f[g]) << (8 * g);
+    uint32_t inc = packed;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += y;
+    }
+    const uint32_t tot = __shfl_sync(0xffffffffu, inc, 31), exc = inc - packed;
+    const int cnt = (int)((tot & 0xFFu) + ((tot >> 8) & 0xFFu) + ((tot >> 16) & 0xFFu) + (tot >> 24));
+    if (m + cnt > kCap) return false;
+    int base = m;
 #pragma unroll
     for (int g = 0; g < G; ++g) {
-        if (!((groups >> g) & 1u)) continue;
-        const uint4 v = vv[g];
-        const int q = 128 * g + 4 * lane;                 // within the quarter
-        uint32_t f = (v.x != pv[g] ? 1u : 0u) | (v.y != v.x ? 2u : 0u) | (v.z != v.y ? 4u : 0u) |
-                     (v.w != v.z ? 8u : 0u);
-        if (q + 4 > qend) f &= q >= qend ? 0u : (1u << (qend - q)) - 1u;
-        const uint32_t b0 = __ballot_sync(0xffffffffu, f & 1u), b1 = __ballot_sync(0xffffffffu, f & 2u);
-        const uint32_t b2 = __ballot_sync(0xffffffffu, f & 4u), b3 = __ballot_sync(0xffffffffu, f & 8u);
-        const int cnt = __popc(b0) + __popc(b1) + __popc(b2) + __popc(b3);
-        if (m + cnt > kCap) return false;
-        int o = m + __popc(b0 & lt) + __popc(b1 & lt) + __popc(b2 & lt) + __popc(b3 & lt);
-        const int qq = kQ * qi + q;
-        if (f & 1u) { W.cq[o] = (uint16_t)qq; W.ce[o] = v.x; ++o; }
-        if (f & 2u) { W.cq[o] = (uint16_t)(qq + 1); W.ce[o] = v.y; ++o; }
-        if (f & 4u) { W.cq[o] = (uint16_t)(qq + 2); W.ce[o] = v.z; ++o; }
-        if (f & 8u) { W.cq[o] = (uint16_t)(qq + 3); W.ce[o] = v.w; }
-        m += cnt;
+        if (f[g]) {
+            const uint4 v = vv[g];
+            const int qq = kQ * qi + 128 * g + 4 * lane;
+            int o = base + (int)((exc >> (8 * g)) & 0xFFu);
+            if (f[g] & 1u) { W.cq[o] = (uint16_t)qq; W.ce[o] = v.x; ++o; }
+            if (f[g] & 2u) { W.cq[o] = (uint16_t)(qq + 1); W.ce[o] = v.y; ++o; }
+            if (f[g] & 4u) { W.cq[o] = (uint16_t)(qq + 2); W.ce[o] = v.z; ++o; }
+            if (f[g] & 8u) { W.cq[o] = (uint16_t)(qq + 3); W.ce[o] = v.w; }
+        }
+        base += (int)((tot >> (8 * g)) & 0xFFu);
     }
+    m += cnt;
     return true;
 }
 
@@ -818,8 +827,8 @@ __device__ bool detect_quarter0(const uint32_t* data, int len, int qi, WarpRing&
                                 uint2& carry)
 {
     const int lane = threadIdx.x & 31;
-    const uint32_t lt = (1u << lane) - 1u;
     constexpr int G = kQ / 128;
+    static_assert(G == 4, "four groups' counts in the bytes of one word");
     uint4 vv[G];
     uint2 pv[G];
 #pragma unroll
@@ -830,30 +839,38 @@ __device__ bool detect_quarter0(const uint32_t* data, int len, int qi, WarpRing&
     if (lane == 0) pv[0] = qi == 0 ? make_uint2(~vv[0].x, vv[0].y) : carry;     // unit 0 is always listed
     carry = make_uint2(__shfl_sync(0xffffffffu, vv[G - 1].z, 31), __shfl_sync(0xffffffffu, vv[G - 1].w, 31));
     const int uend = min(len / 2 - kQ / 2 * qi, kQ / 2);                         // units of this quarter
-    uint32_t mine = 0u;
+    uint32_t f[G], packed = 0u;
 #pragma unroll
     for (int g = 0; g < G; ++g) {
-        const uint4 v = vv[g];
-        const uint32_t x = (v.x ^ pv[g].x) | (v.y ^ pv[g].y) | (v.z ^ v.x) | (v.w ^ v.y);
-        mine |= (x != 0u && 64 * g + 2 * lane < uend ? 1u : 0u) << g;
-    }
-    const uint32_t groups = __reduce_or_sync(0xffffffffu, mine);
-#pragma unroll
-    for (int g = 0; g < G; ++g) {
-        if (!((groups >> g) & 1u)) continue;
         const uint4 v = vv[g];
         const int u = 64 * g + 2 * lane;                  // within the quarter
-        uint32_t f = (v.x != pv[g].x || v.y != pv[g].y ? 1u : 0u) | (v.z != v.x || v.w != v.y ? 2u : 0u);
-        if (u + 2 > uend) f &= u >= uend ? 0u : 1u;
-        const uint32_t b0 = __ballot_sync(0xffffffffu, f & 1u), b1 = __ballot_sync(0xffffffffu, f & 2u);
-        const int cnt = __popc(b0) + __popc(b1);
-        if (m + cnt > kCap) return false;
-        int o = m + __popc(b0 & lt) + __popc(b1 & lt);
-        const int uu = kQ / 2 * qi + u;
-        if (f & 1u) { W.cq[o] = (uint16_t)uu; W.ce[o] = v.x; ch[o] = v.y; ++o; }
-        if (f & 2u) { W.cq[o] = (uint16_t)(uu + 1); W.ce[o] = v.z; ch[o] = v.w; }
-        m += cnt;
+        f[g] = (uint32_t)(v.x != pv[g].x || v.y != pv[g].y) | ((uint32_t)(v.z != v.x || v.w != v.y) << 1);
+        if (u + 2 > uend) f[g] &= u >= uend ? 0u : 1u;
+        packed |= (uint32_t)__popc(f[g]) << (8 * g);
     }
+    // one warp scan of the four groups' per-lane counts (bytes of a word)
+    uint32_t inc = packed;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += y;
+    }
+    const uint32_t tot = __shfl_sync(0xffffffffu, inc, 31), exc = inc - packed;
+    const int cnt = (int)((tot & 0xFFu) + ((tot >> 8) & 0xFFu) + ((tot >> 16) & 0xFFu) + (tot >> 24));
+    if (m + cnt > kCap) return false;
+    int base = m;
+#pragma unroll
+    for (int g = 0; g < G; ++g) {
+        if (f[g]) {
+            const uint4 v = vv[g];
+            const int uu = kQ / 2 * qi + 64 * g + 2 * lane;
+            int o = base + (int)((exc >> (8 * g)) & 0xFFu);
+            if (f[g] & 1u) { W.cq[o] = (uint16_t)uu; W.ce[o] = v.x; ch[o] = v.y; ++o; }
+            if (f[g] & 2u) { W.cq[o] = (uint16_t)(uu + 1); W.ce[o] = v.z; ch[o] = v.w; }
+        }
+        base += (int)((tot >> (8 * g)) & 0xFFu);
+    }
+    m += cnt;
     return true;
 }
 
