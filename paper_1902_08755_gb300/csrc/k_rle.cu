@@ -89,8 +89,11 @@ __device__ void write_header(uint8_t* d, const RleJobDesc& jb)
 
 // Copy n stage bytes (src 4-byte aligned) to o, threads t, t+nt, ...: byte
 // stores up to o's first word boundary and after its last, word stores of
-// funnel-shifted stage words between.
-__device__ __forceinline__ void copy_out(uint8_t* o, const uint8_t* src, uint32_t n, uint32_t t, uint32_t nt)
+// funnel-shifted stage words between.  The two buffers never overlap, and a
+// thread's loads (eight words at a time, and its head and tail bytes) are all
+// issued before its stores.  Reads up to one word past src + n.
+__device__ __forceinline__ void copy_out(uint8_t* __restrict__ o, const uint8_t* __restrict__ src, uint32_t n,
+                                         uint32_t t, uint32_t nt)
 {
     const uintptr_t a0 = reinterpret_cast<uintptr_t>(o), a1 = a0 + n;
     const uintptr_t w0 = (a0 + 3) & ~(uintptr_t)3, w1 = a1 & ~(uintptr_t)3;
@@ -98,17 +101,29 @@ __device__ __forceinline__ void copy_out(uint8_t* o, const uint8_t* src, uint32_
         for (uint32_t i = t; i < n; i += nt) o[i] = src[i];
         return;
     }
-    const uint32_t head = (uint32_t)(w0 - a0), tail0 = (uint32_t)(w1 - a0);
-    if (t < head) o[t] = src[t];
-    for (uint32_t i = tail0 + t; i < n; i += nt) o[i] = src[i];
+    const uint32_t head = (uint32_t)(w0 - a0), tail0 = (uint32_t)(w1 - a0);   // head, n - tail0 < 4 <= nt
+    const bool hh = t < head, th = tail0 + t < n;
+    const uint8_t hb = hh ? src[t] : 0, tb = th ? src[tail0 + t] : 0;
     const uint32_t nw = (uint32_t)((w1 - w0) >> 2);
-    const uint32_t* s32 = reinterpret_cast<const uint32_t*>(src);
+    const uint32_t* __restrict__ s32 = reinterpret_cast<const uint32_t*>(src);
     const uint32_t sh = 8u * head;
-    uint32_t* o32 = reinterpret_cast<uint32_t*>(w0);
-    for (uint32_t k = t; k < nw; k += nt) {
-        // bytes [head + 4k, head + 4k + 4), head < 4
-        o32[k] = __funnelshift_r(s32[k], s32[k + 1], sh);
+    uint32_t* __restrict__ o32 = reinterpret_cast<uint32_t*>(w0);
+    for (uint32_t k0 = t; k0 < nw; k0 += 8u * nt) {
+        uint32_t v[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            // bytes [head + 4k, head + 4k + 4), head < 4
+            const uint32_t k = k0 + (uint32_t)j * nt;
+            v[j] = k < nw ? __funnelshift_r(s32[k], s32[k + 1], sh) : 0u;
+        }
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const uint32_t k = k0 + (uint32_t)j * nt;
+            if (k < nw) o32[k] = v[j];
+        }
     }
+    if (hh) o[t] = hb;
+    if (th) o[tail0 + t] = tb;
 }
 
 // ---- compressor: one warp per chunk ---------------------------------------
@@ -1240,31 +1255,33 @@ k_rle_scan(const __grid_constant__ RleJobList<N> J, ChunkRec* rec)
     }
 }
 
-// Placing kernel: one warp per chunk copies its streams from the pool to their
-// place and writes its end-table entries (four; one in mode 0).  Chunks to be
-// coded again are left to the recoding kernel.
+// Placing kernel: one half-warp per chunk copies its streams from the pool to
+// their place and writes its end-table entries (four; one in mode 0), so a
+// warp's two chunks have their loads in flight together.  Chunks to be coded
+// again are left to the recoding kernel.
+constexpr int kPlaceLanes = 16;
 template <int N>
 __global__ void __launch_bounds__(128)
 k_rle_place(const __grid_constant__ RleJobList<N> J, const ChunkRec* rec, const uint8_t* pool)
 {
-    const int lane = threadIdx.x & 31;
-    const uint32_t unit = blockIdx.x * 4u + (threadIdx.x >> 5);
+    const int lane = (int)threadIdx.x % kPlaceLanes;
+    const uint32_t unit = blockIdx.x * (128u / kPlaceLanes) + threadIdx.x / kPlaceLanes;
     if (unit >= J.total_units) return;
+    const ChunkRec r = rec[unit];                     // (in flight during the job search)
     const RleJobDesc& jb = J.j[find_job(J, unit)];
     const uint32_t nc = jb.n_chunks;
     if (nc == 0) return;                              // header written by the scan
-    const ChunkRec r = rec[unit];
     if (r.pool == kRecode) return;
     const uint32_t c = unit - jb.first_unit;
     const uint32_t T0 = r.T[0], T1 = r.T[1], T2 = r.T[2], T3 = r.T[3];
     const uint32_t total = T0 + T1 + T2 + T3;
     uint8_t* dst = reinterpret_cast<uint8_t*>(jb.dst);
     if (jb.mode == 0) {                               // one stream, one end-table entry
-        copy_out(dst + 32 + 4ull * nc + r.off, pool + r.pool, total, lane, 32);
+        copy_out(dst + 32 + 4ull * nc + r.off, pool + r.pool, total, lane, kPlaceLanes);
         if (lane == 0) put_u32(dst + 32 + 4ull * c, r.off + total);
         return;
     }
-    copy_out(dst + 32 + 16ull * nc + r.off, pool + r.pool, total, lane, 32);
+    copy_out(dst + 32 + 16ull * nc + r.off, pool + r.pool, total, lane, kPlaceLanes);
     const uint32_t mine = lane == 0 ? T0 : lane == 1 ? T0 + T1 : lane == 2 ? T0 + T1 + T2 : total;
     if (lane < 4) put_u32(dst + 32 + 16ull * c + 4u * lane, r.off + mine);
 }
@@ -1723,7 +1740,7 @@ cudaError_t compress_n(const RleJobDesc* jobs, int n, uint32_t total_units, void
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     k_rle_scan<N><<<n, 1024, 0, s>>>(J, rec);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    k_rle_place<N><<<(total_units + 3) / 4, 128, 0, s>>>(J, rec, pool);
+    k_rle_place<N><<<(total_units + 128 / kPlaceLanes - 1) / (128 / kPlaceLanes), 128, 0, s>>>(J, rec, pool);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if (M0) k_rle0_recode<N, true><<<rgrid, kT, 0, s>>>(J, rec, recode, ticket + 1);
     else k_rle_recode<N, true><<<rgrid, 256, 0, s>>>(J, rec, recode, ticket + 1);
