@@ -1259,7 +1259,7 @@ k_rle_scan(const __grid_constant__ RleJobList<N> J, ChunkRec* rec)
 // their place and writes its end-table entries (four; one in mode 0), so a
 // warp's two chunks have their loads in flight together.  Chunks to be coded
 // again are left to the recoding kernel.
-constexpr int kPlaceLanes = 16;
+constexpr int kPlaceLanes = 8;
 template <int N>
 __global__ void __launch_bounds__(128)
 k_rle_place(const __grid_constant__ RleJobList<N> J, const ChunkRec* rec, const uint8_t* pool)
