@@ -1722,9 +1722,9 @@ cudaError_t compress_n(const RleJobDesc* jobs, int n, uint32_t total_units, void
     const size_t used = rle_compress_scratch_bytes(total_units, 0);
     const uint32_t pool_bytes = (uint32_t)std::min<size_t>(scratch_bytes - used, 0xFFFFFFF0u);
     // pool space is taken in slabs of up to 16 KB per warp where the pool
-    // has room for four slabs per warp of the grid (their unused tails are
-    // then at most a quarter of it), else chunk by chunk
-    uint32_t slab = std::min<uint32_t>(pool_bytes / (4u * (uint32_t)grid * kWPB), 16384u) & ~255u;
+    // has room for eight slabs per warp of the grid (their unused tails are
+    // then at most an eighth of it), else chunk by chunk
+    uint32_t slab = std::min<uint32_t>(pool_bytes / (8u * (uint32_t)grid * kWPB), 16384u) & ~255u;
     if (slab < 4u * kStagePlane) slab = 0u;
     const RleJobList<N> J = make_jobs<N>(jobs, n, total_units);
     int sms = 0;
