@@ -20,9 +20,15 @@
 // exact reverse recurrence over its own layers and writes their gradients.
 // Layers are read from HBM once; per-layer tile records (addresses, clipped
 // ranges) are built once per CTA in shared memory and read as broadcasts.
+// Tiles that every active layer covers, inside the frame, with whole-pixel
+// vector access and one pitch ("lean" tiles, the usual case) run a row pass
+// without range tests; for FP16 layers that pass is software-pipelined (the
+// next row's loads in flight behind the exchange, the row's per-layer state
+// parked in shared memory).
 //
 // The fused variant takes the loss weights w up front (L = sum w * out, so
-// the upstream gradient is w) and also writes out and T_final.
+// the upstream gradient is w) and also writes out and T_final; the output is
+// composed from the segments' partials by (pixel, channel) lanes.
 //
 // Depth compositing (thesis 5.2.1) copies the winner's colour, so its
 // gradient routes grad_out to the winning input and writes zero elsewhere.
@@ -151,7 +157,8 @@ __device__ __forceinline__ void store_grad(const BwdDesc& d, int x, int y, float
 // pixels (PX per lane, adjacent) by ROWS rows.  blockDim.x = 32 * NS: warp s
 // owns segment s of the tile's active layers, at most MS of them.  Tiles that
 // every active layer covers entirely (ROI and gradient rectangle) skip the
-// per-row range checks.
+// per-row range checks; lean tiles (also aligned, one pitch, inside the
+// frame) take the row passes without any tests.
 template <int N, bool F16, bool G16, bool FUSED, int PX, int MS, int ROWS>
 __global__ void __launch_bounds__(32 * kMaxWarps, 1)
 k_alpha_bwd(const __grid_constant__ BwdList<N> L, const __grid_constant__ DstDesc D,
