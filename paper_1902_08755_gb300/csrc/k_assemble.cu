@@ -17,7 +17,7 @@ namespace {
 constexpr int kAT = 256;
 constexpr int kARows = kAT / 32;          // rows a CTA covers at once
 constexpr int kAPasses = 4;                 // row passes per CTA (average and pixel kernels)
-constexpr int kTPasses = 4;                 // row passes per CTA (tile kernel)
+constexpr int kTPasses = 2;                 // row passes per CTA (tile kernel)
 
 template <int BPP> struct Grp;                 // one 16-byte group of pixels
 template <> struct Grp<4> { static constexpr int PX = 4; };
