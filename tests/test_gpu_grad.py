@@ -200,3 +200,43 @@ def test_cfg5_fused_128_fp16_layers_4k_sampled_rows():
             assert np.max(np.abs(got - ref[k].astype(np.float16))) <= 2e-3, k
     del lay, grads
     torch.cuda.empty_cache()
+
+
+@pytest.mark.parametrize("n,pad,roi,gdtype", [
+    (64, 0, None, torch.float16),
+    (37, 6, (0, 0, 64, 32), torch.float16),
+    (40, 2, None, torch.float32),
+    (100, 4, (0, 0, 64, 32), torch.float16),
+])
+def test_fused_fp16_lean_tiles_every_pixel(n, pad, roi, gdtype):
+    """FP16 layers that cover the frame with one pitch: tiles take the lean,
+    software-pipelined row pass (the next row's loads in flight behind the
+    segment exchange) over several CTA row bands and a ragged last band; layer
+    counts that do and do not divide into 8-layer segments, 16 and 32 rows per
+    CTA.  With `roi`, layer 5's ROI covers only the top-left tiles, so lean and
+    general tiles share the launch.  Output, T_final and every gradient element
+    against the oracle."""
+    require_gpu()
+    r = np.random.default_rng(4100 + n)
+    W, H = 96, 40
+    oimgs, gimgs = [], []
+    for i in range(n):
+        a = r.random((H, W + pad)) * 0.2
+        lay = np.empty((H, W + pad, 4))
+        lay[..., :3] = r.random((H, W + pad, 3)) * a[..., None]
+        lay[..., 3] = a
+        lay = lay.astype(np.float16)
+        pvp = (0, 0, W, H)
+        lroi = roi if (roi is not None and i == 5) else pvp
+        oimgs.append(oracle.Image(pvp, lroi, lay))
+        gimgs.append(ec.Image(color=torch.from_numpy(lay).cuda(), pvp=pvp, roi=lroi))
+    w = (r.random((H, W, 4)) * 2 - 1).astype(np.float32)
+    out = torch.empty((H, W, 4), dtype=torch.float16, device="cuda")
+    T = torch.empty((H, W), dtype=torch.float32, device="cuda")
+    grads = [torch.full_like(im.color, float("nan"), dtype=gdtype) for im in gimgs]
+    ec.composite_alpha_fwd_bwd(gimgs, out, torch.from_numpy(w).cuda(), grads, t_final=T)
+    ec.default_context().check_status()
+    fwd, Tref, _ = oracle.composite_alpha(oimgs, (0, 0, W, H))
+    assert np.max(np.abs(np_of(out).astype(np.float64) - fwd)) <= 2e-3
+    assert np.max(np.abs(np_of(T).astype(np.float64) - Tref)) <= 2e-3
+    _check_against_oracle(oimgs, grads, None, (0, 0, W, H), w, gdtype)
