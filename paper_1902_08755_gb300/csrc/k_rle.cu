@@ -1091,14 +1091,15 @@ __device__ uint32_t code0_block(const RleJobDesc& jb, uint32_t q0, int len, uint
     return body + ((len & 1) ? 4u : 0u);
 }
 
-// Coding kernel.  Per chunk a warp: takes its next ticket (the atomic overlaps
-// the wait for the first quarter); reads the four quarters, refilling each
-// slot as soon as it has been read (with the next quarter of this chunk or of
-// the next one); sizes the plane streams; and leaves the chunk's record and,
-// for a sparse chunk, its streams in the pool (space taken with an atomic
-// cursor; a chunk that finds the pool full is coded again when placed, like a
-// dense one; such chunks are listed for the recoding kernel).  No warp waits
-// for another.  M0: basic RLE (mode 0), from unit change points.
+// Coding kernel.  Per chunk a warp: takes its next ticket; reads the chunk's
+// eight quarters, refilling each slot as soon as it has been read (with the
+// next quarter of this chunk or of the next one); sizes the plane streams;
+// and leaves the chunk's record and, for a sparse chunk, its streams in the
+// pool (space from the warp's slab, a fresh slab taken with one atomic on the
+// pool cursor when the chunk does not fit, or from the cursor chunk by chunk
+// when slab is 0; a chunk that finds the pool full is coded again when
+// placed, like a dense one; such chunks are listed for the recoding kernel).
+// No warp waits for another.  M0: basic RLE (mode 0), from unit change points.
 template <int N, bool M0>
 __global__ void __launch_bounds__(32 * kWPB, 16)
 k_rle_compress(const __grid_constant__ RleJobList<N> J, ChunkRec* rec, uint32_t* recode, uint8_t* pool,
@@ -1255,10 +1256,10 @@ k_rle_scan(const __grid_constant__ RleJobList<N> J, ChunkRec* rec)
     }
 }
 
-// Placing kernel: one half-warp per chunk copies its streams from the pool to
-// their place and writes its end-table entries (four; one in mode 0), so a
-// warp's two chunks have their loads in flight together.  Chunks to be coded
-// again are left to the recoding kernel.
+// Placing kernel: kPlaceLanes lanes (a quarter-warp) per chunk copy its
+// streams from the pool to their place and write its end-table entries (four;
+// one in mode 0), so a warp's four chunks have their loads in flight together.
+// Chunks to be coded again are left to the recoding kernel.
 constexpr int kPlaceLanes = 8;
 template <int N>
 __global__ void __launch_bounds__(128)
