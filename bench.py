@@ -12,7 +12,7 @@ another 2x its size is read, so that the timed step neither finds its inputs in
 L2 nor pays for writing back the flush's lines.  Step times are medians.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ec|reference]
-                    [--workload cfg5d|cfg1|cfg2|cfg3|cfg3h|cfg3fused|cfg3hfused|cfg4|cfg5a|cfg5afused|cfg5afusedq|roi2|asm4k|sched2|rle0|yuv2]
+                    [--workload cfg5d|cfg1|cfg2|cfg3|cfg3h|cfg3fused|cfg3hfused|cfg4|cfg5a|cfg5afused|cfg5afusedq|roi2|asm4k|sched2|rle0|rle0big|yuv2]
                     [--sources S]
 
 The default line also carries, measured in the same run: the 16 x 1920x1080
@@ -364,19 +364,23 @@ class CodecPipeline:
     """The cfg2 sources (16 x 1920x1080 RGBA8+Z32, cropped) through the other
     compressors of thesis 5.5, then decoded and depth-composited:
       rle0: basic 64-bit RLE (mode 0) for colour and depth;
-      yuv2: colour through the lossy YUV compressor and RLE mode 1, depth mode 1."""
+      yuv2: colour through the lossy YUV compressor and RLE mode 1, depth mode 1;
+      rle0big: mode 0 on the 64 x 7680x4320 sources of cfg5d (~25% coverage),
+      a size at which every coding warp has many chunks."""
 
     def __init__(self, kind, device):
         import paper_1902_08755_gb300 as ec
         import synthetic as S
         self.ec, self.kind = ec, kind
-        self.W, self.H, self.n = 1920, 1080, 16
+        big = kind == "rle0big"
+        cfg, cov = (5, 0.25) if big else (2, 0.3)
+        self.W, self.H, self.n = (7680, 4320, 64) if big else (1920, 1080, 16)
         self.yuv = kind == "yuv2"
-        self.desc = (f"16 sources 1920x1080 RGBA8+Z32, ~30% coverage, ROI-cropped; "
+        self.desc = (f"{self.n} sources {self.W}x{self.H} RGBA8+Z32, ~{int(cov * 100)}% coverage, ROI-cropped; "
                      + ("colour YUV 4:2:0 (BT.601 fixed point) + RLE mode 1, depth RLE mode 1"
                         if self.yuv else "basic 64-bit RLE (mode 0) for colour and depth")
                      + " -> decode -> depth composite")
-        self.srcs = S.depth_sources(2, self.n, self.W, self.H, 0.3, clustered=True, cropped=True, device=device)
+        self.srcs = S.depth_sources(cfg, self.n, self.W, self.H, cov, clustered=True, cropped=True, device=device)
         self.units = sum(max(0, min(s.roi[2], self.W)) * max(0, min(s.roi[3], self.H)) for s in self.srcs)
         self.stored_px = sum(s.pvp[2] * s.pvp[3] for s in self.srcs)
         self.kernels = (["yuv_encode", "rle_compress", "rle_decompress", "yuv_decode", "composite_depth"]
@@ -1047,7 +1051,7 @@ def make_workload(name, device, sources=0):
         return Assembly(3840, 2160, device)
     if name == "sched2":
         return Schedules(device)
-    if name in ("rle0", "yuv2"):
+    if name in ("rle0", "yuv2", "rle0big"):
         return CodecPipeline(name, device)
     if name == "cfg3":
         return AlphaForward(3, 32, 2048, 2048, 0.3, torch.float32, device)
